@@ -1,0 +1,172 @@
+"""Plain FP64 CPU oracle for the chi0 path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never calls it, shares
+no code with it and has no fallback to it.
+
+Every function follows the paper's statement of the problem (SC'25 BerkeleyGW
+paper, "Overview of the Problem"):
+
+* ``m_conv`` -- plane-wave matrix elements M_vc(G) (definition inline after
+  Eq. ff-ch) in their G-space form  M_vc(G) = sum_K conj(c_v(K)) c_c(K-G);
+* ``psi_dft`` / ``m_from_psi`` / ``m_dft`` -- the same M by the real-space route of
+  the definition: psi on the grid by a direct sum, the pair product, a direct
+  forward sum with e^{+iG.r} and 1/N_r (tiny grids only);
+* ``delta`` -- the energy factor 2/(x-iw) + 2/(x+iw), x = E_v - E_c, left open by
+  Eq. chi_mat and fixed by the hot-path statement (imaginary frequency);
+* ``chi0`` -- Eq. chi_mat without the outer factor 2 (the factor is folded into
+  Delta), every entry summed separately with Neumaier compensation;
+* ``adjoint`` -- gradients of L = Re Tr(W chi0) (GWPT motivation, Eq. gwpt).
+
+All functions are pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle.py``
+(two independent routes to M, orthonormality, Parseval, gauge and translation
+covariance, Hermiticity / semidefiniteness / rank / trace of chi0, the
+large-frequency limit, finite differences of L).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import tempfile
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gw_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP, -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fno-fast-math", "-ffp-contract=off",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P, I, LL, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+            lib.oracle_threads.restype = I
+            lib.oracle_m_conv.argtypes = [I, I, P, P, I, I, P, P, I, P, P]
+            lib.oracle_m_conv.restype = I
+            lib.oracle_psi_dft.argtypes = [I, I, I, I, I, P, P, P]
+            lib.oracle_psi_dft.restype = None
+            lib.oracle_m_from_psi.argtypes = [I, I, I, I, P, I, P, I, P, P]
+            lib.oracle_m_from_psi.restype = None
+            lib.oracle_delta.argtypes = [I, P, I, P, D, P, P]
+            lib.oracle_delta.restype = None
+            lib.oracle_chi0.argtypes = [LL, I, P, P, P]
+            lib.oracle_chi0.restype = None
+            lib.oracle_adjoint.argtypes = [I, I, P, P, P, I, I, P, P, P, I, P, P, D, P, P, P, P, P]
+            lib.oracle_adjoint.restype = I
+            _lib = lib
+    return _lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def threads() -> int:
+    return int(_load().oracle_threads())
+
+
+def m_conv(gv, cv, gc, cc, gchi) -> np.ndarray:
+    """M [nv*nc, ng] complex128, pair index p = v*nc + c."""
+    lib = _load()
+    gv, gc, gchi = _c(gv, np.int32), _c(gc, np.int32), _c(gchi, np.int32)
+    cv, cc = _c(cv, np.complex128), _c(cc, np.complex128)
+    nv, nc, ng = cv.shape[0], cc.shape[0], gchi.shape[0]
+    out = np.empty((nv * nc, ng), np.complex128)
+    rc = lib.oracle_m_conv(nv, gv.shape[0], _p(gv), _p(cv), nc, gc.shape[0], _p(gc), _p(cc), ng, _p(gchi), _p(out))
+    if rc:
+        raise MemoryError("oracle_m_conv")
+    return out
+
+
+def psi_dft(grid, gk, coef) -> np.ndarray:
+    """psi [nb, n0, n1, n2] = sum_K c(K) e^{+iK.r} by a direct sum."""
+    lib = _load()
+    gk, coef = _c(gk, np.int32), _c(coef, np.complex128)
+    n0, n1, n2 = grid
+    out = np.empty((coef.shape[0], n0, n1, n2), np.complex128)
+    lib.oracle_psi_dft(n0, n1, n2, coef.shape[0], gk.shape[0], _p(gk), _p(coef), _p(out))
+    return out
+
+
+def m_from_psi(grid, psiv, psic, gchi) -> np.ndarray:
+    lib = _load()
+    psiv, psic, gchi = _c(psiv, np.complex128), _c(psic, np.complex128), _c(gchi, np.int32)
+    n0, n1, n2 = grid
+    nv, nc, ng = psiv.shape[0], psic.shape[0], gchi.shape[0]
+    out = np.empty((nv * nc, ng), np.complex128)
+    lib.oracle_m_from_psi(n0, n1, n2, nv, _p(psiv), nc, _p(psic), ng, _p(gchi), _p(out))
+    return out
+
+
+def m_dft(grid, gv, cv, gc, cc, gchi) -> np.ndarray:
+    """M by the real-space route (direct sums; tiny grids only)."""
+    return m_from_psi(grid, psi_dft(grid, gv, cv), psi_dft(grid, gc, cc), gchi)
+
+
+def delta(ev, ec, omega: float, return_resid: bool = False):
+    """Delta [nv*nc] float64 for one imaginary frequency omega (eV)."""
+    lib = _load()
+    ev, ec = _c(ev, np.float64), _c(ec, np.float64)
+    out = np.empty(ev.shape[0] * ec.shape[0], np.float64)
+    resid = np.zeros(1, np.float64)
+    lib.oracle_delta(ev.shape[0], _p(ev), ec.shape[0], _p(ec), float(omega), _p(out), _p(resid))
+    return (out, float(resid[0])) if return_resid else out
+
+
+def chi0(M, dl) -> np.ndarray:
+    """chi [ng, ng] complex128 = sum_p conj(M[p,G]) dl[p] M[p,G']."""
+    lib = _load()
+    M, dl = _c(M, np.complex128), _c(dl, np.float64)
+    P, ng = M.shape
+    out = np.empty((ng, ng), np.complex128)
+    lib.oracle_chi0(P, ng, _p(M), _p(dl), _p(out))
+    return out
+
+
+def chi0_bands(prob, omega=None) -> np.ndarray:
+    """chi0 [nw, ng, ng] for a gwgen.Problem (M by convolution)."""
+    M = m_conv(prob.gpsi, prob.cv, prob.gpsi, prob.cc, prob.gchi)
+    ws = prob.omega if omega is None else np.atleast_1d(omega)
+    return np.stack([chi0(M, delta(prob.ev, prob.ec, w)) for w in ws])
+
+
+def adjoint(gv, cv, ev, gc, cc, ec, gchi, W, omega: float = 0.0):
+    """Returns (L, dL/dE_v, dL/dE_c, grad c_v, grad c_c); grad = dL/dRe + i dL/dIm."""
+    lib = _load()
+    gv, gc, gchi = _c(gv, np.int32), _c(gc, np.int32), _c(gchi, np.int32)
+    cv, cc, W = _c(cv, np.complex128), _c(cc, np.complex128), _c(W, np.complex128)
+    ev, ec = _c(ev, np.float64), _c(ec, np.float64)
+    nv, nc, ng = cv.shape[0], cc.shape[0], gchi.shape[0]
+    L = np.zeros(1, np.float64)
+    dEv, dEc = np.empty(nv), np.empty(nc)
+    dcv, dcc = np.empty_like(cv), np.empty_like(cc)
+    rc = lib.oracle_adjoint(nv, gv.shape[0], _p(gv), _p(cv), _p(ev), nc, gc.shape[0], _p(gc), _p(cc), _p(ec),
+                            ng, _p(gchi), _p(W), float(omega), _p(L), _p(dEv), _p(dEc), _p(dcv), _p(dcc))
+    if rc:
+        raise MemoryError("oracle_adjoint")
+    return float(L[0]), dEv, dEc, dcv, dcc
