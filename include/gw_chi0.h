@@ -1,0 +1,185 @@
+/*
+ * gw_chi0.h -- C ABI of the GB300 (sm_103a) independent-particle polarizability library.
+ *
+ * The library computes, on one GPU, the static/imaginary-frequency polarizability of
+ * Eq. chi_mat of the SC'25 BerkeleyGW paper ("Overview of the Problem"):
+ *
+ *     chi_GG'(q, iw) = sum_{v,c} conj(M_vc(q,G)) Delta_vc(iw) M_vc(q,G')
+ *
+ * with the plane-wave matrix elements defined inline after Eq. ff-ch,
+ *
+ *     M_vc(G) = \int psi_v^*(r) e^{iG.r} psi_c(r) dr  (cell-normalised),
+ *
+ * evaluated in two stages: (a) the real-space pair product of the two bands on the
+ * FFT grid, a forward FFT (sign +, scale 1/N_r) and a gather onto the caller's
+ * G-sphere (the MTXEL step of the paper's Epsilon module); (b) the energy-weighted
+ * Hermitian contraction over pairs (the CHI_SUM step, chunked over pairs like the
+ * paper's NV-Block algorithm).  The energy factor, which the paper leaves open, is
+ *
+ *     Delta_vc(iw) = 2/(x - iw) + 2/(x + iw) = 4x/(x^2 + w^2),   x = E_v - E_c < 0,
+ *
+ * with w a non-negative imaginary-axis frequency in eV.  The paper's outer factor 2 is
+ * folded into Delta; no volume or k-point normalisation is applied.
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are interleaved (re, im) pairs of doubles.
+ *   - Pointers marked "device" are caller-owned CUDA device pointers valid for the
+ *     duration of the call; pointers marked "host" are ordinary host memory.  The
+ *     library keeps no caller pointer after a call returns.
+ *   - All GPU work is enqueued on the stream given to gw_chi0_create; calls return
+ *     after enqueueing (except where stated).  The caller synchronises the stream, or
+ *     calls gw_chi0_sync, which also reports device-side errors.
+ *   - No C++ exception crosses this boundary.  Each call returns a gw_status; on error
+ *     a message is kept for gw_chi0_last_error and the handle stays usable.
+ *   - Plane-wave vectors G are integer Miller triples (int32 [n][3]); a cubic cell with
+ *     reciprocal vectors equal to the identity.
+ */
+#ifndef GW_CHI0_H
+#define GW_CHI0_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GW_API __attribute__((visibility("default")))
+#else
+#define GW_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gw_chi0 gw_chi0; /* opaque, library-owned */
+
+typedef enum {
+    GW_OK = 0,
+    GW_ERR_ARG = 1,         /* invalid argument (sizes, ranges, aliasing, energies) */
+    GW_ERR_STATE = 2,       /* a required set_* call has not been made */
+    GW_ERR_OOM = 3,         /* device allocation failed or the memory budget is too small */
+    GW_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    GW_ERR_UNSUPPORTED = 5, /* request not supported by this build / device */
+    GW_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up (reported by gw_chi0_sync) */
+} gw_status;
+
+typedef enum {
+    GW_PREC_FP64 = 0,      /* FP64 FFT + FP64 tensor-core (DMMA) contraction */
+    GW_PREC_OZAKI_BF16 = 1 /* FP64 FFT + split-precision contraction on BF16 tensor cores */
+} gw_prec;
+
+typedef struct {
+    int n[3];                /* FFT grid n0 x n1 x n2 (each a product of 2, 3, 5; 4 <= n <= 128) */
+    int nq;                  /* number of q-point slots (>= 1) */
+    int prec;                /* gw_prec */
+    int nslices;             /* Ozaki slices for GW_PREC_OZAKI_BF16 (3..8); ignored for FP64 */
+    int64_t pair_chunk;      /* pairs per M chunk; 0 = 8192 */
+    size_t mem_budget_bytes; /* cap on library-owned device memory; 0 = no cap */
+    int device;              /* CUDA device ordinal; must be current on the calling thread */
+} gw_chi0_desc;
+
+/*
+ * Create a handle.  stream: a cudaStream_t (may be NULL for the legacy default stream).
+ * Errors: GW_ERR_ARG (bad grid, nq < 1, prec/nslices out of range), GW_ERR_CUDA.
+ */
+GW_API gw_status gw_chi0_create(gw_chi0 **h, const gw_chi0_desc *d, void *cuda_stream);
+
+/* Release every library-owned resource.  Safe on NULL. */
+GW_API void gw_chi0_destroy(gw_chi0 *h);
+
+/* Message of the last failed call on this handle ("" if none).  Owned by the handle. */
+GW_API const char *gw_chi0_last_error(const gw_chi0 *h);
+
+/* Make subsequent calls enqueue on another stream (e.g. the caller's current stream). */
+GW_API gw_status gw_chi0_set_stream(gw_chi0 *h, void *cuda_stream);
+
+/*
+ * Band setup (step a1): psi_n(r) = sum_K c_n(K) e^{+iK.r} on the n0 x n1 x n2 grid (no
+ * 1/N factor), kept in library-owned device memory [nb][n0][n1][n2] complex128.
+ *   iq      q slot for valence bands (0 <= iq < nq); conduction bands (kind = 1) are
+ *           shared by every slot and iq is ignored.
+ *   kind    0 = valence (bands at k+q), 1 = conduction (bands at k).
+ *   gvec    device int32 [ngpsi][3]  plane waves of the coefficient rows.
+ *   coeff   device complex128 [nb][ngpsi].
+ *   energy  device float64 [nb], eV.
+ * Validation (GW_ERR_ARG): nb, ngpsi >= 1; |G| components inside (-n/2, n/2); every
+ * valence energy below every conduction energy once both sets are present.  Reads gvec
+ * and energy back to the host (synchronous on the stream).
+ */
+GW_API gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngpsi, const int32_t *gvec,
+                            const double *coeff, const double *energy);
+
+/*
+ * Dielectric G-sphere of slot iq (the G, G' index set of chi).  gvec: device int32 [ng][3].
+ * Errors (GW_ERR_ARG): ng < 1; the set is not alias-free for the stored bands, i.e.
+ * 2 max|K| + max|G| >= n on some axis.
+ */
+GW_API gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec);
+
+/*
+ * Forward chi0 for nq slots and nw imaginary frequencies (steps a1-a7 after setup).
+ *   iq     host int [nq]      slots to compute.
+ *   omega  host double [nw]   imaginary-axis frequencies w >= 0 (eV).
+ *   chi    device complex128, packed by slot: for slot i, nw blocks of ng_i x ng_i
+ *          (row G, column G'), slot blocks consecutive in the order of iq.  Written in
+ *          full (exactly Hermitian, zero imaginary diagonal); not accumulated into.
+ *   diag   device float64 or NULL: same packing, nw x ng_i values chi_GG computed by an
+ *          independent column reduction of Delta |M|^2 (a trace check).
+ * Errors: GW_ERR_STATE (bands or sphere missing), GW_ERR_ARG, GW_ERR_OOM, GW_ERR_CUDA.
+ */
+GW_API gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const double *omega, double *chi,
+                          double *diag);
+
+/*
+ * Stage (a) alone (steps a2-a4): M[p - pair_begin][g] for pairs p = v*nc + c in
+ * [pair_begin, pair_begin + pair_count) of slot iq.  M: device complex128 [pair_count][ng].
+ */
+GW_API gw_status gw_chi0_pair_elements(gw_chi0 *h, int iq, int64_t pair_begin, int64_t pair_count, double *M);
+
+/*
+ * Stage (b) alone (steps a5-a7) on caller-given matrix elements, using the handle's
+ * precision mode:  chi[w][G][G'] = sum_p conj(M[p][G]) Delta_p(w) M[p][G'],
+ * p = v*nc + c, Delta from ev [nv] and ec [nc] (device float64, eV).
+ *   M     device complex128 [nv*nc][ng]
+ *   omega host double [nw]
+ *   chi   device complex128 [nw][ng][ng], written in full.
+ * Needs no set_* call.
+ */
+GW_API gw_status gw_chi0_contract(gw_chi0 *h, int nv, int nc, const double *ev, const double *ec, int ng,
+                           const double *M, int nw, const double *omega, double *chi);
+
+/*
+ * Adjoint of L = Re Tr(W chi0(iq, w)) for a Hermitian W (GWPT-style sensitivity,
+ * Eq. gwpt motivates it).  Matrix elements are recomputed chunk by chunk.
+ *   W        device complex128 [ng][ng], Hermitian (only its values are read).
+ *   L        host double* or NULL: the value of L (synchronous when non-NULL).
+ *   dE_v     device float64 [nv]; dE_c device float64 [nc]: dL/dE.
+ *   dcoeff_v device complex128 [nv][ngpsi_v]; dcoeff_c [nc][ngpsi_c]:
+ *            dL/dRe c + i dL/dIm c for every coefficient of the stored band sets.
+ * Outputs are written in full.  Errors as gw_chi0_compute.
+ */
+GW_API gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, double *L, double *dE_v,
+                          double *dE_c, double *dcoeff_v, double *dcoeff_c);
+
+/*
+ * Synchronise the handle's stream and report device-side status: GW_ERR_TIMEOUT if a
+ * bounded wait inside a kernel gave up since the last gw_chi0_sync, GW_ERR_CUDA on a
+ * CUDA error, else GW_OK.  Clears the device status word.
+ */
+GW_API gw_status gw_chi0_sync(gw_chi0 *h);
+
+/*
+ * Per-kernel timing.  When enabled, every library kernel launch is bracketed by CUDA
+ * events on the handle's stream.  gw_chi0_timing fills, for up to n kernel classes,
+ * names (host char[n][32]), total milliseconds and launch counts since the last reset
+ * (synchronises the stream).  Returns the number of classes.
+ */
+GW_API gw_status gw_chi0_set_timing(gw_chi0 *h, int enable);
+GW_API int gw_chi0_timing(gw_chi0 *h, int n, char (*names)[32], double *ms, int64_t *launches, int reset);
+
+/* Library-owned device bytes currently held by the handle. */
+GW_API size_t gw_chi0_device_bytes(const gw_chi0 *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GW_CHI0_H */

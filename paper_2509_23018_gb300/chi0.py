@@ -1,0 +1,199 @@
+"""Python binding of the chi0 C ABI (argument marshalling only).
+
+Names follow include/gw_chi0.h: ``create``, ``set_bands``, ``set_gsphere``,
+``compute``, ``pair_elements``, ``contract``, ``adjoint``, ``sync``, ``destroy``.
+Torch supplies device memory and the stream; every arithmetic step runs in the
+CUDA library.  Complex tensors are complex128 (interleaved re/im doubles).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import torch
+
+from . import _lib
+
+
+class GwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream_handle():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+PREC = {"fp64": _lib.GW_PREC_FP64, "ozaki": _lib.GW_PREC_OZAKI_BF16, "ozaki_bf16": _lib.GW_PREC_OZAKI_BF16}
+
+
+class Chi0:
+    """One handle of the library (one device, one stream at a time)."""
+
+    def __init__(self, grid: Sequence[int], nq: int = 1, prec: str = "fp64", nslices: int = 6,
+                 pair_chunk: int = 8192, mem_budget_bytes: int = 0, device: int | None = None):
+        self.lib = _lib.load()
+        dev = torch.cuda.current_device() if device is None else device
+        d = _lib.Desc()
+        for a in range(3):
+            d.n[a] = int(grid[a])
+        d.nq, d.prec, d.nslices = int(nq), PREC[prec], int(nslices)
+        d.pair_chunk, d.mem_budget_bytes, d.device = int(pair_chunk), int(mem_budget_bytes), int(dev)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            st = self.lib.gw_chi0_create(ctypes.byref(h), ctypes.byref(d), _stream_handle())
+        if st != 0:
+            raise GwError(st, "gw_chi0_create failed")
+        self.h = h
+        self.grid = tuple(int(x) for x in grid)
+        self.nq, self.prec, self.device = int(nq), prec, dev
+        self.ng = {}
+        self.nb = {}
+        self.ngpsi = {}
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, st):
+        if st != 0:
+            raise GwError(st, self.lib.gw_chi0_last_error(self.h).decode())
+
+    def _use_current_stream(self):
+        self._check(self.lib.gw_chi0_set_stream(self.h, _stream_handle()))
+
+    # -------------------------------------------------------------- ABI calls
+    def set_bands(self, iq: int, kind: int, gvec: torch.Tensor, coeff: torch.Tensor, energy: torch.Tensor):
+        gvec = gvec.to(device=f"cuda:{self.device}", dtype=torch.int32).contiguous()
+        coeff = coeff.to(device=f"cuda:{self.device}", dtype=torch.complex128).contiguous()
+        energy = energy.to(device=f"cuda:{self.device}", dtype=torch.float64).contiguous()
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_set_bands(self.h, int(iq), int(kind), coeff.shape[0], coeff.shape[1],
+                                               _ptr(gvec), _ptr(coeff), _ptr(energy)))
+        key = ("c",) if kind == 1 else ("v", iq)
+        self.nb[key] = coeff.shape[0]
+        self.ngpsi[key] = coeff.shape[1]
+
+    def set_gsphere(self, iq: int, gvec: torch.Tensor):
+        gvec = gvec.to(device=f"cuda:{self.device}", dtype=torch.int32).contiguous()
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_set_gsphere(self.h, int(iq), gvec.shape[0], _ptr(gvec)))
+        self.ng[iq] = gvec.shape[0]
+
+    def compute(self, iq: Sequence[int] | int, omega: Sequence[float], out: torch.Tensor | None = None,
+                diag: bool = False):
+        """chi0 blocks: list (per slot) of [nw, ng, ng] complex128 views into one packed buffer."""
+        iqs = [int(iq)] if isinstance(iq, int) else [int(x) for x in iq]
+        om = [float(w) for w in omega]
+        nw = len(om)
+        tot = sum(nw * self.ng[q] ** 2 for q in iqs)
+        if out is None:
+            out = torch.empty(tot, dtype=torch.complex128, device=f"cuda:{self.device}")
+        assert out.dtype == torch.complex128 and out.is_contiguous() and out.numel() >= tot
+        dg = torch.empty(sum(nw * self.ng[q] for q in iqs), dtype=torch.float64,
+                         device=f"cuda:{self.device}") if diag else None
+        iq_arr = (ctypes.c_int * len(iqs))(*iqs)
+        om_arr = (ctypes.c_double * nw)(*om)
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_compute(self.h, len(iqs), iq_arr, nw, om_arr, _ptr(out), _ptr(dg)))
+        res, dres, off, doff = [], [], 0, 0
+        for q in iqs:
+            n = self.ng[q]
+            res.append(out[off:off + nw * n * n].view(nw, n, n))
+            if diag:
+                dres.append(dg[doff:doff + nw * n].view(nw, n))
+            off += nw * n * n
+            doff += nw * n
+        return (res, dres) if diag else res
+
+    def pair_elements(self, iq: int, begin: int, count: int, out: torch.Tensor | None = None):
+        n = self.ng[iq]
+        if out is None:
+            out = torch.empty((count, n), dtype=torch.complex128, device=f"cuda:{self.device}")
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_pair_elements(self.h, int(iq), int(begin), int(count), _ptr(out)))
+        return out
+
+    def contract(self, ev: torch.Tensor, ec: torch.Tensor, M: torch.Tensor, omega: Sequence[float],
+                 out: torch.Tensor | None = None):
+        ev = ev.to(device=f"cuda:{self.device}", dtype=torch.float64).contiguous()
+        ec = ec.to(device=f"cuda:{self.device}", dtype=torch.float64).contiguous()
+        M = M.to(device=f"cuda:{self.device}", dtype=torch.complex128).contiguous()
+        ng = M.shape[1]
+        nw = len(omega)
+        if out is None:
+            out = torch.empty((nw, ng, ng), dtype=torch.complex128, device=f"cuda:{self.device}")
+        om_arr = (ctypes.c_double * nw)(*[float(w) for w in omega])
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_contract(self.h, ev.shape[0], ec.shape[0], _ptr(ev), _ptr(ec), ng, _ptr(M),
+                                              nw, om_arr, _ptr(out)))
+        return out
+
+    def adjoint(self, iq: int, W: torch.Tensor, omega: float = 0.0, want_L: bool = True):
+        W = W.to(device=f"cuda:{self.device}", dtype=torch.complex128).contiguous()
+        dev = f"cuda:{self.device}"
+        nv, nc = self.nb[("v", iq)], self.nb[("c",)]
+        dEv = torch.empty(nv, dtype=torch.float64, device=dev)
+        dEc = torch.empty(nc, dtype=torch.float64, device=dev)
+        dcv = torch.empty((nv, self.ngpsi[("v", iq)]), dtype=torch.complex128, device=dev)
+        dcc = torch.empty((nc, self.ngpsi[("c",)]), dtype=torch.complex128, device=dev)
+        L = ctypes.c_double(0.0)
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_adjoint(self.h, int(iq), float(omega), _ptr(W),
+                                             ctypes.byref(L) if want_L else None, _ptr(dEv), _ptr(dEc),
+                                             _ptr(dcv), _ptr(dcc)))
+        return (L.value if want_L else None), dEv, dEc, dcv, dcc
+
+    def sync(self):
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_sync(self.h))
+
+    def set_timing(self, enable: bool):
+        self._check(self.lib.gw_chi0_set_timing(self.h, 1 if enable else 0))
+
+    def timing(self, reset: bool = True):
+        n = 32
+        names = (ctypes.c_char * 32 * n)()
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        k = self.lib.gw_chi0_timing(self.h, n, names, ms, cnt, 1 if reset else 0)
+        return {bytes(names[i]).split(b"\0")[0].decode(): (ms[i], cnt[i]) for i in range(min(k, n))}
+
+    def device_bytes(self) -> int:
+        return int(self.lib.gw_chi0_device_bytes(self.h))
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            self.lib.gw_chi0_destroy(self.h)
+            self.h = None
+
+    close = destroy
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()
+
+
+def create(grid, **kw) -> Chi0:
+    return Chi0(grid, **kw)
+
+
+def from_problem(prob, prec: str = "fp64", nslices: int = 6, pair_chunk: int = 8192, **kw) -> Chi0:
+    """Handle with one q slot loaded from a gwgen.Problem (inputs copied to the GPU)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    h = Chi0(prob.grid, nq=1, prec=prec, nslices=nslices, pair_chunk=pair_chunk, **kw)
+    g = torch.as_tensor(prob.gpsi, device=dev)
+    h.set_bands(0, 1, g, torch.as_tensor(prob.cc, device=dev), torch.as_tensor(prob.ec, device=dev))
+    h.set_bands(0, 0, g, torch.as_tensor(prob.cv, device=dev), torch.as_tensor(prob.ev, device=dev))
+    h.set_gsphere(0, torch.as_tensor(prob.gchi, device=dev))
+    return h

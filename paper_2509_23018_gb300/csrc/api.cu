@@ -1,0 +1,677 @@
+// Host side of the C ABI declared in include/gw_chi0.h: handle state, validation,
+// library-owned device memory, per-chunk orchestration and optional per-kernel timing.
+#include "../../include/gw_chi0.h"
+#include "internal.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using gw::FftAxis;
+
+namespace {
+
+struct BandSet {
+    int nb = 0, ngpsi = 0;
+    double2 *psi = nullptr;     // [nb][N_r]
+    double *energy = nullptr;   // [nb] device copy
+    int32_t *gvec = nullptr;    // [ngpsi][3] device copy (adjoint)
+    int32_t *gofs = nullptr;    // [ngpsi] grid offsets
+    std::vector<int32_t> g;     // host copy
+    std::vector<double> e;      // host copy
+    int maxabs[3] = {0, 0, 0};
+};
+
+struct Sphere {
+    int ng = 0;
+    std::vector<int32_t> g;
+    int maxabs[3] = {0, 0, 0};
+    int K2 = 0;
+    int *kz = nullptr;          // device [K2]
+    int32_t *gpack = nullptr;   // device [ng]
+    int32_t *gvec = nullptr;    // device [ng][3]
+};
+
+struct TimerRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+
+} // namespace
+
+struct gw_chi0 {
+    gw_chi0_desc d{};
+    cudaStream_t st = nullptr;
+    std::string err;
+    int64_t nr = 0;
+    FftAxis ax[3]{};
+    double2 *tw = nullptr;
+    BandSet cond;
+    std::vector<BandSet> val;
+    std::vector<Sphere> sph;
+    double2 *Mbuf = nullptr;
+    size_t Mcap = 0; // elements
+    double *dbuf = nullptr;
+    size_t dcap = 0;
+    int *status = nullptr;
+    size_t bytes = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    // timing
+    bool timing = false;
+    std::vector<TimerRec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::map<std::string, std::pair<double, int64_t>> acc;
+};
+
+namespace {
+
+gw_status fail(gw_chi0 *h, gw_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    return s;
+}
+
+gw_status cuda_fail(gw_chi0 *h, cudaError_t e, const char *what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? GW_ERR_OOM : GW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, x, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (x);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+gw_status dalloc(gw_chi0 *h, void **p, size_t n, const char *what)
+{
+    if (n == 0) n = 16;
+    if (h->d.mem_budget_bytes && h->bytes + n > h->d.mem_budget_bytes)
+        return fail(h, GW_ERR_OOM, "%s: %zu bytes would exceed the memory budget (%zu held, budget %zu)", what, n,
+                    h->bytes, h->d.mem_budget_bytes);
+    cudaError_t e = cudaMalloc(p, n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, GW_ERR_OOM, "%s: cudaMalloc(%zu) failed: %s", what, n, cudaGetErrorString(e));
+    }
+    h->bytes += n;
+    return GW_OK;
+}
+
+void dfree(gw_chi0 *h, void *p, size_t n)
+{
+    if (!p) return;
+    cudaFree(p);
+    h->bytes -= (n == 0 ? 16 : n);
+}
+
+bool factor(int n, FftAxis &a)
+{
+    a.n = n;
+    a.nst = 0;
+    int m = n;
+    while (m % 8 == 0 && m != 16 && a.nst < gw::kMaxStages) { a.rad[a.nst++] = 8; m /= 8; }
+    while (m % 4 == 0 && a.nst < gw::kMaxStages) { a.rad[a.nst++] = 4; m /= 4; }
+    for (int r : {2, 3, 5})
+        while (m % r == 0 && a.nst < gw::kMaxStages) { a.rad[a.nst++] = r; m /= r; }
+    return m == 1;
+}
+
+int mod(int a, int n) { return ((a % n) + n) % n; }
+
+// ------------------------------------------------------------------ timing helpers
+cudaEvent_t ev_get(gw_chi0 *h)
+{
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Scope {
+    gw_chi0 *h;
+    const char *name;
+    cudaEvent_t a = nullptr;
+    Scope(gw_chi0 *h_, const char *n) : h(h_), name(n)
+    {
+        if (h->timing) {
+            a = ev_get(h);
+            cudaEventRecord(a, h->st);
+        }
+    }
+    ~Scope()
+    {
+        if (h->timing) {
+            cudaEvent_t b = ev_get(h);
+            cudaEventRecord(b, h->st);
+            h->pending.push_back({name, a, b});
+        }
+    }
+};
+
+void drain_timing(gw_chi0 *h)
+{
+    if (h->pending.empty()) return;
+    cudaStreamSynchronize(h->st);
+    for (auto &r : h->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &x = h->acc[r.name];
+        x.first += ms;
+        x.second += 1;
+        h->pool.push_back(r.a);
+        h->pool.push_back(r.b);
+    }
+    h->pending.clear();
+}
+
+// ------------------------------------------------------------------ buffers
+gw_status ensure_work(gw_chi0 *h, size_t m_elems, size_t d_elems)
+{
+    if (m_elems > h->Mcap) {
+        dfree(h, h->Mbuf, h->Mcap * sizeof(double2));
+        h->Mbuf = nullptr;
+        h->Mcap = 0;
+        gw_status s = dalloc(h, (void **)&h->Mbuf, m_elems * sizeof(double2), "M chunk buffer");
+        if (s) return s;
+        h->Mcap = m_elems;
+    }
+    if (d_elems > h->dcap) {
+        dfree(h, h->dbuf, h->dcap * sizeof(double));
+        h->dbuf = nullptr;
+        h->dcap = 0;
+        gw_status s = dalloc(h, (void **)&h->dbuf, d_elems * sizeof(double), "Delta buffer");
+        if (s) return s;
+        h->dcap = d_elems;
+    }
+    return GW_OK;
+}
+
+gw_status make_tmap(gw_chi0 *h, CUtensorMap *map, const void *M, int64_t P, int ng)
+{
+    if (((uintptr_t)M & 15) != 0) return fail(h, GW_ERR_ARG, "M must be 16-byte aligned");
+    cuuint64_t dims[2] = {(cuuint64_t)2 * ng, (cuuint64_t)P};
+    cuuint64_t strides[1] = {(cuuint64_t)2 * ng * sizeof(double)};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * gw::contract_f64_tile()), (cuuint32_t)gw::contract_f64_bk()};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = h->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(M), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GW_OK;
+}
+
+int pick_ksplit(int ng, int64_t P, int nw)
+{
+    // enough blocks for several full waves of 2 resident blocks on each of the SMs
+    int sms = 152;
+    int dev;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int nt = (ng + gw::contract_f64_tile() - 1) / gw::contract_f64_tile();
+    int64_t tiles = (int64_t)nt * (nt + 1) / 2 * nw;
+    int64_t want = 8LL * sms;
+    int64_t ks = (want + tiles - 1) / tiles;
+    int64_t kmax = (P + 255) / 256; // at least 256 pairs per block
+    if (ks > kmax) ks = kmax;
+    if (ks < 1) ks = 1;
+    return (int)ks;
+}
+
+gw_status contract_chunk(gw_chi0 *h, const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride,
+                         int nw, double2 *chi)
+{
+    CUtensorMap map;
+    gw_status s = make_tmap(h, &map, M, P, ng);
+    if (s) return s;
+    Scope sc(h, "contract_f64");
+    CK(h, gw::launch_contract_f64(&map, delta, dstride, P, ng, nw, (double *)chi, pick_ksplit(ng, P, nw), h->status,
+                                  h->st),
+       "contract_f64");
+    return GW_OK;
+}
+
+bool alias_free(const gw_chi0 *h, const BandSet &v, const BandSet &c, const Sphere &s, int *axis)
+{
+    for (int a = 0; a < 3; ++a)
+        if (v.maxabs[a] + c.maxabs[a] + s.maxabs[a] >= h->d.n[a]) {
+            *axis = a;
+            return false;
+        }
+    return true;
+}
+
+gw_status check_slot(gw_chi0 *h, int iq)
+{
+    if (iq < 0 || iq >= h->d.nq) return fail(h, GW_ERR_ARG, "q slot %d out of range [0, %d)", iq, h->d.nq);
+    const BandSet &v = h->val[iq];
+    const Sphere &s = h->sph[iq];
+    if (v.nb == 0) return fail(h, GW_ERR_STATE, "valence bands of slot %d not set", iq);
+    if (h->cond.nb == 0) return fail(h, GW_ERR_STATE, "conduction bands not set");
+    if (s.ng == 0) return fail(h, GW_ERR_STATE, "G-sphere of slot %d not set", iq);
+    int ax;
+    if (!alias_free(h, v, h->cond, s, &ax))
+        return fail(h, GW_ERR_ARG, "slot %d: max|K_v| + max|K_c| + max|G| >= n on axis %d (aliasing)", iq, ax);
+    double vmax = *std::max_element(v.e.begin(), v.e.end());
+    double cmin = *std::min_element(h->cond.e.begin(), h->cond.e.end());
+    if (!(vmax < cmin)) return fail(h, GW_ERR_ARG, "slot %d: a valence energy is not below every conduction energy", iq);
+    return GW_OK;
+}
+
+gw::PairPlan pair_plan(gw_chi0 *h, const Sphere &s)
+{
+    gw::PairPlan pp;
+    for (int a = 0; a < 3; ++a) {
+        pp.n[a] = h->d.n[a];
+        pp.ax[a] = h->ax[a];
+    }
+    pp.K2 = s.K2;
+    pp.kz = s.kz;
+    pp.ng = s.ng;
+    pp.gpack = s.gpack;
+    return pp;
+}
+
+void free_bands(gw_chi0 *h, BandSet &b)
+{
+    dfree(h, b.psi, sizeof(double2) * (size_t)b.nb * h->nr);
+    dfree(h, b.energy, sizeof(double) * b.nb);
+    dfree(h, b.gvec, sizeof(int32_t) * 3 * b.ngpsi);
+    dfree(h, b.gofs, sizeof(int32_t) * b.ngpsi);
+    b = BandSet();
+}
+
+void free_sphere(gw_chi0 *h, Sphere &s)
+{
+    dfree(h, s.kz, sizeof(int) * s.K2);
+    dfree(h, s.gpack, sizeof(int32_t) * s.ng);
+    dfree(h, s.gvec, sizeof(int32_t) * 3 * s.ng);
+    s = Sphere();
+}
+
+} // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+gw_status gw_chi0_create(gw_chi0 **out, const gw_chi0_desc *d, void *stream)
+{
+    if (!out || !d) return GW_ERR_ARG;
+    *out = nullptr;
+    gw_chi0 *h = new (std::nothrow) gw_chi0();
+    if (!h) return GW_ERR_OOM;
+    h->d = *d;
+    h->st = (cudaStream_t)stream;
+    if (h->d.pair_chunk <= 0) h->d.pair_chunk = 8192;
+    if (h->d.nq < 1) { delete h; return GW_ERR_ARG; }
+    if (h->d.prec != GW_PREC_FP64 && h->d.prec != GW_PREC_OZAKI_BF16) { delete h; return GW_ERR_ARG; }
+    if (h->d.prec == GW_PREC_OZAKI_BF16 && (h->d.nslices < 3 || h->d.nslices > 8)) { delete h; return GW_ERR_ARG; }
+    for (int a = 0; a < 3; ++a) {
+        int n = h->d.n[a];
+        if (n < 4 || n > 128 || !factor(n, h->ax[a])) { delete h; return GW_ERR_ARG; }
+    }
+    if (cudaSetDevice(h->d.device) != cudaSuccess) { cudaGetLastError(); delete h; return GW_ERR_CUDA; }
+    h->nr = (int64_t)h->d.n[0] * h->d.n[1] * h->d.n[2];
+    h->val.resize(h->d.nq);
+    h->sph.resize(h->d.nq);
+
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        delete h;
+        return GW_ERR_CUDA;
+    }
+    h->encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+
+    // twiddle tables e^{+2 pi i t/n}, computed in extended precision on the host
+    int ntot = h->d.n[0] + h->d.n[1] + h->d.n[2];
+    std::vector<double2> tw(ntot);
+    int off = 0;
+    for (int a = 0; a < 3; ++a) {
+        int n = h->d.n[a];
+        for (int t = 0; t < n; ++t) {
+            long double ang = 2.0L * 3.141592653589793238462643383279502884L * (long double)t / (long double)n;
+            tw[off + t] = make_double2((double)cosl(ang), (double)sinl(ang));
+        }
+        off += n;
+    }
+    if (dalloc(h, (void **)&h->tw, sizeof(double2) * ntot, "twiddles") ||
+        dalloc(h, (void **)&h->status, sizeof(int), "status word")) {
+        gw_chi0_destroy(h);
+        return GW_ERR_OOM;
+    }
+    if (cudaMemcpy(h->tw, tw.data(), sizeof(double2) * ntot, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        gw_chi0_destroy(h);
+        return GW_ERR_CUDA;
+    }
+    off = 0;
+    for (int a = 0; a < 3; ++a) {
+        h->ax[a].tw = h->tw + off;
+        off += h->d.n[a];
+    }
+    *out = h;
+    return GW_OK;
+}
+
+void gw_chi0_destroy(gw_chi0 *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->st);
+    free_bands(h, h->cond);
+    for (auto &b : h->val) free_bands(h, b);
+    for (auto &s : h->sph) free_sphere(h, s);
+    dfree(h, h->Mbuf, h->Mcap * sizeof(double2));
+    dfree(h, h->dbuf, h->dcap * sizeof(double));
+    dfree(h, h->tw, 0);
+    dfree(h, h->status, 0);
+    for (auto &r : h->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->pool) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete h;
+}
+
+const char *gw_chi0_last_error(const gw_chi0 *h) { return h ? h->err.c_str() : "null handle"; }
+
+gw_status gw_chi0_set_stream(gw_chi0 *h, void *stream)
+{
+    if (!h) return GW_ERR_ARG;
+    h->st = (cudaStream_t)stream;
+    return GW_OK;
+}
+
+gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngpsi, const int32_t *gvec, const double *coeff,
+                            const double *energy)
+{
+    if (!h) return GW_ERR_ARG;
+    if (kind != 0 && kind != 1) return fail(h, GW_ERR_ARG, "kind must be 0 (valence) or 1 (conduction)");
+    if (kind == 0 && (iq < 0 || iq >= h->d.nq)) return fail(h, GW_ERR_ARG, "q slot %d out of range", iq);
+    if (nb < 1 || ngpsi < 1) return fail(h, GW_ERR_ARG, "nb and ngpsi must be >= 1");
+    if (!gvec || !coeff || !energy) return fail(h, GW_ERR_ARG, "null pointer");
+    BandSet nbs;
+    nbs.nb = nb;
+    nbs.ngpsi = ngpsi;
+    nbs.g.resize((size_t)3 * ngpsi);
+    nbs.e.resize(nb);
+    CK(h, cudaMemcpyAsync(nbs.g.data(), gvec, sizeof(int32_t) * 3 * ngpsi, cudaMemcpyDeviceToHost, h->st), "copy gvec");
+    CK(h, cudaMemcpyAsync(nbs.e.data(), energy, sizeof(double) * nb, cudaMemcpyDeviceToHost, h->st), "copy energy");
+    CK(h, cudaStreamSynchronize(h->st), "set_bands sync");
+    std::vector<int32_t> gofs(ngpsi);
+    for (int k = 0; k < ngpsi; ++k) {
+        int idx[3];
+        for (int a = 0; a < 3; ++a) {
+            int g = nbs.g[3 * k + a];
+            if (2 * std::abs(g) >= h->d.n[a])
+                return fail(h, GW_ERR_ARG, "plane wave %d: component %d outside (-n/2, n/2)", k, g);
+            nbs.maxabs[a] = std::max(nbs.maxabs[a], std::abs(g));
+            idx[a] = mod(g, h->d.n[a]);
+        }
+        gofs[k] = (idx[0] * h->d.n[1] + idx[1]) * h->d.n[2] + idx[2];
+    }
+    for (double e : nbs.e)
+        if (!std::isfinite(e)) return fail(h, GW_ERR_ARG, "non-finite band energy");
+    // energy ordering against the other set, when present
+    const BandSet *other = nullptr;
+    if (kind == 0 && h->cond.nb) other = &h->cond;
+    if (other) {
+        double vmax = *std::max_element(nbs.e.begin(), nbs.e.end());
+        double cmin = *std::min_element(other->e.begin(), other->e.end());
+        if (!(vmax < cmin)) return fail(h, GW_ERR_ARG, "a valence energy is not below every conduction energy");
+    }
+    if (kind == 1) {
+        double cmin = *std::min_element(nbs.e.begin(), nbs.e.end());
+        for (auto &v : h->val)
+            if (v.nb && !(*std::max_element(v.e.begin(), v.e.end()) < cmin))
+                return fail(h, GW_ERR_ARG, "a valence energy is not below every conduction energy");
+    }
+    BandSet &dst = kind == 0 ? h->val[iq] : h->cond;
+    free_bands(h, dst);
+    gw_status s;
+    if ((s = dalloc(h, (void **)&nbs.psi, sizeof(double2) * (size_t)nb * h->nr, "psi grids")) ||
+        (s = dalloc(h, (void **)&nbs.energy, sizeof(double) * nb, "energies")) ||
+        (s = dalloc(h, (void **)&nbs.gvec, sizeof(int32_t) * 3 * ngpsi, "gvec")) ||
+        (s = dalloc(h, (void **)&nbs.gofs, sizeof(int32_t) * ngpsi, "grid offsets"))) {
+        free_bands(h, nbs);
+        return s;
+    }
+    CK(h, cudaMemcpyAsync(nbs.energy, energy, sizeof(double) * nb, cudaMemcpyDeviceToDevice, h->st), "energies");
+    CK(h, cudaMemcpyAsync(nbs.gvec, gvec, sizeof(int32_t) * 3 * ngpsi, cudaMemcpyDeviceToDevice, h->st), "gvec");
+    CK(h, cudaMemcpyAsync(nbs.gofs, gofs.data(), sizeof(int32_t) * ngpsi, cudaMemcpyHostToDevice, h->st), "gofs");
+    CK(h, cudaMemsetAsync(nbs.psi, 0, sizeof(double2) * (size_t)nb * h->nr, h->st), "zero psi");
+    {
+        Scope sc(h, "band_scatter");
+        CK(h, gw::launch_scatter((const double2 *)coeff, nbs.gofs, nb, ngpsi, h->nr, nbs.psi, h->st), "scatter");
+    }
+    {
+        Scope sc(h, "band_fft");
+        CK(h, gw::launch_band_fft(nbs.psi, nb, h->d.n, h->ax, h->st), "band fft");
+    }
+    CK(h, cudaStreamSynchronize(h->st), "set_bands sync"); // gofs host vector goes out of scope
+    dst = std::move(nbs);
+    return GW_OK;
+}
+
+gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
+{
+    if (!h) return GW_ERR_ARG;
+    if (iq < 0 || iq >= h->d.nq) return fail(h, GW_ERR_ARG, "q slot %d out of range", iq);
+    if (ng < 1) return fail(h, GW_ERR_ARG, "ng must be >= 1");
+    if (ng > gw::pair_max_ng()) return fail(h, GW_ERR_UNSUPPORTED, "ng = %d exceeds %d", ng, gw::pair_max_ng());
+    if (!gvec) return fail(h, GW_ERR_ARG, "null pointer");
+    Sphere s;
+    s.ng = ng;
+    s.g.resize((size_t)3 * ng);
+    CK(h, cudaMemcpyAsync(s.g.data(), gvec, sizeof(int32_t) * 3 * ng, cudaMemcpyDeviceToHost, h->st), "copy sphere");
+    CK(h, cudaStreamSynchronize(h->st), "set_gsphere sync");
+    std::vector<int> present(h->d.n[2], 0);
+    for (int i = 0; i < ng; ++i)
+        for (int a = 0; a < 3; ++a) {
+            int g = s.g[3 * i + a];
+            if (2 * std::abs(g) >= h->d.n[a]) return fail(h, GW_ERR_ARG, "G %d: component %d outside (-n/2, n/2)", i, g);
+            s.maxabs[a] = std::max(s.maxabs[a], std::abs(g));
+        }
+    for (int i = 0; i < ng; ++i) present[mod(s.g[3 * i + 2], h->d.n[2])] = 1;
+    std::vector<int> kz, pos(h->d.n[2], -1);
+    for (int k = 0; k < h->d.n[2]; ++k)
+        if (present[k]) {
+            pos[k] = (int)kz.size();
+            kz.push_back(k);
+        }
+    std::vector<int32_t> pack(ng);
+    for (int i = 0; i < ng; ++i) {
+        int k0 = mod(s.g[3 * i], h->d.n[0]), k1 = mod(s.g[3 * i + 1], h->d.n[1]);
+        int k2 = pos[mod(s.g[3 * i + 2], h->d.n[2])];
+        pack[i] = k0 | (k1 << 8) | (k2 << 16);
+    }
+    // alias check against whatever bands are already stored
+    int ax;
+    if (h->val[iq].nb && h->cond.nb && !alias_free(h, h->val[iq], h->cond, s, &ax))
+        return fail(h, GW_ERR_ARG, "max|K_v| + max|K_c| + max|G| >= n on axis %d (aliasing)", ax);
+    s.K2 = (int)kz.size();
+    gw_status st;
+    if ((st = dalloc(h, (void **)&s.kz, sizeof(int) * s.K2, "sphere kz")) ||
+        (st = dalloc(h, (void **)&s.gpack, sizeof(int32_t) * ng, "sphere pack")) ||
+        (st = dalloc(h, (void **)&s.gvec, sizeof(int32_t) * 3 * ng, "sphere gvec"))) {
+        free_sphere(h, s);
+        return st;
+    }
+    CK(h, cudaMemcpyAsync(s.kz, kz.data(), sizeof(int) * s.K2, cudaMemcpyHostToDevice, h->st), "kz");
+    CK(h, cudaMemcpyAsync(s.gpack, pack.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, h->st), "pack");
+    CK(h, cudaMemcpyAsync(s.gvec, gvec, sizeof(int32_t) * 3 * ng, cudaMemcpyDeviceToDevice, h->st), "gvec");
+    CK(h, cudaStreamSynchronize(h->st), "set_gsphere sync");
+    free_sphere(h, h->sph[iq]);
+    h->sph[iq] = std::move(s);
+    return GW_OK;
+}
+
+gw_status gw_chi0_pair_elements(gw_chi0 *h, int iq, int64_t pair_begin, int64_t pair_count, double *M)
+{
+    if (!h) return GW_ERR_ARG;
+    gw_status s = check_slot(h, iq);
+    if (s) return s;
+    const BandSet &v = h->val[iq];
+    int64_t P = (int64_t)v.nb * h->cond.nb;
+    if (pair_begin < 0 || pair_count < 0 || pair_begin + pair_count > P)
+        return fail(h, GW_ERR_ARG, "pair range [%lld, %lld) outside [0, %lld)", (long long)pair_begin,
+                    (long long)(pair_begin + pair_count), (long long)P);
+    if (pair_count && !M) return fail(h, GW_ERR_ARG, "null M");
+    Scope sc(h, "pair_mtxel");
+    CK(h, gw::launch_pair(v.psi, h->cond.psi, h->cond.nb, pair_begin, pair_count, pair_plan(h, h->sph[iq]),
+                          (double2 *)M, h->st),
+       "pair kernel");
+    return GW_OK;
+}
+
+gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const double *omega, double *chi, double *diag)
+{
+    if (!h) return GW_ERR_ARG;
+    if (nq < 1 || !iq || nw < 1 || nw > gw::kMaxOmega || !omega || !chi)
+        return fail(h, GW_ERR_ARG, "bad arguments (nq >= 1, 1 <= nw <= %d, non-null pointers)", gw::kMaxOmega);
+    gw::OmegaList om;
+    om.nw = nw;
+    for (int i = 0; i < nw; ++i) {
+        if (!(omega[i] >= 0.0) || !std::isfinite(omega[i])) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
+        om.w[i] = omega[i];
+    }
+    for (int i = 0; i < nq; ++i) {
+        gw_status s = check_slot(h, iq[i]);
+        if (s) return s;
+    }
+    if (h->d.prec != GW_PREC_FP64) return fail(h, GW_ERR_UNSUPPORTED, "precision mode not built yet");
+    size_t off = 0, doff = 0;
+    for (int i = 0; i < nq; ++i) {
+        const Sphere &sp = h->sph[iq[i]];
+        const BandSet &v = h->val[iq[i]];
+        const int ng = sp.ng;
+        const int64_t P = (int64_t)v.nb * h->cond.nb;
+        const int64_t chunk = std::min<int64_t>(h->d.pair_chunk, P);
+        double2 *cq = (double2 *)chi + off;
+        double *dq = diag ? diag + doff : nullptr;
+        CK(h, cudaMemsetAsync(cq, 0, sizeof(double2) * (size_t)nw * ng * ng, h->st), "zero chi");
+        if (dq) CK(h, cudaMemsetAsync(dq, 0, sizeof(double) * (size_t)nw * ng, h->st), "zero diag");
+        gw_status s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw);
+        if (s) return s;
+        gw::PairPlan pp = pair_plan(h, sp);
+        for (int64_t p0 = 0; p0 < P; p0 += chunk) {
+            int64_t cnt = std::min(chunk, P - p0);
+            {
+                Scope sc(h, "pair_mtxel");
+                CK(h, gw::launch_pair(v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf, h->st), "pair kernel");
+            }
+            {
+                Scope sc(h, "delta");
+                CK(h, gw::launch_delta(v.energy, h->cond.energy, h->cond.nb, p0, cnt, om, h->dbuf, h->st), "delta");
+            }
+            s = contract_chunk(h, h->Mbuf, cnt, ng, h->dbuf, cnt, nw, cq);
+            if (s) return s;
+            if (dq) {
+                Scope sc(h, "diag");
+                CK(h, gw::launch_diag(h->Mbuf, cnt, ng, h->dbuf, cnt, nw, dq, ng, h->st), "diag");
+            }
+        }
+        {
+            Scope sc(h, "symmetrize");
+            CK(h, gw::launch_symmetrize(cq, ng, nw, h->st), "symmetrize");
+        }
+        off += (size_t)nw * ng * ng;
+        doff += (size_t)nw * ng;
+    }
+    return GW_OK;
+}
+
+gw_status gw_chi0_contract(gw_chi0 *h, int nv, int nc, const double *ev, const double *ec, int ng, const double *M,
+                           int nw, const double *omega, double *chi)
+{
+    if (!h) return GW_ERR_ARG;
+    if (nv < 1 || nc < 1 || ng < 1 || nw < 1 || nw > gw::kMaxOmega || !ev || !ec || !M || !omega || !chi)
+        return fail(h, GW_ERR_ARG, "bad arguments");
+    gw::OmegaList om;
+    om.nw = nw;
+    for (int i = 0; i < nw; ++i) {
+        if (!(omega[i] >= 0.0) || !std::isfinite(omega[i])) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
+        om.w[i] = omega[i];
+    }
+    if (h->d.prec != GW_PREC_FP64) return fail(h, GW_ERR_UNSUPPORTED, "precision mode not built yet");
+    const int64_t P = (int64_t)nv * nc;
+    gw_status s = ensure_work(h, 0, (size_t)P * nw);
+    if (s) return s;
+    CK(h, cudaMemsetAsync(chi, 0, sizeof(double2) * (size_t)nw * ng * ng, h->st), "zero chi");
+    {
+        Scope sc(h, "delta");
+        CK(h, gw::launch_delta(ev, ec, nc, 0, P, om, h->dbuf, h->st), "delta");
+    }
+    s = contract_chunk(h, (const double2 *)M, P, ng, h->dbuf, P, nw, (double2 *)chi);
+    if (s) return s;
+    Scope sc(h, "symmetrize");
+    CK(h, gw::launch_symmetrize((double2 *)chi, ng, nw, h->st), "symmetrize");
+    return GW_OK;
+}
+
+gw_status gw_chi0_adjoint(gw_chi0 *h, int, double, const double *, double *, double *, double *, double *, double *)
+{
+    if (!h) return GW_ERR_ARG;
+    return fail(h, GW_ERR_UNSUPPORTED, "adjoint not built yet");
+}
+
+gw_status gw_chi0_sync(gw_chi0 *h)
+{
+    if (!h) return GW_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->st), "sync");
+    int st = 0;
+    CK(h, cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+    CK(h, cudaMemset(h->status, 0, sizeof(int)), "status reset");
+    if (st & gw::kStatusTimeout) return fail(h, GW_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    return GW_OK;
+}
+
+gw_status gw_chi0_set_timing(gw_chi0 *h, int enable)
+{
+    if (!h) return GW_ERR_ARG;
+    h->timing = enable != 0;
+    return GW_OK;
+}
+
+int gw_chi0_timing(gw_chi0 *h, int n, char (*names)[32], double *ms, int64_t *launches, int reset)
+{
+    if (!h) return 0;
+    drain_timing(h);
+    int i = 0;
+    for (auto &kv : h->acc) {
+        if (i < n) {
+            if (names) {
+                std::strncpy(names[i], kv.first.c_str(), 31);
+                names[i][31] = 0;
+            }
+            if (ms) ms[i] = kv.second.first;
+            if (launches) launches[i] = kv.second.second;
+        }
+        ++i;
+    }
+    if (reset) h->acc.clear();
+    return i;
+}
+
+size_t gw_chi0_device_bytes(const gw_chi0 *h) { return h ? h->bytes : 0; }
+
+} // extern "C"

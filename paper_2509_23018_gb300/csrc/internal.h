@@ -1,0 +1,51 @@
+// Internal launch interface between the host API and the kernel translation units.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "common.cuh"
+
+namespace gw {
+
+constexpr int kMaxOmega = 64;
+struct OmegaList {
+    int nw;
+    double w[kMaxOmega];
+};
+
+// ---- stage (a): band setup and pair elements (mtxel.cu)
+cudaError_t launch_scatter(const double2 *coeff, const int32_t *gofs, int nb, int ngpsi, int64_t nr, double2 *psi,
+                           cudaStream_t st);
+cudaError_t launch_band_fft(double2 *psi, int nb, const int n[3], const FftAxis ax[3], cudaStream_t st);
+
+struct PairPlan {
+    int n[3];
+    FftAxis ax[3];
+    int K2;              // number of needed frequencies along the last axis
+    const int *kz;       // device [K2]   needed last-axis frequencies (0..n2-1)
+    int ng;
+    const int32_t *gpack; // device [ng]   k0 | k1 << 8 | k2index << 16
+};
+// M[p - p0][g] for p in [p0, p0 + count); pair p = v * nc + c.
+cudaError_t launch_pair(const double2 *psiv, const double2 *psic, int nc, int64_t p0, int64_t count,
+                        const PairPlan &pp, double2 *M, cudaStream_t st);
+int pair_max_ng();
+
+// ---- energy factor, diagonal, symmetrisation (reduce.cu)
+// delta[w][p - p0] = 4x/(x^2 + w^2), x = ev[v] - ec[c]
+cudaError_t launch_delta(const double *ev, const double *ec, int nc, int64_t p0, int64_t count, const OmegaList &om,
+                         double *delta, cudaStream_t st);
+// diag[w][g] += sum_p delta[w][p] |M[p][g]|^2
+cudaError_t launch_diag(const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride, int nw,
+                        double *diag, int64_t diag_wstride, cudaStream_t st);
+// lower triangle <- conj(upper), Im diag <- 0, for nw consecutive ng x ng blocks
+cudaError_t launch_symmetrize(double2 *chi, int ng, int nw, cudaStream_t st);
+
+// ---- stage (b), FP64 tensor cores (contract_f64.cu)
+// chi[w][G][G'] += sum_p conj(M[p][G]) delta[w][p] M[p][G'] on upper-triangle tiles.
+cudaError_t launch_contract_f64(const CUtensorMap *tmap, const double *delta, int64_t dstride, int64_t P, int ng,
+                                int nw, double *chi, int ksplit, int *status, cudaStream_t st);
+int contract_f64_tile();
+int contract_f64_bk();
+
+} // namespace gw

@@ -1,0 +1,97 @@
+// Energy factor (a5), diagonal reduction and Hermitian symmetrisation (a7).
+#include "internal.h"
+
+namespace gw {
+
+// a5: Delta_vc(iw) = 2/(x - iw) + 2/(x + iw) = 4x / (x^2 + w^2),  x = E_v - E_c.
+__global__ void delta_kernel(const double *__restrict__ ev, const double *__restrict__ ec, int nc, int64_t p0,
+                             int64_t count, OmegaList om, double *__restrict__ delta)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int64_t p = p0 + i;
+    int v = (int)(p / nc), c = (int)(p - (int64_t)v * nc);
+    double x = ev[v] - ec[c];
+    for (int w = 0; w < om.nw; ++w) {
+        double ww = om.w[w];
+        delta[(int64_t)w * count + i] = 4.0 * x / fma(x, x, ww * ww);
+    }
+}
+
+cudaError_t launch_delta(const double *ev, const double *ec, int nc, int64_t p0, int64_t count, const OmegaList &om,
+                         double *delta, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    delta_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(ev, ec, nc, p0, count, om, delta);
+    return cudaGetLastError();
+}
+
+// a7: diag[w][g] += sum_p delta[w][p] |M[p][g]|^2.
+// A warp covers 8 consecutive columns (lane & 7) and 4 pair rows at a time (lane >> 3);
+// the four row-partial sums of a column are combined with warp shuffles, then one
+// lane per column adds the warp's result into diag.
+__global__ void diag_kernel(const double2 *__restrict__ M, int64_t P, int ng, const double *__restrict__ delta,
+                            int64_t dstride, double *__restrict__ diag, int64_t diag_wstride)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int g = blockIdx.x * 8 + (lane & 7);
+    const int w = blockIdx.z;
+    const double *dl = delta + (int64_t)w * dstride;
+    double acc = 0.0;
+    if (g < ng) {
+        for (int64_t p = ((int64_t)blockIdx.y * nwarp + wid) * 4 + (lane >> 3); p < P;
+             p += (int64_t)gridDim.y * nwarp * 4) {
+            double2 m = M[p * ng + g];
+            acc = fma(dl[p], fma(m.x, m.x, m.y * m.y), acc);
+        }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (lane < 8 && g < ng) atomicAdd(diag + (int64_t)w * diag_wstride + g, acc);
+}
+
+cudaError_t launch_diag(const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride, int nw,
+                        double *diag, int64_t diag_wstride, cudaStream_t st)
+{
+    if (P == 0 || nw == 0) return cudaSuccess;
+    int gx = (ng + 7) / 8;
+    int64_t rows = (P + 31) / 32;
+    int gy = (int)(rows < 64 ? rows : 64);
+    diag_kernel<<<dim3(gx, gy, nw), 256, 0, st>>>(M, P, ng, delta, dstride, diag, diag_wstride);
+    return cudaGetLastError();
+}
+
+// a7: chi[G][G'] = conj(chi[G'][G]) for G > G'; Im chi[G][G] = 0.  32 x 32 tiles through
+// shared memory so both the read of the upper tile and the write of the lower tile
+// are row-contiguous.
+__global__ void symmetrize_kernel(double2 *__restrict__ chi, int ng, int nt)
+{
+    __shared__ double2 t[32][33];
+    int b = blockIdx.x, bi = 0;
+    while (b > bi) { b -= bi + 1; ++bi; } // lower-triangle tile (bi, bj), bj <= bi
+    const int bj = b;
+    double2 *c = chi + (int64_t)blockIdx.z * ng * ng;
+    // read upper tile (bj, bi): rows G' in block bj, columns G in block bi
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int Gp = bj * 32 + r, G = bi * 32 + threadIdx.x;
+        if (Gp < ng && G < ng) t[r][threadIdx.x] = c[(int64_t)Gp * ng + G];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int G = bi * 32 + r, Gp = bj * 32 + threadIdx.x;
+        if (G >= ng || Gp >= ng || Gp > G) continue;
+        double2 u = t[threadIdx.x][r]; // chi[Gp][G]
+        if (Gp == G) c[(int64_t)G * ng + G] = make_double2(u.x, 0.0);
+        else c[(int64_t)G * ng + Gp] = make_double2(u.x, -u.y);
+    }
+}
+
+cudaError_t launch_symmetrize(double2 *chi, int ng, int nw, cudaStream_t st)
+{
+    if (ng == 0 || nw == 0) return cudaSuccess;
+    int nt = (ng + 31) / 32;
+    symmetrize_kernel<<<dim3(nt * (nt + 1) / 2, 1, nw), dim3(32, 8), 0, st>>>(chi, ng, nt);
+    return cudaGetLastError();
+}
+
+} // namespace gw
