@@ -115,6 +115,8 @@ CONFIGS = {
     "c3_72cube": Config("c3_72cube", (72, 72, 72), 256, 2048, 20000, 6000, index=2),
     "c4_batch": Config("c4_batch", (40, 40, 40), 64, 512, 8000, 3000, nw=16, nq=64, index=3),
     "c5_adjoint": Config("c5_adjoint", (40, 40, 40), 96, 768, 4500, 1500, index=4),
+    # one 8192-pair chunk of the 48^3 workload: the small case kernel profiles are taken on
+    "p1_48cube_onechunk": Config("p1_48cube_onechunk", (48, 48, 48), 8, 1024, 6000, 2000, index=1),
 }
 
 

@@ -446,14 +446,27 @@ gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngpsi, con
                 return fail(h, GW_ERR_ARG, "a valence energy is not below every conduction energy");
     }
     BandSet &dst = kind == 0 ? h->val[iq] : h->cond;
-    free_bands(h, dst);
-    gw_status s;
-    if ((s = dalloc(h, (void **)&nbs.psi, sizeof(double2) * (size_t)nb * h->nr, "psi grids")) ||
-        (s = dalloc(h, (void **)&nbs.energy, sizeof(double) * nb, "energies")) ||
-        (s = dalloc(h, (void **)&nbs.gvec, sizeof(int32_t) * 3 * ngpsi, "gvec")) ||
-        (s = dalloc(h, (void **)&nbs.gofs, sizeof(int32_t) * ngpsi, "grid offsets"))) {
-        free_bands(h, nbs);
-        return s;
+    if (dst.nb == nb && dst.ngpsi == ngpsi) {
+        // same shape: reuse the device buffers (no allocation on repeated setup)
+        nbs.psi = dst.psi;
+        nbs.energy = dst.energy;
+        nbs.gvec = dst.gvec;
+        nbs.gofs = dst.gofs;
+        dst.psi = nullptr;
+        dst.energy = nullptr;
+        dst.gvec = nullptr;
+        dst.gofs = nullptr;
+        dst = BandSet();
+    } else {
+        free_bands(h, dst);
+        gw_status s;
+        if ((s = dalloc(h, (void **)&nbs.psi, sizeof(double2) * (size_t)nb * h->nr, "psi grids")) ||
+            (s = dalloc(h, (void **)&nbs.energy, sizeof(double) * nb, "energies")) ||
+            (s = dalloc(h, (void **)&nbs.gvec, sizeof(int32_t) * 3 * ngpsi, "gvec")) ||
+            (s = dalloc(h, (void **)&nbs.gofs, sizeof(int32_t) * ngpsi, "grid offsets"))) {
+            free_bands(h, nbs);
+            return s;
+        }
     }
     CK(h, cudaMemcpyAsync(nbs.energy, energy, sizeof(double) * nb, cudaMemcpyDeviceToDevice, h->st), "energies");
     CK(h, cudaMemcpyAsync(nbs.gvec, gvec, sizeof(int32_t) * 3 * ngpsi, cudaMemcpyDeviceToDevice, h->st), "gvec");
@@ -465,7 +478,7 @@ gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngpsi, con
     }
     {
         Scope sc(h, "band_fft");
-        CK(h, gw::launch_band_fft(nbs.psi, nb, h->d.n, h->ax, h->st), "band fft");
+        CK(h, gw::launch_band_fft(nbs.psi, nb, h->d.n, h->ax, h->st), "band fft"); // two kernels
     }
     CK(h, cudaStreamSynchronize(h->st), "set_bands sync"); // gofs host vector goes out of scope
     dst = std::move(nbs);
@@ -510,7 +523,16 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
         return fail(h, GW_ERR_ARG, "max|K_v| + max|K_c| + max|G| >= n on axis %d (aliasing)", ax);
     s.K2 = (int)kz.size();
     gw_status st;
-    if ((st = dalloc(h, (void **)&s.kz, sizeof(int) * s.K2, "sphere kz")) ||
+    Sphere &old = h->sph[iq];
+    if (old.ng == ng && old.K2 == s.K2) {
+        s.kz = old.kz;
+        s.gpack = old.gpack;
+        s.gvec = old.gvec;
+        old.kz = nullptr;
+        old.gpack = nullptr;
+        old.gvec = nullptr;
+        old = Sphere();
+    } else if ((st = dalloc(h, (void **)&s.kz, sizeof(int) * s.K2, "sphere kz")) ||
         (st = dalloc(h, (void **)&s.gpack, sizeof(int32_t) * ng, "sphere pack")) ||
         (st = dalloc(h, (void **)&s.gvec, sizeof(int32_t) * 3 * ng, "sphere gvec"))) {
         free_sphere(h, s);

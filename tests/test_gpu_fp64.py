@@ -131,7 +131,7 @@ def test_errors_are_reported(gw):
     assert e.value.status == 1
     h.set_bands(0, 0, g, dev(p.cv), dev(p.ev))
     # |K| <= 5 bands with a |G| <= 2 sphere alias on a 12-grid: 5 + 5 + 2 >= 12
-    wide = gwgen.make_problem((12, 12, 12), 2, 3, 500, 27, seed=9)
+    wide = gwgen.make_problem((12, 12, 12), 2, 3, 500, 18, seed=9)  # |G| <= 1
     h2 = handle(gw, wide)
     with pytest.raises(gw.GwError) as e:
         h2.set_gsphere(0, dev(gwgen.gsphere(57)))
