@@ -61,6 +61,13 @@ struct gw_chi0 {
     size_t Mcap = 0; // elements
     double *dbuf = nullptr;
     size_t dcap = 0;
+    // split-precision work buffers
+    void *Zbuf = nullptr;      // bf16 slices [s][2 ng][kpad]
+    size_t Zcap = 0;           // bytes
+    double *spbuf = nullptr;   // sqrt(-Delta) [nw][chunk]
+    size_t spcap = 0;
+    int *Ebuf = nullptr;       // column exponents [ng]
+    size_t Ecap = 0;
     int *status = nullptr;
     size_t bytes = 0;
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -233,9 +240,69 @@ int pick_ksplit(int ng, int64_t P, int nw)
     return (int)ks;
 }
 
+gw_status grow(gw_chi0 *h, void **p, size_t *cap, size_t bytes, const char *what)
+{
+    if (bytes <= *cap) return GW_OK;
+    dfree(h, *p, *cap);
+    *p = nullptr;
+    *cap = 0;
+    gw_status s = dalloc(h, p, bytes, what);
+    if (s) return s;
+    *cap = bytes;
+    return GW_OK;
+}
+
+gw_status make_tmap_z(gw_chi0 *h, CUtensorMap *map, void *Z, int64_t kpad, int nrows, int s, int box_rows)
+{
+    cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)nrows, (cuuint64_t)s};
+    cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)kpad * 2 * nrows};
+    cuuint32_t box[3] = {(cuuint32_t)gw::oz_box_k(), (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = h->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Z, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, GW_ERR_CUDA, "cuTensorMapEncodeTiled (slices) failed (%d)", (int)r);
+    return GW_OK;
+}
+
+// Split-precision contraction of one chunk for each frequency (chi blocks [nw][ng][ng]).
+gw_status contract_chunk_ozaki(gw_chi0 *h, const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride,
+                               int nw, double2 *chi)
+{
+    const int s = h->d.nslices;
+    const int64_t kpad = (P + 63) / 64 * 64;
+    gw_status st;
+    if ((st = grow(h, &h->Zbuf, &h->Zcap, (size_t)s * 2 * ng * kpad * 2, "slice buffer")) ||
+        (st = grow(h, (void **)&h->spbuf, &h->spcap, sizeof(double) * (size_t)nw * dstride, "scale buffer")) ||
+        (st = grow(h, (void **)&h->Ebuf, &h->Ecap, sizeof(int) * (size_t)ng, "exponent buffer")))
+        return st;
+    {
+        Scope sc(h, "oz_split");
+        CK(h, gw::launch_oz_sqrt(delta, (int64_t)nw * dstride, h->spbuf, h->st), "oz sqrt");
+    }
+    CUtensorMap ta, tb;
+    if ((st = make_tmap_z(h, &ta, h->Zbuf, kpad, 2 * ng, s, gw::oz_box_rows_a())) ||
+        (st = make_tmap_z(h, &tb, h->Zbuf, kpad, 2 * ng, s, gw::oz_box_rows_b())))
+        return st;
+    for (int w = 0; w < nw; ++w) {
+        const double *sp = h->spbuf + (int64_t)w * dstride;
+        {
+            Scope sc(h, "oz_split");
+            CK(h, gw::launch_oz_colexp(M, P, ng, sp, h->Ebuf, h->st), "oz exponents");
+            CK(h, gw::launch_oz_slice(M, P, ng, sp, h->Ebuf, s, kpad, h->Zbuf, h->st), "oz slices");
+        }
+        Scope sc(h, "ozaki_gemm");
+        CK(h, gw::launch_oz_gemm(&ta, &tb, ng, kpad, s, h->Ebuf, (double *)(chi + (int64_t)w * ng * ng), h->status,
+                                 h->st),
+           "oz gemm");
+    }
+    return GW_OK;
+}
+
 gw_status contract_chunk(gw_chi0 *h, const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride,
                          int nw, double2 *chi)
 {
+    if (h->d.prec == GW_PREC_OZAKI_BF16) return contract_chunk_ozaki(h, M, P, ng, delta, dstride, nw, chi);
     CUtensorMap map;
     gw_status s = make_tmap(h, &map, M, P, ng);
     if (s) return s;
@@ -381,6 +448,9 @@ void gw_chi0_destroy(gw_chi0 *h)
     for (auto &s : h->sph) free_sphere(h, s);
     dfree(h, h->Mbuf, h->Mcap * sizeof(double2));
     dfree(h, h->dbuf, h->dcap * sizeof(double));
+    dfree(h, h->Zbuf, h->Zcap);
+    dfree(h, h->spbuf, h->spcap);
+    dfree(h, h->Ebuf, h->Ecap);
     dfree(h, h->tw, 0);
     dfree(h, h->status, 0);
     for (auto &r : h->pending) {
@@ -580,7 +650,6 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
         gw_status s = check_slot(h, iq[i]);
         if (s) return s;
     }
-    if (h->d.prec != GW_PREC_FP64) return fail(h, GW_ERR_UNSUPPORTED, "precision mode not built yet");
     size_t off = 0, doff = 0;
     for (int i = 0; i < nq; ++i) {
         const Sphere &sp = h->sph[iq[i]];
@@ -634,17 +703,28 @@ gw_status gw_chi0_contract(gw_chi0 *h, int nv, int nc, const double *ev, const d
         if (!(omega[i] >= 0.0) || !std::isfinite(omega[i])) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
         om.w[i] = omega[i];
     }
-    if (h->d.prec != GW_PREC_FP64) return fail(h, GW_ERR_UNSUPPORTED, "precision mode not built yet");
     const int64_t P = (int64_t)nv * nc;
-    gw_status s = ensure_work(h, 0, (size_t)P * nw);
+    {
+        std::vector<double> hv(nv), hc(nc);
+        CK(h, cudaMemcpyAsync(hv.data(), ev, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->st), "copy ev");
+        CK(h, cudaMemcpyAsync(hc.data(), ec, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->st), "copy ec");
+        CK(h, cudaStreamSynchronize(h->st), "contract sync");
+        if (!(*std::max_element(hv.begin(), hv.end()) < *std::min_element(hc.begin(), hc.end())))
+            return fail(h, GW_ERR_ARG, "a valence energy is not below every conduction energy");
+    }
+    const int64_t chunk = std::min<int64_t>(h->d.pair_chunk, P);
+    gw_status s = ensure_work(h, 0, (size_t)chunk * nw);
     if (s) return s;
     CK(h, cudaMemsetAsync(chi, 0, sizeof(double2) * (size_t)nw * ng * ng, h->st), "zero chi");
-    {
-        Scope sc(h, "delta");
-        CK(h, gw::launch_delta(ev, ec, nc, 0, P, om, h->dbuf, h->st), "delta");
+    for (int64_t p0 = 0; p0 < P; p0 += chunk) {
+        const int64_t cnt = std::min(chunk, P - p0);
+        {
+            Scope sc(h, "delta");
+            CK(h, gw::launch_delta(ev, ec, nc, p0, cnt, om, h->dbuf, h->st), "delta");
+        }
+        s = contract_chunk(h, (const double2 *)M + p0 * ng, cnt, ng, h->dbuf, cnt, nw, (double2 *)chi);
+        if (s) return s;
     }
-    s = contract_chunk(h, (const double2 *)M, P, ng, h->dbuf, P, nw, (double2 *)chi);
-    if (s) return s;
     Scope sc(h, "symmetrize");
     CK(h, gw::launch_symmetrize((double2 *)chi, ng, nw, h->st), "symmetrize");
     return GW_OK;

@@ -48,4 +48,20 @@ cudaError_t launch_contract_f64(const CUtensorMap *tmap, const double *delta, in
 int contract_f64_tile();
 int contract_f64_bk();
 
+// ---- stage (b), split precision on BF16 tensor cores (ozaki.cu)
+// sp[i] = sqrt(-delta[i])
+cudaError_t launch_oz_sqrt(const double *delta, int64_t n, double *sp, cudaStream_t st);
+// E[g] = column exponent of s_p M[p][g] over the chunk
+cudaError_t launch_oz_colexp(const double2 *M, int64_t P, int ng, const double *sp, int *E, cudaStream_t st);
+// Z[i][j][p] bf16 slices, rows p in [P, kpad) zero
+cudaError_t launch_oz_slice(const double2 *M, int64_t P, int ng, const double *sp, const int *E, int s,
+                            int64_t kpad, void *Z, cudaStream_t st);
+// chi[G][G'] (upper triangle) += recombined slice products of the chunk
+cudaError_t launch_oz_gemm(const CUtensorMap *tmA, const CUtensorMap *tmB, int ng, int64_t kpad, int s, const int *E,
+                           double *chi, int *status, cudaStream_t st);
+int oz_box_rows_a();
+int oz_box_rows_b();
+int oz_box_k();
+int oz_tiles(int ng);
+
 } // namespace gw

@@ -1,0 +1,94 @@
+"""Split-precision (Ozaki, BF16 tensor cores) contraction against the CPU oracle.
+
+Bar for the split path: relative Frobenius error <= 1e-9 at the default slice count,
+error 0 when every input is a small integer that one slice holds exactly, and an
+error that falls as slices are added.
+"""
+import numpy as np
+import pytest
+
+import gwgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_SPLIT = 1e-9
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def gw():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import paper_2509_23018_gb300 as gw
+    return gw
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+
+
+@pytest.fixture(scope="module")
+def c1():
+    cfg = gwgen.CONFIGS["c1_24cube"]
+    p = gwgen.config_problem(cfg)
+    M = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)
+    return p, M
+
+
+@pytest.mark.parametrize("ng,nv,nc", [(40, 3, 37), (200, 16, 64), (129, 5, 77)])
+def test_small_integers_exact(gw, ng, nv, nc):
+    """Integer M and Delta = -1 (x = -4 at w = 0): the split is exact, so is the result."""
+    rng = np.random.default_rng(ng)
+    M = rng.integers(-3, 4, (nv * nc, ng)) + 1j * rng.integers(-3, 4, (nv * nc, ng))
+    ev, ec = np.full(nv, -2.0), np.full(nc, 2.0)
+    want = -(np.conj(M).T @ M)  # exact in float64 (small integers)
+    h = gw.Chi0((8, 8, 8), prec="ozaki", nslices=4)
+    chi = h.contract(dev(ev), dev(ec), dev(M), [0.0]).cpu().numpy()[0]
+    h.sync()
+    assert np.array_equal(chi, want)
+
+
+def test_split_c1_matches_oracle(gw, c1):
+    p, M = c1
+    errs = {}
+    for s in (3, 4, 5, 6, 7, 8):
+        h = gw.Chi0(p.grid, prec="ozaki", nslices=s)
+        chi = h.contract(dev(p.ev), dev(p.ec), dev(M), [0.0, 5.0]).cpu().numpy()
+        h.sync()
+        e = []
+        for i, w in enumerate([0.0, 5.0]):
+            ref = oracle.chi0(M, oracle.delta(p.ev, p.ec, w))
+            e.append(rel(chi[i], ref))
+            assert np.array_equal(chi[i], chi[i].conj().T)
+        errs[s] = max(e)
+    print("split error per slice count:", errs)
+    assert errs[6] <= TOL_SPLIT
+    for s in (3, 4, 5, 6):
+        assert errs[s + 1] <= errs[s] * 1.01 or errs[s + 1] < 1e-14
+
+
+@pytest.mark.parametrize("chunk", [8192, 100])
+def test_split_full_path_c1(gw, c1, chunk):
+    p, M = c1
+    h = gw.from_problem(p, prec="ozaki", nslices=6, pair_chunk=chunk)
+    (chi,) = h.compute(0, [0.0, 2.0])
+    chi = chi.cpu().numpy()
+    h.sync()
+    for i, w in enumerate([0.0, 2.0]):
+        assert rel(chi[i], oracle.chi0(M, oracle.delta(p.ev, p.ec, w))) <= TOL_SPLIT
+
+
+@pytest.mark.parametrize("ng", [1, 7, 64, 65, 129, 300])
+def test_split_ragged(gw, ng):
+    p = gwgen.make_problem((16, 15, 18), 3, 9, 150, ng, seed=5)
+    h = gw.from_problem(p, prec="ozaki", nslices=6, pair_chunk=10)
+    (chi,) = h.compute(0, [0.0])
+    chi = chi.cpu().numpy()[0]
+    h.sync()
+    Mo = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)
+    assert rel(chi, oracle.chi0(Mo, oracle.delta(p.ev, p.ec, 0.0))) <= TOL_SPLIT
