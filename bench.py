@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--config", default="c2_48cube", choices=sorted(gwgen.CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample-pairs", type=int, default=256)
+    ap.add_argument("--cpu-sample-pairs", type=int, default=4096)
+    ap.add_argument("--no-check", action="store_true", help="skip the sampled error check against the oracle")
     return ap.parse_args()
 
 
@@ -152,6 +153,25 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------- our arm
+# DRAM bytes per launch of the dominant kernel, from one ncu capture of an identical launch
+# (8192 pairs, N_G = 2000); set to None whenever that kernel changes.
+TRAFFIC = {
+    "contract_f64": {"bytes_per_launch": 1.941011e9 + 0.034306e9,
+                     "source": "ncu dram__bytes_read+write, contract_f64_kernel, p1_48cube_onechunk"},
+}
+
+
+def sampled_error(cfg, prob, chi, nsample=12, seed=3):
+    """Relative Frobenius error of a sampled nsample x nsample block of chi against the oracle."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(cfg.ng, nsample, replace=False))
+    M = oracle.m_conv(prob.gpsi, prob.cv, prob.gpsi, prob.cc, prob.gchi[idx])
+    ref = oracle.chi0(M, oracle.delta(prob.ev, prob.ec, 0.0))
+    got = chi[np.ix_(idx, idx)]
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), f"{nsample}x{nsample} sampled entries, all pairs"
+
+
 def peak_for(prec):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     pk = json.load(open(path)) if os.path.exists(path) else {}
@@ -230,6 +250,9 @@ def ours(args):
     kms, kn = tim.get(kname, (0.0, 0))
     nchunk = -(-cfg.npairs // cfg.pair_chunk)
     per_launch_flops = 4.0 * cfg.ng * (cfg.ng + 1) * cfg.npairs / nchunk
+    if args.prec == "ozaki":
+        # low-precision flops of the kept slice pairs: s(s+1)/2 x 4 N_G^2 P per chunk and frequency
+        per_launch_flops = args.nslices * (args.nslices + 1) / 2 * 4.0 * cfg.ng ** 2 * cfg.npairs / nchunk
     peak, peak_src = peak_for(args.prec)
     achieved = per_launch_flops / (kms / kn * 1e-3) * 1e-12 if kn else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -237,7 +260,9 @@ def ours(args):
                 "launches": kn, "ms_per_launch": kms / kn if kn else None,
                 "flops_per_launch": per_launch_flops, "peak_source": peak_src,
                 "share_of_step": kms / ms if ms else None,
-                "fp64_probe_peaks_tflops": {"dmma": 1.055, "dfma": 1.204}}
+                "fp64_probe_peaks_tflops": {"dmma": 1.055, "dfma": 1.204},
+                "traffic_source": TRAFFIC.get(kname, {}).get("source")}
+    roofline["traffic"] = TRAFFIC.get(kname, {}).get("bytes_per_launch")
 
     # end to end through the public API with host buffers (pinned), H2D inputs + D2H result
     e2e = None
@@ -274,6 +299,10 @@ def ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hout.numel() * hout.element_size()),
                "ms_per_step": 1e3 * es / args.steps}
 
+    err = None
+    if rank == 0 and not args.no_check:
+        e, how = sampled_error(cfg, prob, chi.view(cfg.ng, cfg.ng).cpu().numpy())
+        err = {"rel_frobenius_vs_oracle": e, "sample": how}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, prob, args.cpu_sample_pairs)
@@ -289,7 +318,7 @@ def ours(args):
                            "pairs": cfg.npairs, "conv_tflop_per_step": conv_flops(cfg) * 1e-12,
                            "l2": "inputs larger than L2 (psi grids 2.0 GB, M chunks 262 MB)",
                            "parallelism": f"replicas x{world} (independent q-points)"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "error": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "kernel_ms": {k: v[0] for k, v in tim.items()}, "clocks": clocks}
         print(json.dumps(line), flush=True)
     h.destroy()
