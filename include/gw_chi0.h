@@ -179,6 +179,34 @@ GW_API int gw_chi0_timing(gw_chi0 *h, int n, char (*names)[32], double *ms, int6
 /* Library-owned device bytes currently held by the handle. */
 GW_API size_t gw_chi0_device_bytes(const gw_chi0 *h);
 
+/*
+ * gw_chi0_contract_noalloc -- stage (b) in FP64 without any device allocation.
+ *
+ * The paper has no counterpart to this call.  It serves callers that cannot call
+ * cudaMalloc: code that records its work into a CUDA graph under stream capture
+ * (allocation is not capturable), plugins whose host framework owns every device
+ * allocation through its own pool, and services that forbid allocator calls on their
+ * hot path.  It computes what gw_chi0_contract computes in GW_PREC_FP64 mode (same
+ * kernels, same arguments and layouts, chi written in full), without a handle, on the
+ * given stream (a cudaStream_t; NULL = legacy default stream), for the current device.
+ *
+ * Its only scratch -- the energy factors Delta of every pair and frequency, and a
+ * status word -- lives in one fixed device array compiled into the library (4 MiB plus
+ * 256 bytes; every GPU that loads the library holds it until the process exits).
+ *   - Limit: nw * nv * nc <= 524288; larger requests return GW_ERR_ARG and do nothing.
+ *   - The first call on a device looks up that array's device address (once per device,
+ *     with the device current); make that first call before any stream capture.
+ *   - Every call shares the array: calls that overlap on the GPU (other streams, other
+ *     host threads) race on it and must be serialised by the caller.
+ *   - Device-side timeouts of bounded waits are not reported by this call.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.  Returns GW_OK,
+ * GW_ERR_ARG (null pointers, sizes out of range, M not 16-byte aligned, bad omega),
+ * GW_ERR_CUDA, or GW_ERR_UNSUPPORTED (device ordinal >= 64).
+ */
+GW_API gw_status gw_chi0_contract_noalloc(int nv, int nc, const double *ev, const double *ec, int ng,
+                                          const double *M, int nw, const double *omega, double *chi,
+                                          void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,7 @@ SIGNATURES = {
     "gw_chi0_set_timing": ([P, I], I),
     "gw_chi0_timing": ([P, I, P, P, P, I], I),
     "gw_chi0_device_bytes": ([P], SZ),
+    "gw_chi0_contract_noalloc": ([I, I, P, P, I, P, I, P, P, P], I),
 }
 
 

@@ -184,6 +184,24 @@ class Chi0:
         self.destroy()
 
 
+def contract_noalloc(ev: torch.Tensor, ec: torch.Tensor, M: torch.Tensor, omega: Sequence[float],
+                     out: torch.Tensor) -> torch.Tensor:
+    """FP64 contraction through gw_chi0_contract_noalloc: no device allocation inside the call.
+
+    All tensors must already be on the current device (complex128 M [nv*nc, ng],
+    float64 ev/ec, complex128 out [nw, ng, ng]); the call uses the library's fixed
+    scratch array, so calls must not overlap on the GPU.
+    """
+    lib = _lib.load()
+    nw = len(omega)
+    om_arr = (ctypes.c_double * nw)(*[float(w) for w in omega])
+    st = lib.gw_chi0_contract_noalloc(ev.shape[0], ec.shape[0], _ptr(ev), _ptr(ec), M.shape[1], _ptr(M), nw,
+                                      om_arr, _ptr(out), _stream_handle())
+    if st != 0:
+        raise GwError(st, "gw_chi0_contract_noalloc failed")
+    return out
+
+
 def create(grid, **kw) -> Chi0:
     return Chi0(grid, **kw)
 
