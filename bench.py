@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "ozaki"])
     ap.add_argument("--nslices", type=int, default=6)
+    ap.add_argument("--mtxel", default=None, choices=["fp64", "twofloat"],
+                    help="stage (a) arithmetic; default fp64 with --prec fp64, twofloat with --prec ozaki")
     ap.add_argument("--config", default="c2_48cube", choices=sorted(gwgen.CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -203,7 +205,8 @@ def ours(args):
     ev, ec = torch.as_tensor(prob.ev, device=dev), torch.as_tensor(prob.ec, device=dev)
     gchi = torch.as_tensor(prob.gchi, device=dev)
     omega = [0.0]
-    h = gw.Chi0(cfg.grid, nq=1, prec=args.prec, nslices=args.nslices, pair_chunk=cfg.pair_chunk)
+    mtxel = args.mtxel or ("fp64" if args.prec == "fp64" else "twofloat")
+    h = gw.Chi0(cfg.grid, nq=1, prec=args.prec, nslices=args.nslices, pair_chunk=cfg.pair_chunk, mtxel=mtxel)
     chi = torch.empty(cfg.ng * cfg.ng, dtype=torch.complex128, device=dev)
     h.ng[0] = cfg.ng
 
@@ -315,6 +318,7 @@ def ours(args):
                 "config": {"workload": f"{cfg.name}: grid {cfg.grid[0]}^3, {cfg.nv}+{cfg.nc} bands, "
                                        f"N_Gpsi={cfg.ngpsi}, N_G={cfg.ng}, chunks of {cfg.pair_chunk} pairs, omega=0",
                            "prec": args.prec, "nslices": args.nslices if args.prec == "ozaki" else None,
+                           "mtxel": mtxel,
                            "pairs": cfg.npairs, "conv_tflop_per_step": conv_flops(cfg) * 1e-12,
                            "l2": "inputs larger than L2 (psi grids 2.0 GB, M chunks 262 MB)",
                            "parallelism": f"replicas x{world} (independent q-points)"},

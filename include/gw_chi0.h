@@ -67,6 +67,11 @@ typedef enum {
     GW_PREC_OZAKI_BF16 = 1 /* FP64 FFT + split-precision contraction on BF16 tensor cores */
 } gw_prec;
 
+typedef enum {
+    GW_MTXEL_FP64 = 0,     /* stage (a) transforms in FP64 */
+    GW_MTXEL_TWOFLOAT = 1  /* stage (a) pair transforms in two-float (FP32 pair, ~48-bit) arithmetic */
+} gw_mtxel_prec;
+
 typedef struct {
     int n[3];                /* FFT grid n0 x n1 x n2 (each a product of 2, 3, 5; 4 <= n <= 128) */
     int nq;                  /* number of q-point slots (>= 1) */
@@ -75,11 +80,12 @@ typedef struct {
     int64_t pair_chunk;      /* pairs per M chunk; 0 = 8192 */
     size_t mem_budget_bytes; /* cap on library-owned device memory; 0 = no cap */
     int device;              /* CUDA device ordinal; must be current on the calling thread */
+    int mtxel_prec;          /* gw_mtxel_prec */
 } gw_chi0_desc;
 
 /*
  * Create a handle.  stream: a cudaStream_t (may be NULL for the legacy default stream).
- * Errors: GW_ERR_ARG (bad grid, nq < 1, prec/nslices out of range), GW_ERR_CUDA.
+ * Errors: GW_ERR_ARG (bad grid, nq < 1, prec/nslices/mtxel_prec out of range), GW_ERR_CUDA.
  */
 GW_API gw_status gw_chi0_create(gw_chi0 **h, const gw_chi0_desc *d, void *cuda_stream);
 

@@ -18,6 +18,7 @@ GW_OK, GW_ERR_ARG, GW_ERR_STATE, GW_ERR_OOM, GW_ERR_CUDA, GW_ERR_UNSUPPORTED, GW
 STATUS_NAMES = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_STATE", 3: "GW_ERR_OOM", 4: "GW_ERR_CUDA",
                 5: "GW_ERR_UNSUPPORTED", 6: "GW_ERR_TIMEOUT"}
 GW_PREC_FP64, GW_PREC_OZAKI_BF16 = 0, 1
+GW_MTXEL_FP64, GW_MTXEL_TWOFLOAT = 0, 1
 
 # Every entry point declared in include/gw_chi0.h, with its ctypes signature.
 P, I, I64, D, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
@@ -25,7 +26,7 @@ P, I, I64, D, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_doubl
 
 class Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("nq", I), ("prec", I), ("nslices", I), ("pair_chunk", I64),
-                ("mem_budget_bytes", SZ), ("device", I)]
+                ("mem_budget_bytes", SZ), ("device", I), ("mtxel_prec", I)]
 
 
 SIGNATURES = {

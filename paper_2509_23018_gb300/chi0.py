@@ -30,13 +30,15 @@ def _stream_handle():
 
 
 PREC = {"fp64": _lib.GW_PREC_FP64, "ozaki": _lib.GW_PREC_OZAKI_BF16, "ozaki_bf16": _lib.GW_PREC_OZAKI_BF16}
+MTXEL = {"fp64": _lib.GW_MTXEL_FP64, "twofloat": _lib.GW_MTXEL_TWOFLOAT}
 
 
 class Chi0:
     """One handle of the library (one device, one stream at a time)."""
 
     def __init__(self, grid: Sequence[int], nq: int = 1, prec: str = "fp64", nslices: int = 6,
-                 pair_chunk: int = 8192, mem_budget_bytes: int = 0, device: int | None = None):
+                 pair_chunk: int = 8192, mem_budget_bytes: int = 0, device: int | None = None,
+                 mtxel: str = "fp64"):
         self.lib = _lib.load()
         dev = torch.cuda.current_device() if device is None else device
         d = _lib.Desc()
@@ -44,6 +46,7 @@ class Chi0:
             d.n[a] = int(grid[a])
         d.nq, d.prec, d.nslices = int(nq), PREC[prec], int(nslices)
         d.pair_chunk, d.mem_budget_bytes, d.device = int(pair_chunk), int(mem_budget_bytes), int(dev)
+        d.mtxel_prec = MTXEL[mtxel]
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             st = self.lib.gw_chi0_create(ctypes.byref(h), ctypes.byref(d), _stream_handle())

@@ -54,6 +54,7 @@ struct gw_chi0 {
     int64_t nr = 0;
     FftAxis ax[3]{};
     double2 *tw = nullptr;
+    float4 *twf = nullptr;
     BandSet cond;
     std::vector<BandSet> val;
     std::vector<Sphere> sph;
@@ -340,6 +341,13 @@ gw_status check_slot(gw_chi0 *h, int iq)
     return GW_OK;
 }
 
+cudaError_t run_pair(gw_chi0 *h, const void *psiv, const void *psic, int nc, int64_t p0, int64_t cnt,
+                     const gw::PairPlan &pp, double2 *M)
+{
+    if (h->d.mtxel_prec == GW_MTXEL_TWOFLOAT) return gw::launch_pair_tf(psiv, psic, nc, p0, cnt, pp, M, h->st);
+    return gw::launch_pair((const double2 *)psiv, (const double2 *)psic, nc, p0, cnt, pp, M, h->st);
+}
+
 gw::PairPlan pair_plan(gw_chi0 *h, const Sphere &s)
 {
     gw::PairPlan pp;
@@ -388,6 +396,7 @@ gw_status gw_chi0_create(gw_chi0 **out, const gw_chi0_desc *d, void *stream)
     if (h->d.nq < 1) { delete h; return GW_ERR_ARG; }
     if (h->d.prec != GW_PREC_FP64 && h->d.prec != GW_PREC_OZAKI_BF16) { delete h; return GW_ERR_ARG; }
     if (h->d.prec == GW_PREC_OZAKI_BF16 && (h->d.nslices < 3 || h->d.nslices > 8)) { delete h; return GW_ERR_ARG; }
+    if (h->d.mtxel_prec != GW_MTXEL_FP64 && h->d.mtxel_prec != GW_MTXEL_TWOFLOAT) { delete h; return GW_ERR_ARG; }
     for (int a = 0; a < 3; ++a) {
         int n = h->d.n[a];
         if (n < 4 || n > 128 || !factor(n, h->ax[a])) { delete h; return GW_ERR_ARG; }
@@ -419,12 +428,19 @@ gw_status gw_chi0_create(gw_chi0 **out, const gw_chi0_desc *d, void *stream)
         }
         off += n;
     }
+    std::vector<float4> twf(ntot);
+    for (int t = 0; t < ntot; ++t) {
+        float rh = (float)tw[t].x, ih = (float)tw[t].y;
+        twf[t] = make_float4(rh, (float)(tw[t].x - (double)rh), ih, (float)(tw[t].y - (double)ih));
+    }
     if (dalloc(h, (void **)&h->tw, sizeof(double2) * ntot, "twiddles") ||
+        dalloc(h, (void **)&h->twf, sizeof(float4) * ntot, "twiddles (two-float)") ||
         dalloc(h, (void **)&h->status, sizeof(int), "status word")) {
         gw_chi0_destroy(h);
         return GW_ERR_OOM;
     }
     if (cudaMemcpy(h->tw, tw.data(), sizeof(double2) * ntot, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->twf, twf.data(), sizeof(float4) * ntot, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         gw_chi0_destroy(h);
@@ -433,6 +449,7 @@ gw_status gw_chi0_create(gw_chi0 **out, const gw_chi0_desc *d, void *stream)
     off = 0;
     for (int a = 0; a < 3; ++a) {
         h->ax[a].tw = h->tw + off;
+        h->ax[a].twf = h->twf + off;
         off += h->d.n[a];
     }
     *out = h;
@@ -451,8 +468,12 @@ void gw_chi0_destroy(gw_chi0 *h)
     dfree(h, h->Zbuf, h->Zcap);
     dfree(h, h->spbuf, h->spcap);
     dfree(h, h->Ebuf, h->Ecap);
-    dfree(h, h->tw, 0);
-    dfree(h, h->status, 0);
+    {
+        size_t ntw = (size_t)h->d.n[0] + h->d.n[1] + h->d.n[2];
+        dfree(h, h->tw, sizeof(double2) * ntw);
+        dfree(h, h->twf, sizeof(float4) * ntw);
+    }
+    dfree(h, h->status, sizeof(int));
     for (auto &r : h->pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -550,6 +571,10 @@ gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngpsi, con
         Scope sc(h, "band_fft");
         CK(h, gw::launch_band_fft(nbs.psi, nb, h->d.n, h->ax, h->st), "band fft"); // two kernels
     }
+    if (h->d.mtxel_prec == GW_MTXEL_TWOFLOAT) {
+        Scope sc(h, "band_to_twofloat");
+        CK(h, gw::launch_psi_to_tf(nbs.psi, (int64_t)nb * h->nr, h->st), "psi to two-float");
+    }
     CK(h, cudaStreamSynchronize(h->st), "set_bands sync"); // gofs host vector goes out of scope
     dst = std::move(nbs);
     return GW_OK;
@@ -629,8 +654,8 @@ gw_status gw_chi0_pair_elements(gw_chi0 *h, int iq, int64_t pair_begin, int64_t 
                     (long long)(pair_begin + pair_count), (long long)P);
     if (pair_count && !M) return fail(h, GW_ERR_ARG, "null M");
     Scope sc(h, "pair_mtxel");
-    CK(h, gw::launch_pair(v.psi, h->cond.psi, h->cond.nb, pair_begin, pair_count, pair_plan(h, h->sph[iq]),
-                          (double2 *)M, h->st),
+    CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, pair_begin, pair_count, pair_plan(h, h->sph[iq]),
+                   (double2 *)M),
        "pair kernel");
     return GW_OK;
 }
@@ -668,7 +693,7 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
             int64_t cnt = std::min(chunk, P - p0);
             {
                 Scope sc(h, "pair_mtxel");
-                CK(h, gw::launch_pair(v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf, h->st), "pair kernel");
+                CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
             }
             {
                 Scope sc(h, "delta");

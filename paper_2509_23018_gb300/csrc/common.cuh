@@ -31,7 +31,8 @@ struct FftAxis {
     int n;
     int nst;
     int rad[kMaxStages];
-    const double2 *tw; // device, n entries
+    const double2 *tw;  // device, n entries
+    const float4 *twf;  // device, n entries in two-float form (re.hi, re.lo, im.hi, im.lo)
 };
 
 // Device-side status word bits (written by bounded waits that gave up).

@@ -1,0 +1,229 @@
+// Two-float ("float-float") arithmetic and the matching FFT building blocks.
+//
+// A value is the unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2,
+// i.e. about 48 significand bits.  On this GPU the FP32 pipes are about 60x faster
+// than FP64, so transforms in two-float arithmetic run several times faster than in
+// FP64 while keeping a relative rounding level near 2^-46.  The error-free building
+// blocks are the classical ones: Knuth's two-sum, Dekker's fast two-sum (|a| >= |b|)
+// and the FMA-based exact product (the rounding error of a*b is fma(a, b, -a*b)).
+// Explicit __f*_rn intrinsics keep the compiler from contracting or reassociating
+// the compensation steps.
+#pragma once
+#include "common.cuh"
+
+namespace gw {
+
+struct tf {
+    float hi, lo;
+};
+struct tcx {
+    tf re, im;
+};
+
+__device__ __forceinline__ tf tf_fast2sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ tf tf_2sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ tf tf_add(tf x, tf y)
+{
+    tf s = tf_2sum(x.hi, y.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return tf_fast2sum(s.hi, e);
+}
+__device__ __forceinline__ tf tf_sub(tf x, tf y)
+{
+    tf s = tf_2sum(x.hi, -y.hi);
+    float e = __fadd_rn(s.lo, __fsub_rn(x.lo, y.lo));
+    return tf_fast2sum(s.hi, e);
+}
+__device__ __forceinline__ tf tf_neg(tf x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ tf tf_mul(tf x, tf y)
+{
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return tf_fast2sum(p, e);
+}
+// x*a + y*b with one final renormalisation
+__device__ __forceinline__ tf tf_dot2(tf x, tf a, tf y, tf b)
+{
+    float p1 = __fmul_rn(x.hi, a.hi), p2 = __fmul_rn(y.hi, b.hi);
+    float e = __fmaf_rn(x.hi, a.hi, -p1);
+    e = __fadd_rn(e, __fmaf_rn(y.hi, b.hi, -p2));
+    tf s = tf_2sum(p1, p2);
+    e = __fadd_rn(e, s.lo);
+    e = __fmaf_rn(x.hi, a.lo, e);
+    e = __fmaf_rn(x.lo, a.hi, e);
+    e = __fmaf_rn(y.hi, b.lo, e);
+    e = __fmaf_rn(y.lo, b.hi, e);
+    return tf_fast2sum(s.hi, e);
+}
+__device__ __forceinline__ tf tf_scale(tf x, float c) // c a power of two
+{
+    return {__fmul_rn(x.hi, c), __fmul_rn(x.lo, c)};
+}
+__device__ __forceinline__ double tf_to_d(tf x) { return (double)x.hi + (double)x.lo; }
+
+__device__ __forceinline__ tcx tc_add(tcx a, tcx b) { return {tf_add(a.re, b.re), tf_add(a.im, b.im)}; }
+__device__ __forceinline__ tcx tc_sub(tcx a, tcx b) { return {tf_sub(a.re, b.re), tf_sub(a.im, b.im)}; }
+__device__ __forceinline__ tcx tc_muli(tcx a) { return {tf_neg(a.im), a.re}; }
+// a * w
+__device__ __forceinline__ tcx tc_mul(tcx a, tcx w)
+{
+    return {tf_dot2(a.re, w.re, tf_neg(a.im), w.im), tf_dot2(a.re, w.im, a.im, w.re)};
+}
+// conj(a) * b
+__device__ __forceinline__ tcx tc_mulc(tcx a, tcx b)
+{
+    return {tf_dot2(a.re, b.re, a.im, b.im), tf_dot2(a.re, b.im, tf_neg(a.im), b.re)};
+}
+// real two-float constant times a complex value
+__device__ __forceinline__ tcx tc_rmul(tcx a, tf c) { return {tf_mul(a.re, c), tf_mul(a.im, c)}; }
+
+__device__ __forceinline__ tcx tc_load(const float4 *p)
+{
+    float4 v = *p;
+    return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ void tc_store(float4 *p, tcx a) { *p = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+
+// two-float butterfly constants (hi + lo of the FP64 values)
+struct TfConsts {
+    tf sin60, c1, s1, c2, s2, rs2;
+};
+__device__ __forceinline__ tf tf_from(double x)
+{
+    float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ void tdft2(tcx *v)
+{
+    tcx a = v[0], b = v[1];
+    v[0] = tc_add(a, b);
+    v[1] = tc_sub(a, b);
+}
+__device__ __forceinline__ void tdft4(tcx *v)
+{
+    tcx a = tc_add(v[0], v[2]), b = tc_sub(v[0], v[2]);
+    tcx c = tc_add(v[1], v[3]), d = tc_muli(tc_sub(v[1], v[3]));
+    v[0] = tc_add(a, c);
+    v[2] = tc_sub(a, c);
+    v[1] = tc_add(b, d);
+    v[3] = tc_sub(b, d);
+}
+__device__ __forceinline__ void tdft3(tcx *v, const TfConsts &k)
+{
+    tcx t = tc_add(v[1], v[2]);
+    tcx s = tc_sub(v[1], v[2]);
+    tcx y0 = tc_add(v[0], t);
+    tcx m = tc_sub(v[0], {tf_scale(t.re, 0.5f), tf_scale(t.im, 0.5f)});
+    tcx is = tc_muli(tc_rmul(s, k.sin60));
+    v[0] = y0;
+    v[1] = tc_add(m, is);
+    v[2] = tc_sub(m, is);
+}
+__device__ __forceinline__ void tdft5(tcx *v, const TfConsts &k)
+{
+    tcx t1 = tc_add(v[1], v[4]), t2 = tc_add(v[2], v[3]);
+    tcx t3 = tc_sub(v[1], v[4]), t4 = tc_sub(v[2], v[3]);
+    tcx y0 = tc_add(v[0], tc_add(t1, t2));
+    tcx a1 = tc_add(v[0], tc_add(tc_rmul(t1, k.c1), tc_rmul(t2, k.c2)));
+    tcx a2 = tc_add(v[0], tc_add(tc_rmul(t1, k.c2), tc_rmul(t2, k.c1)));
+    tcx b1 = tc_muli(tc_add(tc_rmul(t3, k.s1), tc_rmul(t4, k.s2)));
+    tcx b2 = tc_muli(tc_sub(tc_rmul(t3, k.s2), tc_rmul(t4, k.s1)));
+    v[0] = y0;
+    v[1] = tc_add(a1, b1);
+    v[4] = tc_sub(a1, b1);
+    v[2] = tc_add(a2, b2);
+    v[3] = tc_sub(a2, b2);
+}
+__device__ __forceinline__ void tdft8(tcx *v, const TfConsts &k)
+{
+    tcx e[4] = {v[0], v[2], v[4], v[6]};
+    tcx o[4] = {v[1], v[3], v[5], v[7]};
+    tdft4(e);
+    tdft4(o);
+    // o[k] *= e^{+i pi k/4}
+    o[1] = tc_rmul({tf_sub(o[1].re, o[1].im), tf_add(o[1].re, o[1].im)}, k.rs2);
+    o[2] = tc_muli(o[2]);
+    o[3] = tc_rmul({tf_neg(tf_add(o[3].re, o[3].im)), tf_sub(o[3].re, o[3].im)}, k.rs2);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[j] = tc_add(e[j], o[j]);
+        v[j + 4] = tc_sub(e[j], o[j]);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void tdftR(tcx *v, const TfConsts &k)
+{
+    if constexpr (R == 2) tdft2(v);
+    else if constexpr (R == 3) tdft3(v, k);
+    else if constexpr (R == 4) tdft4(v);
+    else if constexpr (R == 5) tdft5(v, k);
+    else tdft8(v, k);
+}
+
+// Stockham stage (same index scheme as the FP64 version in fft.cuh), two-float data.
+template <int R>
+__device__ __forceinline__ void tstockham_stage(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines,
+                                                int ls, int es, int n, int Ns, const float4 *__restrict__ tw,
+                                                const TfConsts &k)
+{
+    const int nb = n / R;
+    const int total = nlines * nb;
+    const int tstride = n / (Ns * R);
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        int l = b / nb, j = b - l * nb;
+        int kk = j % Ns;
+        const float4 *xl = x + l * ls;
+        tcx v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + (j + r * nb) * es);
+        if (Ns > 1) {
+            int e = kk * tstride;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = tc_mul(v[r], tc_load(tw + (r * e) % n));
+        }
+        tdftR<R>(v, k);
+        float4 *yl = y + l * ls;
+        int o = (j / Ns) * Ns * R + kk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) tc_store(yl + (o + r * Ns) * es, v[r]);
+    }
+}
+
+// Full line transform in two-float arithmetic; returns the buffer holding the result.
+__device__ inline float4 *tfft_lines(float4 *a, float4 *b, int nlines, int ls, int es, const FftAxis &ax,
+                                     const float4 *tw, const TfConsts &k)
+{
+    int Ns = 1;
+    float4 *x = a, *y = b;
+    for (int s = 0; s < ax.nst; ++s) {
+        int R = ax.rad[s];
+        switch (R) {
+        case 2: tstockham_stage<2>(x, y, nlines, ls, es, ax.n, Ns, tw, k); break;
+        case 3: tstockham_stage<3>(x, y, nlines, ls, es, ax.n, Ns, tw, k); break;
+        case 4: tstockham_stage<4>(x, y, nlines, ls, es, ax.n, Ns, tw, k); break;
+        case 5: tstockham_stage<5>(x, y, nlines, ls, es, ax.n, Ns, tw, k); break;
+        default: tstockham_stage<8>(x, y, nlines, ls, es, ax.n, Ns, tw, k); break;
+        }
+        __syncthreads();
+        Ns *= R;
+        float4 *t = x;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+
+} // namespace gw

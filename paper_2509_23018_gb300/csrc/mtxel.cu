@@ -9,6 +9,7 @@
 // MTXEL kernel takes ("Fourier transformations", Sec. Fast Full-Frequency GW).
 #include "internal.h"
 #include "fft.cuh"
+#include "fft_tf.cuh"
 
 namespace gw {
 
@@ -162,6 +163,131 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel(const double2 *__res
 }
 
 int pair_max_ng() { return 32 * kPairThreads; }
+
+// Same algorithm as pair_kernel, in two-float arithmetic on the FP32 pipes.  The band
+// grids hold (re.hi, re.lo, im.hi, im.lo) per point (see launch_psi_to_tf); the output
+// M is FP64.
+template <int NPT>
+__global__ void __launch_bounds__(kPairThreads) pair_kernel_tf(const float4 *__restrict__ psiv,
+                                                                const float4 *__restrict__ psic, int nc, int64_t p0,
+                                                                PairPlan pp, TfConsts kc, tf inv_nr,
+                                                                double2 *__restrict__ M)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n0 = pp.n[0], n1 = pp.n[1], n2 = pp.n[2];
+    const int ns = n1 * n2;
+    float4 *a = (float4 *)smem, *b = a + ns;
+    float4 *tw0 = b + ns, *tw1 = tw0 + n0, *tw2 = tw1 + n1;
+    int *kz = (int *)(tw2 + n2);
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) tw0[i] = pp.ax[0].twf[i];
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = pp.ax[1].twf[i];
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = pp.ax[2].twf[i];
+    for (int i = threadIdx.x; i < pp.K2; i += blockDim.x) kz[i] = pp.kz[i];
+
+    const int64_t p = p0 + blockIdx.x;
+    const int v = (int)(p / nc), c = (int)(p - (int64_t)v * nc);
+    const int64_t nr = (int64_t)n0 * ns;
+    const float4 *pv = psiv + (int64_t)v * nr;
+    const float4 *pc = psic + (int64_t)c * nr;
+
+    tcx F[NPT];
+    int sel[NPT], k0[NPT], e0[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        int g = threadIdx.x + j * kPairThreads;
+        F[j] = {{0.f, 0.f}, {0.f, 0.f}};
+        int pk = (g < pp.ng) ? pp.gpack[g] : 0;
+        k0[j] = pk & 255;
+        sel[j] = (pk >> 16) * n1 + ((pk >> 8) & 255);
+        e0[j] = 0;
+    }
+    __syncthreads();
+
+    for (int i0 = 0; i0 < n0; ++i0) {
+        const float4 *sv = pv + (int64_t)i0 * ns, *sc = pc + (int64_t)i0 * ns;
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) tc_store(a + i, tc_mulc(tc_load(sv + i), tc_load(sc + i)));
+        __syncthreads();
+        float4 *r = tfft_lines(a, b, n1, n2, 1, pp.ax[2], tw2, kc); // along i2
+        float4 *o = (r == a) ? b : a;
+        for (int i = threadIdx.x; i < pp.K2 * n1; i += blockDim.x) {
+            int q = i / n1, i1 = i - q * n1;
+            o[i] = r[i1 * n2 + kz[q]];
+        }
+        __syncthreads();
+        float4 *t = tfft_lines(o, r, pp.K2, n1, 1, pp.ax[1], tw1, kc); // along i1 on the kept columns
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            tcx u = tc_mul(tc_load(t + sel[j]), tc_load(tw0 + e0[j]));
+            F[j] = tc_add(F[j], u);
+            e0[j] += k0[j];
+            if (e0[j] >= n0) e0[j] -= n0;
+        }
+        __syncthreads();
+    }
+    double2 *out = M + (int64_t)blockIdx.x * pp.ng;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        int g = threadIdx.x + j * kPairThreads;
+        if (g < pp.ng) out[g] = make_double2(tf_to_d(tf_mul(F[j].re, inv_nr)), tf_to_d(tf_mul(F[j].im, inv_nr)));
+    }
+}
+
+template <int NPT>
+static cudaError_t launch_pair_tf_t(const float4 *psiv, const float4 *psic, int nc, int64_t p0, int64_t count,
+                                    const PairPlan &pp, const TfConsts &kc, tf inv_nr, double2 *M, cudaStream_t st)
+{
+    size_t sm = sizeof(float4) * (2 * (size_t)pp.n[1] * pp.n[2] + pp.n[0] + pp.n[1] + pp.n[2]) + sizeof(int) * pp.K2;
+    cudaError_t e = cudaFuncSetAttribute(pair_kernel_tf<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    pair_kernel_tf<NPT><<<(unsigned)count, kPairThreads, sm, st>>>(psiv, psic, nc, p0, pp, kc, inv_nr, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_tf(const void *psiv, const void *psic, int nc, int64_t p0, int64_t count, const PairPlan &pp,
+                           double2 *M, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    TfConsts kc;
+    auto from = [](double x) {
+        float h = (float)x;
+        return tf{h, (float)(x - (double)h)};
+    };
+    kc.sin60 = from(kSin60);
+    kc.c1 = from(kC1);
+    kc.s1 = from(kS1);
+    kc.c2 = from(kC2);
+    kc.s2 = from(kS2);
+    kc.rs2 = from(kRs2);
+    tf inv = from(1.0 / ((double)pp.n[0] * pp.n[1] * pp.n[2]));
+    const float4 *a = (const float4 *)psiv, *b = (const float4 *)psic;
+    int need = (pp.ng + kPairThreads - 1) / kPairThreads;
+    if (need <= 2) return launch_pair_tf_t<2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 4) return launch_pair_tf_t<4>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 8) return launch_pair_tf_t<8>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 12) return launch_pair_tf_t<12>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 16) return launch_pair_tf_t<16>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 24) return launch_pair_tf_t<24>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 32) return launch_pair_tf_t<32>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    return cudaErrorInvalidValue;
+}
+
+// In place: FP64 complex grid values -> two-float (re.hi, re.lo, im.hi, im.lo); both are 16 bytes.
+__global__ void psi_to_tf_kernel(double2 *__restrict__ psi, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 z = psi[i];
+    float rh = __double2float_rn(z.x), ih = __double2float_rn(z.y);
+    float4 o = make_float4(rh, __double2float_rn(z.x - (double)rh), ih, __double2float_rn(z.y - (double)ih));
+    *(float4 *)(psi + i) = o;
+}
+
+cudaError_t launch_psi_to_tf(void *psi, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    psi_to_tf_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((double2 *)psi, n);
+    return cudaGetLastError();
+}
 
 template <int NPT>
 static cudaError_t launch_pair_t(const double2 *psiv, const double2 *psic, int nc, int64_t p0, int64_t count,
