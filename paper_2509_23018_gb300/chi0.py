@@ -205,6 +205,32 @@ def contract_noalloc(ev: torch.Tensor, ec: torch.Tensor, M: torch.Tensor, omega:
     return out
 
 
+class Chi0Fn(torch.autograd.Function):
+    """chi0(iw) of one q-point as a differentiable function of the band coefficients and energies.
+
+    forward(handle, gvec, cv, ev, cc, ec, gchi, omega) loads the bands into slot 0 of
+    ``handle`` and returns chi [ng, ng] (complex128).  backward receives dL/dchi for a
+    real L; because chi is Hermitian only the Hermitian part W of that gradient matters,
+    L = Re Tr(W chi) locally, and the gradients come from gw_chi0_adjoint (torch's
+    convention for complex inputs: dL/dRe + i dL/dIm).
+    """
+
+    @staticmethod
+    def forward(ctx, handle, gvec, cv, ev, cc, ec, gchi, omega):
+        handle.set_bands(0, 1, gvec, cc.detach(), ec.detach())
+        handle.set_bands(0, 0, gvec, cv.detach(), ev.detach())
+        handle.set_gsphere(0, gchi)
+        (chi,) = handle.compute(0, [float(omega)])
+        ctx.handle, ctx.omega = handle, float(omega)
+        return chi[0].clone()
+
+    @staticmethod
+    def backward(ctx, gchi_out):
+        W = 0.5 * (gchi_out + gchi_out.conj().transpose(0, 1))
+        _, dEv, dEc, dcv, dcc = ctx.handle.adjoint(0, W.contiguous(), omega=ctx.omega, want_L=False)
+        return None, None, dcv, dEv, dcc, dEc, None, None
+
+
 def create(grid, **kw) -> Chi0:
     return Chi0(grid, **kw)
 

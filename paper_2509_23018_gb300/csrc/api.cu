@@ -38,6 +38,7 @@ struct Sphere {
     int *kz = nullptr;          // device [K2]
     int32_t *gpack = nullptr;   // device [ng]
     int32_t *gvec = nullptr;    // device [ng][3]
+    std::vector<int> cstart, cg; // (k1, k2) cells of the sphere, CSR (adjoint back-projection)
 };
 
 struct TimerRec {
@@ -617,6 +618,18 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
     if (h->val[iq].nb && h->cond.nb && !alias_free(h, h->val[iq], h->cond, s, &ax))
         return fail(h, GW_ERR_ARG, "max|K_v| + max|K_c| + max|G| >= n on axis %d (aliasing)", ax);
     s.K2 = (int)kz.size();
+    {
+        // group sphere points by their (k2 column, k1) cell
+        std::vector<std::pair<int, int>> key(ng);
+        for (int i = 0; i < ng; ++i) key[i] = {(pack[i] >> 16) * h->d.n[1] + ((pack[i] >> 8) & 255), i};
+        std::sort(key.begin(), key.end());
+        s.cg.resize(ng);
+        for (int i = 0; i < ng; ++i) {
+            if (i == 0 || key[i].first != key[i - 1].first) s.cstart.push_back(i);
+            s.cg[i] = key[i].second;
+        }
+        s.cstart.push_back(ng);
+    }
     gw_status st;
     Sphere &old = h->sph[iq];
     if (old.ng == ng && old.K2 == s.K2) {
@@ -755,10 +768,105 @@ gw_status gw_chi0_contract(gw_chi0 *h, int nv, int nc, const double *ev, const d
     return GW_OK;
 }
 
-gw_status gw_chi0_adjoint(gw_chi0 *h, int, double, const double *, double *, double *, double *, double *, double *)
+gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, double *L, double *dE_v, double *dE_c,
+                          double *dcoeff_v, double *dcoeff_c)
 {
     if (!h) return GW_ERR_ARG;
-    return fail(h, GW_ERR_UNSUPPORTED, "adjoint not built yet");
+    gw_status s = check_slot(h, iq);
+    if (s) return s;
+    if (!W || !dE_v || !dE_c || !dcoeff_v || !dcoeff_c) return fail(h, GW_ERR_ARG, "null pointer");
+    if (!(omega >= 0.0) || !std::isfinite(omega)) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
+    const BandSet &v = h->val[iq];
+    const BandSet &c = h->cond;
+    const Sphere &sp = h->sph[iq];
+    const int nv = v.nb, nc = c.nb, ng = sp.ng;
+    const int64_t nr = h->nr;
+    const bool tf = h->d.mtxel_prec == GW_MTXEL_TWOFLOAT;
+    // valence bands per chunk: bounded by the pair chunk and by 2 GiB of back-projected grids
+    int64_t vch = std::max<int64_t>(1, h->d.pair_chunk / nc);
+    vch = std::min<int64_t>(vch, std::max<int64_t>(1, (int64_t(2) << 30) / ((int64_t)nc * nr * 16)));
+    vch = std::min<int64_t>(vch, nv);
+    const int64_t cmax = vch * nc;
+    // work buffers, held only for this call
+    double2 *Mb = nullptr, *Yb = nullptr, *Hb = nullptr, *pbv = nullptr, *pbc = nullptr;
+    double *Lacc = nullptr;
+    int *cs = nullptr, *cg = nullptr;
+    const int ncell = (int)sp.cstart.size() - 1;
+    size_t szM = sizeof(double2) * cmax * ng, szH = sizeof(double2) * cmax * nr;
+    size_t szV = sizeof(double2) * (size_t)nv * nr, szC = sizeof(double2) * (size_t)nc * nr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(h->st);
+        dfree(h, Mb, szM);
+        dfree(h, Yb, szM);
+        dfree(h, Hb, szH);
+        dfree(h, pbv, szV);
+        dfree(h, pbc, szC);
+        dfree(h, Lacc, sizeof(double));
+        dfree(h, cs, sizeof(int) * (ncell + 1));
+        dfree(h, cg, sizeof(int) * ng);
+    };
+#define ACK(x, what)                       \
+    do {                                   \
+        cudaError_t e_ = (x);              \
+        if (e_ != cudaSuccess) {           \
+            gw_status r_ = cuda_fail(h, e_, what); \
+            cleanup();                     \
+            return r_;                     \
+        }                                  \
+    } while (0)
+    if ((s = dalloc(h, (void **)&Mb, szM, "adjoint M")) || (s = dalloc(h, (void **)&Yb, szM, "adjoint Y")) ||
+        (s = dalloc(h, (void **)&Hb, szH, "adjoint grids")) || (s = dalloc(h, (void **)&pbv, szV, "valence adjoint")) ||
+        (s = dalloc(h, (void **)&pbc, szC, "conduction adjoint")) ||
+        (s = dalloc(h, (void **)&Lacc, sizeof(double), "L")) ||
+        (s = dalloc(h, (void **)&cs, sizeof(int) * (ncell + 1), "cells")) ||
+        (s = dalloc(h, (void **)&cg, sizeof(int) * ng, "cells"))) {
+        cleanup();
+        return s;
+    }
+    ACK(cudaMemcpyAsync(cs, sp.cstart.data(), sizeof(int) * (ncell + 1), cudaMemcpyHostToDevice, h->st), "cells");
+    ACK(cudaMemcpyAsync(cg, sp.cg.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, h->st), "cells");
+    ACK(cudaMemsetAsync(Lacc, 0, sizeof(double), h->st), "zero");
+    ACK(cudaMemsetAsync(dE_v, 0, sizeof(double) * nv, h->st), "zero");
+    ACK(cudaMemsetAsync(dE_c, 0, sizeof(double) * nc, h->st), "zero");
+    ACK(cudaMemsetAsync(pbv, 0, szV, h->st), "zero");
+    ACK(cudaMemsetAsync(pbc, 0, szC, h->st), "zero");
+    gw::PairPlan pp = pair_plan(h, sp);
+    for (int v0 = 0; v0 < nv; v0 += (int)vch) {
+        const int nvc = (int)std::min<int64_t>(vch, nv - v0);
+        const int64_t p0 = (int64_t)v0 * nc, cnt = (int64_t)nvc * nc;
+        {
+            Scope sc(h, "pair_mtxel");
+            ACK(run_pair(h, v.psi, c.psi, nc, p0, cnt, pp, Mb), "pair kernel");
+        }
+        {
+            Scope sc(h, "adj_zgemm");
+            ACK(gw::launch_zgemm(Mb, (const double2 *)W, Yb, cnt, ng, ng, h->st), "Y = M W");
+        }
+        {
+            Scope sc(h, "adj_rows");
+            ACK(gw::launch_adj_rows(Mb, Yb, cnt, ng, nc, p0, v.energy, c.energy, omega, Lacc, dE_v, dE_c, h->st),
+                "row reductions");
+        }
+        {
+            Scope sc(h, "adj_pair");
+            ACK(gw::launch_adj_pair(Yb, cnt, pp, cs, cg, ncell, Hb, h->st), "back-projection");
+        }
+        {
+            Scope sc(h, "adj_products");
+            ACK(gw::launch_adj_products(v.psi, c.psi, v0, nvc, nc, Hb, nr, tf, pbv, pbc, h->st), "products");
+        }
+    }
+    {
+        Scope sc(h, "adj_band");
+        ACK(gw::launch_band_adjoint(pbv, nv, h->d.n, h->ax, v.gofs, v.ngpsi, (double2 *)dcoeff_v, h->st),
+            "valence band adjoint");
+        ACK(gw::launch_band_adjoint(pbc, nc, h->d.n, h->ax, c.gofs, c.ngpsi, (double2 *)dcoeff_c, h->st),
+            "conduction band adjoint");
+    }
+    if (L) ACK(cudaMemcpyAsync(L, Lacc, sizeof(double), cudaMemcpyDeviceToHost, h->st), "L");
+#undef ACK
+    cleanup(); // synchronises: L is valid on return
+    return GW_OK;
 }
 
 gw_status gw_chi0_sync(gw_chi0 *h)

@@ -69,4 +69,15 @@ int oz_box_rows_b();
 int oz_box_k();
 int oz_tiles(int ng);
 
+// ---- adjoint of L = Re Tr(W chi) (adjoint.cu)
+cudaError_t launch_zgemm(const double2 *A, const double2 *B, double2 *C, int64_t mr, int kd, int nc, cudaStream_t st);
+cudaError_t launch_adj_rows(const double2 *M, double2 *Y, int64_t P, int ng, int nc, int64_t p0, const double *ev,
+                            const double *ec, double w, double *L, double *dEv, double *dEc, cudaStream_t st);
+cudaError_t launch_adj_pair(const double2 *Gb, int64_t P, const PairPlan &pp, const int *cell_start,
+                            const int *cell_g, int ncell, double2 *H, cudaStream_t st);
+cudaError_t launch_adj_products(const void *psiv, const void *psic, int v0, int nvc, int nc, const double2 *H,
+                                int64_t nr, bool tf, double2 *pbv, double2 *pbc, cudaStream_t st);
+cudaError_t launch_band_adjoint(double2 *pb, int nb, const int n[3], const FftAxis ax[3], const int32_t *gofs,
+                                int ngpsi, double2 *dc, cudaStream_t st);
+
 } // namespace gw
