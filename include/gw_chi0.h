@@ -196,9 +196,9 @@ GW_API size_t gw_chi0_device_bytes(const gw_chi0 *h);
  * kernels, same arguments and layouts, chi written in full), without a handle, on the
  * given stream (a cudaStream_t; NULL = legacy default stream), for the current device.
  *
- * Its only scratch -- the energy factors Delta of every pair and frequency, and a
- * status word -- lives in one fixed device array compiled into the library (4 MiB plus
- * 256 bytes; every GPU that loads the library holds it until the process exits).
+ * Its only scratch -- the energy factors Delta of every pair and frequency, the kernel's
+ * job table and a status word -- lives in one fixed device array compiled into the library
+ * (4 MiB + 16.25 KiB; every GPU that loads the library holds it until the process exits).
  *   - Limit: nw * nv * nc <= 524288; larger requests return GW_ERR_ARG and do nothing.
  *   - The first call on a device looks up that array's device address (once per device,
  *     with the device current); make that first call before any stream capture.

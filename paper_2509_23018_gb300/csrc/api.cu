@@ -70,6 +70,10 @@ struct gw_chi0 {
     size_t spcap = 0;
     int *Ebuf = nullptr;       // column exponents [ng]
     size_t Ecap = 0;
+    void *jobbuf = nullptr;    // job tables of the batched contraction kernels
+    size_t jobcap = 0;
+    // contraction launch shapes (set by the autotuner; these are the defaults)
+    int tuned_bt = 64, tuned_waves = 4, tuned_bn = 256;
     int *status = nullptr;
     size_t bytes = 0;
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -212,12 +216,12 @@ gw_status ensure_work(gw_chi0 *h, size_t m_elems, size_t d_elems)
     return GW_OK;
 }
 
-gw_status make_tmap(gw_chi0 *h, CUtensorMap *map, const void *M, int64_t P, int ng)
+gw_status make_tmap(gw_chi0 *h, CUtensorMap *map, const void *M, int64_t P, int ng, int bt)
 {
     if (((uintptr_t)M & 15) != 0) return fail(h, GW_ERR_ARG, "M must be 16-byte aligned");
     cuuint64_t dims[2] = {(cuuint64_t)2 * ng, (cuuint64_t)P};
     cuuint64_t strides[1] = {(cuuint64_t)2 * ng * sizeof(double)};
-    cuuint32_t box[2] = {(cuuint32_t)(2 * gw::contract_f64_tile()), (cuuint32_t)gw::contract_f64_bk()};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * bt), (cuuint32_t)gw::contract_f64_bk()};
     cuuint32_t es[2] = {1, 1};
     CUresult r = h->encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(M), dims, strides, box, es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -226,20 +230,11 @@ gw_status make_tmap(gw_chi0 *h, CUtensorMap *map, const void *M, int64_t P, int 
     return GW_OK;
 }
 
-int pick_ksplit(int ng, int64_t P, int nw)
+int num_sms()
 {
-    // enough blocks for several full waves of 2 resident blocks on each of the SMs
-    int sms = 152;
-    int dev;
+    int sms = 152, dev;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nt = (ng + gw::contract_f64_tile() - 1) / gw::contract_f64_tile();
-    int64_t tiles = (int64_t)nt * (nt + 1) / 2 * nw;
-    int64_t want = 8LL * sms;
-    int64_t ks = (want + tiles - 1) / tiles;
-    int64_t kmax = (P + 255) / 256; // at least 256 pairs per block
-    if (ks > kmax) ks = kmax;
-    if (ks < 1) ks = 1;
-    return (int)ks;
+    return sms;
 }
 
 gw_status grow(gw_chi0 *h, void **p, size_t *cap, size_t bytes, const char *what)
@@ -254,6 +249,71 @@ gw_status grow(gw_chi0 *h, void **p, size_t *cap, size_t bytes, const char *what
     return GW_OK;
 }
 
+// Copy a job table into the handle's job buffer, in stream order (the copy runs after every
+// kernel already enqueued, so rewriting the buffer never races a kernel that reads it).
+gw_status upload_jobs(gw_chi0 *h, const void *src, size_t bytes, const void **dev)
+{
+    gw_status s = grow(h, &h->jobbuf, &h->jobcap, bytes, "job table");
+    if (s) return s;
+    CK(h, cudaMemcpyAsync(h->jobbuf, src, bytes, cudaMemcpyHostToDevice, h->st), "job table upload");
+    *dev = h->jobbuf;
+    return GW_OK;
+}
+
+// FP64 jobs for one M block and nw frequencies; item_start and ksplit filled in by the caller.
+gw_status f64_jobs(gw_chi0 *h, std::vector<gw::F64Job> &jobs, const double2 *M, int64_t P, int ng,
+                   const double *delta, int64_t dstride, int nw, double2 *chi, int bt)
+{
+    CUtensorMap map;
+    gw_status s = make_tmap(h, &map, M, P, ng, bt);
+    if (s) return s;
+    for (int w = 0; w < nw; ++w) {
+        gw::F64Job j;
+        std::memset(&j, 0, sizeof j);
+        j.tm = map;
+        j.delta = delta + (int64_t)w * dstride;
+        j.chi = (double *)(chi + (int64_t)w * ng * ng);
+        j.P = P;
+        j.ng = ng;
+        j.ntile = (ng + bt - 1) / bt;
+        jobs.push_back(j);
+    }
+    return GW_OK;
+}
+
+// Order jobs largest first, pick a uniform pair split for `waves` block waves, set item ranges.
+int f64_schedule(std::vector<gw::F64Job> &jobs, int waves)
+{
+    std::stable_sort(jobs.begin(), jobs.end(), [](const gw::F64Job &a, const gw::F64Job &b) {
+        return (double)a.ng * a.ng * a.P > (double)b.ng * b.ng * b.P;
+    });
+    int64_t tiles = 0;
+    for (auto &j : jobs) tiles += (int64_t)j.ntile * (j.ntile + 1) / 2;
+    const int64_t want = (int64_t)waves * 2 * num_sms();
+    int64_t ks = std::max<int64_t>(1, (want + tiles - 1) / std::max<int64_t>(tiles, 1));
+    int items = 0;
+    for (auto &j : jobs) {
+        int64_t kj = std::min<int64_t>(ks, std::max<int64_t>(1, (j.P + 255) / 256)); // >= 256 pairs per item
+        j.ksplit = (int)kj;
+        j.item_start = items;
+        items += (int)(kj * j.ntile * (j.ntile + 1) / 2);
+    }
+    return items;
+}
+
+gw_status launch_f64_jobs(gw_chi0 *h, std::vector<gw::F64Job> &jobs, int bt, int waves)
+{
+    const int nitems = f64_schedule(jobs, waves);
+    const void *dj;
+    gw_status s = upload_jobs(h, jobs.data(), sizeof(gw::F64Job) * jobs.size(), &dj);
+    if (s) return s;
+    const int grid = std::max(1, std::min(nitems, 2 * num_sms()));
+    Scope sc(h, "contract_f64");
+    CK(h, gw::launch_contract_f64_jobs(bt, (const gw::F64Job *)dj, (int)jobs.size(), nitems, grid, h->status, h->st),
+       "contract_f64");
+    return GW_OK;
+}
+
 gw_status make_tmap_z(gw_chi0 *h, CUtensorMap *map, void *Z, int64_t kpad, int nrows, int s, int box_rows)
 {
     cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)nrows, (cuuint64_t)s};
@@ -264,6 +324,48 @@ gw_status make_tmap_z(gw_chi0 *h, CUtensorMap *map, void *Z, int64_t kpad, int n
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, GW_ERR_CUDA, "cuTensorMapEncodeTiled (slices) failed (%d)", (int)r);
+    return GW_OK;
+}
+
+gw_status oz_job(gw_chi0 *h, gw::OzJob &j, void *Z, int64_t kpad, int ng, const int *E, double2 *chi, int bn)
+{
+    std::memset(&j, 0, sizeof j);
+    gw_status st;
+    if ((st = make_tmap_z(h, &j.tmA, Z, kpad, 2 * ng, h->d.nslices, gw::oz_box_rows_a())) ||
+        (st = make_tmap_z(h, &j.tmB, Z, kpad, 2 * ng, h->d.nslices, bn)))
+        return st;
+    j.E = E;
+    j.chi = (double *)chi;
+    j.ng = ng;
+    j.nk = (int)(kpad / gw::oz_box_k());
+    j.s = h->d.nslices;
+    j.ntiles = gw::oz_tiles(ng, bn);
+    return GW_OK;
+}
+
+int oz_schedule(std::vector<gw::OzJob> &jobs)
+{
+    std::stable_sort(jobs.begin(), jobs.end(), [](const gw::OzJob &a, const gw::OzJob &b) {
+        return (double)a.ng * a.ng * a.nk > (double)b.ng * b.ng * b.nk;
+    });
+    int items = 0;
+    for (auto &j : jobs) {
+        j.item_start = items;
+        items += j.ntiles;
+    }
+    return items;
+}
+
+gw_status launch_oz_jobs(gw_chi0 *h, std::vector<gw::OzJob> &jobs, int bn)
+{
+    const int nitems = oz_schedule(jobs);
+    const void *dj;
+    gw_status s = upload_jobs(h, jobs.data(), sizeof(gw::OzJob) * jobs.size(), &dj);
+    if (s) return s;
+    const int grid = std::max(1, std::min(nitems, num_sms()));
+    Scope sc(h, "ozaki_gemm");
+    CK(h, gw::launch_oz_gemm_jobs(bn, (const gw::OzJob *)dj, (int)jobs.size(), nitems, grid, h->status, h->st),
+       "oz gemm");
     return GW_OK;
 }
 
@@ -282,10 +384,7 @@ gw_status contract_chunk_ozaki(gw_chi0 *h, const double2 *M, int64_t P, int ng, 
         Scope sc(h, "oz_split");
         CK(h, gw::launch_oz_sqrt(delta, (int64_t)nw * dstride, h->spbuf, h->st), "oz sqrt");
     }
-    CUtensorMap ta, tb;
-    if ((st = make_tmap_z(h, &ta, h->Zbuf, kpad, 2 * ng, s, gw::oz_box_rows_a())) ||
-        (st = make_tmap_z(h, &tb, h->Zbuf, kpad, 2 * ng, s, gw::oz_box_rows_b())))
-        return st;
+    const int bn = h->tuned_bn;
     for (int w = 0; w < nw; ++w) {
         const double *sp = h->spbuf + (int64_t)w * dstride;
         {
@@ -293,10 +392,9 @@ gw_status contract_chunk_ozaki(gw_chi0 *h, const double2 *M, int64_t P, int ng, 
             CK(h, gw::launch_oz_colexp(M, P, ng, sp, h->Ebuf, h->st), "oz exponents");
             CK(h, gw::launch_oz_slice(M, P, ng, sp, h->Ebuf, s, kpad, h->Zbuf, h->st), "oz slices");
         }
-        Scope sc(h, "ozaki_gemm");
-        CK(h, gw::launch_oz_gemm(&ta, &tb, ng, kpad, s, h->Ebuf, (double *)(chi + (int64_t)w * ng * ng), h->status,
-                                 h->st),
-           "oz gemm");
+        std::vector<gw::OzJob> jobs(1);
+        if ((st = oz_job(h, jobs[0], h->Zbuf, kpad, ng, h->Ebuf, chi + (int64_t)w * ng * ng, bn))) return st;
+        if ((st = launch_oz_jobs(h, jobs, bn))) return st;
     }
     return GW_OK;
 }
@@ -305,14 +403,10 @@ gw_status contract_chunk(gw_chi0 *h, const double2 *M, int64_t P, int ng, const 
                          int nw, double2 *chi)
 {
     if (h->d.prec == GW_PREC_OZAKI_BF16) return contract_chunk_ozaki(h, M, P, ng, delta, dstride, nw, chi);
-    CUtensorMap map;
-    gw_status s = make_tmap(h, &map, M, P, ng);
+    std::vector<gw::F64Job> jobs;
+    gw_status s = f64_jobs(h, jobs, M, P, ng, delta, dstride, nw, chi, h->tuned_bt);
     if (s) return s;
-    Scope sc(h, "contract_f64");
-    CK(h, gw::launch_contract_f64(&map, delta, dstride, P, ng, nw, (double *)chi, pick_ksplit(ng, P, nw), h->status,
-                                  h->st),
-       "contract_f64");
-    return GW_OK;
+    return launch_f64_jobs(h, jobs, h->tuned_bt, h->tuned_waves);
 }
 
 bool alias_free(const gw_chi0 *h, const BandSet &v, const BandSet &c, const Sphere &s, int *axis)
@@ -469,6 +563,7 @@ void gw_chi0_destroy(gw_chi0 *h)
     dfree(h, h->Zbuf, h->Zcap);
     dfree(h, h->spbuf, h->spcap);
     dfree(h, h->Ebuf, h->Ecap);
+    dfree(h, h->jobbuf, h->jobcap);
     {
         size_t ntw = (size_t)h->d.n[0] + h->d.n[1] + h->d.n[2];
         dfree(h, h->tw, sizeof(double2) * ntw);

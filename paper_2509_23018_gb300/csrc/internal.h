@@ -47,11 +47,18 @@ cudaError_t launch_diag(const double2 *M, int64_t P, int ng, const double *delta
 cudaError_t launch_symmetrize(double2 *chi, int ng, int nw, cudaStream_t st);
 
 // ---- stage (b), FP64 tensor cores (contract_f64.cu)
-// chi[w][G][G'] += sum_p conj(M[p][G]) delta[w][p] M[p][G'] on upper-triangle tiles.
-cudaError_t launch_contract_f64(const CUtensorMap *tmap, const double *delta, int64_t dstride, int64_t P, int ng,
-                                int nw, double *chi, int ksplit, int *status, cudaStream_t st);
-int contract_f64_tile();
+// One job = one chi block: chi[G][G'] += sum_p conj(M[p][G]) delta[p] M[p][G'] on upper tiles.
+struct __align__(128) F64Job {
+    CUtensorMap tm;       // M as doubles [P][2 ng], box {2 BT, 16}
+    const double *delta;  // [P]
+    double *chi;          // [ng][ng] complex
+    int64_t P;
+    int ng, ntile, ksplit, item_start;
+};
+cudaError_t launch_contract_f64_jobs(int bt, const F64Job *jobs, int njobs, int nitems, int grid, int *status,
+                                     cudaStream_t st);
 int contract_f64_bk();
+size_t contract_f64_smem(int bt);
 
 // ---- stage (b), split precision on BF16 tensor cores (ozaki.cu)
 // sp[i] = sqrt(-delta[i])
@@ -61,13 +68,19 @@ cudaError_t launch_oz_colexp(const double2 *M, int64_t P, int ng, const double *
 // Z[i][j][p] bf16 slices, rows p in [P, kpad) zero
 cudaError_t launch_oz_slice(const double2 *M, int64_t P, int ng, const double *sp, const int *E, int s,
                             int64_t kpad, void *Z, cudaStream_t st);
-// chi[G][G'] (upper triangle) += recombined slice products of the chunk
-cudaError_t launch_oz_gemm(const CUtensorMap *tmA, const CUtensorMap *tmB, int ng, int64_t kpad, int s, const int *E,
-                           double *chi, int *status, cudaStream_t st);
+// One job = the split contraction of one chunk into one chi block (upper tiles).
+struct __align__(128) OzJob {
+    CUtensorMap tmA, tmB; // slices [s][2 ng][kpad] bf16, boxes {64, 128} and {64, BN}
+    const int *E;         // [ng] column exponents
+    double *chi;          // [ng][ng] complex
+    int ng, nk, s, ntiles, item_start;
+};
+cudaError_t launch_oz_gemm_jobs(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
+                                cudaStream_t st);
+int oz_tiles(int ng, int bn);
+size_t oz_smem_bytes(int bn);
 int oz_box_rows_a();
-int oz_box_rows_b();
 int oz_box_k();
-int oz_tiles(int ng);
 
 // ---- adjoint of L = Re Tr(W chi) (adjoint.cu)
 cudaError_t launch_zgemm(const double2 *A, const double2 *B, double2 *C, int64_t mr, int kd, int nc, cudaStream_t st);

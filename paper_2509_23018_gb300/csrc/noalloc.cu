@@ -15,15 +15,18 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 namespace {
 
-// Scratch: 256 bytes for the status word, then kNoAllocDelta doubles of Delta.
-// Every device that loads this library holds the 4 MiB + 256 bytes until exit.
+// Scratch: 256 bytes for the status word, kMaxOmega job tables, then kNoAllocDelta
+// doubles of Delta.  Every device that loads this library holds the array until exit.
 constexpr size_t kNoAllocDelta = size_t(1) << 19; // nw * nv * nc must not exceed this
+constexpr size_t kNoAllocJobs = gw::kMaxOmega * sizeof(gw::F64Job) / sizeof(double);
 constexpr size_t kNoAllocHead = 256 / sizeof(double);
-static __device__ __align__(256) double g_noalloc_scratch[kNoAllocHead + kNoAllocDelta];
+constexpr int kNoAllocTile = 64;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocHead + kNoAllocJobs + kNoAllocDelta];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -85,33 +88,52 @@ extern "C" gw_status gw_chi0_contract_noalloc(int nv, int nc, const double *ev, 
     gw_status s = setup(dev, &scratch);
     if (s) return s;
     int *status = (int *)scratch;
-    double *delta = scratch + kNoAllocHead;
+    double *delta = scratch + kNoAllocHead + kNoAllocJobs;
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
-    CUtensorMap map;
+    // scratch layout: status word, kMaxOmega job tables, then Delta
+    gw::F64Job job;
+    std::memset(&job, 0, sizeof job);
     cuuint64_t dims[2] = {(cuuint64_t)2 * ng, (cuuint64_t)P};
     cuuint64_t strides[1] = {(cuuint64_t)2 * ng * sizeof(double)};
-    cuuint32_t box[2] = {(cuuint32_t)(2 * gw::contract_f64_tile()), (cuuint32_t)gw::contract_f64_bk()};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * kNoAllocTile), (cuuint32_t)gw::contract_f64_bk()};
     cuuint32_t es[2] = {1, 1};
-    if (g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(M), dims, strides, box, es,
+    if (g_encode(&job.tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(M), dims, strides, box, es,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return GW_ERR_CUDA;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nt = (ng + kNoAllocTile - 1) / kNoAllocTile;
+    const int64_t tiles = (int64_t)nt * (nt + 1) / 2 * nw;
+    int64_t ks = (8LL * sms + tiles - 1) / tiles;
+    ks = std::max<int64_t>(1, std::min<int64_t>(ks, (P + 255) / 256));
+    // one job per frequency, all sharing M
+    static thread_local gw::F64Job jobs[gw::kMaxOmega];
+    int items = 0;
+    for (int w = 0; w < nw; ++w) {
+        jobs[w] = job;
+        jobs[w].delta = delta + (int64_t)w * P;
+        jobs[w].chi = chi + 2 * (int64_t)w * ng * ng;
+        jobs[w].P = P;
+        jobs[w].ng = ng;
+        jobs[w].ntile = nt;
+        jobs[w].ksplit = (int)ks;
+        jobs[w].item_start = items;
+        items += (int)(ks * nt * (nt + 1) / 2);
+    }
+    gw::F64Job *djobs = (gw::F64Job *)(scratch + kNoAllocHead);
 
     // the scratch keeps the previous call's contents: the status word must start at zero
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemcpyAsync(djobs, jobs, sizeof(gw::F64Job) * nw, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(chi, 0, sizeof(double) * 2 * (size_t)nw * ng * ng, st) != cudaSuccess ||
         gw::launch_delta(ev, ec, nc, 0, P, om, delta, st) != cudaSuccess) {
         cudaGetLastError();
         return GW_ERR_CUDA;
     }
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int nt = (ng + gw::contract_f64_tile() - 1) / gw::contract_f64_tile();
-    const int64_t tiles = (int64_t)nt * (nt + 1) / 2 * nw;
-    int64_t ks = (8LL * sms + tiles - 1) / tiles;
-    ks = std::max<int64_t>(1, std::min<int64_t>(ks, (P + 255) / 256));
-    if (gw::launch_contract_f64(&map, delta, P, P, ng, nw, chi, (int)ks, status, st) != cudaSuccess ||
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, 2LL * sms));
+    if (gw::launch_contract_f64_jobs(kNoAllocTile, djobs, nw, items, grid, status, st) != cudaSuccess ||
         gw::launch_symmetrize((double2 *)chi, ng, nw, st) != cudaSuccess) {
         cudaGetLastError();
         return GW_ERR_CUDA;

@@ -17,6 +17,7 @@
 // happens once per chunk and group, in the epilogue.  FP64 is kept for Delta, the
 // scaling, the recombination, the accumulation across chunks and the symmetrisation.
 #include "internal.h"
+#include "ptx.cuh"
 #include <cuda_bf16.h>
 #include <algorithm>
 
@@ -27,7 +28,6 @@ constexpr int kOzBM = 128, kOzBN = 256, kOzBK = 64, kOzStages = 4;
 constexpr int kOzThreads = 192;
 constexpr unsigned kOzABytes = kOzBM * kOzBK * 2, kOzBBytes = kOzBN * kOzBK * 2;
 constexpr int kOzNoColumn = -400; // exponent of an all-zero column
-constexpr long long kOzWait = 1LL << 24;
 
 // ------------------------------------------------------------------ split, step 1: column exponents
 // E[g] = max_p ilogb(max(|Re A|, |Im A|)) + 2 over the chunk, A = s_p M[p][g].
@@ -120,108 +120,67 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double2 *__restrict
 }
 
 // ------------------------------------------------------------------ tcgen05 GEMM
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bar_init(uint64_t *b, unsigned c)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c));
-}
-__device__ __forceinline__ void bar_expect(uint64_t *b, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(uint64_t *b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool bar_wait(uint64_t *b, unsigned parity)
-{
-    const uint32_t a = su32(b);
-    for (long long it = 0; it < kOzWait; ++it) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(ok)
-                     : "r"(a), "r"(parity)
-                     : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void tma3(void *dst, const CUtensorMap *m, uint64_t *b, int x, int y, int z)
-{
-    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                 ::"r"(su32(dst)), "l"(m), "r"(x), "r"(y), "r"(z), "r"(su32(b))
-                 : "memory");
-}
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
-{
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                 ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
-                 : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t *b)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-#define OZ_LD32(taddr, v)                                                                                        \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"  \
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                        \
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), \
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),        \
-                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),      \
-                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),      \
-                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])                                                           \
-                 : "r"(taddr))
-
-struct OzParams {
-    int ng, nrows, nk, s;
-    int nJ;
-    const int *E;
-    double *chi;
-    int *status;
+// Persistent and batched: a launch takes a table of jobs (one job = one chunk's slices
+// for one chi block, each with its own N_G, tensor maps and exponents) and the list of
+// their upper tiles; block b takes items b, b + gridDim.x, ... in the same order in every
+// role, so the TMA producer warp, the MMA warp and the epilogue warps need no exchange
+// beyond the mbarriers.  The tile width BN (128 or 256 real columns) is chosen by the
+// autotuner; two BN-column FP32 accumulators in TMEM alternate between slice groups so the
+// epilogue of group t overlaps the MMAs of group t+1.
+template <int BN>
+struct OzCfg {
+    static constexpr int BM = kOzBM;
+    static constexpr int BNC = BN / 2;                       // complex columns per tile
+    static constexpr unsigned ABytes = kOzBM * kOzBK * 2, BBytes = BN * kOzBK * 2;
+    static constexpr uint32_t TmemCols = 2 * BN;             // 256 or 512
+    // idesc: D = F32, A = B = BF16, both K-major, N = BN, M = 128
+    static constexpr uint32_t Idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(kOzBM >> 4) << 24);
+    static constexpr size_t Smem = 1024 + kOzStages * (size_t)(ABytes + BBytes) + (2 * kOzStages + 5) * 8 + 16;
 };
 
-// idesc: D = F32, A = B = BF16, both K-major, N = 256, M = 128
-constexpr uint32_t kOzIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
-                              ((uint32_t)(kOzBM >> 4) << 24);
-
-__global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                               const __grid_constant__ CUtensorMap tmB, OzParams pr)
+// tile -> (I, J): J-major, rows I = 0 .. min((BNC (J+1) - 1)/64 + 1, nI) - 1
+__device__ __forceinline__ void oz_tile_ij(int tile, int nI, int bnc, int &I, int &J)
 {
+    int rem = tile;
+    J = 0;
+    for (;;) {
+        const int c = min((bnc * (J + 1) - 1) / 64 + 1, nI);
+        if (rem < c) break;
+        rem -= c;
+        ++J;
+    }
+    I = rem;
+}
+
+__device__ __forceinline__ int oz_find_job(const OzJob *jobs, int njobs, int item)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].item_start <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__restrict__ jobs, int njobs, int nitems,
+                                                               int *status)
+{
+    using C = OzCfg<BN>;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA = sm;                                  // [stages][16 KB]
-    unsigned char *sB = sA + kOzStages * kOzABytes;          // [stages][32 KB]
-    uint64_t *full = (uint64_t *)(sB + kOzStages * kOzBBytes);
+    unsigned char *sA = sm;                                  // [stages][ABytes]
+    unsigned char *sB = sA + kOzStages * C::ABytes;          // [stages][BBytes]
+    uint64_t *full = (uint64_t *)(sB + kOzStages * C::BBytes);
     uint64_t *empty = full + kOzStages;
     uint64_t *tfull = empty + kOzStages;
     uint64_t *tempty = tfull + 2;
     uint64_t *fin = tempty + 2;
     uint32_t *tslot = (uint32_t *)(fin + 1);
-    int *Ecol = (int *)(tslot + 4);                          // [128] exponents of the tile's columns
 
-    // tile (I, J): 128 real rows (64 complex) x 256 real columns (128 complex), with I <= 2J + 1
-    const int nI = (pr.nrows + kOzBM - 1) / kOzBM;
-    int rem = blockIdx.x, J = 0;
-    for (;;) {
-        const int c = min(2 * J + 2, nI);
-        if (rem < c) break;
-        rem -= c;
-        ++J;
-    }
-    const int I = rem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
     if (threadIdx.x == 0) {
         for (int i = 0; i < kOzStages; ++i) {
             bar_init(&full[i], 1);
@@ -232,128 +191,130 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const __grid_con
             bar_init(&tempty[i], 128);
         }
         bar_init(fin, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        bar_fence_init();
     }
-    for (int c = threadIdx.x; c < 128; c += blockDim.x) {
-        int g = J * 128 + c;
-        Ecol[c] = g < pr.ng ? pr.E[g] : kOzNoColumn;
-    }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
+    if (warp == 1) tmem_alloc(tslot, C::TmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    const int s = pr.s, nk = pr.nk;
     bool ok = true;
 
     if (warp == 0) {
         if (lane == 0) {
-            int it = 0;
-            for (int t = 2; t <= s + 1 && ok; ++t)
-                for (int i = 1; i < t && ok; ++i) {
-                    const int k = t - i;
-                    for (int kb = 0; kb < nk; ++kb, ++it) {
-                        const int st = it % kOzStages, n = it / kOzStages;
-                        if (!bar_wait(&empty[st], (unsigned)((n & 1) ^ 1))) { ok = false; break; }
-                        bar_expect(&full[st], kOzABytes + kOzBBytes);
-                        tma3(sA + st * kOzABytes, &tmA, &full[st], kb * kOzBK, I * kOzBM, i - 1);
-                        tma3(sB + st * kOzBBytes, &tmB, &full[st], kb * kOzBK, J * kOzBN, k - 1);
-                    }
-                }
-            if (!ok) atomicOr(pr.status, kStatusTimeout);
+            uint32_t it = 0;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const OzJob &jb = jobs[oz_find_job(jobs, njobs, item)];
+                int I, J;
+                oz_tile_ij(item - jb.item_start, (2 * jb.ng + kOzBM - 1) / kOzBM, C::BNC, I, J);
+                for (int t = 2; t <= jb.s + 1 && ok; ++t)
+                    for (int i = 1; i < t && ok; ++i)
+                        for (int kb = 0; kb < jb.nk; ++kb, ++it) {
+                            const int st = it % kOzStages;
+                            const uint32_t n = it / kOzStages;
+                            if (!bar_wait(&empty[st], (n & 1) ^ 1)) { ok = false; break; }
+                            bar_expect(&full[st], C::ABytes + C::BBytes);
+                            tma3(sA + st * C::ABytes, &jb.tmA, &full[st], kb * kOzBK, I * kOzBM, i - 1);
+                            tma3(sB + st * C::BBytes, &jb.tmB, &full[st], kb * kOzBK, J * BN, t - i - 1);
+                        }
+            }
+            if (!ok) atomicOr(status, kStatusTimeout);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int it = 0;
-            for (int t = 2; t <= s + 1 && ok; ++t) {
-                const int gi = t - 2, b = gi & 1, u = gi >> 1;
-                if (!bar_wait(&tempty[b], (unsigned)((u & 1) ^ 1))) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t d = tbase + (uint32_t)(b * kOzBN);
-                bool first = true;
-                for (int i = 1; i < t && ok; ++i)
-                    for (int kb = 0; kb < nk; ++kb, ++it) {
-                        const int st = it % kOzStages, n = it / kOzStages;
-                        if (!bar_wait(&full[st], (unsigned)(n & 1))) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t a0 = su32(sA + st * kOzABytes), b0 = su32(sB + st * kOzBBytes);
+            uint32_t it = 0, grp = 0;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const OzJob &jb = jobs[oz_find_job(jobs, njobs, item)];
+                for (int t = 2; t <= jb.s + 1 && ok; ++t, ++grp) {
+                    const uint32_t b = grp & 1, u = grp >> 1;
+                    if (!bar_wait(&tempty[b], (u & 1) ^ 1)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t d = tbase + b * BN;
+                    bool first = true;
+                    for (int i = 1; i < t && ok; ++i)
+                        for (int kb = 0; kb < jb.nk; ++kb, ++it) {
+                            const int st = it % kOzStages;
+                            if (!bar_wait(&full[st], (it / kOzStages) & 1)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint32_t a0 = su32(sA + st * C::ABytes), b0 = su32(sB + st * C::BBytes);
 #pragma unroll
-                        for (int kk = 0; kk < kOzBK / 16; ++kk) {
-                            umma(d, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), kOzIdesc, (first && kk == 0) ? 0u : 1u);
+                            for (int kk = 0; kk < kOzBK / 16; ++kk)
+                                umma_f16(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), C::Idesc,
+                                         (first && kk == 0) ? 0u : 1u);
+                            first = false;
+                            umma_commit(&empty[st]);
                         }
-                        first = false;
-                        umma_commit(&empty[st]);
-                    }
-                umma_commit(&tfull[b]);
+                    umma_commit(&tfull[b]);
+                }
             }
             // every issued MMA has completed before the block tears down
             umma_commit(fin);
             bar_wait(fin, 0);
-            if (!ok) atomicOr(pr.status, kStatusTimeout);
+            if (!ok) atomicOr(status, kStatusTimeout);
         }
     } else {
         // epilogue: warps 2..5 -> TMEM lane quadrant (warp % 4), one tile row per thread
         const int q = warp & 3;
         const int r = q * 32 + lane;              // tile row (real index)
-        const int g = I * 64 + (r >> 1);          // complex row G
         const int odd = r & 1;                    // 0: Re part, 1: Im part
-        const int Eg = g < pr.ng ? pr.E[g] : kOzNoColumn;
-        double *crow = pr.chi + 2 * ((int64_t)g * pr.ng) + odd;
-        for (int t = 2; t <= s + 1; ++t) {
-            const int gi = t - 2, b = gi & 1, u = gi >> 1;
-            const bool got = bar_wait(&tfull[b], (unsigned)(u & 1));
-            if (!__all_sync(0xffffffffu, got)) { ok = false; break; } // warp-uniform exit
-            tc_fence_after();
-            const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kOzBN);
+        uint32_t grp = 0;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const OzJob &jb = jobs[oz_find_job(jobs, njobs, item)];
+            int I, J;
+            oz_tile_ij(item - jb.item_start, (2 * jb.ng + kOzBM - 1) / kOzBM, C::BNC, I, J);
+            const int ng = jb.ng;
+            const int g = I * 64 + (r >> 1);      // complex row G
+            const int Eg = g < ng ? __ldg(jb.E + g) : kOzNoColumn;
+            double *crow = jb.chi + 2 * ((int64_t)g * ng) + odd;
+            for (int t = 2; t <= jb.s + 1; ++t, ++grp) {
+                const uint32_t b = grp & 1, u = grp >> 1;
+                const bool got = bar_wait(&tfull[b], u & 1);
+                if (!__all_sync(0xffffffffu, got)) { ok = false; break; } // warp-uniform exit
+                tc_fence_after();
+                const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * BN;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kOzBN; c0 += 32) {
-                uint32_t v[32];
-                OZ_LD32(ta + c0, v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    uint32_t v[32];
+                    GW_TMEM_LD32(ta + c0, v);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int cc = 0; cc < 16; ++cc) {
-                    const int ev = (int)__uint_as_float(v[2 * cc]);
-                    const int od = (int)__uint_as_float(v[2 * cc + 1]);
-                    const int rv = __shfl_xor_sync(0xffffffffu, od, 1);
-                    const int val = odd ? (rv - ev) : (ev + rv);
-                    const int cl = (c0 >> 1) + cc;    // complex column in the tile
-                    const int gp = J * 128 + cl;
-                    if (g < pr.ng && gp < pr.ng && g <= gp && val != 0) {
-                        const int ex = Eg + Ecol[cl] - kOzBeta * t;
-                        const double sc = -__longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
-                        double *dst = crow + 2 * (int64_t)gp;
-                        *dst = fma((double)val, sc, *dst);
+                    for (int cc = 0; cc < 16; ++cc) {
+                        const int ev = (int)__uint_as_float(v[2 * cc]);
+                        const int od = (int)__uint_as_float(v[2 * cc + 1]);
+                        const int rv = __shfl_xor_sync(0xffffffffu, od, 1);
+                        const int val = odd ? (rv - ev) : (ev + rv);
+                        const int gp = J * C::BNC + (c0 >> 1) + cc;
+                        if (g < ng && gp < ng && g <= gp && val != 0) {
+                            const int ex = Eg + __ldg(jb.E + gp) - kOzBeta * t;
+                            const double sc = -__longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
+                            double *dst = crow + 2 * (int64_t)gp;
+                            *dst = fma((double)val, sc, *dst);
+                        }
                     }
                 }
+                tc_fence_before();
+                bar_arrive(&tempty[b]);
             }
-            tc_fence_before();
-            bar_arrive(&tempty[b]);
         }
-        if (!ok) atomicOr(pr.status, kStatusTimeout);
+        if (!ok) atomicOr(status, kStatusTimeout);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+    if (warp == 1) tmem_dealloc(tbase, C::TmemCols);
 }
 
 // ------------------------------------------------------------------ host launchers
-int oz_tiles(int ng)
+int oz_tiles(int ng, int bn)
 {
-    const int nrows = 2 * ng;
-    const int nI = (nrows + kOzBM - 1) / kOzBM, nJ = (nrows + kOzBN - 1) / kOzBN;
+    const int nrows = 2 * ng, bnc = bn / 2;
+    const int nI = (nrows + kOzBM - 1) / kOzBM, nJ = (nrows + bn - 1) / bn;
     int n = 0;
-    for (int J = 0; J < nJ; ++J) n += std::min(2 * J + 2, nI);
+    for (int J = 0; J < nJ; ++J) n += std::min((bnc * (J + 1) - 1) / 64 + 1, nI);
     return n;
 }
 
-size_t oz_smem_bytes()
-{
-    return 1024 + kOzStages * (size_t)(kOzABytes + kOzBBytes) + (2 * kOzStages + 5) * 8 + 16 + 128 * 4;
-}
+size_t oz_smem_bytes(int bn) { return bn == 128 ? OzCfg<128>::Smem : OzCfg<256>::Smem; }
 
 cudaError_t launch_oz_sqrt(const double *delta, int64_t n, double *sp, cudaStream_t st)
 {
@@ -383,27 +344,26 @@ cudaError_t launch_oz_slice(const double2 *M, int64_t P, int ng, const double *s
     return cudaGetLastError();
 }
 
-cudaError_t launch_oz_gemm(const CUtensorMap *tmA, const CUtensorMap *tmB, int ng, int64_t kpad, int s, const int *E,
-                           double *chi, int *status, cudaStream_t st)
+cudaError_t launch_oz_gemm_jobs(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
+                                cudaStream_t st)
 {
-    OzParams pr;
-    pr.ng = ng;
-    pr.nrows = 2 * ng;
-    pr.nk = (int)(kpad / kOzBK);
-    pr.s = s;
-    pr.nJ = (pr.nrows + kOzBN - 1) / kOzBN;
-    pr.E = E;
-    pr.chi = chi;
-    pr.status = status;
-    const size_t sm = oz_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    oz_gemm_kernel<<<oz_tiles(ng), kOzThreads, sm, st>>>(*tmA, *tmB, pr);
+    if (nitems == 0) return cudaSuccess;
+    cudaError_t e;
+    if (bn == 128) {
+        e = cudaFuncSetAttribute(oz_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)OzCfg<128>::Smem);
+        if (e != cudaSuccess) return e;
+        oz_gemm_kernel<128><<<grid, kOzThreads, OzCfg<128>::Smem, st>>>(jobs, njobs, nitems, status);
+    } else {
+        e = cudaFuncSetAttribute(oz_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)OzCfg<256>::Smem);
+        if (e != cudaSuccess) return e;
+        oz_gemm_kernel<256><<<grid, kOzThreads, OzCfg<256>::Smem, st>>>(jobs, njobs, nitems, status);
+    }
     return cudaGetLastError();
 }
 
 int oz_box_rows_a() { return kOzBM; }
-int oz_box_rows_b() { return kOzBN; }
 int oz_box_k() { return kOzBK; }
 
 } // namespace gw
