@@ -136,6 +136,31 @@ GW_API gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, cons
                           double *diag);
 
 /*
+ * Batched forward chi0 (step a8): the same result and output packing as gw_chi0_compute,
+ * for many slots and frequencies at once.  Every requested slot's matrix elements are
+ * produced once and kept resident (library memory: sum over slots of P_q x N_G(q) x 16
+ * bytes, plus the split slices of one frequency in GW_PREC_OZAKI_BF16 mode); the
+ * contraction of all (q, w) blocks then runs as one persistent launch (FP64) or one
+ * persistent launch per frequency covering every slot (split precision), ordered largest
+ * block first.  The whole sequence is captured once per call signature (slots, sphere
+ * sizes, frequencies, output pointers) into a CUDA graph and replayed on later calls.
+ * On the first call of a problem shape an autotuner times the contraction's launch-shape
+ * candidates (FP64 tile edge 32/64 and wave count; split-precision tile width 128/256
+ * columns) and keeps the fastest for the handle (see gw_chi0_tuning).  The first call
+ * synchronises the stream; replays are asynchronous.  Slots must be distinct.
+ * Errors: as gw_chi0_compute; GW_ERR_OOM when the resident buffers do not fit.
+ */
+GW_API gw_status gw_chi0_compute_batch(gw_chi0 *h, int nq, const int *iq, int nw, const double *omega, double *chi,
+                                       double *diag);
+
+/*
+ * Launch shapes in use (chosen by the autotuner of gw_chi0_compute_batch, or defaults):
+ * FP64 tile edge (complex), FP64 waves, split-precision tile width (real columns).
+ * Returns the number of problem shapes tuned so far.  Any pointer may be NULL.
+ */
+GW_API int gw_chi0_tuning(const gw_chi0 *h, int *tile_f64, int *waves_f64, int *tile_split);
+
+/*
  * Stage (a) alone (steps a2-a4): M[p - pair_begin][g] for pairs p = v*nc + c in
  * [pair_begin, pair_begin + pair_count) of slot iq.  M: device complex128 [pair_count][ng].
  */

@@ -37,6 +37,8 @@ SIGNATURES = {
     "gw_chi0_set_bands": ([P, I, I, I, I, P, P, P], I),
     "gw_chi0_set_gsphere": ([P, I, I, P], I),
     "gw_chi0_compute": ([P, I, P, I, P, P, P], I),
+    "gw_chi0_compute_batch": ([P, I, P, I, P, P, P], I),
+    "gw_chi0_tuning": ([P, P, P, P], I),
     "gw_chi0_pair_elements": ([P, I, I64, I64, P], I),
     "gw_chi0_contract": ([P, I, I, P, P, I, P, I, P, P], I),
     "gw_chi0_adjoint": ([P, I, D, P, P, P, P, P, P], I),

@@ -85,8 +85,18 @@ class Chi0:
         self._check(self.lib.gw_chi0_set_gsphere(self.h, int(iq), gvec.shape[0], _ptr(gvec)))
         self.ng[iq] = gvec.shape[0]
 
+    def compute_batch(self, iq: Sequence[int], omega: Sequence[float], out: torch.Tensor | None = None,
+                      diag: bool = False):
+        """Batched chi0 (all slots and frequencies, graph-captured); same packing as ``compute``."""
+        return self.compute(iq, omega, out=out, diag=diag, _batch=True)
+
+    def tuning(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        n = self.lib.gw_chi0_tuning(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return {"tile_f64": a.value, "waves_f64": b.value, "tile_split": c.value, "shapes_tuned": n}
+
     def compute(self, iq: Sequence[int] | int, omega: Sequence[float], out: torch.Tensor | None = None,
-                diag: bool = False):
+                diag: bool = False, _batch: bool = False):
         """chi0 blocks: list (per slot) of [nw, ng, ng] complex128 views into one packed buffer."""
         iqs = [int(iq)] if isinstance(iq, int) else [int(x) for x in iq]
         om = [float(w) for w in omega]
@@ -100,7 +110,8 @@ class Chi0:
         iq_arr = (ctypes.c_int * len(iqs))(*iqs)
         om_arr = (ctypes.c_double * nw)(*om)
         self._use_current_stream()
-        self._check(self.lib.gw_chi0_compute(self.h, len(iqs), iq_arr, nw, om_arr, _ptr(out), _ptr(dg)))
+        fn = self.lib.gw_chi0_compute_batch if _batch else self.lib.gw_chi0_compute
+        self._check(fn(self.h, len(iqs), iq_arr, nw, om_arr, _ptr(out), _ptr(dg)))
         res, dres, off, doff = [], [], 0, 0
         for q in iqs:
             n = self.ng[q]

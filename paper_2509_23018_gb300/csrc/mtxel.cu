@@ -135,7 +135,22 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel(const double2 *__res
 
     for (int i0 = 0; i0 < n0; ++i0) {
         const double2 *sv = pv + (int64_t)i0 * ns, *sc = pc + (int64_t)i0 * ns;
-        for (int i = threadIdx.x; i < ns; i += blockDim.x) a[i] = cmulc(__ldg(sv + i), __ldg(sc + i));
+        for (int i = threadIdx.x; i < ns; i += 3 * blockDim.x) {
+            double2 xv[3], xc[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int k = i + u * blockDim.x;
+                if (k < ns) {
+                    xv[u] = __ldg(sv + k);
+                    xc[u] = __ldg(sc + k);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int k = i + u * blockDim.x;
+                if (k < ns) a[k] = cmulc(xv[u], xc[u]);
+            }
+        }
         __syncthreads();
         double2 *r = fft_lines(a, b, n1, n2, 1, pp.ax[2], tw2); // along i2
         double2 *o = (r == a) ? b : a;
@@ -205,7 +220,23 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel_tf(const float4 *__r
 
     for (int i0 = 0; i0 < n0; ++i0) {
         const float4 *sv = pv + (int64_t)i0 * ns, *sc = pc + (int64_t)i0 * ns;
-        for (int i = threadIdx.x; i < ns; i += blockDim.x) tc_store(a + i, tc_mulc(tc_load(sv + i), tc_load(sc + i)));
+        // three points per thread in flight, so the band loads overlap
+        for (int i = threadIdx.x; i < ns; i += 3 * blockDim.x) {
+            tcx xv[3], xc[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int k = i + u * blockDim.x;
+                if (k < ns) {
+                    xv[u] = tc_load(sv + k);
+                    xc[u] = tc_load(sc + k);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int k = i + u * blockDim.x;
+                if (k < ns) tc_store(a + k, tc_mulc(xv[u], xc[u]));
+            }
+        }
         __syncthreads();
         float4 *r = tfft_lines(a, b, n1, n2, 1, pp.ax[2], tw2, kc); // along i2
         float4 *o = (r == a) ? b : a;
