@@ -191,6 +191,7 @@ def ours(args):
     import torch
     import torch.distributed as dist
     import paper_2509_23018_gb300 as gw
+    from paper_2509_23018_gb300.shard import max_over_ranks
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -240,10 +241,7 @@ def ours(args):
     tim = h.timing(reset=True)
     h.set_timing(False)
     h.sync()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device=dev)
     ms_step = ms / args.steps
     value = conv_flops(cfg) * world * args.steps / (ms * 1e-3) * 1e-12
     launches = int(sum(v[1] for v in tim.values()))
@@ -293,10 +291,7 @@ def ours(args):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         es = t1 - t0
-        if world > 1:
-            t = torch.tensor([es], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            es = float(t.item())
+        es = max_over_ranks(es, device=dev)
         h2d = sum(x.numel() * x.element_size() for x in (hg, hcv, hcc, hev, hec, hgc))
         e2e = {"value": conv_flops(cfg) * world * args.steps / es * 1e-12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hout.numel() * hout.element_size()),
