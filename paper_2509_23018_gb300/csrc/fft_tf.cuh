@@ -227,3 +227,85 @@ __device__ inline float4 *tfft_lines(float4 *a, float4 *b, int nlines, int ls, i
 }
 
 } // namespace gw
+
+namespace gw {
+
+// ------------------------------------------------------------------ compile-time line plans
+// The same Stockham scheme with the line length known at compile time: the butterfly
+// and twiddle index arithmetic folds into constants, which matters because the two-float
+// butterflies leave little issue bandwidth to spare.  Radix order as on the host:
+// 3s, 5s, 4s, one 8 (a 2 merged with a 4), 2.
+struct RadPlan {
+    int nst;
+    int r[kMaxStages];
+};
+constexpr RadPlan make_rad_plan(int n)
+{
+    RadPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}};
+    int m = n, n4 = 0, n2 = 0, n3 = 0, n5 = 0;
+    while (m % 4 == 0) { ++n4; m /= 4; }
+    while (m % 2 == 0) { ++n2; m /= 2; }
+    while (m % 3 == 0) { ++n3; m /= 3; }
+    while (m % 5 == 0) { ++n5; m /= 5; }
+    int n8 = 0;
+    if (n2 && n4) { n2 = 0; --n4; n8 = 1; }
+    for (int i = 0; i < n3; ++i) p.r[p.nst++] = 3;
+    for (int i = 0; i < n5; ++i) p.r[p.nst++] = 5;
+    for (int i = 0; i < n4; ++i) p.r[p.nst++] = 4;
+    for (int i = 0; i < n8; ++i) p.r[p.nst++] = 8;
+    for (int i = 0; i < n2; ++i) p.r[p.nst++] = 2;
+    return p;
+}
+
+// lines of N contiguous points, line l at x + l * ls
+template <int N, int R, int NS>
+__device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines, int ls,
+                                          const float4 *__restrict__ tw, const TfConsts &k)
+{
+    constexpr int nb = N / R;
+    constexpr int tstride = N / (NS * R); // r * kk * tstride < N: no reduction needed
+    const int total = nlines * nb;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int l = b / nb, j = b - l * nb;
+        const int kk = j % NS;
+        const float4 *xl = x + l * ls;
+        tcx v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + j + r * nb);
+        if constexpr (NS > 1) {
+            const int e = kk * tstride;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = tc_mul(v[r], tc_load(tw + r * e));
+        }
+        tdftR<R>(v, k);
+        float4 *yl = y + l * ls;
+        const int o = (j / NS) * (NS * R) + kk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) tc_store(yl + o + r * NS, v[r]);
+    }
+}
+
+template <int N, int S, int NS>
+__device__ __forceinline__ float4 *tstages_ct(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
+                                              const TfConsts &k)
+{
+    constexpr RadPlan P = make_rad_plan(N);
+    if constexpr (S >= P.nst) {
+        return x;
+    } else {
+        constexpr int R = P.r[S];
+        tstage_ct<N, R, NS>(x, y, nlines, ls, tw, k);
+        __syncthreads();
+        return tstages_ct<N, S + 1, NS * R>(y, x, nlines, ls, tw, k);
+    }
+}
+
+// Full two-float transform of nlines contiguous lines of length N; returns the result buffer.
+template <int N>
+__device__ __forceinline__ float4 *tfft_lines_ct(float4 *a, float4 *b, int nlines, int ls, const float4 *tw,
+                                                 const TfConsts &k)
+{
+    return tstages_ct<N, 0, 1>(a, b, nlines, ls, tw, k);
+}
+
+} // namespace gw

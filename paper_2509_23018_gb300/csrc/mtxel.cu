@@ -10,6 +10,7 @@
 #include "internal.h"
 #include "fft.cuh"
 #include "fft_tf.cuh"
+#include "pair_tf_ct.cuh"
 
 namespace gw {
 
@@ -96,7 +97,6 @@ cudaError_t launch_band_fft(double2 *psi, int nb, const int n[3], const FftAxis 
 // transforms those columns along i1, and adds e^{+2 pi i k0 i0/n0} times the selected
 // (k1, k2) values into the per-G accumulators, which live in registers (NPT per thread).
 // The i0 axis is thus a direct sum onto the sphere, which also performs the gather.
-constexpr int kPairThreads = 256;
 
 template <int NPT>
 __global__ void __launch_bounds__(kPairThreads) pair_kernel(const double2 *__restrict__ psiv,
@@ -292,6 +292,16 @@ cudaError_t launch_pair_tf(const void *psiv, const void *psic, int nc, int64_t p
     tf inv = from(1.0 / ((double)pp.n[0] * pp.n[1] * pp.n[2]));
     const float4 *a = (const float4 *)psiv, *b = (const float4 *)psic;
     int need = (pp.ng + kPairThreads - 1) / kPairThreads;
+    if (need <= 32 && pp.n[1] == pp.n[2]) {
+        // grid-specialised kernels for the slab shapes of the standard workloads
+        switch (pp.n[1]) {
+        case 24: return launch_pair_tf_g24(a, b, nc, p0, count, pp, kc, inv, M, st);
+        case 40: return launch_pair_tf_g40(a, b, nc, p0, count, pp, kc, inv, M, st);
+        case 48: return launch_pair_tf_g48(a, b, nc, p0, count, pp, kc, inv, M, st);
+        case 72: return launch_pair_tf_g72(a, b, nc, p0, count, pp, kc, inv, M, st);
+        default: break;
+        }
+    }
     if (need <= 2) return launch_pair_tf_t<2>(a, b, nc, p0, count, pp, kc, inv, M, st);
     if (need <= 4) return launch_pair_tf_t<4>(a, b, nc, p0, count, pp, kc, inv, M, st);
     if (need <= 8) return launch_pair_tf_t<8>(a, b, nc, p0, count, pp, kc, inv, M, st);

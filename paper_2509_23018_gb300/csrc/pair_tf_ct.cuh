@@ -1,0 +1,132 @@
+// Two-float pair kernel specialised for a slab shape N1 x N2 known at compile time
+// (instantiated per grid in pair_tf_g*.cu so the translation units compile in parallel).
+// It is the algorithm of pair_kernel_tf in mtxel.cu with constant index arithmetic.
+#pragma once
+#include "internal.h"
+#include "fft_tf.cuh"
+
+namespace gw {
+
+constexpr int kPairThreads = 256;
+
+// Grid-specialised version: slab dimensions N1 x N2 known at compile time.
+template <int NPT, int N1, int N2>
+__global__ void __launch_bounds__(kPairThreads) pair_kernel_tf_ct(const float4 *__restrict__ psiv,
+                                                                   const float4 *__restrict__ psic, int nc, int64_t p0,
+                                                                   PairPlan pp, TfConsts kc, tf inv_nr,
+                                                                   double2 *__restrict__ M)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int ns = N1 * N2;
+    const int n0 = pp.n[0];
+    float4 *a = (float4 *)smem, *b = a + ns;
+    float4 *tw0 = b + ns, *tw1 = tw0 + n0, *tw2 = tw1 + N1;
+    int *kz = (int *)(tw2 + N2);
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) tw0[i] = pp.ax[0].twf[i];
+    for (int i = threadIdx.x; i < N1; i += blockDim.x) tw1[i] = pp.ax[1].twf[i];
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) tw2[i] = pp.ax[2].twf[i];
+    for (int i = threadIdx.x; i < pp.K2; i += blockDim.x) kz[i] = pp.kz[i];
+    const int K2 = pp.K2;
+
+    const int64_t p = p0 + blockIdx.x;
+    const int v = (int)(p / nc), c = (int)(p - (int64_t)v * nc);
+    const int64_t nr = (int64_t)n0 * ns;
+    const float4 *pv = psiv + (int64_t)v * nr;
+    const float4 *pc = psic + (int64_t)c * nr;
+
+    tcx F[NPT];
+    int sel[NPT], k0[NPT], e0[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        int g = threadIdx.x + j * kPairThreads;
+        F[j] = {{0.f, 0.f}, {0.f, 0.f}};
+        int pk = (g < pp.ng) ? pp.gpack[g] : 0;
+        k0[j] = pk & 255;
+        sel[j] = (pk >> 16) * N1 + ((pk >> 8) & 255);
+        e0[j] = 0;
+    }
+    __syncthreads();
+
+    for (int i0 = 0; i0 < n0; ++i0) {
+        const float4 *sv = pv + (int64_t)i0 * ns, *sc = pc + (int64_t)i0 * ns;
+        constexpr int per = (ns + kPairThreads - 1) / kPairThreads;
+        constexpr int PF = per < 3 ? per : 3;
+        for (int i = threadIdx.x; i < ns; i += PF * kPairThreads) {
+            tcx xv[PF], xc[PF];
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int kk = i + u * kPairThreads;
+                if (kk < ns) {
+                    xv[u] = tc_load(sv + kk);
+                    xc[u] = tc_load(sc + kk);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int kk = i + u * kPairThreads;
+                if (kk < ns) tc_store(a + kk, tc_mulc(xv[u], xc[u]));
+            }
+        }
+        __syncthreads();
+        float4 *r = tfft_lines_ct<N2>(a, b, N1, N2, tw2, kc); // along i2
+        float4 *o = (r == a) ? b : a;
+        for (int i = threadIdx.x; i < K2 * N1; i += blockDim.x) {
+            const int q = i / N1, i1 = i - q * N1;
+            o[i] = r[i1 * N2 + kz[q]];
+        }
+        __syncthreads();
+        float4 *t = tfft_lines_ct<N1>(o, r, K2, N1, tw1, kc); // along i1 on the kept columns
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            tcx u = tc_mul(tc_load(t + sel[j]), tc_load(tw0 + e0[j]));
+            F[j] = tc_add(F[j], u);
+            e0[j] += k0[j];
+            if (e0[j] >= n0) e0[j] -= n0;
+        }
+        __syncthreads();
+    }
+    double2 *out = M + (int64_t)blockIdx.x * pp.ng;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        int g = threadIdx.x + j * kPairThreads;
+        if (g < pp.ng) out[g] = make_double2(tf_to_d(tf_mul(F[j].re, inv_nr)), tf_to_d(tf_mul(F[j].im, inv_nr)));
+    }
+}
+
+template <int NPT, int N1, int N2>
+inline cudaError_t launch_pair_tf_ct(const float4 *psiv, const float4 *psic, int nc, int64_t p0, int64_t count,
+                                     const PairPlan &pp, const TfConsts &kc, tf inv_nr, double2 *M, cudaStream_t st)
+{
+    size_t sm = sizeof(float4) * (2 * (size_t)N1 * N2 + pp.n[0] + N1 + N2) + sizeof(int) * pp.K2;
+    cudaError_t e =
+        cudaFuncSetAttribute(pair_kernel_tf_ct<NPT, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    pair_kernel_tf_ct<NPT, N1, N2><<<(unsigned)count, kPairThreads, sm, st>>>(psiv, psic, nc, p0, pp, kc, inv_nr, M);
+    return cudaGetLastError();
+}
+
+template <int N1, int N2>
+inline cudaError_t launch_pair_tf_grid(const float4 *a, const float4 *b, int nc, int64_t p0, int64_t count,
+                                       const PairPlan &pp, const TfConsts &kc, tf inv, double2 *M, cudaStream_t st)
+{
+    int need = (pp.ng + kPairThreads - 1) / kPairThreads;
+    if (need <= 2) return launch_pair_tf_ct<2, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 4) return launch_pair_tf_ct<4, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 8) return launch_pair_tf_ct<8, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 12) return launch_pair_tf_ct<12, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 16) return launch_pair_tf_ct<16, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 24) return launch_pair_tf_ct<24, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    return launch_pair_tf_ct<32, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+}
+
+
+cudaError_t launch_pair_tf_g24(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,
+                               const TfConsts &, tf, double2 *, cudaStream_t);
+cudaError_t launch_pair_tf_g40(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,
+                               const TfConsts &, tf, double2 *, cudaStream_t);
+cudaError_t launch_pair_tf_g48(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,
+                               const TfConsts &, tf, double2 *, cudaStream_t);
+cudaError_t launch_pair_tf_g72(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,
+                               const TfConsts &, tf, double2 *, cudaStream_t);
+
+} // namespace gw

@@ -1,0 +1,12 @@
+// Two-float pair kernel instantiated for 24 x 24 slabs.
+#include "pair_tf_ct.cuh"
+
+namespace gw {
+
+cudaError_t launch_pair_tf_g24(const float4 *a, const float4 *b, int nc, int64_t p0, int64_t count,
+                               const PairPlan &pp, const TfConsts &kc, tf inv, double2 *M, cudaStream_t st)
+{
+    return launch_pair_tf_grid<24, 24>(a, b, nc, p0, count, pp, kc, inv, M, st);
+}
+
+} // namespace gw
