@@ -1010,17 +1010,17 @@ gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngpsi, con
     CK(h, cudaMemcpyAsync(nbs.gvec, gvec, sizeof(int32_t) * 3 * ngpsi, cudaMemcpyDeviceToDevice, h->st), "gvec");
     CK(h, cudaMemcpyAsync(nbs.gofs, gofs.data(), sizeof(int32_t) * ngpsi, cudaMemcpyHostToDevice, h->st), "gofs");
     CK(h, cudaMemsetAsync(nbs.psi, 0, sizeof(double2) * (size_t)nb * h->nr, h->st), "zero psi");
-    {
-        Scope sc(h, "band_scatter");
-        CK(h, gw::launch_scatter((const double2 *)coeff, nbs.gofs, nb, ngpsi, h->nr, nbs.psi, h->st), "scatter");
-    }
-    {
+    if (h->d.mtxel_prec == GW_MTXEL_TWOFLOAT) {
+        Scope sc(h, "band_setup_tf");
+        CK(h, gw::launch_band_setup_tf((const double2 *)coeff, nbs.gofs, nb, ngpsi, nbs.psi, h->d.n, h->ax, h->st),
+           "band setup (two-float)"); // three kernels
+    } else {
+        {
+            Scope sc(h, "band_scatter");
+            CK(h, gw::launch_scatter((const double2 *)coeff, nbs.gofs, nb, ngpsi, h->nr, nbs.psi, h->st), "scatter");
+        }
         Scope sc(h, "band_fft");
         CK(h, gw::launch_band_fft(nbs.psi, nb, h->d.n, h->ax, h->st), "band fft"); // two kernels
-    }
-    if (h->d.mtxel_prec == GW_MTXEL_TWOFLOAT) {
-        Scope sc(h, "band_to_twofloat");
-        CK(h, gw::launch_psi_to_tf(nbs.psi, (int64_t)nb * h->nr, h->st), "psi to two-float");
     }
     CK(h, cudaStreamSynchronize(h->st), "set_bands sync"); // gofs host vector goes out of scope
     dst = std::move(nbs);

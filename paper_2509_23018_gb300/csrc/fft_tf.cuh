@@ -285,6 +285,56 @@ __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *
     }
 }
 
+// Last stage variant: output i of line l goes to y[pos[i] * cls + l] when pos[i] >= 0 and is
+// dropped otherwise (an output-pruned transform whose kept outputs land transposed).
+template <int N, int R, int NS>
+__device__ __forceinline__ void tstage_ct_keep(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines,
+                                               int ls, const float4 *__restrict__ tw, const TfConsts &k,
+                                               const int *__restrict__ pos, int cls)
+{
+    constexpr int nb = N / R;
+    constexpr int tstride = N / (NS * R);
+    const int total = nlines * nb;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+        const int l = b / nb, j = b - l * nb;
+        const int kk = j % NS;
+        const float4 *xl = x + l * ls;
+        tcx v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + j + r * nb);
+        if constexpr (NS > 1) {
+            const int e = kk * tstride;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = tc_mul(v[r], tc_load(tw + r * e));
+        }
+        tdftR<R>(v, k);
+        const int o = (j / NS) * (NS * R) + kk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int q = pos[o + r * NS];
+            if (q >= 0) tc_store(y + q * cls + l, v[r]);
+        }
+    }
+}
+
+// All stages; the last one keeps only the outputs listed in pos (see tstage_ct_keep).
+template <int N, int S, int NS>
+__device__ __forceinline__ float4 *tstages_ct_keep(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
+                                                   const TfConsts &k, const int *pos, int cls)
+{
+    constexpr RadPlan P = make_rad_plan(N);
+    constexpr int R = P.r[S];
+    if constexpr (S + 1 == P.nst) {
+        tstage_ct_keep<N, R, NS>(x, y, nlines, ls, tw, k, pos, cls);
+        __syncthreads();
+        return y;
+    } else {
+        tstage_ct<N, R, NS>(x, y, nlines, ls, tw, k);
+        __syncthreads();
+        return tstages_ct_keep<N, S + 1, NS * R>(y, x, nlines, ls, tw, k, pos, cls);
+    }
+}
+
 template <int N, int S, int NS>
 __device__ __forceinline__ float4 *tstages_ct(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
                                               const TfConsts &k)

@@ -30,11 +30,13 @@ struct PairPlan {
 cudaError_t launch_pair(const double2 *psiv, const double2 *psic, int nc, int64_t p0, int64_t count,
                         const PairPlan &pp, double2 *M, cudaStream_t st);
 int pair_max_ng();
-// the same in two-float arithmetic; psiv/psic hold two-float grids (launch_psi_to_tf)
+// the same in two-float arithmetic; psiv/psic hold two-float grids (launch_band_setup_tf)
 cudaError_t launch_pair_tf(const void *psiv, const void *psic, int nc, int64_t p0, int64_t count,
                            const PairPlan &pp, double2 *M, cudaStream_t st);
-// in-place conversion of n FP64 complex grid values to two-float form
-cudaError_t launch_psi_to_tf(void *psi, int64_t n, cudaStream_t st);
+// band setup in two-float arithmetic: scatter (with hi/lo split) + 3D FFT, psi in two-float form
+cudaError_t launch_band_setup_tf(const double2 *coeff, const int32_t *gofs, int nb, int ngpsi, void *psi,
+                                 const int n[3], const FftAxis ax[3], cudaStream_t st);
+
 
 // ---- energy factor, diagonal, symmetrisation (reduce.cu)
 // delta[w][p - p0] = 4x/(x^2 + w^2), x = ev[v] - ec[c]

@@ -91,6 +91,100 @@ cudaError_t launch_band_fft(double2 *psi, int nb, const int n[3], const FftAxis 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ a1 in two-float arithmetic
+// Coefficients are split into hi + lo FP32 pairs as they are scattered; the three axes
+// are then transformed in two-float arithmetic, in place, with the same kernels' layout.
+__global__ void scatter_tf_kernel(const double2 *__restrict__ coeff, const int32_t *__restrict__ gofs, int nb,
+                                  int ngpsi, int64_t nr, float4 *__restrict__ psi)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t tot = (int64_t)nb * ngpsi;
+    if (i >= tot) return;
+    int b = (int)(i / ngpsi), k = (int)(i - (int64_t)b * ngpsi);
+    double2 z = coeff[i];
+    float rh = __double2float_rn(z.x), ih = __double2float_rn(z.y);
+    psi[(int64_t)b * nr + gofs[k]] =
+        make_float4(rh, __double2float_rn(z.x - (double)rh), ih, __double2float_rn(z.y - (double)ih));
+}
+
+__global__ void __launch_bounds__(256) band_fft_slab_tf_kernel(float4 *__restrict__ psi, int n0, int n1, int n2,
+                                                                FftAxis ax1, FftAxis ax2, TfConsts kc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ns = n1 * n2;
+    float4 *a = (float4 *)smem, *b = a + ns, *tw1 = b + ns, *tw2 = tw1 + n1;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = ax1.twf[i];
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = ax2.twf[i];
+    float4 *g = psi + ((int64_t)blockIdx.y * n0 + blockIdx.x) * ns;
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) a[i] = g[i];
+    __syncthreads();
+    float4 *r = tfft_lines(a, b, n1, n2, 1, ax2, tw2, kc);  // along i2
+    float4 *o = (r == a) ? b : a;
+    r = tfft_lines(r, o, n2, 1, n2, ax1, tw1, kc);          // along i1 (strided lines)
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) g[i] = r[i];
+}
+
+__global__ void __launch_bounds__(256) band_fft_axis0_tf_kernel(float4 *__restrict__ psi, int n0, int n1, int n2,
+                                                                 FftAxis ax0, TfConsts kc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int np = n0 * n2;
+    float4 *a = (float4 *)smem, *b = a + np, *tw0 = b + np;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) tw0[i] = ax0.twf[i];
+    float4 *g = psi + (int64_t)blockIdx.y * n0 * n1 * n2 + (int64_t)blockIdx.x * n2;
+    const int64_t rs = (int64_t)n1 * n2;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        int i0 = i / n2, i2 = i - i0 * n2;
+        a[i] = g[i0 * rs + i2];
+    }
+    __syncthreads();
+    float4 *r = tfft_lines(a, b, n2, 1, n2, ax0, tw0, kc);   // lines along i0, stride n2
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        int i0 = i / n2, i2 = i - i0 * n2;
+        g[i0 * rs + i2] = r[i];
+    }
+}
+
+TfConsts tf_consts()
+{
+    auto from = [](double x) {
+        float h = (float)x;
+        return tf{h, (float)(x - (double)h)};
+    };
+    TfConsts kc;
+    kc.sin60 = from(kSin60);
+    kc.c1 = from(kC1);
+    kc.s1 = from(kS1);
+    kc.c2 = from(kC2);
+    kc.s2 = from(kS2);
+    kc.rs2 = from(kRs2);
+    return kc;
+}
+
+cudaError_t launch_band_setup_tf(const double2 *coeff, const int32_t *gofs, int nb, int ngpsi, void *psi,
+                                 const int n[3], const FftAxis ax[3], cudaStream_t st)
+{
+    const int64_t nr = (int64_t)n[0] * n[1] * n[2];
+    const int64_t tot = (int64_t)nb * ngpsi;
+    if (tot == 0) return cudaSuccess;
+    float4 *p = (float4 *)psi;
+    scatter_tf_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(coeff, gofs, nb, ngpsi, nr, p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const TfConsts kc = tf_consts();
+    size_t sm1 = sizeof(float4) * (2 * (size_t)n[1] * n[2] + n[1] + n[2]);
+    size_t sm0 = sizeof(float4) * (2 * (size_t)n[0] * n[2] + n[0]);
+    if ((e = cudaFuncSetAttribute(band_fft_slab_tf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(band_fft_axis0_tf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0)) !=
+            cudaSuccess)
+        return e;
+    band_fft_slab_tf_kernel<<<dim3(n[0], nb), 256, sm1, st>>>(p, n[0], n[1], n[2], ax[1], ax[2], kc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    band_fft_axis0_tf_kernel<<<dim3(n[1], nb), 256, sm0, st>>>(p, n[0], n[1], n[2], ax[0], kc);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ a2-a4: fused pair kernel
 // One block per pair.  The block walks the n0 slabs of the grid; per slab it forms the
 // pair product, transforms along i2 (all lines), keeps the K2 needed i2-frequencies,
@@ -180,7 +274,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel(const double2 *__res
 int pair_max_ng() { return 32 * kPairThreads; }
 
 // Same algorithm as pair_kernel, in two-float arithmetic on the FP32 pipes.  The band
-// grids hold (re.hi, re.lo, im.hi, im.lo) per point (see launch_psi_to_tf); the output
+// grids hold (re.hi, re.lo, im.hi, im.lo) per point (see launch_band_setup_tf); the output
 // M is FP64.
 template <int NPT>
 __global__ void __launch_bounds__(kPairThreads) pair_kernel_tf(const float4 *__restrict__ psiv,
@@ -278,18 +372,10 @@ cudaError_t launch_pair_tf(const void *psiv, const void *psic, int nc, int64_t p
                            double2 *M, cudaStream_t st)
 {
     if (count == 0) return cudaSuccess;
-    TfConsts kc;
-    auto from = [](double x) {
-        float h = (float)x;
-        return tf{h, (float)(x - (double)h)};
-    };
-    kc.sin60 = from(kSin60);
-    kc.c1 = from(kC1);
-    kc.s1 = from(kS1);
-    kc.c2 = from(kC2);
-    kc.s2 = from(kS2);
-    kc.rs2 = from(kRs2);
-    tf inv = from(1.0 / ((double)pp.n[0] * pp.n[1] * pp.n[2]));
+    const TfConsts kc = tf_consts();
+    const double invd = 1.0 / ((double)pp.n[0] * pp.n[1] * pp.n[2]);
+    const float invh = (float)invd;
+    const tf inv{invh, (float)(invd - (double)invh)};
     const float4 *a = (const float4 *)psiv, *b = (const float4 *)psic;
     int need = (pp.ng + kPairThreads - 1) / kPairThreads;
     if (need <= 32 && pp.n[1] == pp.n[2]) {
@@ -312,23 +398,6 @@ cudaError_t launch_pair_tf(const void *psiv, const void *psic, int nc, int64_t p
     return cudaErrorInvalidValue;
 }
 
-// In place: FP64 complex grid values -> two-float (re.hi, re.lo, im.hi, im.lo); both are 16 bytes.
-__global__ void psi_to_tf_kernel(double2 *__restrict__ psi, int64_t n)
-{
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double2 z = psi[i];
-    float rh = __double2float_rn(z.x), ih = __double2float_rn(z.y);
-    float4 o = make_float4(rh, __double2float_rn(z.x - (double)rh), ih, __double2float_rn(z.y - (double)ih));
-    *(float4 *)(psi + i) = o;
-}
-
-cudaError_t launch_psi_to_tf(void *psi, int64_t n, cudaStream_t st)
-{
-    if (n == 0) return cudaSuccess;
-    psi_to_tf_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((double2 *)psi, n);
-    return cudaGetLastError();
-}
 
 template <int NPT>
 static cudaError_t launch_pair_t(const double2 *psiv, const double2 *psic, int nc, int64_t p0, int64_t count,

@@ -21,11 +21,15 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel_tf_ct(const float4 *
     const int n0 = pp.n[0];
     float4 *a = (float4 *)smem, *b = a + ns;
     float4 *tw0 = b + ns, *tw1 = tw0 + n0, *tw2 = tw1 + N1;
-    int *kz = (int *)(tw2 + N2);
+    int *pos = (int *)(tw2 + N2); // pos[k2] = index of k2 among the kept i2-frequencies, or -1
     for (int i = threadIdx.x; i < n0; i += blockDim.x) tw0[i] = pp.ax[0].twf[i];
     for (int i = threadIdx.x; i < N1; i += blockDim.x) tw1[i] = pp.ax[1].twf[i];
-    for (int i = threadIdx.x; i < N2; i += blockDim.x) tw2[i] = pp.ax[2].twf[i];
-    for (int i = threadIdx.x; i < pp.K2; i += blockDim.x) kz[i] = pp.kz[i];
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+        tw2[i] = pp.ax[2].twf[i];
+        pos[i] = -1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < pp.K2; i += blockDim.x) pos[pp.kz[i]] = i;
     const int K2 = pp.K2;
 
     const int64_t p = p0 + blockIdx.x;
@@ -49,6 +53,14 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel_tf_ct(const float4 *
 
     for (int i0 = 0; i0 < n0; ++i0) {
         const float4 *sv = pv + (int64_t)i0 * ns, *sc = pc + (int64_t)i0 * ns;
+        if (i0 + 1 < n0) {
+            // pull the next slab of both bands towards L2 while this one is transformed
+            const char *nv = (const char *)(sv + ns), *nc2 = (const char *)(sc + ns);
+            for (int o = threadIdx.x * 128; o < ns * 16; o += blockDim.x * 128) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nv + o));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nc2 + o));
+            }
+        }
         constexpr int per = (ns + kPairThreads - 1) / kPairThreads;
         constexpr int PF = per < 3 ? per : 3;
         for (int i = threadIdx.x; i < ns; i += PF * kPairThreads) {
@@ -68,13 +80,9 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel_tf_ct(const float4 *
             }
         }
         __syncthreads();
-        float4 *r = tfft_lines_ct<N2>(a, b, N1, N2, tw2, kc); // along i2
-        float4 *o = (r == a) ? b : a;
-        for (int i = threadIdx.x; i < K2 * N1; i += blockDim.x) {
-            const int q = i / N1, i1 = i - q * N1;
-            o[i] = r[i1 * N2 + kz[q]];
-        }
-        __syncthreads();
+        // along i2; the last stage writes only the kept frequencies, as columns [k2'][i1]
+        float4 *o = tstages_ct_keep<N2, 0, 1>(a, b, N1, N2, tw2, kc, pos, N1);
+        float4 *r = (o == a) ? b : a;
         float4 *t = tfft_lines_ct<N1>(o, r, K2, N1, tw1, kc); // along i1 on the kept columns
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
@@ -97,7 +105,7 @@ template <int NPT, int N1, int N2>
 inline cudaError_t launch_pair_tf_ct(const float4 *psiv, const float4 *psic, int nc, int64_t p0, int64_t count,
                                      const PairPlan &pp, const TfConsts &kc, tf inv_nr, double2 *M, cudaStream_t st)
 {
-    size_t sm = sizeof(float4) * (2 * (size_t)N1 * N2 + pp.n[0] + N1 + N2) + sizeof(int) * pp.K2;
+    size_t sm = sizeof(float4) * (2 * (size_t)N1 * N2 + pp.n[0] + N1 + N2) + sizeof(int) * N2;
     cudaError_t e =
         cudaFuncSetAttribute(pair_kernel_tf_ct<NPT, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
