@@ -7,7 +7,14 @@ grid, 128 valence + 1024 conduction bands on a 6000-G wavefunction sphere,
 N_G = 2000, chunks of 8192 pairs, omega = 0 (about 4.2 TFLOP in the contraction
 by the 8 N_G^2 P convention).
 
+The headline mode is the split-precision contraction (7 BF16 slices, two-float stage
+(a)) with its error against the oracle stated on sampled entries; the same line carries
+the native FP64 tensor-core path on the same input under "fp64_dmma".
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|ozaki] [--impl ours|reference]
+    python bench.py --sweep      slice-count sweep on one 72^3 chunk (error and throughput)
+    python bench.py --batch      64 q-points x 16 frequencies in one graph (40^3)
+    python bench.py --adjoint    adjoint of Re Tr(W chi) on 40^3, 96+768 bands, N_G = 1500
 
 Multi-GPU: the path has no exchange step; N ranks run N independent q-points
 (weak scaling, no collective on the data path).
@@ -39,8 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "ozaki"])
-    ap.add_argument("--nslices", type=int, default=6)
+    ap.add_argument("--prec", default="ozaki", choices=["fp64", "ozaki"])
+    ap.add_argument("--nslices", type=int, default=7)
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the native FP64 DMMA run on the same input (split-precision mode only)")
     ap.add_argument("--mtxel", default=None, choices=["fp64", "twofloat"],
                     help="stage (a) arithmetic; default fp64 with --prec fp64, twofloat with --prec ozaki")
     ap.add_argument("--config", default="c2_48cube", choices=sorted(gwgen.CONFIGS))
@@ -48,6 +57,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-pairs", type=int, default=4096)
     ap.add_argument("--no-check", action="store_true", help="skip the sampled error check against the oracle")
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--batch", action="store_true")
+    ap.add_argument("--adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -187,27 +199,18 @@ def peak_for(prec):
     return bf16_sus, f"of {src} bf16 sustained"
 
 
-def ours(args):
+def run_mode(args, cfg, prob, dev, prec, nslices, mtxel, steps, warmup, with_e2e, world):
+    """Time `steps` passes of the whole path in one precision mode; returns a result dict."""
     import torch
-    import torch.distributed as dist
     import paper_2509_23018_gb300 as gw
     from paper_2509_23018_gb300.shard import max_over_ranks
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    cfg = gwgen.CONFIGS[args.config]
-    seed = gwgen.BASE_SEED + cfg.index + 1000 * rank  # each rank: its own q-point
-    prob = gwgen.config_problem(cfg, seed=seed)
-    dev = torch.device("cuda", local)
     gpsi = torch.as_tensor(prob.gpsi, device=dev)
     cv, cc = torch.as_tensor(prob.cv, device=dev), torch.as_tensor(prob.cc, device=dev)
     ev, ec = torch.as_tensor(prob.ev, device=dev), torch.as_tensor(prob.ec, device=dev)
     gchi = torch.as_tensor(prob.gchi, device=dev)
     omega = [0.0]
-    mtxel = args.mtxel or ("fp64" if args.prec == "fp64" else "twofloat")
-    h = gw.Chi0(cfg.grid, nq=1, prec=args.prec, nslices=args.nslices, pair_chunk=cfg.pair_chunk, mtxel=mtxel)
+    h = gw.Chi0(cfg.grid, nq=1, prec=prec, nslices=nslices, pair_chunk=cfg.pair_chunk, mtxel=mtxel)
     chi = torch.empty(cfg.ng * cfg.ng, dtype=torch.complex128, device=dev)
     h.ng[0] = cfg.ng
 
@@ -217,57 +220,36 @@ def ours(args):
         h.set_gsphere(0, gchi)
         h.compute(0, omega, out=chi)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     h.sync()
     h.set_timing(True)
     h.timing(reset=True)
-    clk = Clocks(local)
+    clk = Clocks(dev.index)
     clk.start()
     if world > 1:
-        dist.barrier()
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record()
     torch.cuda.synchronize()
     if world > 1:
-        dist.barrier()
+        torch.distributed.barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), device=dev)
     tim = h.timing(reset=True)
     h.set_timing(False)
     h.sync()
-    ms = max_over_ranks(ms, device=dev)
-    ms_step = ms / args.steps
-    value = conv_flops(cfg) * world * args.steps / (ms * 1e-3) * 1e-12
-    launches = int(sum(v[1] for v in tim.values()))
+    res = {"ms_per_step": ms / steps, "value": conv_flops(cfg) * world * steps / (ms * 1e-3) * 1e-12,
+           "launches": int(sum(v[1] for v in tim.values())), "kernel_ms": {k: v[0] for k, v in tim.items()},
+           "clocks": clocks, "timing": tim, "total_ms": ms}
 
-    # dominant kernel: the contraction
-    kname = "contract_f64" if args.prec == "fp64" else "ozaki_gemm"
-    kms, kn = tim.get(kname, (0.0, 0))
-    nchunk = -(-cfg.npairs // cfg.pair_chunk)
-    per_launch_flops = 4.0 * cfg.ng * (cfg.ng + 1) * cfg.npairs / nchunk
-    if args.prec == "ozaki":
-        # low-precision flops of the kept slice pairs: s(s+1)/2 x 4 N_G^2 P per chunk and frequency
-        per_launch_flops = args.nslices * (args.nslices + 1) / 2 * 4.0 * cfg.ng ** 2 * cfg.npairs / nchunk
-    peak, peak_src = peak_for(args.prec)
-    achieved = per_launch_flops / (kms / kn * 1e-3) * 1e-12 if kn else None
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None, "kernel": kname,
-                "launches": kn, "ms_per_launch": kms / kn if kn else None,
-                "flops_per_launch": per_launch_flops, "peak_source": peak_src,
-                "share_of_step": kms / ms if ms else None,
-                "fp64_probe_peaks_tflops": {"dmma": 1.055, "dfma": 1.204},
-                "traffic_source": TRAFFIC.get(kname, {}).get("source")}
-    roofline["traffic"] = TRAFFIC.get(kname, {}).get("bytes_per_launch")
-
-    # end to end through the public API with host buffers (pinned), H2D inputs + D2H result
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         hcv, hcc = cv.cpu().pin_memory(), cc.cpu().pin_memory()
         hev, hec = ev.cpu().pin_memory(), ec.cpu().pin_memory()
         hg, hgc = gpsi.cpu().pin_memory(), gchi.cpu().pin_memory()
@@ -284,51 +266,195 @@ def ours(args):
         e2e_step()
         torch.cuda.synchronize()
         if world > 1:
-            dist.barrier()
+            torch.distributed.barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             e2e_step()
         torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        es = t1 - t0
-        es = max_over_ranks(es, device=dev)
+        es = max_over_ranks(time.perf_counter() - t0, device=dev)
         h2d = sum(x.numel() * x.element_size() for x in (hg, hcv, hcc, hev, hec, hgc))
-        e2e = {"value": conv_flops(cfg) * world * args.steps / es * 1e-12, "unit": "TFLOP/s",
+        e2e = {"value": conv_flops(cfg) * world * steps / es * 1e-12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hout.numel() * hout.element_size()),
-               "ms_per_step": 1e3 * es / args.steps}
+               "ms_per_step": 1e3 * es / steps}
+    res["e2e"] = e2e
+    res["chi"] = chi.view(cfg.ng, cfg.ng).cpu().numpy()
+    h.destroy()
+    return res
 
+
+def roofline_for(cfg, prec, nslices, res):
+    kname = "contract_f64" if prec == "fp64" else "ozaki_gemm"
+    kms, kn = res["timing"].get(kname, (0.0, 0))
+    nchunk = -(-cfg.npairs // cfg.pair_chunk)
+    per_launch_flops = 4.0 * cfg.ng * (cfg.ng + 1) * cfg.npairs / nchunk
+    if prec == "ozaki":
+        # low-precision flops of the kept slice pairs: s(s+1)/2 x 4 N_G^2 P per chunk and frequency
+        per_launch_flops = nslices * (nslices + 1) / 2 * 4.0 * cfg.ng ** 2 * cfg.npairs / nchunk
+    peak, peak_src = peak_for(prec)
+    achieved = per_launch_flops / (kms / kn * 1e-3) * 1e-12 if kn else None
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": TRAFFIC.get(kname, {}).get("bytes_per_launch"), "kernel": kname,
+            "launches": kn, "ms_per_launch": kms / kn if kn else None, "flops_per_launch": per_launch_flops,
+            "peak_source": peak_src, "share_of_step": kms / res["total_ms"] if res["total_ms"] else None,
+            "traffic_source": TRAFFIC.get(kname, {}).get("source"),
+            "fp64_probe_peaks_tflops": {"dmma": 1.055, "dfma": 1.204}}
+
+
+def ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    cfg = gwgen.CONFIGS[args.config]
+    seed = gwgen.BASE_SEED + cfg.index + 1000 * rank  # each rank: its own q-point
+    prob = gwgen.config_problem(cfg, seed=seed)
+    dev = torch.device("cuda", local)
+    mtxel = args.mtxel or ("fp64" if args.prec == "fp64" else "twofloat")
+    main = run_mode(args, cfg, prob, dev, args.prec, args.nslices, mtxel, args.steps, args.warmup,
+                    not args.no_e2e, world)
+    roofline = roofline_for(cfg, args.prec, args.nslices, main)
     err = None
     if rank == 0 and not args.no_check:
-        e, how = sampled_error(cfg, prob, chi.view(cfg.ng, cfg.ng).cpu().numpy())
+        e, how = sampled_error(cfg, prob, main["chi"])
         err = {"rel_frobenius_vs_oracle": e, "sample": how}
+    # the native FP64 tensor-core path on the same input, for the FP64-vs-split comparison
+    other = None
+    if args.prec == "ozaki" and not args.no_fp64_compare:
+        f = run_mode(args, cfg, prob, dev, "fp64", 0, "fp64", max(1, min(2, args.steps)), 1, False, world)
+        other = {"value": f["value"], "unit": "TFLOP/s", "ms_per_q": f["ms_per_step"], "mtxel": "fp64",
+                 "roofline": roofline_for(cfg, "fp64", 0, f), "kernel_ms_per_step":
+                     {k: v / max(1, min(2, args.steps)) for k, v in f["kernel_ms"].items()}}
+        if rank == 0 and not args.no_check:
+            other["rel_frobenius_vs_oracle"], _ = sampled_error(cfg, prob, f["chi"])
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, prob, args.cpu_sample_pairs)
         cpu.pop("seconds", None)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_q": ms_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "bf16-split/f64",
-                "data": "synthetic",
+        line = {"metric": METRIC, "value": main["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "ms_per_q": main["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.prec == "fp64" else "bf16-split/f64", "data": "synthetic",
                 "config": {"workload": f"{cfg.name}: grid {cfg.grid[0]}^3, {cfg.nv}+{cfg.nc} bands, "
                                        f"N_Gpsi={cfg.ngpsi}, N_G={cfg.ng}, chunks of {cfg.pair_chunk} pairs, omega=0",
                            "prec": args.prec, "nslices": args.nslices if args.prec == "ozaki" else None,
-                           "mtxel": mtxel,
-                           "pairs": cfg.npairs, "conv_tflop_per_step": conv_flops(cfg) * 1e-12,
+                           "mtxel": mtxel, "pairs": cfg.npairs, "conv_tflop_per_step": conv_flops(cfg) * 1e-12,
                            "l2": "inputs larger than L2 (psi grids 2.0 GB, M chunks 262 MB)",
                            "parallelism": f"replicas x{world} (independent q-points)"},
-                "error": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "kernel_ms": {k: v[0] for k, v in tim.items()}, "clocks": clocks}
+                "error": err, "roofline": roofline, "fp64_dmma": other, "cpu_baseline": cpu, "e2e": main["e2e"],
+                "gpu_launches": main["launches"], "kernel_ms": main["kernel_ms"], "clocks": main["clocks"]}
         print(json.dumps(line), flush=True)
-    h.destroy()
     if world > 1:
         dist.destroy_process_group()
+
+
+def sweep(args):
+    """Slice-count sweep on one 8192-pair chunk of the 72^3 workload (N_G = 6000)."""
+    import torch
+    import oracle
+    import paper_2509_23018_gb300 as gw
+    cfg = gwgen.CONFIGS["p3_72cube_onechunk"]
+    prob = gwgen.config_problem(cfg)
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(3)
+    idx = np.sort(rng.choice(cfg.ng, 12, replace=False))
+    M = oracle.m_conv(prob.gpsi, prob.cv, prob.gpsi, prob.cc, prob.gchi[idx])
+    ref = oracle.chi0(M, oracle.delta(prob.ev, prob.ec, 0.0))
+    out = {"workload": f"{cfg.name}: grid 72^3, {cfg.nv}+{cfg.nc} bands, N_Gpsi={cfg.ngpsi}, N_G={cfg.ng}",
+           "sample": "12x12 sampled entries vs the oracle, all pairs", "slices": {}}
+    for s_ in (4, 5, 6, 7, 8):
+        r = run_mode(args, cfg, prob, dev, "ozaki", s_, "twofloat", 2, 1, False, 1)
+        rf = roofline_for(cfg, "ozaki", s_, r)
+        got = r["chi"][np.ix_(idx, idx)]
+        out["slices"][s_] = {"rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                             "gemm_tflops": rf["achieved"], "gemm_frac": rf["frac"], "gemm_ms": rf["ms_per_launch"],
+                             "ms_per_step": r["ms_per_step"]}
+    r = run_mode(args, cfg, prob, dev, "fp64", 0, "fp64", 1, 1, False, 1)
+    got = r["chi"][np.ix_(idx, idx)]
+    rf = roofline_for(cfg, "fp64", 0, r)
+    out["fp64_dmma"] = {"rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                        "contract_tflops": rf["achieved"], "contract_ms": rf["ms_per_launch"],
+                        "ms_per_step": r["ms_per_step"]}
+    print(json.dumps(out), flush=True)
+
+
+def batch(args):
+    """64 q-points (4x4x4 grid), N_G uniform in [300, 3000], 16 frequencies, one graph per call."""
+    import torch
+    import paper_2509_23018_gb300 as gw
+    cfg = gwgen.CONFIGS["c4_batch"]
+    b = gwgen.make_batch(cfg.grid, cfg.nv, cfg.nc, cfg.ngpsi, 300, 3000, 4, 16, seed=gwgen.BASE_SEED + cfg.index)
+    dev = torch.device("cuda", 0)
+    h = gw.Chi0(cfg.grid, nq=len(b.qs), prec="ozaki", nslices=args.nslices, mtxel="twofloat")
+    g = torch.as_tensor(b.gpsi, device=dev)
+    h.set_bands(0, 1, g, torch.as_tensor(b.cc, device=dev), torch.as_tensor(b.ec, device=dev))
+    for iq in range(len(b.qs)):
+        h.set_bands(iq, 0, g, torch.as_tensor(b.cv[iq], device=dev), torch.as_tensor(b.ev[iq], device=dev))
+        h.set_gsphere(iq, torch.as_tensor(b.gchi[iq], device=dev))
+    slots = list(range(len(b.qs)))
+    ngs = [len(x) for x in b.gchi]
+    out = torch.empty(sum(16 * n * n for n in ngs), dtype=torch.complex128, device=dev)
+    t0 = time.perf_counter()
+    h.compute_batch(slots, list(b.omega), out=out)  # tunes, captures, runs
+    torch.cuda.synchronize()
+    first = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.set_timing(True)
+    h.timing(reset=True)
+    e0.record()
+    for _ in range(args.steps):
+        h.compute_batch(slots, list(b.omega), out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    P = cfg.nv * cfg.nc
+    conv = sum(8.0 * n * n * P * 16 for n in ngs)
+    print(json.dumps({"workload": "64 q (4^3 grid) x 16 imaginary frequencies (Gauss-Legendre on [0,100] eV), "
+                                  "40^3, 64+512 bands, N_Gpsi=8000, N_G in [300,3000]",
+                      "prec": "ozaki", "nslices": args.nslices, "ms_per_call": ms, "ms_per_q": ms / len(b.qs),
+                      "conv_tflops": conv / (ms * 1e-3) * 1e-12, "first_call_s": first,
+                      "tuning": h.tuning(), "timing_ms": {k: v[0] / args.steps for k, v in h.timing().items()}}),
+          flush=True)
+
+
+def adjoint(args):
+    """Adjoint of L = Re Tr(W chi0) on 40^3, 96+768 bands, N_G = 1500 (M recomputed per chunk)."""
+    import torch
+    import paper_2509_23018_gb300 as gw
+    cfg = gwgen.CONFIGS["c5_adjoint"]
+    prob = gwgen.config_problem(cfg)
+    W = gwgen.hermitian(np.random.default_rng(gwgen.BASE_SEED + 4), cfg.ng)
+    dev = torch.device("cuda", 0)
+    h = gw.from_problem(prob, mtxel=args.mtxel or "twofloat")
+    Wd = torch.as_tensor(W, device=dev)
+    h.adjoint(0, Wd)
+    torch.cuda.synchronize()
+    h.set_timing(True)
+    h.timing(reset=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L, dEv, dEc, dcv, dcc = h.adjoint(0, Wd)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / args.steps
+    print(json.dumps({"workload": "L = Re Tr(W chi0), 40^3, 96+768 bands, N_Gpsi=4500, N_G=1500",
+                      "s_per_adjoint": sec, "L": L,
+                      "timing_ms": {k: v[0] / args.steps for k, v in h.timing().items()}}), flush=True)
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.sweep:
+        sweep(args)
+    elif args.batch:
+        batch(args)
+    elif args.adjoint:
+        adjoint(args)
     else:
         ours(args)
 
