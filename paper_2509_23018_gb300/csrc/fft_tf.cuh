@@ -350,6 +350,65 @@ __device__ __forceinline__ float4 *tstages_ct(float4 *x, float4 *y, int nlines, 
     }
 }
 
+// Warp-level variants: one warp transforms its own lines; stages are separated by
+// __syncwarp only, so warps that own disjoint lines never wait for each other.
+template <int N, int R, int NS, bool KEEP>
+__device__ __forceinline__ void wstage_ct(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines, int ls,
+                                          const float4 *__restrict__ tw, const TfConsts &k,
+                                          const int *__restrict__ pos, float4 *__restrict__ kd, int cls, int l0)
+{
+    constexpr int nb = N / R;
+    constexpr int tstride = N / (NS * R);
+    const int lane = threadIdx.x & 31;
+    const int total = nlines * nb;
+    for (int b = lane; b < total; b += 32) {
+        const int l = b / nb, j = b - l * nb;
+        const int kk = j % NS;
+        const float4 *xl = x + l * ls;
+        tcx v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + j + r * nb);
+        if constexpr (NS > 1) {
+            const int e = kk * tstride;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = tc_mul(v[r], tc_load(tw + r * e));
+        }
+        tdftR<R>(v, k);
+        const int o = (j / NS) * (NS * R) + kk;
+        if constexpr (KEEP) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int q = pos[o + r * NS];
+                if (q >= 0) tc_store(kd + q * cls + l0 + l, v[r]);
+            }
+        } else {
+            float4 *yl = y + l * ls;
+#pragma unroll
+            for (int r = 0; r < R; ++r) tc_store(yl + o + r * NS, v[r]);
+        }
+    }
+}
+
+// Lines x[l * ls], l < nlines, owned by the calling warp; y is the warp's scratch of the
+// same shape.  With KEEP the last stage writes output i of line l to kd[pos[i] * cls + l0 + l]
+// (dropped when pos[i] < 0) and kd is returned; otherwise the result buffer (x or y).
+template <int N, int S, int NS, bool KEEP>
+__device__ __forceinline__ float4 *wstages_ct(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
+                                              const TfConsts &k, const int *pos, float4 *kd, int cls, int l0)
+{
+    constexpr RadPlan P = make_rad_plan(N);
+    constexpr int R = P.r[S];
+    if constexpr (S + 1 == P.nst) {
+        wstage_ct<N, R, NS, KEEP>(x, y, nlines, ls, tw, k, pos, kd, cls, l0);
+        __syncwarp();
+        return KEEP ? kd : y;
+    } else {
+        wstage_ct<N, R, NS, false>(x, y, nlines, ls, tw, k, pos, kd, cls, l0);
+        __syncwarp();
+        return wstages_ct<N, S + 1, NS * R, KEEP>(y, x, nlines, ls, tw, k, pos, kd, cls, l0);
+    }
+}
+
 // Full two-float transform of nlines contiguous lines of length N; returns the result buffer.
 template <int N>
 __device__ __forceinline__ float4 *tfft_lines_ct(float4 *a, float4 *b, int nlines, int ls, const float4 *tw,

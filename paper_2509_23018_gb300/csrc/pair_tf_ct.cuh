@@ -9,18 +9,25 @@ namespace gw {
 
 constexpr int kPairThreads = 256;
 
-// Grid-specialised version: slab dimensions N1 x N2 known at compile time.
+// Grid-specialised version: slab dimensions N1 x N2 known at compile time.  Warp w owns
+// slab lines [w N1/8, (w+1) N1/8) for the product and the i2 transform (private ping-pong
+// regions A/B, __syncwarp between stages); the kept i2-frequencies land transposed in C;
+// the K2 columns are transformed along i1 by warps round-robin (C <-> D); the i0 sum reads
+// the result.  Two block barriers per slab.
 template <int NPT, int N1, int N2>
-__global__ void __launch_bounds__(kPairThreads) pair_kernel_tf_ct(const float4 *__restrict__ psiv,
+__global__ void __launch_bounds__(kPairThreads, 2) pair_kernel_tf_ct(const float4 *__restrict__ psiv,
                                                                    const float4 *__restrict__ psic, int nc, int64_t p0,
                                                                    PairPlan pp, TfConsts kc, tf inv_nr,
                                                                    double2 *__restrict__ M)
 {
+    static_assert(N1 % (kPairThreads / 32) == 0, "slab rows must split evenly over the warps");
+    constexpr int NW = kPairThreads / 32, LPW = N1 / NW; // warps, lines per warp
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int ns = N1 * N2;
     const int n0 = pp.n[0];
-    float4 *a = (float4 *)smem, *b = a + ns;
-    float4 *tw0 = b + ns, *tw1 = tw0 + n0, *tw2 = tw1 + N1;
+    const int K2 = pp.K2;
+    float4 *A = (float4 *)smem, *B = A + ns, *C = B + ns, *D = C + K2 * N1;
+    float4 *tw0 = D + K2 * N1, *tw1 = tw0 + n0, *tw2 = tw1 + N1;
     int *pos = (int *)(tw2 + N2); // pos[k2] = index of k2 among the kept i2-frequencies, or -1
     for (int i = threadIdx.x; i < n0; i += blockDim.x) tw0[i] = pp.ax[0].twf[i];
     for (int i = threadIdx.x; i < N1; i += blockDim.x) tw1[i] = pp.ax[1].twf[i];
@@ -29,14 +36,15 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel_tf_ct(const float4 *
         pos[i] = -1;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < pp.K2; i += blockDim.x) pos[pp.kz[i]] = i;
-    const int K2 = pp.K2;
+    for (int i = threadIdx.x; i < K2; i += blockDim.x) pos[pp.kz[i]] = i;
 
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t p = p0 + blockIdx.x;
     const int v = (int)(p / nc), c = (int)(p - (int64_t)v * nc);
     const int64_t nr = (int64_t)n0 * ns;
-    const float4 *pv = psiv + (int64_t)v * nr;
-    const float4 *pc = psic + (int64_t)c * nr;
+    const float4 *pv = psiv + (int64_t)v * nr + warp * LPW * N2;
+    const float4 *pc = psic + (int64_t)c * nr + warp * LPW * N2;
+    float4 *Aw = A + warp * LPW * N2, *Bw = B + warp * LPW * N2;
 
     tcx F[NPT];
     int sel[NPT], k0[NPT], e0[NPT];
@@ -51,39 +59,46 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel_tf_ct(const float4 *
     }
     __syncthreads();
 
+    constexpr int WPTS = LPW * N2;                     // points per warp
+    constexpr int PER = (WPTS + 31) / 32;
+    constexpr int PF = PER < 3 ? PER : 3;
     for (int i0 = 0; i0 < n0; ++i0) {
         const float4 *sv = pv + (int64_t)i0 * ns, *sc = pc + (int64_t)i0 * ns;
         if (i0 + 1 < n0) {
-            // pull the next slab of both bands towards L2 while this one is transformed
+            // pull this warp's part of the next slab of both bands towards L2
             const char *nv = (const char *)(sv + ns), *nc2 = (const char *)(sc + ns);
-            for (int o = threadIdx.x * 128; o < ns * 16; o += blockDim.x * 128) {
+            for (int o = lane * 128; o < WPTS * 16; o += 32 * 128) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(nv + o));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(nc2 + o));
             }
         }
-        constexpr int per = (ns + kPairThreads - 1) / kPairThreads;
-        constexpr int PF = per < 3 ? per : 3;
-        for (int i = threadIdx.x; i < ns; i += PF * kPairThreads) {
+        for (int i = lane; i < WPTS; i += PF * 32) {
             tcx xv[PF], xc[PF];
 #pragma unroll
             for (int u = 0; u < PF; ++u) {
-                const int kk = i + u * kPairThreads;
-                if (kk < ns) {
+                const int kk = i + u * 32;
+                if (kk < WPTS) {
                     xv[u] = tc_load(sv + kk);
                     xc[u] = tc_load(sc + kk);
                 }
             }
 #pragma unroll
             for (int u = 0; u < PF; ++u) {
-                const int kk = i + u * kPairThreads;
-                if (kk < ns) tc_store(a + kk, tc_mulc(xv[u], xc[u]));
+                const int kk = i + u * 32;
+                if (kk < WPTS) tc_store(Aw + kk, tc_mulc(xv[u], xc[u]));
             }
         }
-        __syncthreads();
-        // along i2; the last stage writes only the kept frequencies, as columns [k2'][i1]
-        float4 *o = tstages_ct_keep<N2, 0, 1>(a, b, N1, N2, tw2, kc, pos, N1);
-        float4 *r = (o == a) ? b : a;
-        float4 *t = tfft_lines_ct<N1>(o, r, K2, N1, tw1, kc); // along i1 on the kept columns
+        __syncwarp();
+        // along i2 on this warp's lines; kept frequencies go to C as columns [k2'][i1]
+        wstages_ct<N2, 0, 1, true>(Aw, Bw, LPW, N2, tw2, kc, pos, C, N1, warp * LPW);
+        __syncthreads(); // C complete
+        // along i1 on the K2 kept columns, warps round-robin over columns
+        for (int q = warp; q < K2; q += NW)
+            wstages_ct<N1, 0, 1, false>(C + q * N1, D + q * N1, 1, N1, tw1, kc, pos, nullptr, 0, 0);
+        // every column takes the same number of stages, so all results sit in the same buffer
+        constexpr bool in_d = (make_rad_plan(N1).nst & 1) != 0;
+        float4 *t = in_d ? D : C;
+        __syncthreads(); // all columns transformed
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             tcx u = tc_mul(tc_load(t + sel[j]), tc_load(tw0 + e0[j]));
@@ -91,7 +106,11 @@ __global__ void __launch_bounds__(kPairThreads) pair_kernel_tf_ct(const float4 *
             e0[j] += k0[j];
             if (e0[j] >= n0) e0[j] -= n0;
         }
-        __syncthreads();
+        // With the result in D no barrier is needed here: the next slab writes A, B
+        // (warp-private), C only in its last i2 stage, and D only after the next "C
+        // complete" barrier.  With the result in C, C must not be rewritten before every
+        // warp has read it.
+        if constexpr (!in_d) __syncthreads();
     }
     double2 *out = M + (int64_t)blockIdx.x * pp.ng;
 #pragma unroll
@@ -105,7 +124,7 @@ template <int NPT, int N1, int N2>
 inline cudaError_t launch_pair_tf_ct(const float4 *psiv, const float4 *psic, int nc, int64_t p0, int64_t count,
                                      const PairPlan &pp, const TfConsts &kc, tf inv_nr, double2 *M, cudaStream_t st)
 {
-    size_t sm = sizeof(float4) * (2 * (size_t)N1 * N2 + pp.n[0] + N1 + N2) + sizeof(int) * N2;
+    size_t sm = sizeof(float4) * (2 * (size_t)N1 * N2 + 2 * (size_t)pp.K2 * N1 + pp.n[0] + N1 + N2) + sizeof(int) * N2;
     cudaError_t e =
         cudaFuncSetAttribute(pair_kernel_tf_ct<NPT, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -1,0 +1,75 @@
+"""Full-size parity, in the launch configuration bench.py times, on outputs the oracle can compute.
+
+48^3 grid, 128 + 1024 bands on 6000 plane waves, N_G = 2000, 8192-pair chunks: a sampled
+block of chi (all 131072 pairs contribute) and sampled rows of M against the oracle, plus
+properties that hold at any size (Hermitian, negative semidefinite at w = 0, trace).
+"""
+import numpy as np
+import pytest
+
+import gwgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def gw():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import paper_2509_23018_gb300 as gw
+    return gw
+
+
+@pytest.fixture(scope="module")
+def c2():
+    cfg = gwgen.CONFIGS["c2_48cube"]
+    p = gwgen.config_problem(cfg)
+    rng = np.random.default_rng(17)
+    idx = np.sort(rng.choice(cfg.ng, 10, replace=False))
+    Mcols = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi[idx])   # all pairs, 10 columns
+    ref = oracle.chi0(Mcols, oracle.delta(p.ev, p.ec, 0.0))
+    prs = np.sort(rng.choice(cfg.npairs, 16, replace=False))
+    return cfg, p, idx, ref, prs
+
+
+@pytest.mark.parametrize("prec,nslices,mtxel,tol", [("fp64", 6, "fp64", 1e-11), ("ozaki", 7, "twofloat", 1e-11),
+                                                    ("ozaki", 6, "twofloat", 1e-9)])
+def test_c2_sampled(gw, c2, prec, nslices, mtxel, tol):
+    cfg, p, idx, ref, prs = c2
+    h = gw.from_problem(p, prec=prec, nslices=nslices, mtxel=mtxel, pair_chunk=cfg.pair_chunk)
+    (chi,), (dg,) = h.compute(0, [0.0], diag=True)
+    chi_d = chi[0]
+    # properties at full size, on the device
+    assert torch.equal(chi_d, chi_d.conj().T)
+    ev = torch.linalg.eigvalsh(chi_d)
+    assert float(ev.max()) <= 50 * tol * float(ev.abs().max())  # NSD up to the mode's error level
+    assert abs(float(torch.trace(chi_d).real) - float(dg[0].sum())) <= 1e-10 * abs(float(dg[0].sum()))
+    got = chi_d.cpu().numpy()[np.ix_(idx, idx)]
+    assert rel(got, ref) <= tol
+    # sampled pair rows of M (stage a alone)
+    for pr in prs[:4]:
+        m = h.pair_elements(0, int(pr), 1).cpu().numpy()[0]
+        v, c = divmod(int(pr), cfg.nc)
+        mo = oracle.m_conv(p.gpsi, p.cv[v:v + 1], p.gpsi, p.cc[c:c + 1], p.gchi)[0]
+        assert rel(m, mo) < 1e-12
+    h.sync()
+    h.destroy()
+
+
+def test_adjoint_40cube_reduced_bands(gw):
+    """Adjoint on the 40^3 / 4500 / 1500 shapes with reduced bands (12 + 48) vs the oracle adjoint."""
+    p = gwgen.make_problem((40, 40, 40), 12, 48, 4500, 1500, seed=gwgen.BASE_SEED + 4)
+    W = gwgen.hermitian(np.random.default_rng(gwgen.BASE_SEED + 4), 1500)
+    Lo, dEvo, dEco, dcvo, dcco = oracle.adjoint(p.gpsi, p.cv, p.ev, p.gpsi, p.cc, p.ec, p.gchi, W, 0.0)
+    h = gw.from_problem(p, mtxel="twofloat", pair_chunk=192)
+    L, dEv, dEc, dcv, dcc = h.adjoint(0, torch.as_tensor(W, device="cuda"))
+    h.sync()
+    assert abs(L - Lo) <= 1e-10 * abs(Lo)
+    for a, b in ((dEv, dEvo), (dEc, dEco), (dcv, dcvo), (dcc, dcco)):
+        assert rel(a.cpu().numpy(), b) < 1e-10
