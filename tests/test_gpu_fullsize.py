@@ -49,7 +49,8 @@ def test_c2_sampled(gw, c2, prec, nslices, mtxel, tol):
     assert torch.equal(chi_d, chi_d.conj().T)
     ev = torch.linalg.eigvalsh(chi_d)
     assert float(ev.max()) <= 50 * tol * float(ev.abs().max())  # NSD up to the mode's error level
-    assert abs(float(torch.trace(chi_d).real) - float(dg[0].sum())) <= 1e-10 * abs(float(dg[0].sum()))
+    # trace of chi against the independent FP64 column reduction of Delta |M|^2
+    assert abs(float(torch.trace(chi_d).real) - float(dg[0].sum())) <= max(tol, 1e-12) * abs(float(dg[0].sum()))
     got = chi_d.cpu().numpy()[np.ix_(idx, idx)]
     assert rel(got, ref) <= tol
     # sampled pair rows of M (stage a alone)
