@@ -72,9 +72,27 @@ __device__ __forceinline__ tf tf_scale(tf x, float c) // c a power of two
 }
 __device__ __forceinline__ double tf_to_d(tf x) { return (double)x.hi + (double)x.lo; }
 
+// Lazy sums: the exact sum of the hi parts plus every low-order term, without the final
+// renormalisation.  Chains of these inside one butterfly keep the ~2^-46 relative level;
+// tc_norm renormalises the butterfly's outputs once.
+__device__ __forceinline__ tf tf_addl(tf x, tf y)
+{
+    tf s = tf_2sum(x.hi, y.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+__device__ __forceinline__ tf tf_subl(tf x, tf y)
+{
+    tf s = tf_2sum(x.hi, -y.hi);
+    return {s.hi, __fadd_rn(s.lo, __fsub_rn(x.lo, y.lo))};
+}
+__device__ __forceinline__ tf tf_norm(tf x) { return tf_fast2sum(x.hi, x.lo); }
+
 __device__ __forceinline__ tcx tc_add(tcx a, tcx b) { return {tf_add(a.re, b.re), tf_add(a.im, b.im)}; }
 __device__ __forceinline__ tcx tc_sub(tcx a, tcx b) { return {tf_sub(a.re, b.re), tf_sub(a.im, b.im)}; }
 __device__ __forceinline__ tcx tc_muli(tcx a) { return {tf_neg(a.im), a.re}; }
+__device__ __forceinline__ tcx tc_addl(tcx a, tcx b) { return {tf_addl(a.re, b.re), tf_addl(a.im, b.im)}; }
+__device__ __forceinline__ tcx tc_subl(tcx a, tcx b) { return {tf_subl(a.re, b.re), tf_subl(a.im, b.im)}; }
+__device__ __forceinline__ tcx tc_norm(tcx a) { return {tf_norm(a.re), tf_norm(a.im)}; }
 // a * w
 __device__ __forceinline__ tcx tc_mul(tcx a, tcx w)
 {
@@ -111,25 +129,30 @@ __device__ __forceinline__ void tdft2(tcx *v)
     v[0] = tc_add(a, b);
     v[1] = tc_sub(a, b);
 }
+template <bool NORM = true>
 __device__ __forceinline__ void tdft4(tcx *v)
 {
-    tcx a = tc_add(v[0], v[2]), b = tc_sub(v[0], v[2]);
-    tcx c = tc_add(v[1], v[3]), d = tc_muli(tc_sub(v[1], v[3]));
-    v[0] = tc_add(a, c);
-    v[2] = tc_sub(a, c);
-    v[1] = tc_add(b, d);
-    v[3] = tc_sub(b, d);
+    tcx a = tc_addl(v[0], v[2]), b = tc_subl(v[0], v[2]);
+    tcx c = tc_addl(v[1], v[3]), d = tc_muli(tc_subl(v[1], v[3]));
+    v[0] = tc_addl(a, c);
+    v[2] = tc_subl(a, c);
+    v[1] = tc_addl(b, d);
+    v[3] = tc_subl(b, d);
+    if constexpr (NORM) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = tc_norm(v[r]);
+    }
 }
 __device__ __forceinline__ void tdft3(tcx *v, const TfConsts &k)
 {
-    tcx t = tc_add(v[1], v[2]);
-    tcx s = tc_sub(v[1], v[2]);
-    tcx y0 = tc_add(v[0], t);
-    tcx m = tc_sub(v[0], {tf_scale(t.re, 0.5f), tf_scale(t.im, 0.5f)});
+    tcx t = tc_addl(v[1], v[2]);
+    tcx s = tc_subl(v[1], v[2]);
+    tcx y0 = tc_addl(v[0], t);
+    tcx m = tc_subl(v[0], {tf_scale(t.re, 0.5f), tf_scale(t.im, 0.5f)});
     tcx is = tc_muli(tc_rmul(s, k.sin60));
-    v[0] = y0;
-    v[1] = tc_add(m, is);
-    v[2] = tc_sub(m, is);
+    v[0] = tc_norm(y0);
+    v[1] = tc_norm(tc_addl(m, is));
+    v[2] = tc_norm(tc_subl(m, is));
 }
 __device__ __forceinline__ void tdft5(tcx *v, const TfConsts &k)
 {
@@ -150,16 +173,16 @@ __device__ __forceinline__ void tdft8(tcx *v, const TfConsts &k)
 {
     tcx e[4] = {v[0], v[2], v[4], v[6]};
     tcx o[4] = {v[1], v[3], v[5], v[7]};
-    tdft4(e);
-    tdft4(o);
+    tdft4<false>(e);
+    tdft4<false>(o);
     // o[k] *= e^{+i pi k/4}
-    o[1] = tc_rmul({tf_sub(o[1].re, o[1].im), tf_add(o[1].re, o[1].im)}, k.rs2);
+    o[1] = tc_rmul({tf_subl(o[1].re, o[1].im), tf_addl(o[1].re, o[1].im)}, k.rs2);
     o[2] = tc_muli(o[2]);
-    o[3] = tc_rmul({tf_neg(tf_add(o[3].re, o[3].im)), tf_sub(o[3].re, o[3].im)}, k.rs2);
+    o[3] = tc_rmul({tf_neg(tf_addl(o[3].re, o[3].im)), tf_subl(o[3].re, o[3].im)}, k.rs2);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        v[j] = tc_add(e[j], o[j]);
-        v[j + 4] = tc_sub(e[j], o[j]);
+        v[j] = tc_norm(tc_addl(e[j], o[j]));
+        v[j + 4] = tc_norm(tc_subl(e[j], o[j]));
     }
 }
 
@@ -168,7 +191,7 @@ __device__ __forceinline__ void tdftR(tcx *v, const TfConsts &k)
 {
     if constexpr (R == 2) tdft2(v);
     else if constexpr (R == 3) tdft3(v, k);
-    else if constexpr (R == 4) tdft4(v);
+    else if constexpr (R == 4) tdft4<true>(v);
     else if constexpr (R == 5) tdft5(v, k);
     else tdft8(v, k);
 }

@@ -12,8 +12,8 @@ constexpr int kPairThreads = 256;
 // Grid-specialised version: slab dimensions N1 x N2 known at compile time.  Warp w owns
 // slab lines [w N1/8, (w+1) N1/8) for the product and the i2 transform (private ping-pong
 // regions A/B, __syncwarp between stages); the kept i2-frequencies land transposed in C;
-// the K2 columns are transformed along i1 by warps round-robin (C <-> D); the i0 sum reads
-// the result.  Two block barriers per slab.
+// the block transforms the K2 columns along i1 (C <-> D); the i0 sum reads the result.
+// One block barrier before the i1 transform and one after each of its stages.
 template <int NPT, int N1, int N2>
 __global__ void __launch_bounds__(kPairThreads, 2) pair_kernel_tf_ct(const float4 *__restrict__ psiv,
                                                                    const float4 *__restrict__ psic, int nc, int64_t p0,
@@ -92,13 +92,10 @@ __global__ void __launch_bounds__(kPairThreads, 2) pair_kernel_tf_ct(const float
         // along i2 on this warp's lines; kept frequencies go to C as columns [k2'][i1]
         wstages_ct<N2, 0, 1, true>(Aw, Bw, LPW, N2, tw2, kc, pos, C, N1, warp * LPW);
         __syncthreads(); // C complete
-        // along i1 on the K2 kept columns, warps round-robin over columns
-        for (int q = warp; q < K2; q += NW)
-            wstages_ct<N1, 0, 1, false>(C + q * N1, D + q * N1, 1, N1, tw1, kc, pos, nullptr, 0, 0);
-        // every column takes the same number of stages, so all results sit in the same buffer
+        // along i1 on the K2 kept columns, the whole block on each stage (a column alone
+        // would leave most lanes of a warp idle); ends with a barrier
+        float4 *t = tfft_lines_ct<N1>(C, D, K2, N1, tw1, kc);
         constexpr bool in_d = (make_rad_plan(N1).nst & 1) != 0;
-        float4 *t = in_d ? D : C;
-        __syncthreads(); // all columns transformed
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             tcx u = tc_mul(tc_load(t + sel[j]), tc_load(tw0 + e0[j]));
