@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="ozaki", choices=["fp64", "ozaki"])
     ap.add_argument("--nslices", type=int, default=7)
+    ap.add_argument("--path", default="batch", choices=["batch", "stream"],
+                    help="batch: resident M, persistent contraction, CUDA graph (gw_chi0_compute_batch); "
+                         "stream: chunk-by-chunk launches (gw_chi0_compute)")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the native FP64 DMMA run on the same input (split-precision mode only)")
     ap.add_argument("--mtxel", default=None, choices=["fp64", "twofloat"],
@@ -214,11 +217,13 @@ def run_mode(args, cfg, prob, dev, prec, nslices, mtxel, steps, warmup, with_e2e
     chi = torch.empty(cfg.ng * cfg.ng, dtype=torch.complex128, device=dev)
     h.ng[0] = cfg.ng
 
+    run = h.compute_batch if args.path == "batch" else h.compute
+
     def step():
         h.set_bands(0, 1, gpsi, cc, ec)
         h.set_bands(0, 0, gpsi, cv, ev)
         h.set_gsphere(0, gchi)
-        h.compute(0, omega, out=chi)
+        run([0], omega, out=chi)
 
     for _ in range(warmup):
         step()
@@ -260,7 +265,7 @@ def run_mode(args, cfg, prob, dev, prec, nslices, mtxel, steps, warmup, with_e2e
             h.set_bands(0, 1, d[0], d[2], d[4])
             h.set_bands(0, 0, d[0], d[1], d[3])
             h.set_gsphere(0, d[5])
-            h.compute(0, omega, out=chi)
+            run([0], omega, out=chi)
             hout.copy_(chi, non_blocking=True)
 
         e2e_step()
@@ -342,7 +347,8 @@ def ours(args):
                 "config": {"workload": f"{cfg.name}: grid {cfg.grid[0]}^3, {cfg.nv}+{cfg.nc} bands, "
                                        f"N_Gpsi={cfg.ngpsi}, N_G={cfg.ng}, chunks of {cfg.pair_chunk} pairs, omega=0",
                            "prec": args.prec, "nslices": args.nslices if args.prec == "ozaki" else None,
-                           "mtxel": mtxel, "pairs": cfg.npairs, "conv_tflop_per_step": conv_flops(cfg) * 1e-12,
+                           "mtxel": mtxel, "path": args.path, "pairs": cfg.npairs,
+                           "conv_tflop_per_step": conv_flops(cfg) * 1e-12,
                            "l2": "inputs larger than L2 (psi grids 2.0 GB, M chunks 262 MB)",
                            "parallelism": f"replicas x{world} (independent q-points)"},
                 "error": err, "roofline": roofline, "fp64_dmma": other, "cpu_baseline": cpu, "e2e": main["e2e"],

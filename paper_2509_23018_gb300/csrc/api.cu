@@ -514,8 +514,15 @@ void free_sphere(gw_chi0 *h, Sphere &s)
 // call signature into a CUDA graph and replayed.  Launch shapes come from a small
 // autotuner that times the candidates on the first call of a signature.
 struct BatchLayout {
-    std::vector<int64_t> P, moff, doff, kpad, zoff, eoff, coff, dgoff;
+    std::vector<int64_t> P, moff, doff, coff, dgoff;
     std::vector<int> ng;
+    // split precision: pair segments of at most pair_chunk pairs, each with its own
+    // column exponents and slices (the exactness bound of the slice sums is per segment)
+    struct Seg {
+        int q;
+        int64_t p0, cnt, kpad, zoff, eoff;
+    };
+    std::vector<Seg> seg;
     size_t Mtot = 0, Dtot = 0, Ztot = 0, Etot = 0;
 };
 
@@ -523,25 +530,32 @@ BatchLayout batch_layout(gw_chi0 *h, int nq, const int *iq, int nw)
 {
     BatchLayout L;
     size_t coff = 0, dgoff = 0;
+    const int64_t kseg = h->d.pair_chunk;
     for (int i = 0; i < nq; ++i) {
         const int ng = h->sph[iq[i]].ng;
         const int64_t P = (int64_t)h->val[iq[i]].nb * h->cond.nb;
-        const int64_t kpad = (P + 63) / 64 * 64;
         L.ng.push_back(ng);
         L.P.push_back(P);
-        L.kpad.push_back(kpad);
         L.moff.push_back((int64_t)L.Mtot);
         L.doff.push_back((int64_t)L.Dtot);
-        L.zoff.push_back((int64_t)L.Ztot);
-        L.eoff.push_back((int64_t)L.Etot);
         L.coff.push_back((int64_t)coff);
         L.dgoff.push_back((int64_t)dgoff);
         L.Mtot += (size_t)P * ng;
         L.Dtot += (size_t)nw * P;
-        L.Ztot += (size_t)h->d.nslices * 2 * ng * kpad;
-        L.Etot += (size_t)ng;
         coff += (size_t)nw * ng * ng;
         dgoff += (size_t)nw * ng;
+        for (int64_t p0 = 0; p0 < P; p0 += kseg) {
+            BatchLayout::Seg sg;
+            sg.q = i;
+            sg.p0 = p0;
+            sg.cnt = std::min(kseg, P - p0);
+            sg.kpad = (sg.cnt + 63) / 64 * 64;
+            sg.zoff = (int64_t)L.Ztot;
+            sg.eoff = (int64_t)L.Etot;
+            L.Ztot += (size_t)h->d.nslices * 2 * ng * sg.kpad;
+            L.Etot += (size_t)ng;
+            L.seg.push_back(sg);
+        }
     }
     return L;
 }
@@ -593,13 +607,15 @@ gw_status batch_stage_a(gw_chi0 *h, int nq, const int *iq, const gw::OmegaList &
 
 gw_status batch_oz_split(gw_chi0 *h, int nq, int w, const BatchLayout &L)
 {
+    (void)nq;
     Scope sc(h, "oz_split");
-    for (int i = 0; i < nq; ++i) {
-        const double *sp = h->SPall + L.doff[i] + (int64_t)w * L.P[i];
-        const double2 *M = h->Mall + L.moff[i];
-        CK(h, gw::launch_oz_colexp(M, L.P[i], L.ng[i], sp, h->Eall + L.eoff[i], h->st), "oz exponents");
-        CK(h, gw::launch_oz_slice(M, L.P[i], L.ng[i], sp, h->Eall + L.eoff[i], h->d.nslices, L.kpad[i],
-                                  (uint16_t *)h->Zall + L.zoff[i], h->st),
+    for (const auto &sg : L.seg) {
+        const int ng = L.ng[sg.q];
+        const double *sp = h->SPall + L.doff[sg.q] + (int64_t)w * L.P[sg.q] + sg.p0;
+        const double2 *M = h->Mall + L.moff[sg.q] + sg.p0 * ng;
+        CK(h, gw::launch_oz_colexp(M, sg.cnt, ng, sp, h->Eall + sg.eoff, h->st), "oz exponents");
+        CK(h, gw::launch_oz_slice(M, sg.cnt, ng, sp, h->Eall + sg.eoff, h->d.nslices, sg.kpad,
+                                  (uint16_t *)h->Zall + sg.zoff, h->st),
            "oz slices");
     }
     return GW_OK;
@@ -620,11 +636,13 @@ gw_status batch_f64_jobs(gw_chi0 *h, int nq, int nw, const BatchLayout &L, doubl
 gw_status batch_oz_jobs(gw_chi0 *h, int nq, int w, const BatchLayout &L, double2 *chi, int bn,
                         std::vector<gw::OzJob> &jobs)
 {
+    (void)nq;
     jobs.clear();
-    for (int i = 0; i < nq; ++i) {
+    for (const auto &sg : L.seg) {
+        const int ng = L.ng[sg.q];
         gw::OzJob j;
-        gw_status s = oz_job(h, j, (uint16_t *)h->Zall + L.zoff[i], L.kpad[i], L.ng[i], h->Eall + L.eoff[i],
-                             chi + L.coff[i] + (int64_t)w * L.ng[i] * L.ng[i], bn);
+        gw_status s = oz_job(h, j, (uint16_t *)h->Zall + sg.zoff, sg.kpad, ng, h->Eall + sg.eoff,
+                             chi + L.coff[sg.q] + (int64_t)w * ng * ng, bn);
         if (s) return s;
         jobs.push_back(j);
     }

@@ -14,7 +14,8 @@
 // hence exact in the FP32 accumulator; for t >= 4 it stays exact while |C_t| <= 2^24,
 // which holds unless the slices are adversarially correlated.  The FP64 recombination
 //     chi += -2^(E_G + E_G' - 6t) (integer combination of C_t)
-// happens once per chunk and group, in the epilogue.  FP64 is kept for Delta, the
+// happens once per chunk and group, in the epilogue, with FP64 atomic adds so that the
+// chunks (pair segments) of one chi block may run concurrently in one launch.  FP64 is kept for Delta, the
 // scaling, the recombination, the accumulation across chunks and the symmetrisation.
 #include "internal.h"
 #include "ptx.cuh"
@@ -287,8 +288,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                         if (g < ng && gp < ng && g <= gp && val != 0) {
                             const int ex = Eg + __ldg(jb.E + gp) - kOzBeta * t;
                             const double sc = -__longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
-                            double *dst = crow + 2 * (int64_t)gp;
-                            *dst = fma((double)val, sc, *dst);
+                            // atomic: blocks of other pair segments may add into the same entry
+                            atomicAdd(crow + 2 * (int64_t)gp, (double)val * sc);
                         }
                     }
                 }
