@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="ozaki", choices=["fp64", "ozaki"])
     ap.add_argument("--nslices", type=int, default=7)
-    ap.add_argument("--path", default="batch", choices=["batch", "stream"],
+    ap.add_argument("--path", default="stream", choices=["batch", "stream"],
                     help="batch: resident M, persistent contraction, CUDA graph (gw_chi0_compute_batch); "
                          "stream: chunk-by-chunk launches (gw_chi0_compute)")
     ap.add_argument("--no-fp64-compare", action="store_true",
