@@ -199,6 +199,15 @@ GW_API gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double 
 GW_API gw_status gw_chi0_sync(gw_chi0 *h);
 
 /*
+ * Failure-detection check: enqueue one device wait, bounded by `iterations` tries, on an
+ * mbarrier that nothing arrives at -- the same bounded wait the contraction kernels use on
+ * their TMA and MMA barriers.  When the bound runs out the kernel records a timeout in the
+ * handle's status word and returns; the next gw_chi0_sync reports GW_ERR_TIMEOUT and the
+ * handle (and CUDA context) stay usable.  Nothing faults, traps or hangs.
+ */
+GW_API gw_status gw_chi0_check_watchdog(gw_chi0 *h, long long iterations);
+
+/*
  * Per-kernel timing.  When enabled, every library kernel launch is bracketed by CUDA
  * events on the handle's stream.  gw_chi0_timing fills, for up to n kernel classes,
  * names (host char[n][32]), total milliseconds and launch counts since the last reset

@@ -43,6 +43,7 @@ SIGNATURES = {
     "gw_chi0_contract": ([P, I, I, P, P, I, P, I, P, P], I),
     "gw_chi0_adjoint": ([P, I, D, P, P, P, P, P, P], I),
     "gw_chi0_sync": ([P], I),
+    "gw_chi0_check_watchdog": ([P, ctypes.c_longlong], I),
     "gw_chi0_set_timing": ([P, I], I),
     "gw_chi0_timing": ([P, I, P, P, P, I], I),
     "gw_chi0_device_bytes": ([P], SZ),

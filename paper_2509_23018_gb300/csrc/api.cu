@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <array>
 #include <map>
@@ -175,6 +176,14 @@ bool factor(int n, FftAxis &a)
 }
 
 int mod(int a, int n) { return ((a % n) + n) % n; }
+
+// Host-side fault injection for tests: GW_CHI0_FAULT_AT_CHUNK=k makes the streamed compute
+// fail before enqueueing chunk k (nothing faults on the device).
+int64_t fault_chunk()
+{
+    const char *e = std::getenv("GW_CHI0_FAULT_AT_CHUNK");
+    return e ? std::atoll(e) : -1;
+}
 
 // ------------------------------------------------------------------ timing helpers
 cudaEvent_t ev_get(gw_chi0 *h)
@@ -1166,8 +1175,10 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
         gw_status s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw);
         if (s) return s;
         gw::PairPlan pp = pair_plan(h, sp);
-        for (int64_t p0 = 0; p0 < P; p0 += chunk) {
+        const int64_t fault_at = fault_chunk();
+        for (int64_t p0 = 0, k = 0; p0 < P; p0 += chunk, ++k) {
             int64_t cnt = std::min(chunk, P - p0);
+            if (k == fault_at) return fail(h, GW_ERR_CUDA, "injected host-side fault before chunk %lld", (long long)k);
             {
                 Scope sc(h, "pair_mtxel");
                 CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
@@ -1371,6 +1382,14 @@ gw_status gw_chi0_sync(gw_chi0 *h)
     CK(h, cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
     CK(h, cudaMemset(h->status, 0, sizeof(int)), "status reset");
     if (st & gw::kStatusTimeout) return fail(h, GW_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    return GW_OK;
+}
+
+gw_status gw_chi0_check_watchdog(gw_chi0 *h, long long iterations)
+{
+    if (!h) return GW_ERR_ARG;
+    if (iterations < 1) return fail(h, GW_ERR_ARG, "iterations must be >= 1");
+    CK(h, gw::launch_watchdog(iterations, h->status, h->st), "watchdog");
     return GW_OK;
 }
 

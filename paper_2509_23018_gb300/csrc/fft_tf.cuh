@@ -280,10 +280,10 @@ constexpr RadPlan make_rad_plan(int n)
     return p;
 }
 
-// lines of N contiguous points, line l at x + l * ls
+// lines of N points, line l at x + l * ls, element stride es
 template <int N, int R, int NS>
 __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines, int ls,
-                                          const float4 *__restrict__ tw, const TfConsts &k)
+                                          const float4 *__restrict__ tw, const TfConsts &k, int es = 1)
 {
     constexpr int nb = N / R;
     constexpr int tstride = N / (NS * R); // r * kk * tstride < N: no reduction needed
@@ -294,7 +294,7 @@ __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *
         const float4 *xl = x + l * ls;
         tcx v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + j + r * nb);
+        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + (j + r * nb) * es);
         if constexpr (NS > 1) {
             const int e = kk * tstride;
 #pragma unroll
@@ -304,72 +304,22 @@ __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *
         float4 *yl = y + l * ls;
         const int o = (j / NS) * (NS * R) + kk;
 #pragma unroll
-        for (int r = 0; r < R; ++r) tc_store(yl + o + r * NS, v[r]);
-    }
-}
-
-// Last stage variant: output i of line l goes to y[pos[i] * cls + l] when pos[i] >= 0 and is
-// dropped otherwise (an output-pruned transform whose kept outputs land transposed).
-template <int N, int R, int NS>
-__device__ __forceinline__ void tstage_ct_keep(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines,
-                                               int ls, const float4 *__restrict__ tw, const TfConsts &k,
-                                               const int *__restrict__ pos, int cls)
-{
-    constexpr int nb = N / R;
-    constexpr int tstride = N / (NS * R);
-    const int total = nlines * nb;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int l = b / nb, j = b - l * nb;
-        const int kk = j % NS;
-        const float4 *xl = x + l * ls;
-        tcx v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + j + r * nb);
-        if constexpr (NS > 1) {
-            const int e = kk * tstride;
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = tc_mul(v[r], tc_load(tw + r * e));
-        }
-        tdftR<R>(v, k);
-        const int o = (j / NS) * (NS * R) + kk;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int q = pos[o + r * NS];
-            if (q >= 0) tc_store(y + q * cls + l, v[r]);
-        }
-    }
-}
-
-// All stages; the last one keeps only the outputs listed in pos (see tstage_ct_keep).
-template <int N, int S, int NS>
-__device__ __forceinline__ float4 *tstages_ct_keep(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
-                                                   const TfConsts &k, const int *pos, int cls)
-{
-    constexpr RadPlan P = make_rad_plan(N);
-    constexpr int R = P.r[S];
-    if constexpr (S + 1 == P.nst) {
-        tstage_ct_keep<N, R, NS>(x, y, nlines, ls, tw, k, pos, cls);
-        __syncthreads();
-        return y;
-    } else {
-        tstage_ct<N, R, NS>(x, y, nlines, ls, tw, k);
-        __syncthreads();
-        return tstages_ct_keep<N, S + 1, NS * R>(y, x, nlines, ls, tw, k, pos, cls);
+        for (int r = 0; r < R; ++r) tc_store(yl + (o + r * NS) * es, v[r]);
     }
 }
 
 template <int N, int S, int NS>
 __device__ __forceinline__ float4 *tstages_ct(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
-                                              const TfConsts &k)
+                                              const TfConsts &k, int es)
 {
     constexpr RadPlan P = make_rad_plan(N);
     if constexpr (S >= P.nst) {
         return x;
     } else {
         constexpr int R = P.r[S];
-        tstage_ct<N, R, NS>(x, y, nlines, ls, tw, k);
+        tstage_ct<N, R, NS>(x, y, nlines, ls, tw, k, es);
         __syncthreads();
-        return tstages_ct<N, S + 1, NS * R>(y, x, nlines, ls, tw, k);
+        return tstages_ct<N, S + 1, NS * R>(y, x, nlines, ls, tw, k, es);
     }
 }
 
@@ -432,12 +382,13 @@ __device__ __forceinline__ float4 *wstages_ct(float4 *x, float4 *y, int nlines, 
     }
 }
 
-// Full two-float transform of nlines contiguous lines of length N; returns the result buffer.
+// Full two-float transform of nlines lines of length N (line stride ls, element stride es);
+// returns the result buffer.
 template <int N>
 __device__ __forceinline__ float4 *tfft_lines_ct(float4 *a, float4 *b, int nlines, int ls, const float4 *tw,
-                                                 const TfConsts &k)
+                                                 const TfConsts &k, int es = 1)
 {
-    return tstages_ct<N, 0, 1>(a, b, nlines, ls, tw, k);
+    return tstages_ct<N, 0, 1>(a, b, nlines, ls, tw, k, es);
 }
 
 } // namespace gw

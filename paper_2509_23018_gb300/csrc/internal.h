@@ -45,6 +45,8 @@ cudaError_t launch_delta(const double *ev, const double *ec, int nc, int64_t p0,
 // diag[w][g] += sum_p delta[w][p] |M[p][g]|^2
 cudaError_t launch_diag(const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride, int nw,
                         double *diag, int64_t diag_wstride, cudaStream_t st);
+// a bounded wait that is never satisfied: sets kStatusTimeout in *status after iters tries
+cudaError_t launch_watchdog(long long iters, int *status, cudaStream_t st);
 // lower triangle <- conj(upper), Im diag <- 0, for nw consecutive ng x ng blocks
 cudaError_t launch_symmetrize(double2 *chi, int ng, int nw, cudaStream_t st);
 

@@ -172,6 +172,15 @@ cudaError_t launch_band_setup_tf(const double2 *coeff, const int32_t *gofs, int 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const TfConsts kc = tf_consts();
+    if (n[0] == n[1] && n[1] == n[2]) {
+        switch (n[0]) { // grid-specialised transforms for the standard cubic grids
+        case 24: return launch_band_fft_tf_g24(p, nb, ax, kc, st);
+        case 40: return launch_band_fft_tf_g40(p, nb, ax, kc, st);
+        case 48: return launch_band_fft_tf_g48(p, nb, ax, kc, st);
+        case 72: return launch_band_fft_tf_g72(p, nb, ax, kc, st);
+        default: break;
+        }
+    }
     size_t sm1 = sizeof(float4) * (2 * (size_t)n[1] * n[2] + n[1] + n[2]);
     size_t sm0 = sizeof(float4) * (2 * (size_t)n[0] * n[2] + n[0]);
     if ((e = cudaFuncSetAttribute(band_fft_slab_tf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)) !=

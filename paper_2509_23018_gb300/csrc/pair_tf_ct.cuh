@@ -144,6 +144,66 @@ inline cudaError_t launch_pair_tf_grid(const float4 *a, const float4 *b, int nc,
 }
 
 
+// Band setup in two-float arithmetic for a cubic N^3 grid: the (band, i0) slab kernel
+// transforms along i2 then i1, the (band, i1) plane kernel along i0.
+template <int N>
+__global__ void __launch_bounds__(256) band_slab_tf_ct(float4 *__restrict__ psi, FftAxis ax, TfConsts kc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int ns = N * N;
+    float4 *a = (float4 *)smem, *b = a + ns, *tw = b + ns;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = ax.twf[i];
+    float4 *g = psi + ((int64_t)blockIdx.y * N + blockIdx.x) * ns;
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) a[i] = g[i];
+    __syncthreads();
+    float4 *r = tfft_lines_ct<N>(a, b, N, N, tw, kc);         // along i2
+    float4 *o = (r == a) ? b : a;
+    r = tfft_lines_ct<N>(r, o, N, 1, tw, kc, N);              // along i1 (element stride N)
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) g[i] = r[i];
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) band_axis0_tf_ct(float4 *__restrict__ psi, FftAxis ax, TfConsts kc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int np = N * N;
+    float4 *a = (float4 *)smem, *b = a + np, *tw = b + np;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = ax.twf[i];
+    float4 *g = psi + (int64_t)blockIdx.y * N * N * N + (int64_t)blockIdx.x * N;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int i0 = i / N, i2 = i - i0 * N;
+        a[i] = g[(int64_t)i0 * N * N + i2];
+    }
+    __syncthreads();
+    float4 *r = tfft_lines_ct<N>(a, b, N, 1, tw, kc, N);      // lines along i0, element stride N
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int i0 = i / N, i2 = i - i0 * N;
+        g[(int64_t)i0 * N * N + i2] = r[i];
+    }
+}
+
+template <int N>
+inline cudaError_t launch_band_fft_tf_ct(float4 *psi, int nb, const FftAxis *ax, const TfConsts &kc,
+                                         cudaStream_t st)
+{
+    const size_t sm = sizeof(float4) * (2 * (size_t)N * N + N);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(band_slab_tf_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(band_axis0_tf_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess)
+        return e;
+    band_slab_tf_ct<N><<<dim3(N, nb), 256, sm, st>>>(psi, ax[2], kc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    band_axis0_tf_ct<N><<<dim3(N, nb), 256, sm, st>>>(psi, ax[0], kc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_fft_tf_g24(float4 *, int, const FftAxis *, const TfConsts &, cudaStream_t);
+cudaError_t launch_band_fft_tf_g40(float4 *, int, const FftAxis *, const TfConsts &, cudaStream_t);
+cudaError_t launch_band_fft_tf_g48(float4 *, int, const FftAxis *, const TfConsts &, cudaStream_t);
+cudaError_t launch_band_fft_tf_g72(float4 *, int, const FftAxis *, const TfConsts &, cudaStream_t);
+
 cudaError_t launch_pair_tf_g24(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,
                                const TfConsts &, tf, double2 *, cudaStream_t);
 cudaError_t launch_pair_tf_g40(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,

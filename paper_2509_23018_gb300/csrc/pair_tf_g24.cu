@@ -9,4 +9,9 @@ cudaError_t launch_pair_tf_g24(const float4 *a, const float4 *b, int nc, int64_t
     return launch_pair_tf_grid<24, 24>(a, b, nc, p0, count, pp, kc, inv, M, st);
 }
 
+cudaError_t launch_band_fft_tf_g24(float4 *psi, int nb, const FftAxis *ax, const TfConsts &kc, cudaStream_t st)
+{
+    return launch_band_fft_tf_ct<24>(psi, nb, ax, kc, st);
+}
+
 } // namespace gw

@@ -1,5 +1,6 @@
 // Energy factor (a5), diagonal reduction and Hermitian symmetrisation (a7).
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace gw {
 
@@ -91,6 +92,33 @@ cudaError_t launch_symmetrize(double2 *chi, int ng, int nw, cudaStream_t st)
     if (ng == 0 || nw == 0) return cudaSuccess;
     int nt = (ng + 31) / 32;
     symmetrize_kernel<<<dim3(nt * (nt + 1) / 2, 1, nw), dim3(32, 8), 0, st>>>(chi, ng, nt);
+    return cudaGetLastError();
+}
+
+// Watchdog check: one thread waits, with the given bound, on an mbarrier that nothing
+// arrives at, exactly as the contraction kernels wait on their TMA and MMA barriers; when
+// the bound runs out it records kStatusTimeout and returns, leaving the context usable.
+__global__ void watchdog_kernel(long long iters, int *status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    bar_init(&bar, 1);
+    bar_fence_init();
+    const uint32_t a = su32(&bar);
+    for (long long it = 0; it < iters; ++it) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok)
+                     : "r"(a), "r"(0u)
+                     : "memory");
+        if (ok) return;
+    }
+    atomicOr(status, kStatusTimeout);
+}
+
+cudaError_t launch_watchdog(long long iters, int *status, cudaStream_t st)
+{
+    watchdog_kernel<<<1, 32, 0, st>>>(iters, status);
     return cudaGetLastError();
 }
 

@@ -155,3 +155,32 @@ def test_memory_budget(gw):
     with pytest.raises(gw.GwError) as e:
         h.set_bands(0, 1, dev(p.gpsi), dev(p.cc), dev(p.ec))
     assert e.value.status == 3  # GW_ERR_OOM
+
+
+def test_watchdog_timeout_is_reported(gw):
+    """A bounded device wait that nothing satisfies reports GW_ERR_TIMEOUT; the handle stays usable."""
+    p = gwgen.make_problem((12, 12, 12), 2, 3, 57, 27, seed=9)
+    h = handle(gw, p)
+    assert h.lib.gw_chi0_check_watchdog(h.h, 2000) == 0
+    with pytest.raises(gw.GwError) as e:
+        h.sync()
+    assert e.value.status == 6  # GW_ERR_TIMEOUT
+    (chi,) = h.compute(0, [0.0])
+    h.sync()  # status was cleared by the previous sync
+    Mo = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)
+    assert rel(chi.cpu().numpy()[0], oracle.chi0(Mo, oracle.delta(p.ev, p.ec, 0.0))) < TOL
+
+
+def test_host_fault_injection(gw, monkeypatch):
+    """An injected host-side failure before chunk 2 is reported; the next call succeeds."""
+    p = gwgen.make_problem((12, 12, 12), 2, 3, 57, 27, seed=9)
+    h = handle(gw, p, pair_chunk=2)
+    monkeypatch.setenv("GW_CHI0_FAULT_AT_CHUNK", "2")
+    with pytest.raises(gw.GwError) as e:
+        h.compute(0, [0.0])
+    assert e.value.status == 4 and "injected" in str(e.value)
+    monkeypatch.delenv("GW_CHI0_FAULT_AT_CHUNK")
+    (chi,) = h.compute(0, [0.0])
+    h.sync()
+    Mo = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)
+    assert rel(chi.cpu().numpy()[0], oracle.chi0(Mo, oracle.delta(p.ev, p.ec, 0.0))) < TOL
