@@ -290,8 +290,11 @@ def run_mode(args, cfg, prob, dev, prec, nslices, mtxel, steps, warmup, with_e2e
 
 
 # FP32 operations of the two-float arithmetic as the kernels implement it (fft_tf.cuh):
-# tf_addl 8, tf_norm 3, tf_add 11, tf_mul 7, tf_dot2 19; complex multiply = 2 tf_dot2.
+# tf_addl 8, tf_norm 3, tf_add 11, tf_mul 7, tf_dot2 19, tf_dot2l 16, tf_acc2 24; a complex
+# multiply is 2 tf_dot2 (38), a lazy twiddle multiply 2 tf_dot2l (32), an accumulation 2 tf_acc2.
 _CMUL = 38
+_CMUL_L = 32
+_ACC = 48
 
 
 def _rad_plan(n):
@@ -311,26 +314,45 @@ def _rad_plan(n):
     return [3] * n3 + [5] * n5 + [4] * n4 + [8] * n8 + [2] * n2
 
 
+def _prune_radix(n):
+    return 3 if n % 3 == 0 else (2 if n % 2 == 0 else 5)
+
+
 def _bfly_ops(r, twiddled):
     base = {2: 2 * 2 * 11, 3: 12 * 8 + 2 * 7 + 4 + 6 * 3, 4: 16 * 8 + 8 * 3,
             5: 8 * 11 + 2 * 11 + 2 * (4 * 7 + 2 * 11) * 2 + 4 * 2 * 11,
             8: 2 * 128 + 2 * (2 * 8 + 2 * 7) + 16 * 8 + 16 * 3}[r]
-    return base + ((r - 1) * _CMUL if twiddled else 0)
+    return base + ((r - 1) * _CMUL_L if twiddled else 0)
 
 
-def _line_ops(n):
+def _head_ops(n):
+    """All stages but the pruned last one of the pruned plan, per line."""
     ops, ns = 0, 1
-    for r in _rad_plan(n):
+    for r in _rad_plan(n // _prune_radix(n)):
         ops += (n // r) * _bfly_ops(r, ns > 1)
         ns *= r
     return ops
 
 
-def twofloat_ops_per_pair(cfg, k2):
+def _prune_out_ops(n):
+    """One output of the pruned last stage: R - 1 lazy twiddle products and sums, one renormalisation."""
+    return (_prune_radix(n) - 1) * (_CMUL_L + 16) + 6
+
+
+def twofloat_ops_per_pair(cfg, k2, k12):
     """FP32 operations of the two-float pair kernel per pair: product, i2 transform of every
-    line, i1 transform of the k2 kept columns, i0 sum onto the sphere."""
+    line (pruned to the k2 kept columns), i1 transform of those columns (pruned to the k12
+    cells of the sphere), i0 direct sum onto the sphere (lazy accumulation)."""
     n0, n1, n2 = cfg.grid
-    return n0 * (n1 * n2 * _CMUL + n1 * _line_ops(n2) + k2 * _line_ops(n1) + cfg.ng * (_CMUL + 2 * 11))
+    i2 = n1 * (_head_ops(n2) + k2 * _prune_out_ops(n2))
+    i1 = k2 * _head_ops(n1) + k12 * _prune_out_ops(n1)
+    i0 = cfg.ng * (_ACC + 6 / 8)
+    return n0 * (n1 * n2 * _CMUL + i2 + i1 + i0)
+
+
+def cells(prob, n):
+    """Number of (k1, k2) cells of the sphere."""
+    return len(set((int(g[1]) % n[1], int(g[2]) % n[2]) for g in prob.gchi))
 
 
 def kept_columns(prob, n2):
@@ -343,7 +365,7 @@ FP32_PEAK_TOPS = 152 * 128 * 2.070e9 * 1e-12  # lanes x max SM clock: FP32 opera
 def roofline_pair(cfg, prob, res):
     kms, kn = res["timing"].get("pair_mtxel", (0.0, 0))
     nchunk = -(-cfg.npairs // cfg.pair_chunk)
-    per_pair = twofloat_ops_per_pair(cfg, kept_columns(prob, cfg.grid[2]))
+    per_pair = twofloat_ops_per_pair(cfg, kept_columns(prob, cfg.grid[2]), cells(prob, cfg.grid))
     per_launch = per_pair * cfg.npairs / nchunk
     achieved = per_launch / (kms / kn * 1e-3) * 1e-12 if kn else None
     return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS, "unit": "FP32 Tops/s",

@@ -41,6 +41,9 @@ struct Sphere {
     int32_t *gpack = nullptr;   // device [ng]
     int32_t *gvec = nullptr;    // device [ng][3]
     std::vector<int> cstart, cg; // (k1, k2) cells of the sphere, CSR (adjoint back-projection)
+    int K12 = 0;                // number of cells
+    int32_t *cell = nullptr;    // device [K12]  k2index << 8 | k1
+    int32_t *gcell = nullptr;   // device [ng]   k0 | cell << 8
 };
 
 struct TimerRec {
@@ -495,6 +498,9 @@ gw::PairPlan pair_plan(gw_chi0 *h, const Sphere &s)
     pp.kz = s.kz;
     pp.ng = s.ng;
     pp.gpack = s.gpack;
+    pp.K12 = s.K12;
+    pp.cell = s.cell;
+    pp.gcell = s.gcell;
     return pp;
 }
 
@@ -512,6 +518,8 @@ void free_sphere(gw_chi0 *h, Sphere &s)
     dfree(h, s.kz, sizeof(int) * s.K2);
     dfree(h, s.gpack, sizeof(int32_t) * s.ng);
     dfree(h, s.gvec, sizeof(int32_t) * 3 * s.ng);
+    dfree(h, s.cell, sizeof(int32_t) * s.K12);
+    dfree(h, s.gcell, sizeof(int32_t) * s.ng);
     s = Sphere();
 }
 
@@ -1103,24 +1111,40 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
         }
         s.cstart.push_back(ng);
     }
+    // cell table of the pruned i1 stage and, per sphere point, its k0 and cell index
+    s.K12 = (int)s.cstart.size() - 1;
+    std::vector<int32_t> cell(s.K12), gcell(ng);
+    for (int d = 0; d < s.K12; ++d) {
+        const int i = s.cg[s.cstart[d]];
+        cell[d] = (pack[i] >> 16) << 8 | ((pack[i] >> 8) & 255);
+        for (int m = s.cstart[d]; m < s.cstart[d + 1]; ++m) gcell[s.cg[m]] = (pack[s.cg[m]] & 255) | d << 8;
+    }
     gw_status st;
     Sphere &old = h->sph[iq];
-    if (old.ng == ng && old.K2 == s.K2) {
+    if (old.ng == ng && old.K2 == s.K2 && old.K12 == s.K12) {
         s.kz = old.kz;
         s.gpack = old.gpack;
         s.gvec = old.gvec;
+        s.cell = old.cell;
+        s.gcell = old.gcell;
         old.kz = nullptr;
         old.gpack = nullptr;
         old.gvec = nullptr;
+        old.cell = nullptr;
+        old.gcell = nullptr;
         old = Sphere();
     } else if ((st = dalloc(h, (void **)&s.kz, sizeof(int) * s.K2, "sphere kz")) ||
         (st = dalloc(h, (void **)&s.gpack, sizeof(int32_t) * ng, "sphere pack")) ||
-        (st = dalloc(h, (void **)&s.gvec, sizeof(int32_t) * 3 * ng, "sphere gvec"))) {
+        (st = dalloc(h, (void **)&s.gvec, sizeof(int32_t) * 3 * ng, "sphere gvec")) ||
+        (st = dalloc(h, (void **)&s.cell, sizeof(int32_t) * s.K12, "sphere cells")) ||
+        (st = dalloc(h, (void **)&s.gcell, sizeof(int32_t) * ng, "sphere gcell"))) {
         free_sphere(h, s);
         return st;
     }
     CK(h, cudaMemcpyAsync(s.kz, kz.data(), sizeof(int) * s.K2, cudaMemcpyHostToDevice, h->st), "kz");
     CK(h, cudaMemcpyAsync(s.gpack, pack.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, h->st), "pack");
+    CK(h, cudaMemcpyAsync(s.cell, cell.data(), sizeof(int32_t) * s.K12, cudaMemcpyHostToDevice, h->st), "cells");
+    CK(h, cudaMemcpyAsync(s.gcell, gcell.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, h->st), "gcell");
     CK(h, cudaMemcpyAsync(s.gvec, gvec, sizeof(int32_t) * 3 * ng, cudaMemcpyDeviceToDevice, h->st), "gvec");
     CK(h, cudaStreamSynchronize(h->st), "set_gsphere sync");
     free_sphere(h, h->sph[iq]);

@@ -52,6 +52,36 @@ __device__ __forceinline__ tf tf_mul(tf x, tf y)
     e = __fmaf_rn(x.lo, y.hi, e);
     return tf_fast2sum(p, e);
 }
+// x*a + y*b without the final renormalisation: hi is the rounded sum of the two leading
+// products, lo collects every lower-order term (|lo| stays within a few ulp of hi)
+__device__ __forceinline__ tf tf_dot2l(tf x, tf a, tf y, tf b)
+{
+    float p1 = __fmul_rn(x.hi, a.hi), p2 = __fmul_rn(y.hi, b.hi);
+    float e = __fmaf_rn(x.hi, a.hi, -p1);
+    e = __fadd_rn(e, __fmaf_rn(y.hi, b.hi, -p2));
+    tf s = tf_2sum(p1, p2);
+    e = __fadd_rn(e, s.lo);
+    e = __fmaf_rn(x.hi, a.lo, e);
+    e = __fmaf_rn(x.lo, a.hi, e);
+    e = __fmaf_rn(y.hi, b.lo, e);
+    e = __fmaf_rn(y.lo, b.hi, e);
+    return {s.hi, e};
+}
+// F += x*a + y*b with F kept lazy: the hi parts are summed exactly (two-sum) and every
+// lower-order term goes into F.lo; renormalise F every few updates.
+__device__ __forceinline__ void tf_acc2(tf &F, tf x, tf a, tf y, tf b)
+{
+    float p1 = __fmul_rn(x.hi, a.hi), p2 = __fmul_rn(y.hi, b.hi);
+    float e = __fmaf_rn(x.hi, a.hi, -p1);
+    e = __fadd_rn(e, __fmaf_rn(y.hi, b.hi, -p2));
+    tf s = tf_2sum(p1, p2);
+    tf u = tf_2sum(F.hi, s.hi);
+    e = __fmaf_rn(x.hi, a.lo, e);
+    e = __fmaf_rn(x.lo, a.hi, e);
+    e = __fmaf_rn(y.hi, b.lo, e);
+    e = __fmaf_rn(y.lo, b.hi, e);
+    F = {u.hi, __fadd_rn(F.lo, __fadd_rn(e, __fadd_rn(s.lo, u.lo)))};
+}
 // x*a + y*b with one final renormalisation
 __device__ __forceinline__ tf tf_dot2(tf x, tf a, tf y, tf b)
 {
@@ -97,6 +127,17 @@ __device__ __forceinline__ tcx tc_norm(tcx a) { return {tf_norm(a.re), tf_norm(a
 __device__ __forceinline__ tcx tc_mul(tcx a, tcx w)
 {
     return {tf_dot2(a.re, w.re, tf_neg(a.im), w.im), tf_dot2(a.re, w.im, a.im, w.re)};
+}
+// a * w, lazy (feeds lazy sums or another renormalising step)
+__device__ __forceinline__ tcx tc_mull(tcx a, tcx w)
+{
+    return {tf_dot2l(a.re, w.re, tf_neg(a.im), w.im), tf_dot2l(a.re, w.im, a.im, w.re)};
+}
+// F += a * w, F lazy
+__device__ __forceinline__ void tc_acc(tcx &F, tcx a, tcx w)
+{
+    tf_acc2(F.re, a.re, w.re, tf_neg(a.im), w.im);
+    tf_acc2(F.im, a.re, w.im, a.im, w.re);
 }
 // conj(a) * b
 __device__ __forceinline__ tcx tc_mulc(tcx a, tcx b)
@@ -280,6 +321,21 @@ constexpr RadPlan make_rad_plan(int n)
     return p;
 }
 
+// Plan whose last stage is formed output by output (pruned): the smallest available radix
+// goes last, so each kept output costs R - 1 twiddle products.
+constexpr int prune_radix(int n) { return n % 3 == 0 ? 3 : (n % 2 == 0 ? 2 : 5); }
+constexpr RadPlan make_prune_plan(int n)
+{
+    RadPlan p = make_rad_plan(n / prune_radix(n));
+    p.r[p.nst++] = prune_radix(n);
+    return p;
+}
+template <int N, bool PR>
+constexpr RadPlan plan_of()
+{
+    return PR ? make_prune_plan(N) : make_rad_plan(N);
+}
+
 // lines of N points, line l at x + l * ls, element stride es
 template <int N, int R, int NS>
 __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines, int ls,
@@ -298,7 +354,7 @@ __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *
         if constexpr (NS > 1) {
             const int e = kk * tstride;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = tc_mul(v[r], tc_load(tw + r * e));
+            for (int r = 1; r < R; ++r) v[r] = tc_mull(v[r], tc_load(tw + r * e));
         }
         tdftR<R>(v, k);
         float4 *yl = y + l * ls;
@@ -308,77 +364,20 @@ __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *
     }
 }
 
-template <int N, int S, int NS>
+// Stages S.. of the plan (all of make_rad_plan(N), or all but the pruned last one of
+// make_prune_plan(N)), block-wide with a barrier after each; returns the result buffer.
+template <int N, int S, int NS, bool PR = false>
 __device__ __forceinline__ float4 *tstages_ct(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
                                               const TfConsts &k, int es)
 {
-    constexpr RadPlan P = make_rad_plan(N);
-    if constexpr (S >= P.nst) {
+    constexpr RadPlan P = plan_of<N, PR>();
+    if constexpr (S >= P.nst - (PR ? 1 : 0)) {
         return x;
     } else {
         constexpr int R = P.r[S];
         tstage_ct<N, R, NS>(x, y, nlines, ls, tw, k, es);
         __syncthreads();
-        return tstages_ct<N, S + 1, NS * R>(y, x, nlines, ls, tw, k, es);
-    }
-}
-
-// Warp-level variants: one warp transforms its own lines; stages are separated by
-// __syncwarp only, so warps that own disjoint lines never wait for each other.
-template <int N, int R, int NS, bool KEEP>
-__device__ __forceinline__ void wstage_ct(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines, int ls,
-                                          const float4 *__restrict__ tw, const TfConsts &k,
-                                          const int *__restrict__ pos, float4 *__restrict__ kd, int cls, int l0)
-{
-    constexpr int nb = N / R;
-    constexpr int tstride = N / (NS * R);
-    const int lane = threadIdx.x & 31;
-    const int total = nlines * nb;
-    for (int b = lane; b < total; b += 32) {
-        const int l = b / nb, j = b - l * nb;
-        const int kk = j % NS;
-        const float4 *xl = x + l * ls;
-        tcx v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + j + r * nb);
-        if constexpr (NS > 1) {
-            const int e = kk * tstride;
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = tc_mul(v[r], tc_load(tw + r * e));
-        }
-        tdftR<R>(v, k);
-        const int o = (j / NS) * (NS * R) + kk;
-        if constexpr (KEEP) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int q = pos[o + r * NS];
-                if (q >= 0) tc_store(kd + q * cls + l0 + l, v[r]);
-            }
-        } else {
-            float4 *yl = y + l * ls;
-#pragma unroll
-            for (int r = 0; r < R; ++r) tc_store(yl + o + r * NS, v[r]);
-        }
-    }
-}
-
-// Lines x[l * ls], l < nlines, owned by the calling warp; y is the warp's scratch of the
-// same shape.  With KEEP the last stage writes output i of line l to kd[pos[i] * cls + l0 + l]
-// (dropped when pos[i] < 0) and kd is returned; otherwise the result buffer (x or y).
-template <int N, int S, int NS, bool KEEP>
-__device__ __forceinline__ float4 *wstages_ct(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
-                                              const TfConsts &k, const int *pos, float4 *kd, int cls, int l0)
-{
-    constexpr RadPlan P = make_rad_plan(N);
-    constexpr int R = P.r[S];
-    if constexpr (S + 1 == P.nst) {
-        wstage_ct<N, R, NS, KEEP>(x, y, nlines, ls, tw, k, pos, kd, cls, l0);
-        __syncwarp();
-        return KEEP ? kd : y;
-    } else {
-        wstage_ct<N, R, NS, false>(x, y, nlines, ls, tw, k, pos, kd, cls, l0);
-        __syncwarp();
-        return wstages_ct<N, S + 1, NS * R, KEEP>(y, x, nlines, ls, tw, k, pos, kd, cls, l0);
+        return tstages_ct<N, S + 1, NS * R, PR>(y, x, nlines, ls, tw, k, es);
     }
 }
 
@@ -389,6 +388,74 @@ __device__ __forceinline__ float4 *tfft_lines_ct(float4 *a, float4 *b, int nline
                                                  const TfConsts &k, int es = 1)
 {
     return tstages_ct<N, 0, 1>(a, b, nlines, ls, tw, k, es);
+}
+
+// Warp-level stage over the calling warp's own lines (L lines of N points at x + l * N);
+// the warp's stages are separated by __syncwarp only.
+template <int N, int R, int NS, int L>
+__device__ __forceinline__ void wstage_ct(const float4 *__restrict__ x, float4 *__restrict__ y,
+                                          const float4 *__restrict__ tw, const TfConsts &k)
+{
+    constexpr int nb = N / R, total = L * nb, rounds = (total + 31) / 32;
+    constexpr int tstride = N / (NS * R);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int it = 0; it < rounds; ++it) {
+        const int b = lane + 32 * it;
+        if (total % 32 == 0 || b < total) {
+            const int l = b / nb, j = b - l * nb;
+            const int kk = j % NS;
+            const float4 *xl = x + l * N;
+            tcx v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = tc_load(xl + j + r * nb);
+            if constexpr (NS > 1) {
+                const int e = kk * tstride;
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = tc_mull(v[r], tc_load(tw + r * e));
+            }
+            tdftR<R>(v, k);
+            float4 *yl = y + l * N;
+            const int o = (j / NS) * (NS * R) + kk;
+#pragma unroll
+            for (int r = 0; r < R; ++r) tc_store(yl + o + r * NS, v[r]);
+        }
+    }
+}
+
+// Warp-level stages S.. of make_prune_plan(N) except the pruned last one; returns the
+// buffer holding their result.
+template <int N, int S, int NS, int L>
+__device__ __forceinline__ float4 *wstages_ct(float4 *x, float4 *y, const float4 *tw, const TfConsts &k)
+{
+    constexpr RadPlan P = make_prune_plan(N);
+    if constexpr (S + 1 >= P.nst) {
+        return x;
+    } else {
+        constexpr int R = P.r[S];
+        wstage_ct<N, R, NS, L>(x, y, tw, k);
+        __syncwarp();
+        return wstages_ct<N, S + 1, NS * R, L>(y, x, tw, k);
+    }
+}
+
+// Output k of the pruned last stage of make_prune_plan(N), R its radix: with the earlier
+// stages done, x holds the R interleaved (N/R)-point transforms Y_r at x[r N/R + j], and
+// X[k] = sum_r W^{r k} Y_r[k mod N/R] (decimation in time; tw[i] = W^i).
+template <int N>
+__device__ __forceinline__ tcx tprune_ct(const float4 *__restrict__ x, int k, const float4 *__restrict__ tw)
+{
+    constexpr int R = prune_radix(N), NS = N / R;
+    const int j = k % NS;
+    tcx acc = tc_load(x + j);
+    int e = 0;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        e += k;
+        if (e >= N) e -= N;
+        acc = tc_addl(acc, tc_mull(tc_load(x + j + r * NS), tc_load(tw + e)));
+    }
+    return tc_norm(acc);
 }
 
 } // namespace gw

@@ -1,131 +1,154 @@
 // Two-float pair kernel specialised for a slab shape N1 x N2 known at compile time
 // (instantiated per grid in pair_tf_g*.cu so the translation units compile in parallel).
-// It is the algorithm of pair_kernel_tf in mtxel.cu with constant index arithmetic.
+// It computes what pair_kernel_tf in mtxel.cu computes, organised for this GPU's FP32 pipes.
 #pragma once
 #include "internal.h"
 #include "fft_tf.cuh"
 
 namespace gw {
 
-constexpr int kPairThreads = 256;
-
-// Grid-specialised version: slab dimensions N1 x N2 known at compile time.  Warp w owns
-// slab lines [w N1/8, (w+1) N1/8) for the product and the i2 transform (private ping-pong
-// regions A/B, __syncwarp between stages); the kept i2-frequencies land transposed in C;
-// the block transforms the K2 columns along i1 (C <-> D); the i0 sum reads the result.
-// One block barrier before the i1 transform and one after each of its stages.
-template <int NPT, int N1, int N2>
-__global__ void __launch_bounds__(kPairThreads, 2) pair_kernel_tf_ct(const float4 *__restrict__ psiv,
-                                                                   const float4 *__restrict__ psic, int nc, int64_t p0,
-                                                                   PairPlan pp, TfConsts kc, tf inv_nr,
-                                                                   double2 *__restrict__ M)
+// Threads per block: warps own whole slab lines, and 6 warps give every radix-4 stage of
+// a 48-point line a full round of lanes (8 lines x 12 butterflies = 3 x 32).
+template <int N1>
+constexpr int pair_threads()
 {
-    static_assert(N1 % (kPairThreads / 32) == 0, "slab rows must split evenly over the warps");
-    constexpr int NW = kPairThreads / 32, LPW = N1 / NW; // warps, lines per warp
-    extern __shared__ __align__(16) unsigned char smem[];
+    return N1 % 6 == 0 ? 192 : 256;
+}
+
+// One block per pair, looping over the i0 slabs of the grid.  Per slab:
+//  i2: warp w owns slab lines [w L, (w+1) L).  The first stage of make_prune_plan(N2) is
+//      fused with the product conj(psi_v) psi_c read from global memory; the middle stages
+//      ping-pong between the warp's parts of A and B; the last stage forms only the K2
+//      kept i2-frequencies, written transposed into C[q][i1] (column stride N1 + 1).
+//  i1: the block transforms the K2 columns (C <-> A, barrier after each stage); the
+//      pruned last stage forms only the K12 (i1, i2) cells that hold sphere points, into T.
+//  i0: each thread adds T[cell] W^{i0 k0} to its sphere points (direct sum over slabs).
+// Barriers per slab: "C complete", one per full i1 stage, "T complete".
+template <int NPT, int N1, int N2>
+__global__ void __launch_bounds__(pair_threads<N1>(), NPT <= 12 ? 2 : 1)
+    pair_kernel_tf_ct(const float4 *__restrict__ psiv, const float4 *__restrict__ psic, int nc, int64_t p0,
+                      PairPlan pp, TfConsts kc, tf inv_nr, double2 *__restrict__ M)
+{
+    constexpr int NT = pair_threads<N1>();
+    static_assert(N1 % (NT / 32) == 0, "slab rows must split evenly over the warps");
+    constexpr int L = N1 / (NT / 32); // lines per warp
+    constexpr int CS = N1 + 1;        // column stride of C and of the i1 stages
     constexpr int ns = N1 * N2;
+    constexpr RadPlan P2 = make_prune_plan(N2);
+    constexpr int R0 = P2.r[0], nb0 = N2 / R0;
+    extern __shared__ __align__(16) unsigned char smem[];
     const int n0 = pp.n[0];
-    const int K2 = pp.K2;
-    float4 *A = (float4 *)smem, *B = A + ns, *C = B + ns, *D = C + K2 * N1;
-    float4 *tw0 = D + K2 * N1, *tw1 = tw0 + n0, *tw2 = tw1 + N1;
-    int *pos = (int *)(tw2 + N2); // pos[k2] = index of k2 among the kept i2-frequencies, or -1
-    for (int i = threadIdx.x; i < n0; i += blockDim.x) tw0[i] = pp.ax[0].twf[i];
-    for (int i = threadIdx.x; i < N1; i += blockDim.x) tw1[i] = pp.ax[1].twf[i];
-    for (int i = threadIdx.x; i < N2; i += blockDim.x) {
-        tw2[i] = pp.ax[2].twf[i];
-        pos[i] = -1;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < K2; i += blockDim.x) pos[pp.kz[i]] = i;
+    const int K2 = pp.K2, K12 = pp.K12;
+    float4 *A = (float4 *)smem, *B = A + ns, *C = B + ns, *T = C + K2 * CS;
+    float4 *tw0 = T + K12, *tw1 = tw0 + n0, *tw2 = tw1 + N1;
+    int *kz = (int *)(tw2 + N2), *cell = kz + K2;
+    for (int i = threadIdx.x; i < n0; i += NT) tw0[i] = pp.ax[0].twf[i];
+    for (int i = threadIdx.x; i < N1; i += NT) tw1[i] = pp.ax[1].twf[i];
+    for (int i = threadIdx.x; i < N2; i += NT) tw2[i] = pp.ax[2].twf[i];
+    for (int i = threadIdx.x; i < K2; i += NT) kz[i] = pp.kz[i];
+    for (int i = threadIdx.x; i < K12; i += NT) cell[i] = pp.cell[i];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t p = p0 + blockIdx.x;
     const int v = (int)(p / nc), c = (int)(p - (int64_t)v * nc);
     const int64_t nr = (int64_t)n0 * ns;
-    const float4 *pv = psiv + (int64_t)v * nr + warp * LPW * N2;
-    const float4 *pc = psic + (int64_t)c * nr + warp * LPW * N2;
-    float4 *Aw = A + warp * LPW * N2, *Bw = B + warp * LPW * N2;
+    const float4 *pv = psiv + (int64_t)v * nr + warp * L * N2;
+    const float4 *pc = psic + (int64_t)c * nr + warp * L * N2;
+    float4 *Aw = A + warp * L * N2, *Bw = B + warp * L * N2;
+    // b -> (line, kept column) of the pruned i2 stage: b / K2 by multiply-high (b K2 < 2^32)
+    const uint32_t magic = 0xffffffffu / (uint32_t)K2 + 1u;
 
     tcx F[NPT];
-    int sel[NPT], k0[NPT], e0[NPT];
+    int gc[NPT], e0[NPT];
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
-        int g = threadIdx.x + j * kPairThreads;
+        const int g = threadIdx.x + j * NT;
         F[j] = {{0.f, 0.f}, {0.f, 0.f}};
-        int pk = (g < pp.ng) ? pp.gpack[g] : 0;
-        k0[j] = pk & 255;
-        sel[j] = (pk >> 16) * N1 + ((pk >> 8) & 255);
+        gc[j] = (g < pp.ng) ? pp.gcell[g] : 0; // k0 | cell << 8
         e0[j] = 0;
     }
     __syncthreads();
 
-    constexpr int WPTS = LPW * N2;                     // points per warp
-    constexpr int PER = (WPTS + 31) / 32;
-    constexpr int PF = PER < 3 ? PER : 3;
     for (int i0 = 0; i0 < n0; ++i0) {
         const float4 *sv = pv + (int64_t)i0 * ns, *sc = pc + (int64_t)i0 * ns;
         if (i0 + 1 < n0) {
             // pull this warp's part of the next slab of both bands towards L2
             const char *nv = (const char *)(sv + ns), *nc2 = (const char *)(sc + ns);
-            for (int o = lane * 128; o < WPTS * 16; o += 32 * 128) {
+            for (int o = lane * 128; o < L * N2 * 16; o += 32 * 128) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(nv + o));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(nc2 + o));
             }
         }
-        for (int i = lane; i < WPTS; i += PF * 32) {
-            tcx xv[PF], xc[PF];
+        // i2, first stage fused with the product
+        {
+            constexpr int total = L * nb0, rounds = (total + 31) / 32;
 #pragma unroll
-            for (int u = 0; u < PF; ++u) {
-                const int kk = i + u * 32;
-                if (kk < WPTS) {
-                    xv[u] = tc_load(sv + kk);
-                    xc[u] = tc_load(sc + kk);
+            for (int it = 0; it < rounds; ++it) {
+                const int b = lane + 32 * it;
+                if (total % 32 == 0 || b < total) {
+                    const int l = b / nb0, j = b - l * nb0;
+                    const float4 *xv = sv + l * N2 + j, *xc = sc + l * N2 + j;
+                    tcx x[R0];
+#pragma unroll
+                    for (int r = 0; r < R0; ++r) x[r] = tc_mulc(tc_load(xv + r * nb0), tc_load(xc + r * nb0));
+                    tdftR<R0>(x, kc);
+                    float4 *yl = Aw + l * N2 + j * R0;
+#pragma unroll
+                    for (int r = 0; r < R0; ++r) tc_store(yl + r, x[r]);
                 }
-            }
-#pragma unroll
-            for (int u = 0; u < PF; ++u) {
-                const int kk = i + u * 32;
-                if (kk < WPTS) tc_store(Aw + kk, tc_mulc(xv[u], xc[u]));
             }
         }
         __syncwarp();
-        // along i2 on this warp's lines; kept frequencies go to C as columns [k2'][i1]
-        wstages_ct<N2, 0, 1, true>(Aw, Bw, LPW, N2, tw2, kc, pos, C, N1, warp * LPW);
+        const float4 *y2 = wstages_ct<N2, 1, R0, L>(Aw, Bw, tw2, kc);
+        // i2, pruned last stage: kept frequency kz[q] of line l -> C[q][warp L + l]
+        for (int b = lane; b < L * K2; b += 32) {
+            const int l = (int)__umulhi((uint32_t)b, magic), q = b - l * K2;
+            tc_store(C + q * CS + warp * L + l, tprune_ct<N2>(y2 + l * N2, kz[q], tw2));
+        }
         __syncthreads(); // C complete
-        // along i1 on the K2 kept columns, the whole block on each stage (a column alone
-        // would leave most lanes of a warp idle); ends with a barrier
-        float4 *t = tfft_lines_ct<N1>(C, D, K2, N1, tw1, kc);
-        constexpr bool in_d = (make_rad_plan(N1).nst & 1) != 0;
+        // i1 on the K2 columns; A (and B after it) are free until the next slab
+        const float4 *y1 = tstages_ct<N1, 0, 1, true>(C, A, K2, CS, tw1, kc, 1);
+        for (int d = threadIdx.x; d < K12; d += NT) {
+            const int cl = cell[d];
+            tc_store(T + d, tprune_ct<N1>(y1 + (cl >> 8) * CS, cl & 255, tw1));
+        }
+        __syncthreads(); // T complete
+        // i0: direct sum over the slabs, lazy accumulation renormalised every 8 slabs
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
-            tcx u = tc_mul(tc_load(t + sel[j]), tc_load(tw0 + e0[j]));
-            F[j] = tc_add(F[j], u);
-            e0[j] += k0[j];
+            tc_acc(F[j], tc_load(T + (gc[j] >> 8)), tc_load(tw0 + e0[j]));
+            e0[j] += gc[j] & 255;
             if (e0[j] >= n0) e0[j] -= n0;
+            if ((i0 & 7) == 7) F[j] = tc_norm(F[j]);
         }
-        // With the result in D no barrier is needed here: the next slab writes A, B
-        // (warp-private), C only in its last i2 stage, and D only after the next "C
-        // complete" barrier.  With the result in C, C must not be rewritten before every
-        // warp has read it.
-        if constexpr (!in_d) __syncthreads();
     }
     double2 *out = M + (int64_t)blockIdx.x * pp.ng;
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
-        int g = threadIdx.x + j * kPairThreads;
-        if (g < pp.ng) out[g] = make_double2(tf_to_d(tf_mul(F[j].re, inv_nr)), tf_to_d(tf_mul(F[j].im, inv_nr)));
+        const int g = threadIdx.x + j * NT;
+        const tcx f = tc_norm(F[j]);
+        if (g < pp.ng) out[g] = make_double2(tf_to_d(tf_mul(f.re, inv_nr)), tf_to_d(tf_mul(f.im, inv_nr)));
     }
+}
+
+template <int N1, int N2>
+constexpr size_t pair_tf_ct_smem_fixed()
+{
+    return sizeof(float4) * (2 * (size_t)N1 * N2 + N1 + N2);
 }
 
 template <int NPT, int N1, int N2>
 inline cudaError_t launch_pair_tf_ct(const float4 *psiv, const float4 *psic, int nc, int64_t p0, int64_t count,
                                      const PairPlan &pp, const TfConsts &kc, tf inv_nr, double2 *M, cudaStream_t st)
 {
-    size_t sm = sizeof(float4) * (2 * (size_t)N1 * N2 + 2 * (size_t)pp.K2 * N1 + pp.n[0] + N1 + N2) + sizeof(int) * N2;
+    const size_t sm = pair_tf_ct_smem_fixed<N1, N2>() +
+                      sizeof(float4) * ((size_t)pp.K2 * (N1 + 1) + pp.K12 + pp.n[0]) +
+                      sizeof(int) * ((size_t)pp.K2 + pp.K12);
     cudaError_t e =
         cudaFuncSetAttribute(pair_kernel_tf_ct<NPT, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    pair_kernel_tf_ct<NPT, N1, N2><<<(unsigned)count, kPairThreads, sm, st>>>(psiv, psic, nc, p0, pp, kc, inv_nr, M);
+    pair_kernel_tf_ct<NPT, N1, N2>
+        <<<(unsigned)count, pair_threads<N1>(), sm, st>>>(psiv, psic, nc, p0, pp, kc, inv_nr, M);
     return cudaGetLastError();
 }
 
@@ -133,16 +156,28 @@ template <int N1, int N2>
 inline cudaError_t launch_pair_tf_grid(const float4 *a, const float4 *b, int nc, int64_t p0, int64_t count,
                                        const PairPlan &pp, const TfConsts &kc, tf inv, double2 *M, cudaStream_t st)
 {
-    int need = (pp.ng + kPairThreads - 1) / kPairThreads;
+    constexpr int NT = pair_threads<N1>();
+    const int need = (pp.ng + NT - 1) / NT;
     if (need <= 2) return launch_pair_tf_ct<2, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
     if (need <= 4) return launch_pair_tf_ct<4, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
     if (need <= 8) return launch_pair_tf_ct<8, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
-    if (need <= 12) return launch_pair_tf_ct<12, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 11) return launch_pair_tf_ct<11, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
     if (need <= 16) return launch_pair_tf_ct<16, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
-    if (need <= 24) return launch_pair_tf_ct<24, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
-    return launch_pair_tf_ct<32, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 22) return launch_pair_tf_ct<22, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    if (need <= 32) return launch_pair_tf_ct<32, N1, N2>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    return cudaErrorInvalidValue;
 }
 
+// Whether the grid-specialised kernel takes this plan: at most 32 sphere points per thread
+// and a shared-memory footprint within the 227 KB a block may opt into.
+inline bool pair_tf_ct_fits(const PairPlan &pp)
+{
+    const int n1 = pp.n[1], n2 = pp.n[2];
+    const int nt = n1 % 6 == 0 ? 192 : 256;
+    const size_t sm = sizeof(float4) * (2 * (size_t)n1 * n2 + n1 + n2 + (size_t)pp.K2 * (n1 + 1) + pp.K12 + pp.n[0]) +
+                      sizeof(int) * ((size_t)pp.K2 + pp.K12);
+    return (pp.ng + nt - 1) / nt <= 32 && sm <= 227 * 1024;
+}
 
 // Band setup in two-float arithmetic for a cubic N^3 grid: the (band, i0) slab kernel
 // transforms along i2 then i1, the (band, i1) plane kernel along i0.
