@@ -43,7 +43,8 @@ struct Sphere {
     std::vector<int> cstart, cg; // (k1, k2) cells of the sphere, CSR (adjoint back-projection)
     int K12 = 0;                // number of cells
     int32_t *cell = nullptr;    // device [K12]  k2index << 8 | k1
-    int32_t *gcell = nullptr;   // device [ng]   k0 | cell << 8
+    int32_t *gcell = nullptr;   // device [ng]   per slot: k0 | cell << 8 of point gorder[slot]
+    int32_t *gorder = nullptr;  // device [ng]   points in (k0, cell) order
 };
 
 struct TimerRec {
@@ -501,6 +502,7 @@ gw::PairPlan pair_plan(gw_chi0 *h, const Sphere &s)
     pp.K12 = s.K12;
     pp.cell = s.cell;
     pp.gcell = s.gcell;
+    pp.gorder = s.gorder;
     return pp;
 }
 
@@ -520,6 +522,7 @@ void free_sphere(gw_chi0 *h, Sphere &s)
     dfree(h, s.gvec, sizeof(int32_t) * 3 * s.ng);
     dfree(h, s.cell, sizeof(int32_t) * s.K12);
     dfree(h, s.gcell, sizeof(int32_t) * s.ng);
+    dfree(h, s.gorder, sizeof(int32_t) * s.ng);
     s = Sphere();
 }
 
@@ -1111,13 +1114,23 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
         }
         s.cstart.push_back(ng);
     }
-    // cell table of the pruned i1 stage and, per sphere point, its k0 and cell index
+    // cell table of the pruned i1 stage; the sphere points in (k0, cell) order with, per
+    // slot of that order, the point's k0 and cell index
     s.K12 = (int)s.cstart.size() - 1;
-    std::vector<int32_t> cell(s.K12), gcell(ng);
-    for (int d = 0; d < s.K12; ++d) {
-        const int i = s.cg[s.cstart[d]];
-        cell[d] = (pack[i] >> 16) << 8 | ((pack[i] >> 8) & 255);
-        for (int m = s.cstart[d]; m < s.cstart[d + 1]; ++m) gcell[s.cg[m]] = (pack[s.cg[m]] & 255) | d << 8;
+    std::vector<int32_t> cell(s.K12), gcell(ng), gorder(ng);
+    {
+        std::vector<int32_t> code(ng);
+        for (int d = 0; d < s.K12; ++d) {
+            const int i = s.cg[s.cstart[d]];
+            cell[d] = (pack[i] >> 16) << 8 | ((pack[i] >> 8) & 255);
+            for (int m = s.cstart[d]; m < s.cstart[d + 1]; ++m) code[s.cg[m]] = (pack[s.cg[m]] & 255) | d << 8;
+        }
+        for (int i = 0; i < ng; ++i) gorder[i] = i;
+        std::stable_sort(gorder.begin(), gorder.end(), [&](int a, int b) {
+            const int ka = code[a] & 255, kb = code[b] & 255;
+            return ka != kb ? ka < kb : code[a] < code[b];
+        });
+        for (int i = 0; i < ng; ++i) gcell[i] = code[gorder[i]];
     }
     gw_status st;
     Sphere &old = h->sph[iq];
@@ -1127,17 +1140,20 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
         s.gvec = old.gvec;
         s.cell = old.cell;
         s.gcell = old.gcell;
+        s.gorder = old.gorder;
         old.kz = nullptr;
         old.gpack = nullptr;
         old.gvec = nullptr;
         old.cell = nullptr;
         old.gcell = nullptr;
+        old.gorder = nullptr;
         old = Sphere();
     } else if ((st = dalloc(h, (void **)&s.kz, sizeof(int) * s.K2, "sphere kz")) ||
         (st = dalloc(h, (void **)&s.gpack, sizeof(int32_t) * ng, "sphere pack")) ||
         (st = dalloc(h, (void **)&s.gvec, sizeof(int32_t) * 3 * ng, "sphere gvec")) ||
         (st = dalloc(h, (void **)&s.cell, sizeof(int32_t) * s.K12, "sphere cells")) ||
-        (st = dalloc(h, (void **)&s.gcell, sizeof(int32_t) * ng, "sphere gcell"))) {
+        (st = dalloc(h, (void **)&s.gcell, sizeof(int32_t) * ng, "sphere gcell")) ||
+        (st = dalloc(h, (void **)&s.gorder, sizeof(int32_t) * ng, "sphere order"))) {
         free_sphere(h, s);
         return st;
     }
@@ -1145,6 +1161,7 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
     CK(h, cudaMemcpyAsync(s.gpack, pack.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, h->st), "pack");
     CK(h, cudaMemcpyAsync(s.cell, cell.data(), sizeof(int32_t) * s.K12, cudaMemcpyHostToDevice, h->st), "cells");
     CK(h, cudaMemcpyAsync(s.gcell, gcell.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, h->st), "gcell");
+    CK(h, cudaMemcpyAsync(s.gorder, gorder.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, h->st), "gorder");
     CK(h, cudaMemcpyAsync(s.gvec, gvec, sizeof(int32_t) * 3 * ng, cudaMemcpyDeviceToDevice, h->st), "gvec");
     CK(h, cudaStreamSynchronize(h->st), "set_gsphere sync");
     free_sphere(h, h->sph[iq]);

@@ -27,7 +27,8 @@ struct PairPlan {
     const int32_t *gpack; // device [ng]   k0 | k1 << 8 | k2index << 16
     int K12;              // number of (k1, k2) cells that hold sphere points
     const int32_t *cell;  // device [K12]  k2index << 8 | k1, ordered by (k2index, k1)
-    const int32_t *gcell; // device [ng]   k0 | cell index << 8
+    const int32_t *gcell; // device [ng]   per slot: k0 | cell index << 8 of point gorder[slot]
+    const int32_t *gorder; // device [ng]  sphere points ordered by (k0, cell)
 };
 // M[p - p0][g] for p in [p0, p0 + count); pair p = v * nc + c.
 cudaError_t launch_pair(const double2 *psiv, const double2 *psic, int nc, int64_t p0, int64_t count,

@@ -390,7 +390,7 @@ cudaError_t launch_pair_tf(const void *psiv, const void *psic, int nc, int64_t p
     const tf inv{invh, (float)(invd - (double)invh)};
     const float4 *a = (const float4 *)psiv, *b = (const float4 *)psic;
     int need = (pp.ng + kPairThreads - 1) / kPairThreads;
-    if (pp.n[1] == pp.n[2] && pair_tf_ct_fits(pp)) {
+    if (pair_tf_ct_fits(pp)) {
         // grid-specialised kernels for the slab shapes of the standard workloads
         switch (pp.n[1]) {
         case 24: return launch_pair_tf_g24(a, b, nc, p0, count, pp, kc, inv, M, st);
