@@ -318,18 +318,22 @@ def _prune_radix(n):
     return 3 if n % 3 == 0 else (2 if n % 2 == 0 else 5)
 
 
-def _bfly_ops(r, twiddled):
+def _bfly_ops(r, twiddled, lazy=False):
+    """One butterfly: the radix-r sums (a lazy radix-4 skips its 4 renormalisations) plus
+    r - 1 lazy twiddle products."""
     base = {2: 2 * 2 * 11, 3: 12 * 8 + 2 * 7 + 4 + 6 * 3, 4: 16 * 8 + 8 * 3,
             5: 8 * 11 + 2 * 11 + 2 * (4 * 7 + 2 * 11) * 2 + 4 * 2 * 11,
             8: 2 * 128 + 2 * (2 * 8 + 2 * 7) + 16 * 8 + 16 * 3}[r]
+    if lazy and r == 4:
+        base -= 8 * 3
     return base + ((r - 1) * _CMUL_L if twiddled else 0)
 
 
-def _head_ops(n):
+def _head_ops(n, lazy=False):
     """All stages but the pruned last one of the pruned plan, per line."""
     ops, ns = 0, 1
     for r in _rad_plan(n // _prune_radix(n)):
-        ops += (n // r) * _bfly_ops(r, ns > 1)
+        ops += (n // r) * _bfly_ops(r, ns > 1, lazy)
         ns *= r
     return ops
 
@@ -341,13 +345,14 @@ def _prune_out_ops(n):
 
 def twofloat_ops_per_pair(cfg, k2, k12):
     """FP32 operations of the two-float pair kernel per pair: product, i2 transform of every
-    line (pruned to the k2 kept columns), i1 transform of those columns (pruned to the k12
-    cells of the sphere), i0 direct sum onto the sphere (lazy accumulation)."""
+    line (lazy butterflies, pruned to the k2 kept columns), i1 transform of those columns
+    (pruned to the k12 cells of the sphere), i0 transform of the k12 cell columns (pruned
+    to the sphere points)."""
     n0, n1, n2 = cfg.grid
-    i2 = n1 * (_head_ops(n2) + k2 * _prune_out_ops(n2))
+    i2 = n1 * (_head_ops(n2, lazy=True) + k2 * _prune_out_ops(n2))
     i1 = k2 * _head_ops(n1) + k12 * _prune_out_ops(n1)
-    i0 = cfg.ng * (_ACC + 6 / 8)
-    return n0 * (n1 * n2 * _CMUL + i2 + i1 + i0)
+    i0 = k12 * _head_ops(n0) + cfg.ng * _prune_out_ops(n0)
+    return n0 * (n1 * n2 * _CMUL + i2 + i1) + i0
 
 
 def cells(prob, n):

@@ -43,8 +43,9 @@ struct Sphere {
     std::vector<int> cstart, cg; // (k1, k2) cells of the sphere, CSR (adjoint back-projection)
     int K12 = 0;                // number of cells
     int32_t *cell = nullptr;    // device [K12]  k2index << 8 | k1
-    int32_t *gcell = nullptr;   // device [ng]   per slot: k0 | cell << 8 of point gorder[slot]
-    int32_t *gorder = nullptr;  // device [ng]   points in (k0, cell) order
+    int *cstart_d = nullptr;    // device [K12 + 1] (cstart)
+    int2 *cpts = nullptr;       // device [ng]   (point, k0 | cell << 8) in cell order
+    int nslots = 0;             // scratch slots the two-float pair kernel needs (0: none)
 };
 
 struct TimerRec {
@@ -99,6 +100,11 @@ struct gw_chi0 {
     };
     std::vector<Graph> graphs;
     int *status = nullptr;
+    // scratch slots of the two-float pair kernel (sized in set_gsphere, outside any capture)
+    float4 *pscr = nullptr;
+    size_t pscr_cap = 0; // bytes
+    int *pflags = nullptr;
+    size_t pflags_cap = 0; // bytes
     size_t bytes = 0;
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     // timing
@@ -282,9 +288,23 @@ int num_sms()
     return sms;
 }
 
+// Captured graphs hold raw device pointers: drop them whenever a buffer they may use is
+// reallocated or the bands or spheres change (they are recaptured on the next call).
+void drop_graphs(gw_chi0 *h)
+{
+    if (h->graphs.empty()) return;
+    cudaStreamSynchronize(h->st); // a replay may still be running
+    for (auto &g : h->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        dfree(h, g.jobs, g.jobs_bytes);
+    }
+    h->graphs.clear();
+}
+
 gw_status grow(gw_chi0 *h, void **p, size_t *cap, size_t bytes, const char *what)
 {
     if (bytes <= *cap) return GW_OK;
+    if (*p) drop_graphs(h);
     dfree(h, *p, *cap);
     *p = nullptr;
     *cap = 0;
@@ -501,8 +521,12 @@ gw::PairPlan pair_plan(gw_chi0 *h, const Sphere &s)
     pp.gpack = s.gpack;
     pp.K12 = s.K12;
     pp.cell = s.cell;
-    pp.gcell = s.gcell;
-    pp.gorder = s.gorder;
+    pp.cstart = s.cstart_d;
+    pp.cpts = s.cpts;
+    pp.scr = h->pscr;
+    pp.slot_flags = h->pflags;
+    pp.nslots = s.nslots;
+    pp.status = h->status;
     return pp;
 }
 
@@ -521,8 +545,8 @@ void free_sphere(gw_chi0 *h, Sphere &s)
     dfree(h, s.gpack, sizeof(int32_t) * s.ng);
     dfree(h, s.gvec, sizeof(int32_t) * 3 * s.ng);
     dfree(h, s.cell, sizeof(int32_t) * s.K12);
-    dfree(h, s.gcell, sizeof(int32_t) * s.ng);
-    dfree(h, s.gorder, sizeof(int32_t) * s.ng);
+    dfree(h, s.cstart_d, sizeof(int) * (s.K12 + 1));
+    dfree(h, s.cpts, sizeof(int2) * s.ng);
     s = Sphere();
 }
 
@@ -944,6 +968,8 @@ void gw_chi0_destroy(gw_chi0 *h)
     dfree(h, h->Ebuf, h->Ecap);
     dfree(h, h->jobbuf, h->jobcap);
     dfree(h, h->Mall, h->Mall_cap);
+    dfree(h, h->pscr, h->pscr_cap);
+    dfree(h, h->pflags, h->pflags_cap);
     dfree(h, h->Dall, h->Dall_cap);
     dfree(h, h->SPall, h->SPall_cap);
     dfree(h, h->Zall, h->Zall_cap);
@@ -985,6 +1011,7 @@ gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngpsi, con
     if (kind == 0 && (iq < 0 || iq >= h->d.nq)) return fail(h, GW_ERR_ARG, "q slot %d out of range", iq);
     if (nb < 1 || ngpsi < 1) return fail(h, GW_ERR_ARG, "nb and ngpsi must be >= 1");
     if (!gvec || !coeff || !energy) return fail(h, GW_ERR_ARG, "null pointer");
+    drop_graphs(h);
     BandSet nbs;
     nbs.nb = nb;
     nbs.ngpsi = ngpsi;
@@ -1072,6 +1099,7 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
     if (ng < 1) return fail(h, GW_ERR_ARG, "ng must be >= 1");
     if (ng > gw::pair_max_ng()) return fail(h, GW_ERR_UNSUPPORTED, "ng = %d exceeds %d", ng, gw::pair_max_ng());
     if (!gvec) return fail(h, GW_ERR_ARG, "null pointer");
+    drop_graphs(h);
     Sphere s;
     s.ng = ng;
     s.g.resize((size_t)3 * ng);
@@ -1114,23 +1142,14 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
         }
         s.cstart.push_back(ng);
     }
-    // cell table of the pruned i1 stage; the sphere points in (k0, cell) order with, per
-    // slot of that order, the point's k0 and cell index
+    // cell table of the pruned i1 stage and the sphere points grouped by cell
     s.K12 = (int)s.cstart.size() - 1;
-    std::vector<int32_t> cell(s.K12), gcell(ng), gorder(ng);
-    {
-        std::vector<int32_t> code(ng);
-        for (int d = 0; d < s.K12; ++d) {
-            const int i = s.cg[s.cstart[d]];
-            cell[d] = (pack[i] >> 16) << 8 | ((pack[i] >> 8) & 255);
-            for (int m = s.cstart[d]; m < s.cstart[d + 1]; ++m) code[s.cg[m]] = (pack[s.cg[m]] & 255) | d << 8;
-        }
-        for (int i = 0; i < ng; ++i) gorder[i] = i;
-        std::stable_sort(gorder.begin(), gorder.end(), [&](int a, int b) {
-            const int ka = code[a] & 255, kb = code[b] & 255;
-            return ka != kb ? ka < kb : code[a] < code[b];
-        });
-        for (int i = 0; i < ng; ++i) gcell[i] = code[gorder[i]];
+    std::vector<int32_t> cell(s.K12);
+    std::vector<int2> cpts(ng);
+    for (int d = 0; d < s.K12; ++d) {
+        const int i = s.cg[s.cstart[d]];
+        cell[d] = (pack[i] >> 16) << 8 | ((pack[i] >> 8) & 255);
+        for (int m = s.cstart[d]; m < s.cstart[d + 1]; ++m) cpts[m] = make_int2(s.cg[m], (pack[s.cg[m]] & 255) | d << 8);
     }
     gw_status st;
     Sphere &old = h->sph[iq];
@@ -1139,30 +1158,43 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
         s.gpack = old.gpack;
         s.gvec = old.gvec;
         s.cell = old.cell;
-        s.gcell = old.gcell;
-        s.gorder = old.gorder;
+        s.cstart_d = old.cstart_d;
+        s.cpts = old.cpts;
         old.kz = nullptr;
         old.gpack = nullptr;
         old.gvec = nullptr;
         old.cell = nullptr;
-        old.gcell = nullptr;
-        old.gorder = nullptr;
+        old.cstart_d = nullptr;
+        old.cpts = nullptr;
         old = Sphere();
     } else if ((st = dalloc(h, (void **)&s.kz, sizeof(int) * s.K2, "sphere kz")) ||
         (st = dalloc(h, (void **)&s.gpack, sizeof(int32_t) * ng, "sphere pack")) ||
         (st = dalloc(h, (void **)&s.gvec, sizeof(int32_t) * 3 * ng, "sphere gvec")) ||
         (st = dalloc(h, (void **)&s.cell, sizeof(int32_t) * s.K12, "sphere cells")) ||
-        (st = dalloc(h, (void **)&s.gcell, sizeof(int32_t) * ng, "sphere gcell")) ||
-        (st = dalloc(h, (void **)&s.gorder, sizeof(int32_t) * ng, "sphere order"))) {
+        (st = dalloc(h, (void **)&s.cstart_d, sizeof(int) * (s.K12 + 1), "sphere cell starts")) ||
+        (st = dalloc(h, (void **)&s.cpts, sizeof(int2) * ng, "sphere points by cell"))) {
         free_sphere(h, s);
         return st;
     }
     CK(h, cudaMemcpyAsync(s.kz, kz.data(), sizeof(int) * s.K2, cudaMemcpyHostToDevice, h->st), "kz");
     CK(h, cudaMemcpyAsync(s.gpack, pack.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, h->st), "pack");
     CK(h, cudaMemcpyAsync(s.cell, cell.data(), sizeof(int32_t) * s.K12, cudaMemcpyHostToDevice, h->st), "cells");
-    CK(h, cudaMemcpyAsync(s.gcell, gcell.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, h->st), "gcell");
-    CK(h, cudaMemcpyAsync(s.gorder, gorder.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, h->st), "gorder");
+    CK(h, cudaMemcpyAsync(s.cstart_d, s.cstart.data(), sizeof(int) * (s.K12 + 1), cudaMemcpyHostToDevice, h->st),
+       "cell starts");
+    CK(h, cudaMemcpyAsync(s.cpts, cpts.data(), sizeof(int2) * ng, cudaMemcpyHostToDevice, h->st), "cell points");
     CK(h, cudaMemcpyAsync(s.gvec, gvec, sizeof(int32_t) * 3 * ng, cudaMemcpyDeviceToDevice, h->st), "gvec");
+    if (h->d.mtxel_prec == GW_MTXEL_TWOFLOAT) {
+        // scratch slots of the grid-specialised two-float pair kernel for this sphere
+        size_t elems = 0;
+        CK(h, gw::pair_tf_scratch(pair_plan(h, s), &s.nslots, &elems), "pair scratch size");
+        if (s.nslots > 0) {
+            if ((st = grow(h, (void **)&h->pscr, &h->pscr_cap, sizeof(float4) * elems * s.nslots, "pair scratch")) ||
+                (st = grow(h, (void **)&h->pflags, &h->pflags_cap, sizeof(int) * s.nslots, "pair scratch flags"))) {
+                free_sphere(h, s);
+                return st;
+            }
+        }
+    }
     CK(h, cudaStreamSynchronize(h->st), "set_gsphere sync");
     free_sphere(h, h->sph[iq]);
     h->sph[iq] = std::move(s);
@@ -1423,6 +1455,7 @@ gw_status gw_chi0_sync(gw_chi0 *h)
     CK(h, cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
     CK(h, cudaMemset(h->status, 0, sizeof(int)), "status reset");
     if (st & gw::kStatusTimeout) return fail(h, GW_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (st & gw::kStatusNoSlot) return fail(h, GW_ERR_CUDA, "a pair block found no free scratch slot");
     return GW_OK;
 }
 

@@ -37,5 +37,6 @@ struct FftAxis {
 
 // Device-side status word bits (written by bounded waits that gave up).
 constexpr int kStatusTimeout = 1;
+constexpr int kStatusNoSlot = 2; // a pair block found no free scratch slot
 
 } // namespace gw

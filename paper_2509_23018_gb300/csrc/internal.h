@@ -27,9 +27,18 @@ struct PairPlan {
     const int32_t *gpack; // device [ng]   k0 | k1 << 8 | k2index << 16
     int K12;              // number of (k1, k2) cells that hold sphere points
     const int32_t *cell;  // device [K12]  k2index << 8 | k1, ordered by (k2index, k1)
-    const int32_t *gcell; // device [ng]   per slot: k0 | cell index << 8 of point gorder[slot]
-    const int32_t *gorder; // device [ng]  sphere points ordered by (k0, cell)
+    const int *cstart;    // device [K12 + 1] points of cell d: cpts[cstart[d] .. cstart[d + 1])
+    const int2 *cpts;     // device [ng]   (point index, k0 | cell << 8), grouped by cell
+    // scratch of the two-float grid-specialised kernel (pair_tf_scratch): nslots slots of
+    // n0 * K12 two-float values, one flag per slot
+    float4 *scr;
+    int *slot_flags;
+    int nslots;
+    int *status;          // device status word (kStatusNoSlot)
 };
+// Scratch the two-float pair kernel needs for a plan: *nslots slots of *slot_elems float4
+// (0 slots: the plan runs on the runtime-shape kernel, which needs none).
+cudaError_t pair_tf_scratch(const PairPlan &pp, int *nslots, size_t *slot_elems);
 // M[p - p0][g] for p in [p0, p0 + count); pair p = v * nc + c.
 cudaError_t launch_pair(const double2 *psiv, const double2 *psic, int nc, int64_t p0, int64_t count,
                         const PairPlan &pp, double2 *M, cudaStream_t st);

@@ -380,6 +380,23 @@ static cudaError_t launch_pair_tf_t(const float4 *psiv, const float4 *psic, int 
     return cudaGetLastError();
 }
 
+cudaError_t pair_tf_scratch(const PairPlan &pp, int *nslots, size_t *slot_elems)
+{
+    *nslots = 0;
+    *slot_elems = 0;
+    if (!pair_tf_ct_fits(pp)) return cudaSuccess;
+    cudaError_t e;
+    switch (pp.n[0]) {
+    case 24: e = pair_tf_slots_g24(pp, nslots); break;
+    case 40: e = pair_tf_slots_g40(pp, nslots); break;
+    case 48: e = pair_tf_slots_g48(pp, nslots); break;
+    case 72: e = pair_tf_slots_g72(pp, nslots); break;
+    default: return cudaSuccess;
+    }
+    if (e == cudaSuccess) *slot_elems = (size_t)pp.n[0] * pp.K12;
+    return e;
+}
+
 cudaError_t launch_pair_tf(const void *psiv, const void *psic, int nc, int64_t p0, int64_t count, const PairPlan &pp,
                            double2 *M, cudaStream_t st)
 {
@@ -390,8 +407,8 @@ cudaError_t launch_pair_tf(const void *psiv, const void *psic, int nc, int64_t p
     const tf inv{invh, (float)(invd - (double)invh)};
     const float4 *a = (const float4 *)psiv, *b = (const float4 *)psic;
     int need = (pp.ng + kPairThreads - 1) / kPairThreads;
-    if (pair_tf_ct_fits(pp)) {
-        // grid-specialised kernels for the slab shapes of the standard workloads
+    if (pair_tf_ct_fits(pp) && pp.scr && pp.slot_flags && pp.nslots > 0) {
+        // grid-specialised kernels for the cubic grids of the standard workloads
         switch (pp.n[1]) {
         case 24: return launch_pair_tf_g24(a, b, nc, p0, count, pp, kc, inv, M, st);
         case 40: return launch_pair_tf_g40(a, b, nc, p0, count, pp, kc, inv, M, st);

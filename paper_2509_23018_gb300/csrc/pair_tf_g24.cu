@@ -1,4 +1,4 @@
-// Two-float pair kernel instantiated for 24 x 24 slabs.
+// Two-float pair kernel and band setup instantiated for the 24^3 grid.
 #include "pair_tf_ct.cuh"
 
 namespace gw {
@@ -6,8 +6,10 @@ namespace gw {
 cudaError_t launch_pair_tf_g24(const float4 *a, const float4 *b, int nc, int64_t p0, int64_t count,
                                const PairPlan &pp, const TfConsts &kc, tf inv, double2 *M, cudaStream_t st)
 {
-    return launch_pair_tf_grid<24, 24>(a, b, nc, p0, count, pp, kc, inv, M, st);
+    return launch_pair_tf_cube<24>(a, b, nc, p0, count, pp, kc, inv, M, st);
 }
+
+cudaError_t pair_tf_slots_g24(const PairPlan &pp, int *nslots) { return pair_tf_cube_slots<24>(pp, nslots); }
 
 cudaError_t launch_band_fft_tf_g24(float4 *psi, int nb, const FftAxis *ax, const TfConsts &kc, cudaStream_t st)
 {
