@@ -18,7 +18,7 @@ constexpr int pair_threads()
 template <int N>
 constexpr int pair_min_blocks()
 {
-    return N <= 48 ? (pair_threads<N>() == 192 ? 3 : 2) : 1;
+    return N <= 48 ? (pair_threads<N>() == 192 ? 4 : 2) : 1;
 }
 // The second full i2 stage (when the plan has one) runs in place when a lane's inputs for
 // all its butterflies fit in registers (at most 16 complex values).
@@ -110,10 +110,8 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
     __shared__ int slot_s;
     const int K2 = pp.K2, K12 = pp.K12;
     const int sizeAB = sizeA + sizeB > K2 * CS ? sizeA + sizeB : K2 * CS; // A (+B) also serve the i1 stages
-    // C alternates between two buffers by slab parity, so the next slab's i2 stages can
-    // fill one while slower warps still read the other
-    float4 *A = (float4 *)smem, *B = A + sizeA, *C0 = A + sizeAB;
-    float4 *tw = C0 + 2 * K2 * CS; // the three axes of a cubic grid share one table
+    float4 *A = (float4 *)smem, *B = A + sizeA, *C = A + sizeAB;
+    float4 *tw = C + K2 * CS; // the three axes of a cubic grid share one table
     int *kz = (int *)(tw + N), *cell = kz + K2;
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = pp.ax[0].twf[i];
     for (int i = threadIdx.x; i < K2; i += NT) kz[i] = pp.kz[i];
@@ -182,7 +180,6 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
             __syncwarp();
         }
         // i2, pruned last stage: kept frequency kz[q] of line l -> C[q][warp L + l]
-        float4 *C = C0 + (i0 & 1) * K2 * CS;
         const float4 *y2 = (two && !inplace) ? Bw : Aw;
         for (int b = lane; b < L * K2; b += 32) {
             const int l = K2 > 1 ? (int)__umulhi((uint32_t)b, magic) : b, q = b - l * K2;
@@ -196,16 +193,13 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
             const int cl = cell[d];
             tc_store(Si + d, tprune_ct<N>(y1 + (cl >> 8) * CS, cl & 255, tw));
         }
-        // With the i1 result in C the next slab may start at once (it writes A and the
-        // other C; its "C complete" barrier orders it after every read of this one); with
-        // the result in A, every read must finish before A is rewritten.
-        if constexpr (make_prune_plan(N).nst % 2 == 0) __syncthreads();
+        __syncthreads(); // i1 done with C and A
     }
     __syncthreads(); // all slabs done: A and C become phase-2 buffers
 
     // Phase 2: i0 transforms of the cell columns, in batches that fit in A..C (lines of
     // stride N + 1, so the transposing stores from the scratch do not collide in banks)
-    const int NB = (sizeAB + 2 * K2 * CS) / (2 * CS);
+    const int NB = (sizeAB + K2 * CS) / (2 * CS);
     float4 *X = A, *Y = A + NB * CS;
     double2 *out = M + row * pp.ng;
     for (int d0 = 0; d0 < K12; d0 += NB) {
@@ -230,15 +224,15 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
     }
 }
 
-// Shared memory of pair_kernel_tf_ct<N> for a plan: A (+ B) (at least the i1 columns), the
-// two C buffers, the twiddle table, kz and the cell table.
+// Shared memory of pair_kernel_tf_ct<N> for a plan: A (+ B) (at least the i1 columns), C,
+// the twiddle table, kz and the cell table (48^3 workload: 50 KB, 4 blocks per SM).
 template <int N>
 inline size_t pair_tf_ct_smem(const PairPlan &pp)
 {
     constexpr RadPlan P = make_prune_plan(N);
     constexpr size_t ab = (size_t)N * N * ((P.nst == 3 && !pair_inplace<N>()) ? 2 : 1);
     const size_t cols = (size_t)pp.K2 * (N + 1);
-    return sizeof(float4) * ((ab > cols ? ab : cols) + 2 * cols + N) + sizeof(int) * ((size_t)pp.K2 + pp.K12);
+    return sizeof(float4) * ((ab > cols ? ab : cols) + cols + N) + sizeof(int) * ((size_t)pp.K2 + pp.K12);
 }
 
 template <int N>
