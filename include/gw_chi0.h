@@ -179,8 +179,37 @@ GW_API gw_status gw_chi0_contract(gw_chi0 *h, int nv, int nc, const double *ev, 
                            const double *M, int nw, const double *omega, double *chi);
 
 /*
+ * Static subspace approximation (Eq. chi_mat_sub and the paragraph around it): chi(w = 0) is
+ * diagonalised and its neig most significant eigenvectors (chi(0) is negative semidefinite:
+ * the most negative eigenvalues) form the N_G x N_Eig projection matrix C_s.
+ *   chi0   device complex128 [ng][ng], Hermitian (read only).
+ *   basis  device complex128 [ng][neig]: C_s, column B the eigenvector of eigenvalue B
+ *          (ascending, most significant first); each column's phase is arbitrary.
+ *   evals  device float64 [neig] or NULL: the eigenvalues.
+ * One dense eigendecomposition (cuSOLVER zheevdx, only the wanted vectors, loaded on first
+ * use; GW_ERR_UNSUPPORTED when it is not installed).  Synchronises the handle's stream.
+ * GW_ERR_ARG unless 1 <= neig <= ng.
+ */
+GW_API gw_status gw_chi0_subspace_basis(gw_chi0 *h, int ng, const double *chi0, int neig, double *basis,
+                                        double *evals);
+
+/*
+ * chi_BB'(i w) = sum_vc conj(M^B_vc) Delta_vc(i w) M^B'_vc with M^B_vc = sum_G M_vc(G) C_s[G][B]
+ * (Eq. chi_mat_sub), for slot iq: per pair chunk, stage (a), the projection onto C_s (split
+ * precision on the BF16 tensor cores, or FP64 DMMA, following the handle's mode), then stage
+ * (b) on the neig columns.  Equals C_s^H chi(i w) C_s.
+ *   basis    device complex128 [ng][neig] (e.g. from gw_chi0_subspace_basis).
+ *   omega    host double [nw], imaginary-axis magnitudes (eV).
+ *   chi_sub  device complex128 [nw][neig][neig], written in full, Hermitian.
+ * Errors as gw_chi0_compute; GW_ERR_ARG unless 1 <= neig <= ng of the slot's sphere.
+ */
+GW_API gw_status gw_chi0_compute_subspace(gw_chi0 *h, int iq, int neig, const double *basis, int nw,
+                                          const double *omega, double *chi_sub);
+
+/*
  * Adjoint of L = Re Tr(W chi0(iq, w)) for a Hermitian W (GWPT-style sensitivity,
- * Eq. gwpt motivates it).  Matrix elements are recomputed chunk by chunk.
+ * Eq. gwpt motivates it).  Matrix elements are recomputed chunk by chunk; Y = M W runs as
+ * a split product on the BF16 tensor cores in split-precision mode, on DMMA otherwise.
  *   W        device complex128 [ng][ng], Hermitian (only its values are read).
  *   L        host double* or NULL: the value of L (synchronous when non-NULL).
  *   dE_v     device float64 [nv]; dE_c device float64 [nc]: dL/dE.

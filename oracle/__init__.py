@@ -16,7 +16,10 @@ paper, "Overview of the Problem"):
   Eq. chi_mat and fixed by the hot-path statement (imaginary frequency);
 * ``chi0`` -- Eq. chi_mat without the outer factor 2 (the factor is folded into
   Delta), every entry summed separately with Neumaier compensation;
-* ``adjoint`` -- gradients of L = Re Tr(W chi0) (GWPT motivation, Eq. gwpt).
+* ``adjoint`` -- gradients of L = Re Tr(W chi0) (GWPT motivation, Eq. gwpt);
+* ``subspace_basis`` / ``chi0_subspace`` -- the static subspace approximation
+  (Eq. chi_mat_sub and the paragraph around it): the N_Eig most significant
+  eigenvectors of chi(0) as C_s, M^B = M C_s, chi_BB' from M^B as in Eq. chi_mat.
 
 All functions are pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle.py``
 (two independent routes to M, orthonormality, Parseval, gauge and translation
@@ -170,3 +173,19 @@ def adjoint(gv, cv, ev, gc, cc, ec, gchi, W, omega: float = 0.0):
     if rc:
         raise MemoryError("oracle_adjoint")
     return float(L[0]), dEv, dEc, dcv, dcc
+
+
+def subspace_basis(chi_w0, neig: int):
+    """The static subspace basis (paragraph of Eq. chi_mat_sub): chi(w = 0) is diagonalised
+    (numpy eigh, FP64) and the neig most significant eigenvectors -- chi(0) is negative
+    semidefinite, so the most negative eigenvalues -- are the columns of C_s [N_G, neig].
+    Returns (C_s, eigenvalues ascending)."""
+    w, v = np.linalg.eigh(np.asarray(chi_w0, np.complex128))
+    return np.ascontiguousarray(v[:, :neig]), w[:neig].copy()
+
+
+def chi0_subspace(M, dl, basis) -> np.ndarray:
+    """Eq. chi_mat_sub: chi_BB' = sum_vc conj(M^B_vc) Delta_vc M^B'_vc with
+    M^B_vc = sum_G M_vc(G) C_s[G][B] (the projection written out as a matrix product)."""
+    return chi0(np.asarray(M, np.complex128) @ np.asarray(basis, np.complex128), dl)
+

@@ -160,6 +160,28 @@ class Chi0:
                                              _ptr(dcv), _ptr(dcc)))
         return (L.value if want_L else None), dEv, dEc, dcv, dcc
 
+    def subspace_basis(self, chi0: torch.Tensor, neig: int):
+        """C_s [ng, neig] and the neig most negative eigenvalues of a Hermitian chi(0) block."""
+        chi0 = chi0.to(device=f"cuda:{self.device}", dtype=torch.complex128).contiguous()
+        ng = chi0.shape[0]
+        basis = torch.empty((ng, int(neig)), dtype=torch.complex128, device=f"cuda:{self.device}")
+        evals = torch.empty(int(neig), dtype=torch.float64, device=f"cuda:{self.device}")
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_subspace_basis(self.h, ng, _ptr(chi0), int(neig), _ptr(basis), _ptr(evals)))
+        return basis, evals
+
+    def compute_subspace(self, iq: int, basis: torch.Tensor, omega: Sequence[float], out: torch.Tensor | None = None):
+        """chi_BB'(i w) = C_s^H chi(i w) C_s from the projected pair elements: [nw, neig, neig]."""
+        basis = basis.to(device=f"cuda:{self.device}", dtype=torch.complex128).contiguous()
+        neig = basis.shape[1]
+        nw = len(omega)
+        if out is None:
+            out = torch.empty((nw, neig, neig), dtype=torch.complex128, device=f"cuda:{self.device}")
+        om_arr = (ctypes.c_double * nw)(*[float(w) for w in omega])
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_compute_subspace(self.h, int(iq), neig, _ptr(basis), nw, om_arr, _ptr(out)))
+        return out
+
     def sync(self):
         self._use_current_stream()
         self._check(self.lib.gw_chi0_sync(self.h))

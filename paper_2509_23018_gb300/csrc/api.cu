@@ -5,6 +5,8 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cusolverDn.h>
+#include <dlfcn.h>
 
 #include <algorithm>
 #include <cmath>
@@ -100,6 +102,27 @@ struct gw_chi0 {
     };
     std::vector<Graph> graphs;
     int *status = nullptr;
+    // split-precision general products (subspace projection, adjoint Y = M W)
+    int *EAbuf = nullptr, *EBbuf = nullptr;
+    size_t EAcap = 0, EBcap = 0;
+    void *ZBbuf = nullptr;      // B operand slices [s][2 nout][kpad]
+    size_t ZBcap = 0;
+    double2 *MBbuf = nullptr;   // projected pair elements of a chunk [chunk][neig]
+    size_t MBcap = 0;
+    // dense eigensolver (cuSOLVER, loaded on first use) for the subspace basis
+    struct {
+        void *lib = nullptr;
+        cusolverDnHandle_t hdl = nullptr;
+        decltype(&cusolverDnCreate) create = nullptr;
+        decltype(&cusolverDnDestroy) destroy = nullptr;
+        decltype(&cusolverDnSetStream) set_stream = nullptr;
+        decltype(&cusolverDnZheevdx_bufferSize) buffer_size = nullptr;
+        decltype(&cusolverDnZheevdx) heevdx = nullptr;
+    } sol;
+    double2 *eigA = nullptr, *eigWork = nullptr;
+    double *eigW = nullptr;
+    int *eigInfo = nullptr;
+    size_t eigA_cap = 0, eigWork_cap = 0, eigW_cap = 0, eigInfo_cap = 0;
     // scratch slots of the two-float pair kernel (sized in set_gsphere, outside any capture)
     float4 *pscr = nullptr;
     size_t pscr_cap = 0; // bytes
@@ -472,6 +495,60 @@ gw_status contract_chunk(gw_chi0 *h, const double2 *M, int64_t P, int ng, const 
     gw_status s = f64_jobs(h, jobs, M, P, ng, delta, dstride, nw, chi, h->tuned_bt);
     if (s) return s;
     return launch_f64_jobs(h, jobs, h->tuned_bt, h->tuned_waves);
+}
+
+// Real K extent of a general product with ka complex inner entries, padded for the TMA boxes.
+int64_t oz_kpad(int ka) { return ((int64_t)2 * ka + 63) / 64 * 64; }
+
+// B operand of a general split product: the columns of B [ka][nout] (complex, row-major)
+// into the handle's ZB / EB buffers.
+gw_status oz_prepare_b(gw_chi0 *h, const double2 *B, int ka, int nout)
+{
+    const int s = h->d.nslices;
+    const int64_t kpad = oz_kpad(ka);
+    gw_status st;
+    if ((st = grow(h, &h->ZBbuf, &h->ZBcap, (size_t)s * 2 * nout * kpad * 2, "product operand slices")) ||
+        (st = grow(h, (void **)&h->EBbuf, &h->EBcap, sizeof(int) * (size_t)nout, "product operand exponents")))
+        return st;
+    CK(h, gw::launch_oz_split_cols(B, ka, nout, s, kpad, h->ZBbuf, h->EBbuf, h->st), "oz column slices");
+    return GW_OK;
+}
+
+// Y[rows][nout] = A[rows][ka] B[ka][nout] (complex, row-major) in split precision, B prepared
+// by oz_prepare_b.  A's slices reuse the contraction's slice buffer (stream order separates
+// the two uses).
+gw_status oz_product(gw_chi0 *h, const double2 *A, int64_t rows, int ka, int nout, double2 *Y)
+{
+    const int s = h->d.nslices;
+    const int64_t kpad = oz_kpad(ka);
+    const int bn = 2 * nout >= 256 ? 256 : 128;
+    gw_status st;
+    if ((st = grow(h, &h->Zbuf, &h->Zcap, (size_t)s * rows * kpad * 2, "slice buffer")) ||
+        (st = grow(h, (void **)&h->EAbuf, &h->EAcap, sizeof(int) * (size_t)rows, "product row exponents")))
+        return st;
+    CK(h, cudaMemsetAsync(Y, 0, sizeof(double2) * (size_t)rows * nout, h->st), "zero product");
+    CK(h, gw::launch_oz_split_rows(A, rows, ka, s, kpad, h->Zbuf, h->EAbuf, h->st), "oz row slices");
+    gw::OzJob j;
+    std::memset(&j, 0, sizeof j);
+    if ((st = make_tmap_z(h, &j.tmA, h->Zbuf, kpad, (int)rows, s, gw::oz_box_rows_a())) ||
+        (st = make_tmap_z(h, &j.tmB, h->ZBbuf, kpad, 2 * nout, s, bn)))
+        return st;
+    j.E = h->EAbuf;
+    j.E2 = h->EBbuf;
+    j.out = (double *)Y;
+    j.ldo = 2 * (int64_t)nout;
+    j.rows_a = (int)rows;
+    j.rows_b = 2 * nout;
+    j.nk = (int)(kpad / gw::oz_box_k());
+    j.s = s;
+    j.ntiles = (int)((rows + gw::oz_box_rows_a() - 1) / gw::oz_box_rows_a()) * ((2 * nout + bn - 1) / bn);
+    j.item_start = 0;
+    const void *dj;
+    if ((st = upload_jobs(h, &j, sizeof j, &dj))) return st;
+    CK(h, gw::launch_oz_gemm_general(bn, (const gw::OzJob *)dj, 1, j.ntiles, std::min(j.ntiles, num_sms()), h->status,
+                                     h->st),
+       "oz general product");
+    return GW_OK;
 }
 
 bool alias_free(const gw_chi0 *h, const BandSet &v, const BandSet &c, const Sphere &s, int *axis)
@@ -970,6 +1047,16 @@ void gw_chi0_destroy(gw_chi0 *h)
     dfree(h, h->Mall, h->Mall_cap);
     dfree(h, h->pscr, h->pscr_cap);
     dfree(h, h->pflags, h->pflags_cap);
+    dfree(h, h->EAbuf, h->EAcap);
+    dfree(h, h->EBbuf, h->EBcap);
+    dfree(h, h->ZBbuf, h->ZBcap);
+    dfree(h, h->MBbuf, h->MBcap);
+    dfree(h, h->eigA, h->eigA_cap);
+    dfree(h, h->eigWork, h->eigWork_cap);
+    dfree(h, h->eigW, h->eigW_cap);
+    dfree(h, h->eigInfo, h->eigInfo_cap);
+    if (h->sol.hdl) h->sol.destroy(h->sol.hdl);
+    if (h->sol.lib) dlclose(h->sol.lib);
     dfree(h, h->Dall, h->Dall_cap);
     dfree(h, h->SPall, h->SPall_cap);
     dfree(h, h->Zall, h->Zall_cap);
@@ -1409,6 +1496,12 @@ gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, dou
     ACK(cudaMemsetAsync(pbv, 0, szV, h->st), "zero");
     ACK(cudaMemsetAsync(pbc, 0, szC, h->st), "zero");
     gw::PairPlan pp = pair_plan(h, sp);
+    // split precision: Y = M W as a split product, W's slices once per call
+    const bool split = h->d.prec == GW_PREC_OZAKI_BF16;
+    if (split && (s = oz_prepare_b(h, (const double2 *)W, ng, ng))) {
+        cleanup();
+        return s;
+    }
     for (int v0 = 0; v0 < nv; v0 += (int)vch) {
         const int nvc = (int)std::min<int64_t>(vch, nv - v0);
         const int64_t p0 = (int64_t)v0 * nc, cnt = (int64_t)nvc * nc;
@@ -1418,7 +1511,14 @@ gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, dou
         }
         {
             Scope sc(h, "adj_zgemm");
-            ACK(gw::launch_zgemm(Mb, (const double2 *)W, Yb, cnt, ng, ng, h->st), "Y = M W");
+            if (split) {
+                if ((s = oz_product(h, Mb, cnt, ng, ng, Yb))) {
+                    cleanup();
+                    return s;
+                }
+            } else {
+                ACK(gw::launch_zgemm(Mb, (const double2 *)W, Yb, cnt, ng, ng, h->st), "Y = M W");
+            }
         }
         {
             Scope sc(h, "adj_rows");
@@ -1497,3 +1597,123 @@ int gw_chi0_timing(gw_chi0 *h, int n, char (*names)[32], double *ms, int64_t *la
 size_t gw_chi0_device_bytes(const gw_chi0 *h) { return h ? h->bytes : 0; }
 
 } // extern "C"
+
+// ------------------------------------------------------------------ static subspace
+namespace {
+gw_status load_solver(gw_chi0 *h)
+{
+    if (h->sol.hdl) return GW_OK;
+    const char *names[] = {"libcusolver.so.12", "libcusolver.so.11", "libcusolver.so",
+                           "/usr/local/cuda/lib64/libcusolver.so.12", "/usr/local/cuda/lib64/libcusolver.so"};
+    for (const char *n : names)
+        if ((h->sol.lib = dlopen(n, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h->sol.lib) return fail(h, GW_ERR_UNSUPPORTED, "the dense eigensolver (libcusolver) was not found");
+    h->sol.create = (decltype(h->sol.create))dlsym(h->sol.lib, "cusolverDnCreate");
+    h->sol.destroy = (decltype(h->sol.destroy))dlsym(h->sol.lib, "cusolverDnDestroy");
+    h->sol.set_stream = (decltype(h->sol.set_stream))dlsym(h->sol.lib, "cusolverDnSetStream");
+    h->sol.buffer_size = (decltype(h->sol.buffer_size))dlsym(h->sol.lib, "cusolverDnZheevdx_bufferSize");
+    h->sol.heevdx = (decltype(h->sol.heevdx))dlsym(h->sol.lib, "cusolverDnZheevdx");
+    if (!h->sol.create || !h->sol.destroy || !h->sol.set_stream || !h->sol.buffer_size || !h->sol.heevdx)
+        return fail(h, GW_ERR_UNSUPPORTED, "libcusolver lacks the Hermitian eigensolver entry points");
+    if (h->sol.create(&h->sol.hdl) != CUSOLVER_STATUS_SUCCESS) {
+        h->sol.hdl = nullptr;
+        return fail(h, GW_ERR_CUDA, "cusolverDnCreate failed");
+    }
+    return GW_OK;
+}
+} // namespace
+
+gw_status gw_chi0_subspace_basis(gw_chi0 *h, int ng, const double *chi0, int neig, double *basis, double *evals)
+{
+    if (!h) return GW_ERR_ARG;
+    if (ng < 1 || neig < 1 || neig > ng) return fail(h, GW_ERR_ARG, "need 1 <= neig <= ng");
+    if (!chi0 || !basis) return fail(h, GW_ERR_ARG, "null pointer");
+    gw_status st = load_solver(h);
+    if (st) return st;
+    const size_t nn = (size_t)ng * ng;
+    if ((st = grow(h, (void **)&h->eigA, &h->eigA_cap, sizeof(double2) * nn, "eigensolver matrix")) ||
+        (st = grow(h, (void **)&h->eigW, &h->eigW_cap, sizeof(double) * (size_t)ng, "eigenvalues")) ||
+        (st = grow(h, (void **)&h->eigInfo, &h->eigInfo_cap, sizeof(int), "eigensolver status")))
+        return st;
+    // The row-major Hermitian chi0 read column-major is its transpose, conj(chi0): the solver
+    // returns the conjugated eigenvectors, which the transposing copy conjugates back.
+    CK(h, cudaMemcpyAsync(h->eigA, chi0, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, h->st), "copy chi0");
+    if (h->sol.set_stream(h->sol.hdl, h->st) != CUSOLVER_STATUS_SUCCESS) return fail(h, GW_ERR_CUDA, "solver stream");
+    int meig = 0, lwork = 0;
+    if (h->sol.buffer_size(h->sol.hdl, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, ng,
+                           (const cuDoubleComplex *)h->eigA, ng, 0.0, 0.0, 1, neig, &meig, h->eigW,
+                           &lwork) != CUSOLVER_STATUS_SUCCESS)
+        return fail(h, GW_ERR_CUDA, "eigensolver workspace query failed");
+    if ((st = grow(h, (void **)&h->eigWork, &h->eigWork_cap, sizeof(double2) * (size_t)std::max(lwork, 1),
+                   "eigensolver workspace")))
+        return st;
+    {
+        Scope sc(h, "subspace_eig");
+        if (h->sol.heevdx(h->sol.hdl, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, ng,
+                          (cuDoubleComplex *)h->eigA, ng, 0.0, 0.0, 1, neig, &meig, h->eigW,
+                          (cuDoubleComplex *)h->eigWork, lwork, h->eigInfo) != CUSOLVER_STATUS_SUCCESS)
+            return fail(h, GW_ERR_CUDA, "eigensolver failed");
+        CK(h, gw::launch_conj_transpose(h->eigA, ng, neig, (double2 *)basis, h->st), "basis");
+    }
+    if (evals)
+        CK(h, cudaMemcpyAsync(evals, h->eigW, sizeof(double) * neig, cudaMemcpyDeviceToDevice, h->st), "eigenvalues");
+    int info = 0;
+    CK(h, cudaMemcpyAsync(&info, h->eigInfo, sizeof(int), cudaMemcpyDeviceToHost, h->st), "solver status");
+    CK(h, cudaStreamSynchronize(h->st), "subspace basis sync");
+    if (info != 0) return fail(h, GW_ERR_CUDA, "eigensolver reported %d", info);
+    if (meig != neig) return fail(h, GW_ERR_CUDA, "eigensolver returned %d of %d vectors", meig, neig);
+    return GW_OK;
+}
+
+gw_status gw_chi0_compute_subspace(gw_chi0 *h, int iq, int neig, const double *basis, int nw, const double *omega,
+                                   double *chi_sub)
+{
+    if (!h) return GW_ERR_ARG;
+    if (nw < 1 || nw > gw::kMaxOmega || !omega || !basis || !chi_sub)
+        return fail(h, GW_ERR_ARG, "bad arguments (1 <= nw <= %d, non-null pointers)", gw::kMaxOmega);
+    gw::OmegaList om;
+    om.nw = nw;
+    for (int i = 0; i < nw; ++i) {
+        if (!(omega[i] >= 0.0) || !std::isfinite(omega[i])) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
+        om.w[i] = omega[i];
+    }
+    gw_status s = check_slot(h, iq);
+    if (s) return s;
+    const Sphere &sp = h->sph[iq];
+    const BandSet &v = h->val[iq];
+    const int ng = sp.ng;
+    if (neig < 1 || neig > ng) return fail(h, GW_ERR_ARG, "need 1 <= neig <= ng");
+    const int64_t P = (int64_t)v.nb * h->cond.nb;
+    const int64_t chunk = std::min<int64_t>(h->d.pair_chunk, P);
+    CK(h, cudaMemsetAsync(chi_sub, 0, sizeof(double2) * (size_t)nw * neig * neig, h->st), "zero chi");
+    if ((s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw)) ||
+        (s = grow(h, (void **)&h->MBbuf, &h->MBcap, sizeof(double2) * (size_t)chunk * neig, "projected M")))
+        return s;
+    const bool split = h->d.prec == GW_PREC_OZAKI_BF16;
+    if (split && (s = oz_prepare_b(h, (const double2 *)basis, ng, neig))) return s;
+    gw::PairPlan pp = pair_plan(h, sp);
+    for (int64_t p0 = 0; p0 < P; p0 += chunk) {
+        const int64_t cnt = std::min(chunk, P - p0);
+        {
+            Scope sc(h, "pair_mtxel");
+            CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
+        }
+        {
+            Scope sc(h, "subspace_projection");
+            if (split) {
+                if ((s = oz_product(h, h->Mbuf, cnt, ng, neig, h->MBbuf))) return s;
+            } else {
+                CK(h, gw::launch_zgemm(h->Mbuf, (const double2 *)basis, h->MBbuf, cnt, ng, neig, h->st), "projection");
+            }
+        }
+        {
+            Scope sc(h, "delta");
+            CK(h, gw::launch_delta(v.energy, h->cond.energy, h->cond.nb, p0, cnt, om, h->dbuf, h->st), "delta");
+        }
+        if ((s = contract_chunk(h, h->MBbuf, cnt, neig, h->dbuf, cnt, nw, (double2 *)chi_sub))) return s;
+    }
+    Scope sc(h, "symmetrize");
+    CK(h, gw::launch_symmetrize((double2 *)chi_sub, neig, nw, h->st), "symmetrize");
+    return GW_OK;
+}
+

@@ -58,6 +58,8 @@ cudaError_t launch_delta(const double *ev, const double *ec, int nc, int64_t p0,
 // diag[w][g] += sum_p delta[w][p] |M[p][g]|^2
 cudaError_t launch_diag(const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride, int nw,
                         double *diag, int64_t diag_wstride, cudaStream_t st);
+// out[g][b] = conj(V[b n + g]) (column-major n x neig -> row-major [n][neig], conjugated)
+cudaError_t launch_conj_transpose(const double2 *V, int n, int neig, double2 *out, cudaStream_t st);
 // a bounded wait that is never satisfied: sets kStatusTimeout in *status after iters tries
 cudaError_t launch_watchdog(long long iters, int *status, cudaStream_t st);
 // lower triangle <- conj(upper), Im diag <- 0, for nw consecutive ng x ng blocks
@@ -91,10 +93,27 @@ struct __align__(128) OzJob {
     const int *E;         // [ng] column exponents
     double *chi;          // [ng][ng] complex
     int ng, nk, s, ntiles, item_start;
+    // general product (launch_oz_gemm_general): out[rows_a][rows_b] real (complex pairs)
+    // += A B with A slices by row (exponents E[rows_a]) and B^T slices by row (exponents
+    // E2[rows_b / 2])
+    const int *E2;
+    double *out;
+    int64_t ldo;
+    int rows_a, rows_b;
 };
 cudaError_t launch_oz_gemm_jobs(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
                                 cudaStream_t st);
 int oz_tiles(int ng, int bn);
+// General split product: Y[rows][nout] (complex, row-major, overwritten) = A[rows][ka] B[ka][nout]
+// (complex, row-major), A split by rows and B by columns into s six-bit BF16 slices.
+// ZA: s * rows * kpad bf16, ZB: s * 2 nout * kpad bf16, EA: rows ints, EB: nout ints,
+// kpad = ka rounded up to a multiple of 32 complex (64 real) entries.
+cudaError_t launch_oz_split_rows(const double2 *A, int64_t rows, int ka, int s, int64_t kpad, void *ZA, int *EA,
+                                 cudaStream_t st);
+cudaError_t launch_oz_split_cols(const double2 *B, int ka, int nout, int s, int64_t kpad, void *ZB, int *EB,
+                                 cudaStream_t st);
+cudaError_t launch_oz_gemm_general(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
+                                   cudaStream_t st);
 size_t oz_smem_bytes(int bn);
 int oz_box_rows_a();
 int oz_box_k();

@@ -120,6 +120,101 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double2 *__restrict
     }
 }
 
+// ------------------------------------------------------------------ general product: slices
+// Y = A B with A split by rows and B by columns: x = 2^E sum_{i=1..s} 2^(-6 i) z_i, the same
+// balanced base-64 digits as oz_slice_kernel, with E = max(ilogb) + 2 over a row of A or a
+// column of B (both parts of a complex entry).
+__device__ __forceinline__ int oz_expo(double a)
+{
+    if (!(a > 0.0)) return kOzNoColumn;
+    const int be = (int)((__double_as_longlong(a) >> 52) & 0x7ff);
+    return (be == 0 ? -1023 : be - 1023) + 2;
+}
+
+__device__ __forceinline__ void oz_digits(double x, int E, int s, uint16_t *out, int64_t plane)
+{
+    const int sh = kOzBeta * s - E;
+    const double sc = __longlong_as_double((long long)(1023 + max(-1022, min(1023, sh))) << 52);
+    long long N = __double2ll_rn(x * sc);
+    for (int i = s - 1; i >= 1; --i) {
+        const int d = (int)((N + 32) & 63) - 32;
+        N = (N - d) >> 6;
+        out[i * plane] = (uint16_t)(__float_as_uint((float)d) >> 16);
+    }
+    out[0] = (uint16_t)(__float_as_uint((float)N) >> 16);
+}
+
+__device__ __forceinline__ int oz_block_max(int e, int *red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0) red[wid] = e;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        e = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : kOzNoColumn;
+        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        if (threadIdx.x == 0) red[0] = e;
+    }
+    __syncthreads();
+    return red[0];
+}
+
+// One block per row p of A [rows][ka] (complex): E[p], then Z[i][p][k], k = 2 g + {Re, Im},
+// zero for k >= 2 ka.
+__global__ void __launch_bounds__(256) oz_split_rows_kernel(const double2 *__restrict__ A, int64_t rows, int ka,
+                                                            int s, int64_t kpad, uint16_t *__restrict__ Z,
+                                                            int *__restrict__ E)
+{
+    __shared__ int red[8];
+    const int64_t p = blockIdx.x;
+    const double2 *a = A + p * ka;
+    int e = kOzNoColumn;
+    for (int g = threadIdx.x; g < ka; g += blockDim.x) {
+        const double2 x = a[g];
+        e = max(e, oz_expo(fmax(fabs(x.x), fabs(x.y))));
+    }
+    e = oz_block_max(e, red);
+    if (threadIdx.x == 0) E[p] = e;
+    uint16_t *zr = Z + p * kpad;
+    for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x) {
+        const int g = (int)(k >> 1);
+        const double x = g < ka ? ((k & 1) ? a[g].y : a[g].x) : 0.0;
+        oz_digits(x, e, s, zr + k, rows * kpad);
+    }
+}
+
+// One block per column b of B [ka][nout] (complex): E[b], then rows 2b (Re of the product)
+// and 2b + 1 (Im) of the real K-major operand B^T: row 2b = (Re B, -Im B), row 2b + 1 =
+// (Im B, Re B) interleaved by g, so that [Re A, Im A] interleaved times them gives Re and
+// Im of (A B)[p][b].
+__global__ void __launch_bounds__(256) oz_split_cols_kernel(const double2 *__restrict__ B, int ka, int nout, int s,
+                                                            int64_t kpad, uint16_t *__restrict__ Z,
+                                                            int *__restrict__ E)
+{
+    __shared__ int red[8];
+    const int b = blockIdx.x;
+    int e = kOzNoColumn;
+    for (int g = threadIdx.x; g < ka; g += blockDim.x) {
+        const double2 x = B[(int64_t)g * nout + b];
+        e = max(e, oz_expo(fmax(fabs(x.x), fabs(x.y))));
+    }
+    e = oz_block_max(e, red);
+    if (threadIdx.x == 0) E[b] = e;
+    const int64_t plane = (int64_t)2 * nout * kpad;
+    uint16_t *z0 = Z + (int64_t)(2 * b) * kpad, *z1 = z0 + kpad;
+    for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x) {
+        const int g = (int)(k >> 1);
+        double x0 = 0.0, x1 = 0.0;
+        if (g < ka) {
+            const double2 x = B[(int64_t)g * nout + b];
+            x0 = (k & 1) ? -x.y : x.x;
+            x1 = (k & 1) ? x.x : x.y;
+        }
+        oz_digits(x0, e, s, z0 + k, plane);
+        oz_digits(x1, e, s, z1 + k, plane);
+    }
+}
+
 // ------------------------------------------------------------------ tcgen05 GEMM
 // Persistent and batched: a launch takes a table of jobs (one job = one chunk's slices
 // for one chi block, each with its own N_G, tensor maps and exponents) and the list of
@@ -154,6 +249,19 @@ __device__ __forceinline__ void oz_tile_ij(int tile, int nI, int bnc, int &I, in
     I = rem;
 }
 
+// tile -> (I, J) for the general product: I-major (blocks that run together share A rows)
+template <bool GEN, int BN>
+__device__ __forceinline__ void oz_tile(const OzJob &jb, int tile, int &I, int &J)
+{
+    if constexpr (GEN) {
+        const int nJ = (jb.rows_b + BN - 1) / BN;
+        I = tile / nJ;
+        J = tile - I * nJ;
+    } else {
+        oz_tile_ij(tile, (2 * jb.ng + kOzBM - 1) / kOzBM, BN / 2, I, J);
+    }
+}
+
 __device__ __forceinline__ int oz_find_job(const OzJob *jobs, int njobs, int item)
 {
     int lo = 0, hi = njobs - 1;
@@ -165,7 +273,9 @@ __device__ __forceinline__ int oz_find_job(const OzJob *jobs, int njobs, int ite
     return lo;
 }
 
-template <int BN>
+// GEN = false: the Hermitian contraction above (upper tiles, chi epilogue).  GEN = true:
+// the general product out += A B (all tiles, each owned by one block, plain FP64 adds).
+template <int BN, bool GEN>
 __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__restrict__ jobs, int njobs, int nitems,
                                                                int *status)
 {
@@ -207,7 +317,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const OzJob &jb = jobs[oz_find_job(jobs, njobs, item)];
                 int I, J;
-                oz_tile_ij(item - jb.item_start, (2 * jb.ng + kOzBM - 1) / kOzBM, C::BNC, I, J);
+                oz_tile<GEN, BN>(jb, item - jb.item_start, I, J);
                 for (int t = 2; t <= jb.s + 1 && ok; ++t)
                     for (int i = 1; i < t && ok; ++i)
                         for (int kb = 0; kb < jb.nk; ++kb, ++it) {
@@ -256,45 +366,83 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
     } else {
         // epilogue: warps 2..5 -> TMEM lane quadrant (warp % 4), one tile row per thread
         const int q = warp & 3;
-        const int r = q * 32 + lane;              // tile row (real index)
-        const int odd = r & 1;                    // 0: Re part, 1: Im part
+        const int r = q * 32 + lane;              // tile row
         uint32_t grp = 0;
-        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const OzJob &jb = jobs[oz_find_job(jobs, njobs, item)];
-            int I, J;
-            oz_tile_ij(item - jb.item_start, (2 * jb.ng + kOzBM - 1) / kOzBM, C::BNC, I, J);
-            const int ng = jb.ng;
-            const int g = I * 64 + (r >> 1);      // complex row G
-            const int Eg = g < ng ? __ldg(jb.E + g) : kOzNoColumn;
-            double *crow = jb.chi + 2 * ((int64_t)g * ng) + odd;
-            for (int t = 2; t <= jb.s + 1; ++t, ++grp) {
-                const uint32_t b = grp & 1, u = grp >> 1;
-                const bool got = bar_wait(&tfull[b], u & 1);
-                if (!__all_sync(0xffffffffu, got)) { ok = false; break; } // warp-uniform exit
-                tc_fence_after();
-                const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * BN;
+        if constexpr (GEN) {
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const OzJob &jb = jobs[oz_find_job(jobs, njobs, item)];
+                int I, J;
+                oz_tile<GEN, BN>(jb, item - jb.item_start, I, J);
+                const int pr = I * kOzBM + r;     // output row
+                const int Ea = pr < jb.rows_a ? __ldg(jb.E + pr) : kOzNoColumn;
+                double *orow = jb.out + (int64_t)pr * jb.ldo;
+                for (int t = 2; t <= jb.s + 1; ++t, ++grp) {
+                    const uint32_t b = grp & 1, u = grp >> 1;
+                    const bool got = bar_wait(&tfull[b], u & 1);
+                    if (!__all_sync(0xffffffffu, got)) { ok = false; break; } // warp-uniform exit
+                    tc_fence_after();
+                    const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * BN;
 #pragma unroll 1
-                for (int c0 = 0; c0 < BN; c0 += 32) {
-                    uint32_t v[32];
-                    GW_TMEM_LD32(ta + c0, v);
-                    tmem_wait_ld();
+                    for (int c0 = 0; c0 < BN; c0 += 32) {
+                        uint32_t v[32];
+                        GW_TMEM_LD32(ta + c0, v);
+                        tmem_wait_ld();
+                        if (pr < jb.rows_a) {
 #pragma unroll
-                    for (int cc = 0; cc < 16; ++cc) {
-                        const int ev = (int)__uint_as_float(v[2 * cc]);
-                        const int od = (int)__uint_as_float(v[2 * cc + 1]);
-                        const int rv = __shfl_xor_sync(0xffffffffu, od, 1);
-                        const int val = odd ? (rv - ev) : (ev + rv);
-                        const int gp = J * C::BNC + (c0 >> 1) + cc;
-                        if (g < ng && gp < ng && g <= gp && val != 0) {
-                            const int ex = Eg + __ldg(jb.E + gp) - kOzBeta * t;
-                            const double sc = -__longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
-                            // atomic: blocks of other pair segments may add into the same entry
-                            atomicAdd(crow + 2 * (int64_t)gp, (double)val * sc);
+                            for (int cc = 0; cc < 32; ++cc) {
+                                const int j = J * BN + c0 + cc; // output real column
+                                const int val = (int)__uint_as_float(v[cc]);
+                                if (j < jb.rows_b && val != 0) {
+                                    const int ex = Ea + __ldg(jb.E2 + (j >> 1)) - kOzBeta * t;
+                                    // the tile belongs to this block alone: a plain add
+                                    orow[j] += (double)val * __longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
+                                }
+                            }
                         }
                     }
+                    tc_fence_before();
+                    bar_arrive(&tempty[b]);
                 }
-                tc_fence_before();
-                bar_arrive(&tempty[b]);
+            }
+        } else {
+            const int odd = r & 1;                    // 0: Re part, 1: Im part
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const OzJob &jb = jobs[oz_find_job(jobs, njobs, item)];
+                int I, J;
+                oz_tile<GEN, BN>(jb, item - jb.item_start, I, J);
+                const int ng = jb.ng;
+                const int g = I * 64 + (r >> 1);      // complex row G
+                const int Eg = g < ng ? __ldg(jb.E + g) : kOzNoColumn;
+                double *crow = jb.chi + 2 * ((int64_t)g * ng) + odd;
+                for (int t = 2; t <= jb.s + 1; ++t, ++grp) {
+                    const uint32_t b = grp & 1, u = grp >> 1;
+                    const bool got = bar_wait(&tfull[b], u & 1);
+                    if (!__all_sync(0xffffffffu, got)) { ok = false; break; } // warp-uniform exit
+                    tc_fence_after();
+                    const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * BN;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < BN; c0 += 32) {
+                        uint32_t v[32];
+                        GW_TMEM_LD32(ta + c0, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int cc = 0; cc < 16; ++cc) {
+                            const int ev = (int)__uint_as_float(v[2 * cc]);
+                            const int od = (int)__uint_as_float(v[2 * cc + 1]);
+                            const int rv = __shfl_xor_sync(0xffffffffu, od, 1);
+                            const int val = odd ? (rv - ev) : (ev + rv);
+                            const int gp = J * C::BNC + (c0 >> 1) + cc;
+                            if (g < ng && gp < ng && g <= gp && val != 0) {
+                                const int ex = Eg + __ldg(jb.E + gp) - kOzBeta * t;
+                                const double sc = -__longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
+                                // atomic: blocks of other pair segments may add into the same entry
+                                atomicAdd(crow + 2 * (int64_t)gp, (double)val * sc);
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    bar_arrive(&tempty[b]);
+                }
             }
         }
         if (!ok) atomicOr(status, kStatusTimeout);
@@ -351,15 +499,50 @@ cudaError_t launch_oz_gemm_jobs(int bn, const OzJob *jobs, int njobs, int nitems
     if (nitems == 0) return cudaSuccess;
     cudaError_t e;
     if (bn == 128) {
-        e = cudaFuncSetAttribute(oz_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(oz_gemm_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)OzCfg<128>::Smem);
         if (e != cudaSuccess) return e;
-        oz_gemm_kernel<128><<<grid, kOzThreads, OzCfg<128>::Smem, st>>>(jobs, njobs, nitems, status);
+        oz_gemm_kernel<128, false><<<grid, kOzThreads, OzCfg<128>::Smem, st>>>(jobs, njobs, nitems, status);
     } else {
-        e = cudaFuncSetAttribute(oz_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(oz_gemm_kernel<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)OzCfg<256>::Smem);
         if (e != cudaSuccess) return e;
-        oz_gemm_kernel<256><<<grid, kOzThreads, OzCfg<256>::Smem, st>>>(jobs, njobs, nitems, status);
+        oz_gemm_kernel<256, false><<<grid, kOzThreads, OzCfg<256>::Smem, st>>>(jobs, njobs, nitems, status);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_split_rows(const double2 *A, int64_t rows, int ka, int s, int64_t kpad, void *ZA, int *EA,
+                                 cudaStream_t st)
+{
+    if (rows == 0) return cudaSuccess;
+    oz_split_rows_kernel<<<(unsigned)rows, 256, 0, st>>>(A, rows, ka, s, kpad, (uint16_t *)ZA, EA);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_split_cols(const double2 *B, int ka, int nout, int s, int64_t kpad, void *ZB, int *EB,
+                                 cudaStream_t st)
+{
+    if (nout == 0) return cudaSuccess;
+    oz_split_cols_kernel<<<(unsigned)nout, 256, 0, st>>>(B, ka, nout, s, kpad, (uint16_t *)ZB, EB);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_gemm_general(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
+                                   cudaStream_t st)
+{
+    if (nitems == 0) return cudaSuccess;
+    cudaError_t e;
+    if (bn == 128) {
+        e = cudaFuncSetAttribute(oz_gemm_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)OzCfg<128>::Smem);
+        if (e != cudaSuccess) return e;
+        oz_gemm_kernel<128, true><<<grid, kOzThreads, OzCfg<128>::Smem, st>>>(jobs, njobs, nitems, status);
+    } else {
+        e = cudaFuncSetAttribute(oz_gemm_kernel<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)OzCfg<256>::Smem);
+        if (e != cudaSuccess) return e;
+        oz_gemm_kernel<256, true><<<grid, kOzThreads, OzCfg<256>::Smem, st>>>(jobs, njobs, nitems, status);
     }
     return cudaGetLastError();
 }

@@ -95,6 +95,33 @@ cudaError_t launch_symmetrize(double2 *chi, int ng, int nw, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// out[g][b] = conj(V[b n + g]): a column-major n x neig block (an eigensolver's vectors of the
+// conjugated matrix) to a row-major [n][neig] basis.  32 x 32 tiles through shared memory.
+__global__ void conj_transpose_kernel(const double2 *__restrict__ V, int n, int neig, double2 *__restrict__ out)
+{
+    __shared__ double2 t[32][33];
+    const int g0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int b = b0 + r, g = g0 + threadIdx.x;
+        if (b < neig && g < n) t[r][threadIdx.x] = V[(int64_t)b * n + g];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int g = g0 + r, b = b0 + threadIdx.x;
+        if (g < n && b < neig) {
+            const double2 x = t[threadIdx.x][r];
+            out[(int64_t)g * neig + b] = make_double2(x.x, -x.y);
+        }
+    }
+}
+
+cudaError_t launch_conj_transpose(const double2 *V, int n, int neig, double2 *out, cudaStream_t st)
+{
+    if (n == 0 || neig == 0) return cudaSuccess;
+    conj_transpose_kernel<<<dim3((n + 31) / 32, (neig + 31) / 32), dim3(32, 8), 0, st>>>(V, n, neig, out);
+    return cudaGetLastError();
+}
+
 // Watchdog check: one thread waits, with the given bound, on an mbarrier that nothing
 // arrives at, exactly as the contraction kernels wait on their TMA and MMA barriers; when
 // the bound runs out it records kStatusTimeout and returns, leaving the context usable.

@@ -305,3 +305,45 @@ def test_adjoint_identity_W_energy_closed_form(adj_case):
     assert abs(L - np.sum(4 * x / (x * x + w * w) * n2)) < 1e-14 * abs(L)
     assert np.allclose(dEv, np.sum(n2 * dd, 1), rtol=1e-13)
     assert np.allclose(dEc, -np.sum(n2 * dd, 0), rtol=1e-13)
+
+
+# ------------------------------------------------------------------ static subspace (next row f1)
+
+@pytest.fixture(scope="module")
+def sub_case():
+    p = tiny(nv=3, nc=8, ngpsi=93, ng=27, seed=19)
+    M = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)
+    chi_0 = oracle.chi0(M, oracle.delta(p.ev, p.ec, 0.0))
+    return p, M, chi_0
+
+
+def test_subspace_basis_eigenpairs(sub_case):
+    """C_s is orthonormal, chi(0) C_s = C_s diag(lambda), and the kept eigenvalues are the most
+    negative ones (chi(0) is negative semidefinite: the most significant)."""
+    _, _, chi_0 = sub_case
+    C, lam = oracle.subspace_basis(chi_0, 8)
+    assert np.abs(C.conj().T @ C - np.eye(8)).max() < 1e-13
+    assert rel(chi_0 @ C, C * lam) < 1e-13
+    rest = np.linalg.eigvalsh(chi_0)[8:]
+    assert lam.max() <= rest.min() and lam.max() < 0
+
+
+def test_subspace_chi_at_zero_is_diagonal(sub_case):
+    """At w = 0 the subspace polarizability is the eigenvalue matrix: C_s^H chi(0) C_s = diag(lambda)."""
+    p, M, chi_0 = sub_case
+    C, lam = oracle.subspace_basis(chi_0, 8)
+    cs = oracle.chi0_subspace(M, oracle.delta(p.ev, p.ec, 0.0), C)
+    assert rel(cs, np.diag(lam).astype(np.complex128)) < 1e-12
+
+
+@pytest.mark.parametrize("w", [2.0, 9.0])
+def test_subspace_chi_is_projected_chi(sub_case, w):
+    """chi_BB'(w) from M^B = M C_s equals C_s^H chi_GG'(w) C_s (the two representations the
+    paper connects), and with the full basis the back-projection C_s chi_BB' C_s^H is chi(w)."""
+    p, M, chi_0 = sub_case
+    dl = oracle.delta(p.ev, p.ec, w)
+    chi_w = oracle.chi0(M, dl)
+    C, _ = oracle.subspace_basis(chi_0, 8)
+    assert rel(oracle.chi0_subspace(M, dl, C), C.conj().T @ chi_w @ C) < 1e-12
+    Cf, _ = oracle.subspace_basis(chi_0, chi_0.shape[0])
+    assert rel(Cf @ oracle.chi0_subspace(M, dl, Cf) @ Cf.conj().T, chi_w) < 1e-12
