@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--subspace", action="store_true")
     return ap.parse_args()
 
 
@@ -537,7 +538,7 @@ def adjoint(args):
     prob = gwgen.config_problem(cfg)
     W = gwgen.hermitian(np.random.default_rng(gwgen.BASE_SEED + 4), cfg.ng)
     dev = torch.device("cuda", 0)
-    h = gw.from_problem(prob, mtxel=args.mtxel or "twofloat")
+    h = gw.from_problem(prob, prec=args.prec, nslices=args.nslices, mtxel=args.mtxel or "twofloat")
     Wd = torch.as_tensor(W, device=dev)
     h.adjoint(0, Wd)
     torch.cuda.synchronize()
@@ -549,8 +550,64 @@ def adjoint(args):
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / args.steps
     print(json.dumps({"workload": "L = Re Tr(W chi0), 40^3, 96+768 bands, N_Gpsi=4500, N_G=1500",
-                      "s_per_adjoint": sec, "L": L,
+                      "prec": args.prec, "nslices": args.nslices, "s_per_adjoint": sec, "L": L,
                       "timing_ms": {k: v[0] / args.steps for k, v in h.timing().items()}}), flush=True)
+
+
+def subspace(args):
+    """Static subspace on the 48^3 workload: chi(0) in the full basis, the N_Eig = 20 % basis,
+    then 19 imaginary frequencies in the subspace, against the same 19 in the full basis."""
+    import torch
+    import paper_2509_23018_gb300 as gw
+    cfg = gwgen.CONFIGS["c2_48cube"]
+    prob = gwgen.config_problem(cfg)
+    neig = cfg.ng // 5
+    om19 = [float(w) for w in gwgen.gl_freqs(19)]
+    mtxel = args.mtxel or "twofloat"
+    h = gw.from_problem(prob, prec=args.prec, nslices=args.nslices, mtxel=mtxel, pair_chunk=cfg.pair_chunk)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    (chi0,), _ = timed(lambda: h.compute(0, [0.0]))  # warm-up (tuning, buffers)
+    (chi0,), t0 = timed(lambda: h.compute(0, [0.0]))
+    (C, lam), tb_first = timed(lambda: h.subspace_basis(chi0[0], neig))  # loads the solver
+    (C, lam), tb = timed(lambda: h.subspace_basis(chi0[0], neig))
+    _ = h.compute_subspace(0, C, om19)
+    h.set_timing(True)
+    h.timing(reset=True)
+    sub, ts = timed(lambda: h.compute_subspace(0, C, om19))
+    kms = {k: v[0] for k, v in h.timing(reset=True).items()}
+    h.set_timing(False)
+    sub0, _ = timed(lambda: h.compute_subspace(0, C, [0.0]))
+    full, tf = timed(lambda: h.compute(0, om19)[0])
+    h.sync()
+    Cn = C.cpu().numpy()
+    # identities at full size: chi_BB'(0) = diag(lambda); chi_BB'(w) = C^H chi(w) C
+    d0 = float(np.linalg.norm(sub0[0].cpu().numpy() - np.diag(lam.cpu().numpy()))
+               / np.linalg.norm(lam.cpu().numpy()))
+    k = len(om19) // 2
+    fk = full[k].cpu().numpy()
+    proj = Cn.conj().T @ fk @ Cn
+    dk = float(np.linalg.norm(sub[k].cpu().numpy() - proj) / np.linalg.norm(proj))
+    approx = float(np.linalg.norm(Cn @ sub[k].cpu().numpy() @ Cn.conj().T - fk) / np.linalg.norm(fk))
+    P = cfg.npairs
+    print(json.dumps({
+        "workload": f"{cfg.name}: 48^3, {cfg.nv}+{cfg.nc} bands, N_G={cfg.ng}, N_Eig={neig} (20 %), "
+                    "19 Gauss-Legendre imaginary frequencies on [0,100] eV",
+        "prec": args.prec, "nslices": args.nslices, "mtxel": mtxel,
+        "ms_chi0_full": t0, "ms_basis": tb, "ms_basis_first_call": tb_first, "ms_19_subspace": ts,
+        "ms_19_full": tf, "kernel_ms_19_subspace": kms,
+        "speedup_19": tf / ts, "subspace_19_over_chi0_full": ts / t0,
+        "conv_tflops_19_subspace": 8.0 * neig * neig * P * 19 / (ts * 1e-3) * 1e-12,
+        "rel_err_chi_sub0_vs_diag_lambda": d0, "rel_err_chi_sub_vs_projected_full": dk,
+        "subspace_approximation_error": approx, "omega_checked": om19[k]}), flush=True)
 
 
 def main():
@@ -561,6 +618,8 @@ def main():
         sweep(args)
     elif args.batch:
         batch(args)
+    elif args.subspace:
+        subspace(args)
     elif args.adjoint:
         adjoint(args)
     else:

@@ -482,6 +482,18 @@ gw_status contract_chunk_ozaki(gw_chi0 *h, const double2 *M, int64_t P, int ng, 
         }
         std::vector<gw::OzJob> jobs(1);
         if ((st = oz_job(h, jobs[0], h->Zbuf, kpad, ng, h->Ebuf, chi + (int64_t)w * ng * ng, bn))) return st;
+        // few tiles (small N_G): split K over jobs so that about one wave of blocks runs,
+        // at least 8 K-steps each; the atomic epilogue adds the parts
+        const int nk = jobs[0].nk;
+        const int ks = std::max(1, std::min(num_sms() / std::max(1, jobs[0].ntiles), nk / 8));
+        if (ks > 1) {
+            const gw::OzJob base = jobs[0];
+            jobs.assign(ks, base);
+            for (int i = 0; i < ks; ++i) {
+                jobs[i].kb0 = (int)((int64_t)nk * i / ks);
+                jobs[i].nk = (int)((int64_t)nk * (i + 1) / ks) - jobs[i].kb0;
+            }
+        }
         if ((st = launch_oz_jobs(h, jobs, bn))) return st;
     }
     return GW_OK;

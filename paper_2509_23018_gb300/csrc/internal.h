@@ -93,6 +93,7 @@ struct __align__(128) OzJob {
     const int *E;         // [ng] column exponents
     double *chi;          // [ng][ng] complex
     int ng, nk, s, ntiles, item_start;
+    int kb0;              // first K-step of this job (jobs may split K; the epilogue adds)
     // general product (launch_oz_gemm_general): out[rows_a][rows_b] real (complex pairs)
     // += A B with A slices by row (exponents E[rows_a]) and B^T slices by row (exponents
     // E2[rows_b / 2])

@@ -325,8 +325,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                             const uint32_t n = it / kOzStages;
                             if (!bar_wait(&empty[st], (n & 1) ^ 1)) { ok = false; break; }
                             bar_expect(&full[st], C::ABytes + C::BBytes);
-                            tma3(sA + st * C::ABytes, &jb.tmA, &full[st], kb * kOzBK, I * kOzBM, i - 1);
-                            tma3(sB + st * C::BBytes, &jb.tmB, &full[st], kb * kOzBK, J * BN, t - i - 1);
+                            tma3(sA + st * C::ABytes, &jb.tmA, &full[st], (jb.kb0 + kb) * kOzBK, I * kOzBM, i - 1);
+                            tma3(sB + st * C::BBytes, &jb.tmB, &full[st], (jb.kb0 + kb) * kOzBK, J * BN, t - i - 1);
                         }
             }
             if (!ok) atomicOr(status, kStatusTimeout);
