@@ -186,3 +186,11 @@ def make_batch(grid, nv, nc, ngpsi, ng_lo, ng_hi, nq_side, nw, seed) -> BatchPro
         evs.append(r.uniform(-10.0, -1.0, nv))
         gch.append(gsphere(int(ngs[iq]), q=q, exclude_zero=not np.any(q != 0)))
     return BatchProblem(tuple(grid), gpsi, cond, ec, qs, cvs, evs, gch, gl_freqs(nw))
+
+
+def coulomb(gchi, q=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Synthetic Coulomb diagonal v_G = 4 pi / |q + G|^2 (reciprocal-lattice index units) for the
+    dielectric-matrix inputs; G = 0 at q = 0 must not be in the sphere."""
+    k = np.asarray(gchi, np.float64) + np.asarray(q, np.float64)
+    return 4.0 * np.pi / np.einsum("ij,ij->i", k, k)
+

@@ -207,6 +207,21 @@ GW_API gw_status gw_chi0_compute_subspace(gw_chi0 *h, int iq, int neig, const do
                                           const double *omega, double *chi_sub);
 
 /*
+ * Inverse dielectric matrix, Eq. epsilon_mat: epsinv(w) = [I - v chi(w)]^-1 with v the diagonal
+ * Coulomb matrix, for nw Hermitian, negative semidefinite chi blocks.
+ *   chi     device complex128 [nw][ng][ng] (e.g. from gw_chi0_compute).
+ *   vcoul   device float64 [ng]: v_G > 0 (the caller's Coulomb form, e.g. 4 pi / |q + G|^2).
+ *   epsinv  device complex128 [nw][ng][ng], written in full.
+ * Method: the Hermitian A = I - s chi s (s = sqrt(v), eigenvalues >= 1) is inverted by the
+ * Newton-Schulz iteration X <- 2X - X A X from X0 = 2/(1 + b) I, b a Gershgorin bound,
+ * with the step count that brings the error below 1e-17 from (b-1)/(b+1); the products run
+ * in the handle's precision mode.  Then epsinv = s X s^-1.  Synchronises once per block.
+ * GW_ERR_ARG for v <= 0 or when I - v chi is not positive.
+ */
+GW_API gw_status gw_chi0_epsilon_inverse(gw_chi0 *h, int ng, int nw, const double *chi, const double *vcoul,
+                                         double *epsinv);
+
+/*
  * Adjoint of L = Re Tr(W chi0(iq, w)) for a Hermitian W (GWPT-style sensitivity,
  * Eq. gwpt motivates it).  Matrix elements are recomputed chunk by chunk; Y = M W runs as
  * a split product on the BF16 tensor cores in split-precision mode, on DMMA otherwise.

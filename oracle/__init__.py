@@ -17,6 +17,7 @@ paper, "Overview of the Problem"):
 * ``chi0`` -- Eq. chi_mat without the outer factor 2 (the factor is folded into
   Delta), every entry summed separately with Neumaier compensation;
 * ``adjoint`` -- gradients of L = Re Tr(W chi0) (GWPT motivation, Eq. gwpt);
+* ``epsilon_inverse`` -- Eq. epsilon_mat, [I - v chi]^-1 by a dense inverse;
 * ``subspace_basis`` / ``chi0_subspace`` -- the static subspace approximation
   (Eq. chi_mat_sub and the paragraph around it): the N_Eig most significant
   eigenvectors of chi(0) as C_s, M^B = M C_s, chi_BB' from M^B as in Eq. chi_mat.
@@ -188,4 +189,12 @@ def chi0_subspace(M, dl, basis) -> np.ndarray:
     """Eq. chi_mat_sub: chi_BB' = sum_vc conj(M^B_vc) Delta_vc M^B'_vc with
     M^B_vc = sum_G M_vc(G) C_s[G][B] (the projection written out as a matrix product)."""
     return chi0(np.asarray(M, np.complex128) @ np.asarray(basis, np.complex128), dl)
+
+
+def epsilon_inverse(chi, vcoul) -> np.ndarray:
+    """Eq. epsilon_mat: eps^-1 = [I - v chi]^-1 with v the diagonal Coulomb matrix (numpy inv,
+    FP64, as a library step)."""
+    chi = np.asarray(chi, np.complex128)
+    v = np.asarray(vcoul, np.float64)
+    return np.linalg.inv(np.eye(chi.shape[0]) - v[:, None] * chi)
 

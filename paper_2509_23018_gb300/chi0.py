@@ -182,6 +182,19 @@ class Chi0:
         self._check(self.lib.gw_chi0_compute_subspace(self.h, int(iq), neig, _ptr(basis), nw, om_arr, _ptr(out)))
         return out
 
+    def epsilon_inverse(self, chi: torch.Tensor, vcoul: torch.Tensor, out: torch.Tensor | None = None):
+        """[I - v chi(w)]^-1 for chi blocks [nw, ng, ng] (or [ng, ng]) and v [ng]."""
+        chi = chi.to(device=f"cuda:{self.device}", dtype=torch.complex128).contiguous()
+        single = chi.dim() == 2
+        chi = chi.view(-1, chi.shape[-2], chi.shape[-1])
+        nw, ng = chi.shape[0], chi.shape[1]
+        v = vcoul.to(device=f"cuda:{self.device}", dtype=torch.float64).contiguous()
+        if out is None:
+            out = torch.empty_like(chi)
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_epsilon_inverse(self.h, ng, nw, _ptr(chi), _ptr(v), _ptr(out)))
+        return out[0] if single else out
+
     def sync(self):
         self._use_current_stream()
         self._check(self.lib.gw_chi0_sync(self.h))

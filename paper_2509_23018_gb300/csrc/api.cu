@@ -109,6 +109,8 @@ struct gw_chi0 {
     size_t ZBcap = 0;
     double2 *MBbuf = nullptr;   // projected pair elements of a chunk [chunk][neig]
     size_t MBcap = 0;
+    void *epsbuf = nullptr;     // dielectric inverse: A, X, T, P [ng][ng], sqrt(v) [ng], bound
+    size_t epscap = 0;
     // dense eigensolver (cuSOLVER, loaded on first use) for the subspace basis
     struct {
         void *lib = nullptr;
@@ -1063,6 +1065,7 @@ void gw_chi0_destroy(gw_chi0 *h)
     dfree(h, h->EBbuf, h->EBcap);
     dfree(h, h->ZBbuf, h->ZBcap);
     dfree(h, h->MBbuf, h->MBcap);
+    dfree(h, h->epsbuf, h->epscap);
     dfree(h, h->eigA, h->eigA_cap);
     dfree(h, h->eigWork, h->eigWork_cap);
     dfree(h, h->eigW, h->eigW_cap);
@@ -1726,6 +1729,63 @@ gw_status gw_chi0_compute_subspace(gw_chi0 *h, int iq, int neig, const double *b
     }
     Scope sc(h, "symmetrize");
     CK(h, gw::launch_symmetrize((double2 *)chi_sub, neig, nw, h->st), "symmetrize");
+    return GW_OK;
+}
+
+// ------------------------------------------------------------------ dielectric matrix inverse
+// Dense product C = A B of two [n][n] complex matrices in the handle's precision mode.
+static gw_status square_product(gw_chi0 *h, const double2 *A, const double2 *B, int n, double2 *C)
+{
+    if (h->d.prec == GW_PREC_OZAKI_BF16) {
+        gw_status st = oz_prepare_b(h, B, n, n);
+        if (st) return st;
+        return oz_product(h, A, n, n, n, C);
+    }
+    CK(h, gw::launch_zgemm(A, B, C, n, n, n, h->st), "product");
+    return GW_OK;
+}
+
+gw_status gw_chi0_epsilon_inverse(gw_chi0 *h, int ng, int nw, const double *chi, const double *vcoul,
+                                  double *epsinv)
+{
+    if (!h) return GW_ERR_ARG;
+    if (ng < 1 || nw < 1 || !chi || !vcoul || !epsinv) return fail(h, GW_ERR_ARG, "bad arguments");
+    {
+        std::vector<double> v(ng);
+        CK(h, cudaMemcpyAsync(v.data(), vcoul, sizeof(double) * ng, cudaMemcpyDeviceToHost, h->st), "read v");
+        CK(h, cudaStreamSynchronize(h->st), "read v");
+        for (int i = 0; i < ng; ++i)
+            if (!(v[i] > 0.0) || !std::isfinite(v[i])) return fail(h, GW_ERR_ARG, "v[%d] must be finite and > 0", i);
+    }
+    const size_t nn = (size_t)ng * ng;
+    gw_status st = grow(h, &h->epsbuf, &h->epscap, sizeof(double2) * 4 * nn + sizeof(double) * ng + 64,
+                        "dielectric work");
+    if (st) return st;
+    double2 *A = (double2 *)h->epsbuf, *X = A + nn, *T = X + nn, *Pm = T + nn;
+    double *sv = (double *)(Pm + nn);
+    unsigned long long *bmax = (unsigned long long *)(((uintptr_t)(sv + ng) + 15) & ~(uintptr_t)15);
+    CK(h, gw::launch_eps_sqrt(vcoul, ng, sv, h->st), "sqrt v");
+    for (int w = 0; w < nw; ++w) {
+        Scope sc(h, "epsilon_inverse");
+        CK(h, gw::launch_eps_sym((const double2 *)chi + (int64_t)w * nn, sv, ng, A, bmax, h->st), "I - s chi s");
+        unsigned long long bits = 0;
+        CK(h, cudaMemcpyAsync(&bits, bmax, sizeof bits, cudaMemcpyDeviceToHost, h->st), "bound");
+        CK(h, cudaStreamSynchronize(h->st), "bound");
+        double b;
+        std::memcpy(&b, &bits, sizeof b);
+        if (!(b >= 1.0) || !std::isfinite(b)) return fail(h, GW_ERR_ARG, "I - v chi is not positive (bound %g)", b);
+        // steps for (b - 1)/(b + 1) squared repeatedly to reach 1e-17, plus one for rounding
+        const double r = (b - 1.0) / (b + 1.0);
+        int steps = 1;
+        if (r > 0.0) steps = (int)std::ceil(std::log2(std::log(1e-17) / std::log(r))) + 1;
+        steps = std::max(steps, 1);
+        CK(h, gw::launch_eps_init(X, ng, bmax, h->st), "X0");
+        for (int k = 0; k < steps; ++k) {
+            if ((st = square_product(h, A, X, ng, T)) || (st = square_product(h, X, T, ng, Pm))) return st;
+            CK(h, gw::launch_eps_step(X, Pm, (int64_t)nn, h->st), "Newton-Schulz step");
+        }
+        CK(h, gw::launch_eps_unsym(X, sv, ng, (double2 *)epsinv + (int64_t)w * nn, h->st), "s X s^-1");
+    }
     return GW_OK;
 }
 

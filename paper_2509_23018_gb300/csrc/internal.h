@@ -58,6 +58,15 @@ cudaError_t launch_delta(const double *ev, const double *ec, int nc, int64_t p0,
 // diag[w][g] += sum_p delta[w][p] |M[p][g]|^2
 cudaError_t launch_diag(const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride, int nw,
                         double *diag, int64_t diag_wstride, cudaStream_t st);
+// ---- dielectric matrix inverse (epsilon.cu)
+cudaError_t launch_eps_sqrt(const double *v, int ng, double *sv, cudaStream_t st);
+// A = I - s chi s and bmax = Gershgorin bound of A (bits of a double)
+cudaError_t launch_eps_sym(const double2 *chi, const double *sv, int ng, double2 *A, unsigned long long *bmax,
+                           cudaStream_t st);
+cudaError_t launch_eps_init(double2 *X, int ng, const unsigned long long *bmax, cudaStream_t st);
+cudaError_t launch_eps_step(double2 *X, const double2 *P, int64_t n, cudaStream_t st);
+cudaError_t launch_eps_unsym(const double2 *X, const double *sv, int ng, double2 *out, cudaStream_t st);
+
 // out[g][b] = conj(V[b n + g]) (column-major n x neig -> row-major [n][neig], conjugated)
 cudaError_t launch_conj_transpose(const double2 *V, int n, int neig, double2 *out, cudaStream_t st);
 // a bounded wait that is never satisfied: sets kStatusTimeout in *status after iters tries

@@ -98,3 +98,31 @@ def test_adjoint_split_product(gw):
     assert abs(L - Lo) <= 1e-10 * abs(Lo)
     for a, b in ((dEv, dEvo), (dEc, dEco), (dcv, dcvo), (dcc, dcco)):
         assert rel(a.cpu().numpy(), b) < 1e-10
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("ozaki", 1e-9)])
+def test_epsilon_inverse_matches_oracle(gw, prec, tol):
+    """[I - v chi(w)]^-1 (Eq. epsilon_mat) for two frequency blocks of the oracle's chi."""
+    p = gwgen.make_problem((24, 24, 24), 6, 24, 600, 200, seed=gwgen.BASE_SEED + 33)
+    M = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)
+    chis = np.stack([oracle.chi0(M, oracle.delta(p.ev, p.ec, w)) for w in (0.0, 5.0)])
+    v = gwgen.coulomb(p.gchi)
+    h = gw.from_problem(p, prec=prec, nslices=7)
+    got = h.epsilon_inverse(torch.as_tensor(chis, device="cuda"), torch.as_tensor(v, device="cuda")).cpu().numpy()
+    h.sync()
+    for i in range(2):
+        assert rel(got[i], oracle.epsilon_inverse(chis[i], v)) <= tol
+
+
+def test_epsilon_inverse_rejects_bad_coulomb(gw):
+    p = gwgen.make_problem((16, 16, 16), 2, 3, 57, 27, seed=3)
+    h = gw.from_problem(p)
+    chi = torch.zeros((27, 27), dtype=torch.complex128, device="cuda")
+    v = torch.ones(27, dtype=torch.float64, device="cuda")
+    v[3] = 0.0
+    with pytest.raises(gw.GwError) as e:
+        h.epsilon_inverse(chi, v)
+    assert e.value.status == 1
+    out = h.epsilon_inverse(chi, torch.ones(27, dtype=torch.float64, device="cuda"))  # still usable: chi = 0
+    h.sync()
+    assert torch.equal(out, torch.eye(27, dtype=torch.complex128, device="cuda"))

@@ -347,3 +347,29 @@ def test_subspace_chi_is_projected_chi(sub_case, w):
     assert rel(oracle.chi0_subspace(M, dl, C), C.conj().T @ chi_w @ C) < 1e-12
     Cf, _ = oracle.subspace_basis(chi_0, chi_0.shape[0])
     assert rel(Cf @ oracle.chi0_subspace(M, dl, Cf) @ Cf.conj().T, chi_w) < 1e-12
+
+
+# ------------------------------------------------------------------ dielectric inverse (next row f2)
+
+def test_epsilon_diagonal_closed_form():
+    """A diagonal chi gives eps^-1 = diag(1 / (1 - v_G chi_GG))."""
+    c = -np.linspace(0.1, 2.0, 7)
+    v = np.linspace(0.5, 3.0, 7)
+    assert rel(oracle.epsilon_inverse(np.diag(c).astype(np.complex128), v), np.diag(1.0 / (1.0 - v * c))) < 1e-15
+
+
+def test_epsilon_structure():
+    """v^-1/2 eps^-1 v^1/2 = [I - v^1/2 chi v^1/2]^-1 is Hermitian with eigenvalues in (0, 1]
+    (chi <= 0), and to first order in v, eps^-1 = I + v chi (v multiplies from the left)."""
+    p = tiny(nv=3, nc=8, ngpsi=93, ng=27, seed=19, exclude_head=True)
+    chi_0 = oracle.chi0(oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi), oracle.delta(p.ev, p.ec, 0.0))
+    v = gwgen.coulomb(p.gchi)
+    e = oracle.epsilon_inverse(chi_0, v)
+    s = np.sqrt(v)
+    h = e * s[None, :] / s[:, None]
+    assert rel(h, h.conj().T) < 1e-13
+    lam = np.linalg.eigvalsh(0.5 * (h + h.conj().T))
+    assert lam.min() > 0 and lam.max() <= 1 + 1e-13
+    t = 1e-6
+    e1 = oracle.epsilon_inverse(chi_0, t * v)
+    assert rel((e1 - np.eye(len(v))) / t, v[:, None] * chi_0) < 1e-5
