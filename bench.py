@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--subspace", action="store_true")
+    ap.add_argument("--epsilon", action="store_true")
     return ap.parse_args()
 
 
@@ -176,6 +177,8 @@ def reference_arm(args):
 TRAFFIC = {
     "contract_f64": {"bytes_per_launch": 1.941011e9 + 0.034306e9,
                      "source": "ncu dram__bytes_read+write, contract_f64_kernel, p1_48cube_onechunk"},
+    "pair_mtxel": {"bytes_per_launch": 3.070e9 + 1.484e9,
+                   "source": "ncu dram__bytes_read+write, pair_kernel_tf_ct<48>, p1_48cube_onechunk"},
     "ozaki_gemm": {"bytes_per_launch": 7.32e9 + 0.219e9,
                    "source": "ncu dram__bytes_read+write, oz_gemm_kernel (s = 7), p1_48cube_onechunk"},
 }
@@ -610,6 +613,38 @@ def subspace(args):
         "subspace_approximation_error": approx, "omega_checked": om19[k]}), flush=True)
 
 
+def epsilon(args):
+    """Inverse dielectric matrix [I - v chi(w)]^-1 on the 48^3 workload (N_G = 2000) for chi(0) and
+    chi at two imaginary frequencies, v_G = 4 pi / |G|^2."""
+    import torch
+    import paper_2509_23018_gb300 as gw
+    cfg = gwgen.CONFIGS["c2_48cube"]
+    prob = gwgen.config_problem(cfg)
+    om = [0.0, 5.0, 20.0]
+    h = gw.from_problem(prob, prec=args.prec, nslices=args.nslices, mtxel=args.mtxel or "twofloat",
+                        pair_chunk=cfg.pair_chunk)
+    (chi,) = h.compute(0, om)
+    v = torch.as_tensor(gwgen.coulomb(prob.gchi), device="cuda")
+    h.epsilon_inverse(chi, v)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.set_timing(True)
+    h.timing(reset=True)
+    e0.record()
+    einv = h.epsilon_inverse(chi, v)
+    e1.record()
+    torch.cuda.synchronize()
+    kms = {k: val[0] for k, val in h.timing(reset=True).items()}
+    ms = e0.elapsed_time(e1)
+    eye = torch.eye(cfg.ng, dtype=torch.complex128, device="cuda")
+    res = [float(torch.linalg.norm((eye - v[:, None] * chi[i]) @ einv[i] - eye) / cfg.ng ** 0.5)
+           for i in range(len(om))]
+    print(json.dumps({"workload": f"{cfg.name}: eps^-1 = [I - v chi(w)]^-1, N_G={cfg.ng}, w = {om} eV, "
+                                  "v_G = 4 pi/|G|^2, chi from the 48^3 workload",
+                      "prec": args.prec, "nslices": args.nslices, "ms_per_block": ms / len(om),
+                      "kernel_ms": kms, "residual_rms": res}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -620,6 +655,8 @@ def main():
         batch(args)
     elif args.subspace:
         subspace(args)
+    elif args.epsilon:
+        epsilon(args)
     elif args.adjoint:
         adjoint(args)
     else:
