@@ -207,6 +207,37 @@ GW_API gw_status gw_chi0_compute_subspace(gw_chi0 *h, int iq, int neig, const do
                                           const double *omega, double *chi_sub);
 
 /*
+ * Forward derivative (JVP) of chi0(iq, i w) along a perturbation of the stored bands: the
+ * first-order change the GWPT working equation (Eq. gwpt) builds from d psi_n,
+ *     dchi = sum_p [conj(dM_p) Delta_p M_p + conj(M_p) Delta_p dM_p + conj(M_p) dDelta_p M_p],
+ *     dM_vc = M(d psi_v, psi_c) + M(psi_v, d psi_c),  dDelta = dDelta/dx (dE_v - dE_c),
+ * computed per chunk with the pair kernel on the tangent grids and the stage-(b) kernels
+ * (the cross term as [chi(M + dM) - chi(M - dM)] / 2).
+ *   dcoeff_v device complex128 [nv][ngpsi_v], dcoeff_c [nc][ngpsi_c]: the tangent coefficients,
+ *            on the plane waves of the stored band sets (no re-orthonormalisation).
+ *   dE_v     device float64 [nv]; dE_c [nc]: the tangent energies.
+ *   omega    host double [nw] (imaginary-axis magnitudes, eV), nw <= 32.
+ *   dchi     device complex128 [nw][ng][ng], written in full, Hermitian.
+ * Work buffers for the tangent grids are held for the call only.  Errors as gw_chi0_compute.
+ */
+GW_API gw_status gw_chi0_jvp(gw_chi0 *h, int iq, int nw, const double *omega, const double *dcoeff_v,
+                             const double *dcoeff_c, const double *dE_v, const double *dE_c, double *dchi);
+
+/*
+ * chi0 on the real frequency axis with broadening eta (Eq. chi_mat with Delta continued from
+ * the imaginary axis, i w -> w + i eta):
+ *     Delta_vc(w) = 2/(x - w - i eta) + 2/(x + w + i eta),  x = E_v - E_c,
+ *     chi(w) = sum_vc conj(M_vc(G)) Delta_vc(w) M_vc(G') = chi_R + i chi_I,
+ * with chi_R, chi_I the Hermitian contractions with Re Delta and Im Delta (Im Delta <= 0 for
+ * w >= 0; Re Delta changes sign near the resonances and is split into its two signs).
+ *   omega  host double [nw], real frequencies >= 0 (eV), nw <= 21.
+ *   eta    broadening > 0 (eV).
+ *   chi    device complex128 [nw][ng][ng], written in full (not Hermitian).
+ * Errors as gw_chi0_compute.
+ */
+GW_API gw_status gw_chi0_compute_real(gw_chi0 *h, int iq, int nw, const double *omega, double eta, double *chi);
+
+/*
  * Inverse dielectric matrix, Eq. epsilon_mat: epsinv(w) = [I - v chi(w)]^-1 with v the diagonal
  * Coulomb matrix, for nw Hermitian, negative semidefinite chi blocks.
  *   chi     device complex128 [nw][ng][ng] (e.g. from gw_chi0_compute).

@@ -17,6 +17,10 @@ paper, "Overview of the Problem"):
 * ``chi0`` -- Eq. chi_mat without the outer factor 2 (the factor is folded into
   Delta), every entry summed separately with Neumaier compensation;
 * ``adjoint`` -- gradients of L = Re Tr(W chi0) (GWPT motivation, Eq. gwpt);
+* ``jvp`` -- the forward derivative of chi0 along band and energy perturbations (the first-order
+  change GWPT builds from d psi, Eq. gwpt);
+* ``delta_real`` / ``chi0_real`` -- the energy factor continued to the real axis with
+  broadening (i w -> w + i eta) and chi0 with that complex Delta;
 * ``epsilon_inverse`` -- Eq. epsilon_mat, [I - v chi]^-1 by a dense inverse;
 * ``subspace_basis`` / ``chi0_subspace`` -- the static subspace approximation
   (Eq. chi_mat_sub and the paragraph around it): the N_Eig most significant
@@ -197,4 +201,32 @@ def epsilon_inverse(chi, vcoul) -> np.ndarray:
     chi = np.asarray(chi, np.complex128)
     v = np.asarray(vcoul, np.float64)
     return np.linalg.inv(np.eye(chi.shape[0]) - v[:, None] * chi)
+
+
+def delta_real(ev, ec, omega: float, eta: float) -> np.ndarray:
+    """Delta_vc(w) = 2/(x - w - i eta) + 2/(x + w + i eta), x = E_v - E_c, in complex arithmetic
+    (the imaginary-axis factor with i w -> w + i eta), pairs p = v * nc + c."""
+    x = (np.asarray(ev, np.float64)[:, None] - np.asarray(ec, np.float64)[None, :]).ravel()
+    z = complex(omega, eta)
+    return 2.0 / (x - z) + 2.0 / (x + z)
+
+
+def chi0_real(M, dc) -> np.ndarray:
+    """chi = sum_p conj(M[p,G]) Delta_p M[p,G'] with complex Delta: the two Hermitian
+    contractions with Re Delta and Im Delta (each by ``chi0``), chi_R + i chi_I."""
+    dc = np.asarray(dc, np.complex128)
+    return chi0(M, dc.real) + 1j * chi0(M, dc.imag)
+
+
+def jvp(gpsi, cv, ev, cc, ec, gchi, dcv, dcc, dev, dec, omega: float) -> np.ndarray:
+    """d chi0 along (dcv, dcc, dev, dec): M and dM = M(d psi_v, psi_c) + M(psi_v, d psi_c) by the
+    G-space convolution, dDelta = d/dx [2/(x - iw) + 2/(x + iw)] (dE_v - dE_c), and
+    dchi = dM^H Delta M + M^H Delta dM + M^H dDelta M (matrix products as library steps)."""
+    M = m_conv(gpsi, cv, gpsi, cc, gchi)
+    dM = m_conv(gpsi, dcv, gpsi, cc, gchi) + m_conv(gpsi, cv, gpsi, dcc, gchi)
+    x = (np.asarray(ev, np.float64)[:, None] - np.asarray(ec, np.float64)[None, :]).ravel()
+    dx = (np.asarray(dev, np.float64)[:, None] - np.asarray(dec, np.float64)[None, :]).ravel()
+    dl = delta(ev, ec, omega)
+    ddl = (-2.0 / (x - 1j * omega) ** 2 - 2.0 / (x + 1j * omega) ** 2).real * dx
+    return (dM.conj().T * dl) @ M + (M.conj().T * dl) @ dM + (M.conj().T * ddl) @ M
 

@@ -45,6 +45,8 @@ SIGNATURES = {
     "gw_chi0_subspace_basis": ([P, I, P, I, P, P], I),
     "gw_chi0_compute_subspace": ([P, I, I, P, I, P, P], I),
     "gw_chi0_epsilon_inverse": ([P, I, I, P, P, P], I),
+    "gw_chi0_compute_real": ([P, I, I, P, D, P], I),
+    "gw_chi0_jvp": ([P, I, I, P, P, P, P, P, P], I),
     "gw_chi0_sync": ([P], I),
     "gw_chi0_check_watchdog": ([P, ctypes.c_longlong], I),
     "gw_chi0_set_timing": ([P, I], I),

@@ -182,6 +182,33 @@ class Chi0:
         self._check(self.lib.gw_chi0_compute_subspace(self.h, int(iq), neig, _ptr(basis), nw, om_arr, _ptr(out)))
         return out
 
+    def jvp(self, iq: int, omega: Sequence[float], dcv: torch.Tensor, dcc: torch.Tensor, dEv: torch.Tensor,
+            dEc: torch.Tensor, out: torch.Tensor | None = None):
+        """d chi0 [nw, ng, ng] along tangent coefficients (dcv [nv, ngpsi_v], dcc [nc, ngpsi_c]) and
+        tangent energies (dEv [nv], dEc [nc])."""
+        dev = f"cuda:{self.device}"
+        args = [t.to(device=dev, dtype=dt).contiguous() for t, dt in
+                ((dcv, torch.complex128), (dcc, torch.complex128), (dEv, torch.float64), (dEc, torch.float64))]
+        n = self.ng[int(iq)]
+        nw = len(omega)
+        if out is None:
+            out = torch.empty((nw, n, n), dtype=torch.complex128, device=dev)
+        om_arr = (ctypes.c_double * nw)(*[float(w) for w in omega])
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_jvp(self.h, int(iq), nw, om_arr, *[_ptr(a) for a in args], _ptr(out)))
+        return out
+
+    def compute_real(self, iq: int, omega: Sequence[float], eta: float, out: torch.Tensor | None = None):
+        """chi0 on the real axis with broadening eta: [nw, ng, ng] complex (not Hermitian)."""
+        n = self.ng[int(iq)]
+        nw = len(omega)
+        if out is None:
+            out = torch.empty((nw, n, n), dtype=torch.complex128, device=f"cuda:{self.device}")
+        om_arr = (ctypes.c_double * nw)(*[float(w) for w in omega])
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_compute_real(self.h, int(iq), nw, om_arr, float(eta), _ptr(out)))
+        return out
+
     def epsilon_inverse(self, chi: torch.Tensor, vcoul: torch.Tensor, out: torch.Tensor | None = None):
         """[I - v chi(w)]^-1 for chi blocks [nw, ng, ng] (or [ng, ng]) and v [ng]."""
         chi = chi.to(device=f"cuda:{self.device}", dtype=torch.complex128).contiguous()

@@ -111,6 +111,8 @@ struct gw_chi0 {
     size_t MBcap = 0;
     void *epsbuf = nullptr;     // dielectric inverse: A, X, T, P [ng][ng], sqrt(v) [ng], bound
     size_t epscap = 0;
+    double2 *realbuf = nullptr; // real-axis chi: the three Hermitian parts per frequency
+    size_t realcap = 0;
     // dense eigensolver (cuSOLVER, loaded on first use) for the subspace basis
     struct {
         void *lib = nullptr;
@@ -1066,6 +1068,7 @@ void gw_chi0_destroy(gw_chi0 *h)
     dfree(h, h->ZBbuf, h->ZBcap);
     dfree(h, h->MBbuf, h->MBcap);
     dfree(h, h->epsbuf, h->epscap);
+    dfree(h, h->realbuf, h->realcap);
     dfree(h, h->eigA, h->eigA_cap);
     dfree(h, h->eigWork, h->eigWork_cap);
     dfree(h, h->eigW, h->eigW_cap);
@@ -1786,6 +1789,158 @@ gw_status gw_chi0_epsilon_inverse(gw_chi0 *h, int ng, int nw, const double *chi,
         }
         CK(h, gw::launch_eps_unsym(X, sv, ng, (double2 *)epsinv + (int64_t)w * nn, h->st), "s X s^-1");
     }
+    return GW_OK;
+}
+
+// ------------------------------------------------------------------ real frequencies
+gw_status gw_chi0_compute_real(gw_chi0 *h, int iq, int nw, const double *omega, double eta, double *chi)
+{
+    if (!h) return GW_ERR_ARG;
+    if (nw < 1 || 3 * nw > gw::kMaxOmega || !omega || !chi)
+        return fail(h, GW_ERR_ARG, "bad arguments (1 <= nw <= %d, non-null pointers)", gw::kMaxOmega / 3);
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(h, GW_ERR_ARG, "eta must be finite and > 0");
+    gw::OmegaList om;
+    om.nw = nw;
+    for (int i = 0; i < nw; ++i) {
+        if (!(omega[i] >= 0.0) || !std::isfinite(omega[i])) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
+        om.w[i] = omega[i];
+    }
+    gw_status s = check_slot(h, iq);
+    if (s) return s;
+    const Sphere &sp = h->sph[iq];
+    const BandSet &v = h->val[iq];
+    const int ng = sp.ng;
+    const int64_t nn = (int64_t)ng * ng;
+    const int64_t P = (int64_t)v.nb * h->cond.nb;
+    const int64_t chunk = std::min<int64_t>(h->d.pair_chunk, P);
+    if ((s = grow(h, (void **)&h->realbuf, &h->realcap, sizeof(double2) * 3 * nw * nn, "real-axis parts")) ||
+        (s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * 3 * nw)))
+        return s;
+    CK(h, cudaMemsetAsync(h->realbuf, 0, sizeof(double2) * 3 * nw * nn, h->st), "zero parts");
+    gw::PairPlan pp = pair_plan(h, sp);
+    for (int64_t p0 = 0; p0 < P; p0 += chunk) {
+        const int64_t cnt = std::min(chunk, P - p0);
+        {
+            Scope sc(h, "pair_mtxel");
+            CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
+        }
+        {
+            Scope sc(h, "delta");
+            CK(h, gw::launch_delta_real(v.energy, h->cond.energy, h->cond.nb, p0, cnt, om, eta, h->dbuf, h->st),
+               "real-axis delta");
+        }
+        if ((s = contract_chunk(h, h->Mbuf, cnt, ng, h->dbuf, cnt, 3 * nw, h->realbuf))) return s;
+    }
+    Scope sc(h, "symmetrize");
+    CK(h, gw::launch_symmetrize(h->realbuf, ng, 3 * nw, h->st), "symmetrize");
+    CK(h, gw::launch_combine_real(h->realbuf, nn, nw, (double2 *)chi, h->st), "combine");
+    return GW_OK;
+}
+
+// ------------------------------------------------------------------ forward derivative (JVP)
+// Real-space grids of caller coefficients on a stored band set's plane waves (the band
+// setup of gw_chi0_set_bands, into psi).
+static gw_status band_grids(gw_chi0 *h, const BandSet &b, const double *coeff, void *psi)
+{
+    CK(h, cudaMemsetAsync(psi, 0, sizeof(double2) * (size_t)b.nb * h->nr, h->st), "zero grids");
+    if (h->d.mtxel_prec == GW_MTXEL_TWOFLOAT) {
+        Scope sc(h, "band_setup_tf");
+        CK(h, gw::launch_band_setup_tf((const double2 *)coeff, b.gofs, b.nb, b.ngpsi, psi, h->d.n, h->ax, h->st),
+           "tangent band setup (two-float)");
+    } else {
+        CK(h, gw::launch_scatter((const double2 *)coeff, b.gofs, b.nb, b.ngpsi, h->nr, (double2 *)psi, h->st),
+           "tangent scatter");
+        CK(h, gw::launch_band_fft((double2 *)psi, b.nb, h->d.n, h->ax, h->st), "tangent band fft");
+    }
+    return GW_OK;
+}
+
+gw_status gw_chi0_jvp(gw_chi0 *h, int iq, int nw, const double *omega, const double *dcoeff_v,
+                      const double *dcoeff_c, const double *dE_v, const double *dE_c, double *dchi)
+{
+    if (!h) return GW_ERR_ARG;
+    if (nw < 1 || 2 * nw > gw::kMaxOmega || !omega || !dcoeff_v || !dcoeff_c || !dE_v || !dE_c || !dchi)
+        return fail(h, GW_ERR_ARG, "bad arguments (1 <= nw <= %d, non-null pointers)", gw::kMaxOmega / 2);
+    gw::OmegaList om;
+    om.nw = nw;
+    for (int i = 0; i < nw; ++i) {
+        if (!(omega[i] >= 0.0) || !std::isfinite(omega[i])) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
+        om.w[i] = omega[i];
+    }
+    gw_status s = check_slot(h, iq);
+    if (s) return s;
+    const BandSet &v = h->val[iq];
+    const BandSet &c = h->cond;
+    const Sphere &sp = h->sph[iq];
+    const int ng = sp.ng, nc = c.nb;
+    const int64_t nn = (int64_t)ng * ng;
+    const int64_t P = (int64_t)v.nb * nc;
+    const int64_t chunk = std::min<int64_t>(h->d.pair_chunk, P);
+    // work held only for this call
+    void *gv = nullptr, *gc = nullptr;
+    double2 *X1 = nullptr, *X2 = nullptr, *T = nullptr;
+    double *wb = nullptr;
+    const size_t szv = sizeof(double2) * (size_t)v.nb * h->nr, szc = sizeof(double2) * (size_t)nc * h->nr;
+    const size_t szx = sizeof(double2) * (size_t)chunk * ng, szt = sizeof(double2) * 4 * nw * nn;
+    const size_t szw = sizeof(double) * 2 * nw * (size_t)chunk;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(h->st);
+        dfree(h, gv, szv);
+        dfree(h, gc, szc);
+        dfree(h, X1, szx);
+        dfree(h, X2, szx);
+        dfree(h, T, szt);
+        dfree(h, wb, szw);
+    };
+    if ((s = dalloc(h, &gv, szv, "tangent valence grids")) || (s = dalloc(h, &gc, szc, "tangent conduction grids")) ||
+        (s = dalloc(h, (void **)&X1, szx, "tangent pairs")) || (s = dalloc(h, (void **)&X2, szx, "tangent pairs")) ||
+        (s = dalloc(h, (void **)&T, szt, "tangent parts")) || (s = dalloc(h, (void **)&wb, szw, "tangent weights")) ||
+        (s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * 2 * nw)) || (s = band_grids(h, v, dcoeff_v, gv)) ||
+        (s = band_grids(h, c, dcoeff_c, gc))) {
+        cleanup();
+        return s;
+    }
+#define JCK(x, what)                            \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) {                \
+            gw_status r_ = cuda_fail(h, e_, what); \
+            cleanup();                          \
+            return r_;                          \
+        }                                       \
+    } while (0)
+    JCK(cudaMemsetAsync(T, 0, szt, h->st), "zero parts");
+    double2 *Tp = T, *Tm = T + (int64_t)nw * nn, *Tw = T + 2 * (int64_t)nw * nn;
+    gw::PairPlan pp = pair_plan(h, sp);
+    for (int64_t p0 = 0; p0 < P; p0 += chunk) {
+        const int64_t cnt = std::min(chunk, P - p0);
+        {
+            Scope sc(h, "pair_mtxel");
+            JCK(run_pair(h, v.psi, c.psi, nc, p0, cnt, pp, h->Mbuf), "pair kernel");
+            JCK(run_pair(h, gv, c.psi, nc, p0, cnt, pp, X1), "pair kernel (tangent valence)");
+            JCK(run_pair(h, v.psi, gc, nc, p0, cnt, pp, X2), "pair kernel (tangent conduction)");
+            JCK(gw::launch_jvp_mix(h->Mbuf, X1, X2, cnt * ng, h->st), "M +- dM");
+        }
+        {
+            Scope sc(h, "delta");
+            JCK(gw::launch_delta(v.energy, c.energy, nc, p0, cnt, om, h->dbuf, h->st), "delta");
+            JCK(gw::launch_delta_jvp(v.energy, c.energy, dE_v, dE_c, nc, p0, cnt, om, wb, h->st), "delta derivative");
+        }
+        // d chi = [chi(M + dM) - chi(M - dM)] / 2 + sum_p conj(M) dDelta M
+        if ((s = contract_chunk(h, X1, cnt, ng, h->dbuf, cnt, nw, Tp)) ||
+            (s = contract_chunk(h, X2, cnt, ng, h->dbuf, cnt, nw, Tm)) ||
+            (s = contract_chunk(h, h->Mbuf, cnt, ng, wb, cnt, 2 * nw, Tw))) {
+            cleanup();
+            return s;
+        }
+    }
+    {
+        Scope sc(h, "symmetrize");
+        JCK(gw::launch_symmetrize(T, ng, 4 * nw, h->st), "symmetrize");
+        JCK(gw::launch_combine_jvp(Tp, Tm, Tw, nn, nw, (double2 *)dchi, h->st), "combine");
+    }
+#undef JCK
+    cleanup();
     return GW_OK;
 }
 

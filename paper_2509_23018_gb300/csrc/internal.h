@@ -55,6 +55,19 @@ cudaError_t launch_band_setup_tf(const double2 *coeff, const int32_t *gofs, int 
 // delta[w][p - p0] = 4x/(x^2 + w^2), x = ev[v] - ec[c]
 cudaError_t launch_delta(const double *ev, const double *ec, int nc, int64_t p0, int64_t count, const OmegaList &om,
                          double *delta, cudaStream_t st);
+// real axis with broadening: delta[3w + k][p - p0], k = 0: min(Re D, 0), 1: -max(Re D, 0), 2: Im D
+cudaError_t launch_delta_real(const double *ev, const double *ec, int nc, int64_t p0, int64_t count,
+                              const OmegaList &om, double eta, double *delta, cudaStream_t st);
+// out[w] = (T[3w] - T[3w+1]) + i T[3w+2]
+cudaError_t launch_combine_real(const double2 *T, int64_t nn, int nw, double2 *out, cudaStream_t st);
+// forward derivative of Delta along (dE_v, dE_c), split: out[2w] = min(dD, 0), out[2w+1] = -max(dD, 0)
+cudaError_t launch_delta_jvp(const double *ev, const double *ec, const double *dev, const double *dec, int nc,
+                             int64_t p0, int64_t count, const OmegaList &om, double *out, cudaStream_t st);
+// d = X1 + X2; X1 = M + d; X2 = M - d
+cudaError_t launch_jvp_mix(const double2 *M, double2 *X1, double2 *X2, int64_t n, cudaStream_t st);
+// out[w] = (Tp[w] - Tm[w]) / 2 + Tw[2w] - Tw[2w+1]
+cudaError_t launch_combine_jvp(const double2 *Tp, const double2 *Tm, const double2 *Tw, int64_t nn, int nw,
+                               double2 *out, cudaStream_t st);
 // diag[w][g] += sum_p delta[w][p] |M[p][g]|^2
 cudaError_t launch_diag(const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride, int nw,
                         double *diag, int64_t diag_wstride, cudaStream_t st);

@@ -19,6 +19,121 @@ __global__ void delta_kernel(const double *__restrict__ ev, const double *__rest
     }
 }
 
+// Real-axis energy factor with broadening: Delta = 2/(x - w - i eta) + 2/(x + w + i eta),
+// x = E_v - E_c < 0, split into three non-positive weights per frequency (block 3 w + k):
+// k = 0: min(Re Delta, 0); k = 1: -max(Re Delta, 0); k = 2: Im Delta (<= 0 for w >= 0, x < 0).
+__global__ void delta_real_kernel(const double *__restrict__ ev, const double *__restrict__ ec, int nc, int64_t p0,
+                                  int64_t count, OmegaList om, double eta, double *__restrict__ delta)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int64_t p = p0 + i;
+    int v = (int)(p / nc), c = (int)(p - (int64_t)v * nc);
+    const double x = ev[v] - ec[c], e2 = eta * eta;
+    for (int w = 0; w < om.nw; ++w) {
+        const double a = x - om.w[w], b = x + om.w[w];
+        const double da = fma(a, a, e2), db = fma(b, b, e2);
+        const double re = 2.0 * a / da + 2.0 * b / db;
+        const double im = 2.0 * eta / da - 2.0 * eta / db;
+        delta[(int64_t)(3 * w) * count + i] = fmin(re, 0.0);
+        delta[(int64_t)(3 * w + 1) * count + i] = -fmax(re, 0.0);
+        delta[(int64_t)(3 * w + 2) * count + i] = fmin(im, 0.0);
+    }
+}
+
+cudaError_t launch_delta_real(const double *ev, const double *ec, int nc, int64_t p0, int64_t count,
+                              const OmegaList &om, double eta, double *delta, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    delta_real_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(ev, ec, nc, p0, count, om, eta, delta);
+    return cudaGetLastError();
+}
+
+// out[w] = (T[3w] - T[3w+1]) + i T[3w+2] for Hermitian parts T (complex [ng][ng] each)
+__global__ void combine_real_kernel(const double2 *__restrict__ T, int64_t nn, int nw, double2 *__restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nn * nw) return;
+    const int64_t w = e / nn, j = e - w * nn;
+    const double2 a = T[(3 * w) * nn + j], b = T[(3 * w + 1) * nn + j], c = T[(3 * w + 2) * nn + j];
+    out[e] = make_double2(a.x - b.x - c.y, a.y - b.y + c.x);
+}
+
+cudaError_t launch_combine_real(const double2 *T, int64_t nn, int nw, double2 *out, cudaStream_t st)
+{
+    const int64_t n = nn * nw;
+    if (n == 0) return cudaSuccess;
+    combine_real_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, nn, nw, out);
+    return cudaGetLastError();
+}
+
+// Forward derivative of Delta(i w) = 4x/(x^2 + w^2) along (dE_v, dE_c): dDelta = 4(w^2 - x^2)/(x^2 +
+// w^2)^2 (dE_v - dE_c), split into two non-positive weights: block 2w: min(dDelta, 0), block
+// 2w + 1: -max(dDelta, 0).
+__global__ void delta_jvp_kernel(const double *__restrict__ ev, const double *__restrict__ ec,
+                                 const double *__restrict__ dev, const double *__restrict__ dec, int nc, int64_t p0,
+                                 int64_t count, OmegaList om, double *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int64_t p = p0 + i;
+    int v = (int)(p / nc), c = (int)(p - (int64_t)v * nc);
+    const double x = ev[v] - ec[c], dx = dev[v] - dec[c];
+    for (int w = 0; w < om.nw; ++w) {
+        const double w2 = om.w[w] * om.w[w], den = fma(x, x, w2);
+        const double dd = 4.0 * (w2 - x * x) / (den * den) * dx;
+        out[(int64_t)(2 * w) * count + i] = fmin(dd, 0.0);
+        out[(int64_t)(2 * w + 1) * count + i] = -fmax(dd, 0.0);
+    }
+}
+
+cudaError_t launch_delta_jvp(const double *ev, const double *ec, const double *dev, const double *dec, int nc,
+                             int64_t p0, int64_t count, const OmegaList &om, double *out, cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    delta_jvp_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(ev, ec, dev, dec, nc, p0, count, om, out);
+    return cudaGetLastError();
+}
+
+// d = X1 + X2 (the tangent dM); X1 = M + d, X2 = M - d
+__global__ void jvp_mix_kernel(const double2 *__restrict__ M, double2 *__restrict__ X1, double2 *__restrict__ X2,
+                               int64_t n)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double2 m = M[e], a = X1[e], b = X2[e];
+    const double dx = a.x + b.x, dy = a.y + b.y;
+    X1[e] = make_double2(m.x + dx, m.y + dy);
+    X2[e] = make_double2(m.x - dx, m.y - dy);
+}
+
+cudaError_t launch_jvp_mix(const double2 *M, double2 *X1, double2 *X2, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    jvp_mix_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(M, X1, X2, n);
+    return cudaGetLastError();
+}
+
+// out[w] = (Tp[w] - Tm[w]) / 2 + Tw[2w] - Tw[2w+1]
+__global__ void combine_jvp_kernel(const double2 *__restrict__ Tp, const double2 *__restrict__ Tm,
+                                   const double2 *__restrict__ Tw, int64_t nn, int nw, double2 *__restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nn * nw) return;
+    const int64_t w = e / nn, j = e - w * nn;
+    const double2 a = Tp[e], b = Tm[e], c = Tw[(2 * w) * nn + j], d = Tw[(2 * w + 1) * nn + j];
+    out[e] = make_double2(0.5 * (a.x - b.x) + c.x - d.x, 0.5 * (a.y - b.y) + c.y - d.y);
+}
+
+cudaError_t launch_combine_jvp(const double2 *Tp, const double2 *Tm, const double2 *Tw, int64_t nn, int nw,
+                               double2 *out, cudaStream_t st)
+{
+    const int64_t n = nn * nw;
+    if (n == 0) return cudaSuccess;
+    combine_jvp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Tp, Tm, Tw, nn, nw, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_delta(const double *ev, const double *ec, int nc, int64_t p0, int64_t count, const OmegaList &om,
                          double *delta, cudaStream_t st)
 {

@@ -126,3 +126,45 @@ def test_epsilon_inverse_rejects_bad_coulomb(gw):
     out = h.epsilon_inverse(chi, torch.ones(27, dtype=torch.float64, device="cuda"))  # still usable: chi = 0
     h.sync()
     assert torch.equal(out, torch.eye(27, dtype=torch.complex128, device="cuda"))
+
+
+@pytest.mark.parametrize("prec,mtxel,tol", [("fp64", "fp64", 1e-11), ("ozaki", "twofloat", 1e-9)])
+def test_compute_real_matches_oracle(gw, case, prec, mtxel, tol):
+    """chi on the real axis with broadening, below, across and above the resonances."""
+    p, M, _, _ = case
+    om, eta = [0.5, 12.0, 40.0], 0.2
+    h = gw.from_problem(p, prec=prec, nslices=7, mtxel=mtxel, pair_chunk=64)
+    got = h.compute_real(0, om, eta).cpu().numpy()
+    h.sync()
+    for i, w in enumerate(om):
+        assert rel(got[i], oracle.chi0_real(M, oracle.delta_real(p.ev, p.ec, w, eta))) <= tol, w
+
+
+def test_compute_real_errors(gw, case):
+    p = case[0]
+    h = gw.from_problem(p)
+    with pytest.raises(gw.GwError) as e:
+        h.compute_real(0, [1.0], 0.0)
+    assert e.value.status == 1
+    with pytest.raises(gw.GwError) as e:
+        h.compute_real(0, [1.0] * 22, 0.1)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("prec,mtxel,tol", [("fp64", "fp64", 1e-11), ("ozaki", "twofloat", 1e-9)])
+def test_jvp_matches_oracle(gw, case, prec, mtxel, tol):
+    """Forward derivative of chi0 along random band and energy perturbations."""
+    p = case[0]
+    rng = np.random.default_rng(91)
+    dcv = (rng.standard_normal(p.cv.shape) + 1j * rng.standard_normal(p.cv.shape)) / np.sqrt(p.cv.shape[1])
+    dcc = (rng.standard_normal(p.cc.shape) + 1j * rng.standard_normal(p.cc.shape)) / np.sqrt(p.cc.shape[1])
+    dev, dec = rng.standard_normal(len(p.ev)), rng.standard_normal(len(p.ec))
+    om = [0.0, 4.0]
+    h = gw.from_problem(p, prec=prec, nslices=7, mtxel=mtxel, pair_chunk=64)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    got = h.jvp(0, om, t(dcv), t(dcc), t(dev), t(dec)).cpu().numpy()
+    h.sync()
+    for i, w in enumerate(om):
+        ref = oracle.jvp(p.gpsi, p.cv, p.ev, p.cc, p.ec, p.gchi, dcv, dcc, dev, dec, w)
+        assert rel(got[i], ref) <= tol, (w, rel(got[i], ref))
+        assert np.array_equal(got[i], got[i].conj().T)

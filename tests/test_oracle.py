@@ -373,3 +373,45 @@ def test_epsilon_structure():
     t = 1e-6
     e1 = oracle.epsilon_inverse(chi_0, t * v)
     assert rel((e1 - np.eye(len(v))) / t, v[:, None] * chi_0) < 1e-5
+
+
+# ------------------------------------------------------------------ real axis (next row f3)
+
+def test_delta_real_limits():
+    """Away from the poles and for eta -> 0, Delta = 2/(x - w) + 2/(x + w); at w = 0 with
+    eta = w' it is the imaginary-axis factor at w' (the continuation i w' -> w + i eta)."""
+    ev, ec = np.array([-3.0, -1.5]), np.array([2.0, 4.5, 7.0])
+    x = (ev[:, None] - ec[None, :]).ravel()
+    d = oracle.delta_real(ev, ec, 0.7, 1e-12)
+    assert np.abs(d - (2 / (x - 0.7) + 2 / (x + 0.7))).max() < 1e-10
+    assert np.abs(oracle.delta_real(ev, ec, 0.0, 2.5) - oracle.delta(ev, ec, 2.5)).max() < 1e-15
+
+
+@pytest.mark.parametrize("w", [0.5, 9.0])
+def test_chi_real_absorptive_part(sub_case, w):
+    """chi(w) = chi_R + i chi_I with chi_I = (chi - chi^H)/(2i) negative semidefinite for w >= 0
+    (absorption), and chi_R = (chi + chi^H)/2 the contraction with Re Delta."""
+    p, M, _ = sub_case
+    dc = oracle.delta_real(p.ev, p.ec, w, 0.3)
+    chi = oracle.chi0_real(M, dc)
+    ci = (chi - chi.conj().T) / 2j
+    assert np.linalg.eigvalsh(ci).max() <= 1e-13 * np.abs(ci).max()
+    assert rel((chi + chi.conj().T) / 2, oracle.chi0(M, dc.real)) < 1e-14
+
+
+@pytest.mark.parametrize("w", [0.0, 3.0])
+def test_jvp_central_differences(w):
+    """The forward derivative against central differences of chi0 along the same direction."""
+    p = tiny(nv=2, nc=4, ngpsi=93, ng=27, seed=23)
+    rng = np.random.default_rng(24)
+    dcv = rng.standard_normal(p.cv.shape) + 1j * rng.standard_normal(p.cv.shape)
+    dcc = rng.standard_normal(p.cc.shape) + 1j * rng.standard_normal(p.cc.shape)
+    dev, dec = rng.standard_normal(len(p.ev)), rng.standard_normal(len(p.ec))
+    got = oracle.jvp(p.gpsi, p.cv, p.ev, p.cc, p.ec, p.gchi, dcv, dcc, dev, dec, w)
+
+    def chi(t):
+        M = oracle.m_conv(p.gpsi, p.cv + t * dcv, p.gpsi, p.cc + t * dcc, p.gchi)
+        return oracle.chi0(M, oracle.delta(p.ev + t * dev, p.ec + t * dec, w))
+
+    h = 1e-6
+    assert rel(got, (chi(h) - chi(-h)) / (2 * h)) < 1e-7
