@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--subspace", action="store_true")
     ap.add_argument("--epsilon", action="store_true")
+    ap.add_argument("--extras", action="store_true", help="real-axis chi and the forward derivative")
     return ap.parse_args()
 
 
@@ -645,6 +646,43 @@ def epsilon(args):
                       "kernel_ms": kms, "residual_rms": res}), flush=True)
 
 
+def extras(args):
+    """Real-axis chi (3 frequencies, eta = 0.1 eV) and the forward derivative (JVP, 1 frequency)
+    on the 48^3 workload; times through CUDA events on the handle's stream."""
+    import torch
+    import paper_2509_23018_gb300 as gw
+    cfg = gwgen.CONFIGS["c2_48cube"]
+    prob = gwgen.config_problem(cfg)
+    h = gw.from_problem(prob, prec=args.prec, nslices=args.nslices, mtxel=args.mtxel or "twofloat",
+                        pair_chunk=cfg.pair_chunk)
+    rng = np.random.default_rng(5)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    dcv = t((rng.standard_normal(prob.cv.shape) + 1j * rng.standard_normal(prob.cv.shape)) / np.sqrt(cfg.ngpsi))
+    dcc = t((rng.standard_normal(prob.cc.shape) + 1j * rng.standard_normal(prob.cc.shape)) / np.sqrt(cfg.ngpsi))
+    dev, dec = t(rng.standard_normal(cfg.nv)), t(rng.standard_normal(cfg.nc))
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    real, tr = timed(lambda: h.compute_real(0, [2.0, 15.0, 40.0], 0.1))
+    d, tj = timed(lambda: h.jvp(0, [0.0], dcv, dcc, dev, dec))
+    (chi,), tc = timed(lambda: h.compute(0, [0.0]))
+    h.sync()
+    ci = (real[1] - real[1].conj().T) / 2j
+    print(json.dumps({"workload": f"{cfg.name}: 48^3, {cfg.nv}+{cfg.nc} bands, N_G={cfg.ng}",
+                      "prec": args.prec, "nslices": args.nslices, "ms_chi_imag_axis_1w": tc,
+                      "ms_chi_real_axis_per_w": tr / 3, "ms_jvp_1w": tj,
+                      "chi_I_max_eig_over_norm": float(torch.linalg.eigvalsh(ci).max() / torch.linalg.norm(ci)),
+                      "jvp_hermitian": bool(torch.equal(d[0], d[0].conj().T))}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -657,6 +695,8 @@ def main():
         subspace(args)
     elif args.epsilon:
         epsilon(args)
+    elif args.extras:
+        extras(args)
     elif args.adjoint:
         adjoint(args)
     else:
