@@ -178,8 +178,6 @@ def reference_arm(args):
 TRAFFIC = {
     "contract_f64": {"bytes_per_launch": 1.941011e9 + 0.034306e9,
                      "source": "ncu dram__bytes_read+write, contract_f64_kernel, p1_48cube_onechunk"},
-    "pair_mtxel": {"bytes_per_launch": 3.070e9 + 1.484e9,
-                   "source": "ncu dram__bytes_read+write, pair_kernel_tf_ct<48>, p1_48cube_onechunk"},
     "ozaki_gemm": {"bytes_per_launch": 7.32e9 + 0.219e9,
                    "source": "ncu dram__bytes_read+write, oz_gemm_kernel (s = 7), p1_48cube_onechunk"},
 }
@@ -349,15 +347,15 @@ def _prune_out_ops(n):
 
 
 def twofloat_ops_per_pair(cfg, k2, k12):
-    """FP32 operations of the two-float pair kernel per pair: product, i2 transform of every
-    line (lazy butterflies, pruned to the k2 kept columns), i1 transform of those columns
+    """FP32 operations of the two-float pair kernel per pair: the lazy product, i2 transform of
+    every line (lazy butterflies, pruned to the k2 kept columns), i1 transform of those columns
     (pruned to the k12 cells of the sphere), i0 transform of the k12 cell columns (pruned
     to the sphere points)."""
     n0, n1, n2 = cfg.grid
     i2 = n1 * (_head_ops(n2, lazy=True) + k2 * _prune_out_ops(n2))
-    i1 = k2 * _head_ops(n1) + k12 * _prune_out_ops(n1)
-    i0 = k12 * _head_ops(n0) + cfg.ng * _prune_out_ops(n0)
-    return n0 * (n1 * n2 * _CMUL + i2 + i1) + i0
+    i1 = k2 * _head_ops(n1, lazy=True) + k12 * _prune_out_ops(n1)
+    i0 = k12 * _head_ops(n0, lazy=True) + cfg.ng * _prune_out_ops(n0)
+    return n0 * (n1 * n2 * _CMUL_L + i2 + i1) + i0
 
 
 def cells(prob, n):

@@ -139,6 +139,11 @@ __device__ __forceinline__ void tc_acc(tcx &F, tcx a, tcx w)
     tf_acc2(F.re, a.re, w.re, tf_neg(a.im), w.im);
     tf_acc2(F.im, a.re, w.im, a.im, w.re);
 }
+// conj(a) * b, lazy (feeds lazy sums)
+__device__ __forceinline__ tcx tc_mulcl(tcx a, tcx b)
+{
+    return {tf_dot2l(a.re, b.re, a.im, b.im), tf_dot2l(a.re, b.im, tf_neg(a.im), b.re)};
+}
 // conj(a) * b
 __device__ __forceinline__ tcx tc_mulc(tcx a, tcx b)
 {
@@ -336,8 +341,9 @@ constexpr RadPlan plan_of()
     return PR ? make_prune_plan(N) : make_rad_plan(N);
 }
 
-// lines of N points, line l at x + l * ls, element stride es
-template <int N, int R, int NS>
+// lines of N points, line l at x + l * ls, element stride es; LAZY leaves radix-4 outputs
+// unrenormalised (for stages whose outputs feed another lazy stage)
+template <int N, int R, int NS, bool LAZY = false>
 __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines, int ls,
                                           const float4 *__restrict__ tw, const TfConsts &k, int es = 1)
 {
@@ -356,7 +362,8 @@ __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = tc_mull(v[r], tc_load(tw + r * e));
         }
-        tdftR<R>(v, k);
+        if constexpr (LAZY && R == 4) tdft4<false>(v);
+        else tdftR<R>(v, k);
         float4 *yl = y + l * ls;
         const int o = (j / NS) * (NS * R) + kk;
 #pragma unroll
@@ -366,6 +373,7 @@ __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *
 
 // Stages S.. of the plan (all of make_rad_plan(N), or all but the pruned last one of
 // make_prune_plan(N)), block-wide with a barrier after each; returns the result buffer.
+// With PR the stages are lazy: their outputs only feed the pruned stage's lazy sums.
 template <int N, int S, int NS, bool PR = false>
 __device__ __forceinline__ float4 *tstages_ct(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
                                               const TfConsts &k, int es)
@@ -375,7 +383,7 @@ __device__ __forceinline__ float4 *tstages_ct(float4 *x, float4 *y, int nlines, 
         return x;
     } else {
         constexpr int R = P.r[S];
-        tstage_ct<N, R, NS>(x, y, nlines, ls, tw, k, es);
+        tstage_ct<N, R, NS, PR>(x, y, nlines, ls, tw, k, es);
         __syncthreads();
         return tstages_ct<N, S + 1, NS * R, PR>(y, x, nlines, ls, tw, k, es);
     }

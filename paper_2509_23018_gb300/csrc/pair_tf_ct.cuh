@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
                     const float4 *xv = sv + l * N + j, *xc = sc + l * N + j;
                     tcx x[R0];
 #pragma unroll
-                    for (int r = 0; r < R0; ++r) x[r] = tc_mulc(tc_load(xv + r * nb0), tc_load(xc + r * nb0));
+                    for (int r = 0; r < R0; ++r) x[r] = tc_mulcl(tc_load(xv + r * nb0), tc_load(xc + r * nb0));
                     tdft_lazy<R0>(x, kc);
                     float4 *yl = Aw + l * N + j * R0;
 #pragma unroll
