@@ -1182,7 +1182,8 @@ gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngpsi, con
     CK(h, cudaMemsetAsync(nbs.psi, 0, sizeof(double2) * (size_t)nb * h->nr, h->st), "zero psi");
     if (h->d.mtxel_prec == GW_MTXEL_TWOFLOAT) {
         Scope sc(h, "band_setup_tf");
-        CK(h, gw::launch_band_setup_tf((const double2 *)coeff, nbs.gofs, nb, ngpsi, nbs.psi, h->d.n, h->ax, h->st),
+        CK(h, gw::launch_band_setup_tf((const double2 *)coeff, nbs.gofs, nb, ngpsi, nbs.psi, h->d.n, h->ax,
+                                       nbs.maxabs, h->st),
            "band setup (two-float)"); // three kernels
     } else {
         {
@@ -1845,7 +1846,8 @@ static gw_status band_grids(gw_chi0 *h, const BandSet &b, const double *coeff, v
     CK(h, cudaMemsetAsync(psi, 0, sizeof(double2) * (size_t)b.nb * h->nr, h->st), "zero grids");
     if (h->d.mtxel_prec == GW_MTXEL_TWOFLOAT) {
         Scope sc(h, "band_setup_tf");
-        CK(h, gw::launch_band_setup_tf((const double2 *)coeff, b.gofs, b.nb, b.ngpsi, psi, h->d.n, h->ax, h->st),
+        CK(h, gw::launch_band_setup_tf((const double2 *)coeff, b.gofs, b.nb, b.ngpsi, psi, h->d.n, h->ax, b.maxabs,
+                                       h->st),
            "tangent band setup (two-float)");
     } else {
         CK(h, gw::launch_scatter((const double2 *)coeff, b.gofs, b.nb, b.ngpsi, h->nr, (double2 *)psi, h->st),

@@ -343,15 +343,19 @@ constexpr RadPlan plan_of()
 
 // lines of N points, line l at x + l * ls, element stride es; LAZY leaves radix-4 outputs
 // unrenormalised (for stages whose outputs feed another lazy stage)
+// lmax >= 0 skips the lines l whose signed index (l, or l - N above N/2) exceeds lmax in
+// magnitude (all-zero lines whose outputs stay zero in both ping-pong buffers).
 template <int N, int R, int NS, bool LAZY = false>
 __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines, int ls,
-                                          const float4 *__restrict__ tw, const TfConsts &k, int es = 1)
+                                          const float4 *__restrict__ tw, const TfConsts &k, int es = 1,
+                                          int lmax = -1)
 {
     constexpr int nb = N / R;
     constexpr int tstride = N / (NS * R); // r * kk * tstride < N: no reduction needed
     const int total = nlines * nb;
     for (int b = threadIdx.x; b < total; b += blockDim.x) {
         const int l = b / nb, j = b - l * nb;
+        if (lmax >= 0 && (l <= N / 2 ? l : N - l) > lmax) continue;
         const int kk = j % NS;
         const float4 *xl = x + l * ls;
         tcx v[R];
@@ -376,26 +380,26 @@ __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *
 // With PR the stages are lazy: their outputs only feed the pruned stage's lazy sums.
 template <int N, int S, int NS, bool PR = false>
 __device__ __forceinline__ float4 *tstages_ct(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
-                                              const TfConsts &k, int es)
+                                              const TfConsts &k, int es, int lmax = -1)
 {
     constexpr RadPlan P = plan_of<N, PR>();
     if constexpr (S >= P.nst - (PR ? 1 : 0)) {
         return x;
     } else {
         constexpr int R = P.r[S];
-        tstage_ct<N, R, NS, PR>(x, y, nlines, ls, tw, k, es);
+        tstage_ct<N, R, NS, PR>(x, y, nlines, ls, tw, k, es, lmax);
         __syncthreads();
-        return tstages_ct<N, S + 1, NS * R, PR>(y, x, nlines, ls, tw, k, es);
+        return tstages_ct<N, S + 1, NS * R, PR>(y, x, nlines, ls, tw, k, es, lmax);
     }
 }
 
 // Full two-float transform of nlines lines of length N (line stride ls, element stride es);
-// returns the result buffer.
+// returns the result buffer.  lmax >= 0: lines beyond it are zero and skipped (see tstage_ct).
 template <int N>
 __device__ __forceinline__ float4 *tfft_lines_ct(float4 *a, float4 *b, int nlines, int ls, const float4 *tw,
-                                                 const TfConsts &k, int es = 1)
+                                                 const TfConsts &k, int es = 1, int lmax = -1)
 {
-    return tstages_ct<N, 0, 1>(a, b, nlines, ls, tw, k, es);
+    return tstages_ct<N, 0, 1>(a, b, nlines, ls, tw, k, es, lmax);
 }
 
 // Warp-level stage over the calling warp's own lines (L lines of N points at x + l * N);

@@ -47,8 +47,9 @@ int pair_max_ng();
 cudaError_t launch_pair_tf(const void *psiv, const void *psic, int nc, int64_t p0, int64_t count,
                            const PairPlan &pp, double2 *M, cudaStream_t st);
 // band setup in two-float arithmetic: scatter (with hi/lo split) + 3D FFT, psi in two-float form
+// maxabs: largest |G_a| of the plane waves (input pruning of the grid-specialised transforms)
 cudaError_t launch_band_setup_tf(const double2 *coeff, const int32_t *gofs, int nb, int ngpsi, void *psi,
-                                 const int n[3], const FftAxis ax[3], cudaStream_t st);
+                                 const int n[3], const FftAxis ax[3], const int maxabs[3], cudaStream_t st);
 
 
 // ---- energy factor, diagonal, symmetrisation (reduce.cu)

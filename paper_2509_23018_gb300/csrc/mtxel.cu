@@ -165,7 +165,7 @@ TfConsts tf_consts()
 }
 
 cudaError_t launch_band_setup_tf(const double2 *coeff, const int32_t *gofs, int nb, int ngpsi, void *psi,
-                                 const int n[3], const FftAxis ax[3], cudaStream_t st)
+                                 const int n[3], const FftAxis ax[3], const int maxabs[3], cudaStream_t st)
 {
     const int64_t nr = (int64_t)n[0] * n[1] * n[2];
     const int64_t tot = (int64_t)nb * ngpsi;
@@ -177,10 +177,10 @@ cudaError_t launch_band_setup_tf(const double2 *coeff, const int32_t *gofs, int 
     const TfConsts kc = tf_consts();
     if (n[0] == n[1] && n[1] == n[2]) {
         switch (n[0]) { // grid-specialised transforms for the standard cubic grids
-        case 24: return launch_band_fft_tf_g24(p, nb, ax, kc, st);
-        case 40: return launch_band_fft_tf_g40(p, nb, ax, kc, st);
-        case 48: return launch_band_fft_tf_g48(p, nb, ax, kc, st);
-        case 72: return launch_band_fft_tf_g72(p, nb, ax, kc, st);
+        case 24: return launch_band_fft_tf_g24(p, nb, ax, kc, maxabs[0], maxabs[1], st);
+        case 40: return launch_band_fft_tf_g40(p, nb, ax, kc, maxabs[0], maxabs[1], st);
+        case 48: return launch_band_fft_tf_g48(p, nb, ax, kc, maxabs[0], maxabs[1], st);
+        case 72: return launch_band_fft_tf_g72(p, nb, ax, kc, maxabs[0], maxabs[1], st);
         default: break;
         }
     }

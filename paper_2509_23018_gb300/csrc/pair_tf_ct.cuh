@@ -285,17 +285,25 @@ inline bool pair_tf_ct_fits(const PairPlan &pp)
 
 // Band setup in two-float arithmetic for a cubic N^3 grid: the (band, i0) slab kernel
 // transforms along i2 then i1, the (band, i1) plane kernel along i0.
+// Input pruning: the coefficients fill |G_a| <= m_a (m >= 0; -1: unknown), so slabs with
+// |G_0| > m_0 are zero and stay zero, and in a slab the i2 lines with |G_1| > m_1 are zero.
 template <int N>
-__global__ void __launch_bounds__(256) band_slab_tf_ct(float4 *__restrict__ psi, FftAxis ax, TfConsts kc)
+__global__ void __launch_bounds__(256) band_slab_tf_ct(float4 *__restrict__ psi, FftAxis ax, TfConsts kc, int m0,
+                                                       int m1)
 {
+    const int i0 = blockIdx.x;
+    if (m0 >= 0 && (i0 <= N / 2 ? i0 : N - i0) > m0) return; // zero slab (the grid was zeroed)
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int ns = N * N;
     float4 *a = (float4 *)smem, *b = a + ns, *tw = b + ns;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = ax.twf[i];
-    float4 *g = psi + ((int64_t)blockIdx.y * N + blockIdx.x) * ns;
-    for (int i = threadIdx.x; i < ns; i += blockDim.x) a[i] = g[i];
+    float4 *g = psi + ((int64_t)blockIdx.y * N + i0) * ns;
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        a[i] = g[i];
+        b[i] = make_float4(0.f, 0.f, 0.f, 0.f); // skipped lines stay zero in both buffers
+    }
     __syncthreads();
-    float4 *r = tfft_lines_ct<N>(a, b, N, N, tw, kc);         // along i2
+    float4 *r = tfft_lines_ct<N>(a, b, N, N, tw, kc, 1, m1); // along i2, zero lines skipped
     float4 *o = (r == a) ? b : a;
     r = tfft_lines_ct<N>(r, o, N, 1, tw, kc, N);              // along i1 (element stride N)
     for (int i = threadIdx.x; i < ns; i += blockDim.x) g[i] = r[i];
@@ -322,7 +330,7 @@ __global__ void __launch_bounds__(256) band_axis0_tf_ct(float4 *__restrict__ psi
 }
 
 template <int N>
-inline cudaError_t launch_band_fft_tf_ct(float4 *psi, int nb, const FftAxis *ax, const TfConsts &kc,
+inline cudaError_t launch_band_fft_tf_ct(float4 *psi, int nb, const FftAxis *ax, const TfConsts &kc, int m0, int m1,
                                          cudaStream_t st)
 {
     const size_t sm = sizeof(float4) * (2 * (size_t)N * N + N);
@@ -332,16 +340,16 @@ inline cudaError_t launch_band_fft_tf_ct(float4 *psi, int nb, const FftAxis *ax,
         (e = cudaFuncSetAttribute(band_axis0_tf_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
             cudaSuccess)
         return e;
-    band_slab_tf_ct<N><<<dim3(N, nb), 256, sm, st>>>(psi, ax[2], kc);
+    band_slab_tf_ct<N><<<dim3(N, nb), 256, sm, st>>>(psi, ax[2], kc, m0, m1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     band_axis0_tf_ct<N><<<dim3(N, nb), 256, sm, st>>>(psi, ax[0], kc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_band_fft_tf_g24(float4 *, int, const FftAxis *, const TfConsts &, cudaStream_t);
-cudaError_t launch_band_fft_tf_g40(float4 *, int, const FftAxis *, const TfConsts &, cudaStream_t);
-cudaError_t launch_band_fft_tf_g48(float4 *, int, const FftAxis *, const TfConsts &, cudaStream_t);
-cudaError_t launch_band_fft_tf_g72(float4 *, int, const FftAxis *, const TfConsts &, cudaStream_t);
+cudaError_t launch_band_fft_tf_g24(float4 *, int, const FftAxis *, const TfConsts &, int, int, cudaStream_t);
+cudaError_t launch_band_fft_tf_g40(float4 *, int, const FftAxis *, const TfConsts &, int, int, cudaStream_t);
+cudaError_t launch_band_fft_tf_g48(float4 *, int, const FftAxis *, const TfConsts &, int, int, cudaStream_t);
+cudaError_t launch_band_fft_tf_g72(float4 *, int, const FftAxis *, const TfConsts &, int, int, cudaStream_t);
 
 cudaError_t launch_pair_tf_g24(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,
                                const TfConsts &, tf, double2 *, cudaStream_t);

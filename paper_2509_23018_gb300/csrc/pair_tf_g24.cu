@@ -11,9 +11,10 @@ cudaError_t launch_pair_tf_g24(const float4 *a, const float4 *b, int nc, int64_t
 
 cudaError_t pair_tf_slots_g24(const PairPlan &pp, int *nslots) { return pair_tf_cube_slots<24>(pp, nslots); }
 
-cudaError_t launch_band_fft_tf_g24(float4 *psi, int nb, const FftAxis *ax, const TfConsts &kc, cudaStream_t st)
+cudaError_t launch_band_fft_tf_g24(float4 *psi, int nb, const FftAxis *ax, const TfConsts &kc, int m0, int m1,
+                                  cudaStream_t st)
 {
-    return launch_band_fft_tf_ct<24>(psi, nb, ax, kc, st);
+    return launch_band_fft_tf_ct<24>(psi, nb, ax, kc, m0, m1, st);
 }
 
 } // namespace gw
