@@ -1,148 +1,8 @@
 // Host side of the C ABI declared in include/gw_chi0.h: handle state, validation,
 // library-owned device memory, per-chunk orchestration and optional per-kernel timing.
-#include "../../include/gw_chi0.h"
-#include "internal.h"
+#include "api_internal.h"
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
-#include <cusolverDn.h>
-#include <dlfcn.h>
-
-#include <algorithm>
-#include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstdlib>
-#include <cstring>
-#include <array>
-#include <map>
-#include <string>
-#include <vector>
-
-using gw::FftAxis;
-
-namespace {
-
-struct BandSet {
-    int nb = 0, ngpsi = 0;
-    double2 *psi = nullptr;     // [nb][N_r]
-    double *energy = nullptr;   // [nb] device copy
-    int32_t *gvec = nullptr;    // [ngpsi][3] device copy (adjoint)
-    int32_t *gofs = nullptr;    // [ngpsi] grid offsets
-    std::vector<int32_t> g;     // host copy
-    std::vector<double> e;      // host copy
-    int maxabs[3] = {0, 0, 0};
-};
-
-struct Sphere {
-    int ng = 0;
-    std::vector<int32_t> g;
-    int maxabs[3] = {0, 0, 0};
-    int K2 = 0;
-    int *kz = nullptr;          // device [K2]
-    int32_t *gpack = nullptr;   // device [ng]
-    int32_t *gvec = nullptr;    // device [ng][3]
-    std::vector<int> cstart, cg; // (k1, k2) cells of the sphere, CSR (adjoint back-projection)
-    int K12 = 0;                // number of cells
-    int32_t *cell = nullptr;    // device [K12]  k2index << 8 | k1
-    int *cstart_d = nullptr;    // device [K12 + 1] (cstart)
-    int2 *cpts = nullptr;       // device [ng]   (point, k0 | cell << 8) in cell order
-    int nslots = 0;             // scratch slots the two-float pair kernel needs (0: none)
-};
-
-struct TimerRec {
-    std::string name;
-    cudaEvent_t a, b;
-};
-
-} // namespace
-
-struct gw_chi0 {
-    gw_chi0_desc d{};
-    cudaStream_t st = nullptr;
-    std::string err;
-    int64_t nr = 0;
-    FftAxis ax[3]{};
-    double2 *tw = nullptr;
-    float4 *twf = nullptr;
-    BandSet cond;
-    std::vector<BandSet> val;
-    std::vector<Sphere> sph;
-    double2 *Mbuf = nullptr;
-    size_t Mcap = 0; // elements
-    double *dbuf = nullptr;
-    size_t dcap = 0;
-    // split-precision work buffers
-    void *Zbuf = nullptr;      // bf16 slices [s][2 ng][kpad]
-    size_t Zcap = 0;           // bytes
-    double *spbuf = nullptr;   // sqrt(-Delta) [nw][chunk]
-    size_t spcap = 0;
-    int *Ebuf = nullptr;       // column exponents [ng]
-    size_t Ecap = 0;
-    void *jobbuf = nullptr;    // job tables of the batched contraction kernels
-    size_t jobcap = 0;
-    // contraction launch shapes (set by the autotuner; these are the defaults)
-    int tuned_bt = 64, tuned_waves = 4, tuned_bn = 256;
-    std::map<std::string, std::array<int, 3>> tune_cache; // signature -> (bt, waves, bn)
-    // batched path: every slot's M resident, one graph per call signature
-    double2 *Mall = nullptr;
-    size_t Mall_cap = 0;
-    double *Dall = nullptr, *SPall = nullptr;
-    size_t Dall_cap = 0, SPall_cap = 0;
-    void *Zall = nullptr;
-    size_t Zall_cap = 0;
-    int *Eall = nullptr;
-    size_t Eall_cap = 0;
-    cudaStream_t cap_st = nullptr;
-    struct Graph {
-        std::string key;
-        cudaGraphExec_t exec = nullptr;
-        void *jobs = nullptr;
-        size_t jobs_bytes = 0;
-    };
-    std::vector<Graph> graphs;
-    int *status = nullptr;
-    // split-precision general products (subspace projection, adjoint Y = M W)
-    int *EAbuf = nullptr, *EBbuf = nullptr;
-    size_t EAcap = 0, EBcap = 0;
-    void *ZBbuf = nullptr;      // B operand slices [s][2 nout][kpad]
-    size_t ZBcap = 0;
-    double2 *MBbuf = nullptr;   // projected pair elements of a chunk [chunk][neig]
-    size_t MBcap = 0;
-    void *epsbuf = nullptr;     // dielectric inverse: A, X, T, P [ng][ng], sqrt(v) [ng], bound
-    size_t epscap = 0;
-    double2 *realbuf = nullptr; // real-axis chi: the three Hermitian parts per frequency
-    size_t realcap = 0;
-    // dense eigensolver (cuSOLVER, loaded on first use) for the subspace basis
-    struct {
-        void *lib = nullptr;
-        cusolverDnHandle_t hdl = nullptr;
-        decltype(&cusolverDnCreate) create = nullptr;
-        decltype(&cusolverDnDestroy) destroy = nullptr;
-        decltype(&cusolverDnSetStream) set_stream = nullptr;
-        decltype(&cusolverDnZheevdx_bufferSize) buffer_size = nullptr;
-        decltype(&cusolverDnZheevdx) heevdx = nullptr;
-    } sol;
-    double2 *eigA = nullptr, *eigWork = nullptr;
-    double *eigW = nullptr;
-    int *eigInfo = nullptr;
-    size_t eigA_cap = 0, eigWork_cap = 0, eigW_cap = 0, eigInfo_cap = 0;
-    // scratch slots of the two-float pair kernel (sized in set_gsphere, outside any capture)
-    float4 *pscr = nullptr;
-    size_t pscr_cap = 0; // bytes
-    int *pflags = nullptr;
-    size_t pflags_cap = 0; // bytes
-    size_t bytes = 0;
-    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    // timing
-    bool timing = false;
-    std::vector<TimerRec> pending;
-    std::vector<cudaEvent_t> pool;
-    std::map<std::string, std::pair<double, int64_t>> acc;
-};
-
-namespace {
-
+namespace gwapi {
 gw_status fail(gw_chi0 *h, gw_status s, const char *fmt, ...)
 {
     char buf[512];
@@ -159,11 +19,7 @@ gw_status cuda_fail(gw_chi0 *h, cudaError_t e, const char *what)
     return fail(h, e == cudaErrorMemoryAllocation ? GW_ERR_OOM : GW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(h, x, what)                                   \
-    do {                                                 \
-        cudaError_t e_ = (x);                            \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
-    } while (0)
+
 
 gw_status dalloc(gw_chi0 *h, void **p, size_t n, const char *what)
 {
@@ -235,26 +91,7 @@ cudaEvent_t ev_get(gw_chi0 *h)
     return e;
 }
 
-struct Scope {
-    gw_chi0 *h;
-    const char *name;
-    cudaEvent_t a = nullptr;
-    Scope(gw_chi0 *h_, const char *n) : h(h_), name(n)
-    {
-        if (h->timing) {
-            a = ev_get(h);
-            cudaEventRecord(a, h->st);
-        }
-    }
-    ~Scope()
-    {
-        if (h->timing) {
-            cudaEvent_t b = ev_get(h);
-            cudaEventRecord(b, h->st);
-            h->pending.push_back({name, a, b});
-        }
-    }
-};
+
 
 void drain_timing(gw_chi0 *h)
 {
@@ -642,336 +479,9 @@ void free_sphere(gw_chi0 *h, Sphere &s)
     dfree(h, s.cpts, sizeof(int2) * s.ng);
     s = Sphere();
 }
+} // namespace gwapi
 
-
-// ------------------------------------------------------------------ batched path (many q, many w)
-// Every requested slot's M is produced once and kept resident; the contraction of all
-// (q, w) blocks then runs as one persistent launch (FP64) or one persistent launch per
-// frequency over all slots (split precision).  The whole sequence is captured once per
-// call signature into a CUDA graph and replayed.  Launch shapes come from a small
-// autotuner that times the candidates on the first call of a signature.
-struct BatchLayout {
-    std::vector<int64_t> P, moff, doff, coff, dgoff;
-    std::vector<int> ng;
-    // split precision: pair segments of at most pair_chunk pairs, each with its own
-    // column exponents and slices (the exactness bound of the slice sums is per segment)
-    struct Seg {
-        int q;
-        int64_t p0, cnt, kpad, zoff, eoff;
-    };
-    std::vector<Seg> seg;
-    size_t Mtot = 0, Dtot = 0, Ztot = 0, Etot = 0;
-};
-
-BatchLayout batch_layout(gw_chi0 *h, int nq, const int *iq, int nw)
-{
-    BatchLayout L;
-    size_t coff = 0, dgoff = 0;
-    const int64_t kseg = h->d.pair_chunk;
-    for (int i = 0; i < nq; ++i) {
-        const int ng = h->sph[iq[i]].ng;
-        const int64_t P = (int64_t)h->val[iq[i]].nb * h->cond.nb;
-        L.ng.push_back(ng);
-        L.P.push_back(P);
-        L.moff.push_back((int64_t)L.Mtot);
-        L.doff.push_back((int64_t)L.Dtot);
-        L.coff.push_back((int64_t)coff);
-        L.dgoff.push_back((int64_t)dgoff);
-        L.Mtot += (size_t)P * ng;
-        L.Dtot += (size_t)nw * P;
-        coff += (size_t)nw * ng * ng;
-        dgoff += (size_t)nw * ng;
-        for (int64_t p0 = 0; p0 < P; p0 += kseg) {
-            BatchLayout::Seg sg;
-            sg.q = i;
-            sg.p0 = p0;
-            sg.cnt = std::min(kseg, P - p0);
-            sg.kpad = (sg.cnt + 63) / 64 * 64;
-            sg.zoff = (int64_t)L.Ztot;
-            sg.eoff = (int64_t)L.Etot;
-            L.Ztot += (size_t)h->d.nslices * 2 * ng * sg.kpad;
-            L.Etot += (size_t)ng;
-            L.seg.push_back(sg);
-        }
-    }
-    return L;
-}
-
-std::string batch_key(gw_chi0 *h, int nq, const int *iq, int nw, const double *omega, const void *chi,
-                      const void *diag)
-{
-    std::string k = "p" + std::to_string(h->d.prec) + "s" + std::to_string(h->d.nslices) + "m" +
-                    std::to_string(h->d.mtxel_prec) + "|";
-    char buf[64];
-    for (int i = 0; i < nq; ++i) k += std::to_string(iq[i]) + ":" + std::to_string(h->sph[iq[i]].ng) + ",";
-    k += "|";
-    for (int i = 0; i < nw; ++i) {
-        snprintf(buf, sizeof buf, "%a,", omega[i]);
-        k += buf;
-    }
-    snprintf(buf, sizeof buf, "|%p|%p", chi, diag);
-    return k + buf;
-}
-
-std::string tune_key(gw_chi0 *h, const BatchLayout &L, int nw)
-{
-    std::string k = "p" + std::to_string(h->d.prec) + "s" + std::to_string(h->d.nslices) + "w" + std::to_string(nw);
-    for (size_t i = 0; i < L.ng.size(); ++i) k += "," + std::to_string(L.ng[i]) + "x" + std::to_string(L.P[i]);
-    return k;
-}
-
-// Enqueue the producer stages: pair elements of every slot, Delta, and (split precision)
-// the square roots.  The slices depend on the frequency and are enqueued per frequency.
-gw_status batch_stage_a(gw_chi0 *h, int nq, const int *iq, const gw::OmegaList &om, const BatchLayout &L)
-{
-    for (int i = 0; i < nq; ++i) {
-        const BandSet &v = h->val[iq[i]];
-        gw::PairPlan pp = pair_plan(h, h->sph[iq[i]]);
-        {
-            Scope sc(h, "pair_mtxel");
-            CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, 0, L.P[i], pp, h->Mall + L.moff[i]), "pair kernel");
-        }
-        Scope sc(h, "delta");
-        CK(h, gw::launch_delta(v.energy, h->cond.energy, h->cond.nb, 0, L.P[i], om, h->Dall + L.doff[i], h->st),
-           "delta");
-    }
-    if (h->d.prec == GW_PREC_OZAKI_BF16) {
-        Scope sc(h, "oz_split");
-        CK(h, gw::launch_oz_sqrt(h->Dall, (int64_t)L.Dtot, h->SPall, h->st), "oz sqrt");
-    }
-    return GW_OK;
-}
-
-gw_status batch_oz_split(gw_chi0 *h, int nq, int w, const BatchLayout &L)
-{
-    (void)nq;
-    Scope sc(h, "oz_split");
-    for (const auto &sg : L.seg) {
-        const int ng = L.ng[sg.q];
-        const double *sp = h->SPall + L.doff[sg.q] + (int64_t)w * L.P[sg.q] + sg.p0;
-        const double2 *M = h->Mall + L.moff[sg.q] + sg.p0 * ng;
-        CK(h, gw::launch_oz_colexp(M, sg.cnt, ng, sp, h->Eall + sg.eoff, h->st), "oz exponents");
-        CK(h, gw::launch_oz_slice(M, sg.cnt, ng, sp, h->Eall + sg.eoff, h->d.nslices, sg.kpad,
-                                  (uint16_t *)h->Zall + sg.zoff, h->st),
-           "oz slices");
-    }
-    return GW_OK;
-}
-
-gw_status batch_f64_jobs(gw_chi0 *h, int nq, int nw, const BatchLayout &L, double2 *chi, int bt,
-                         std::vector<gw::F64Job> &jobs)
-{
-    jobs.clear();
-    for (int i = 0; i < nq; ++i) {
-        gw_status s = f64_jobs(h, jobs, h->Mall + L.moff[i], L.P[i], L.ng[i], h->Dall + L.doff[i], L.P[i], nw,
-                               chi + L.coff[i], bt);
-        if (s) return s;
-    }
-    return GW_OK;
-}
-
-gw_status batch_oz_jobs(gw_chi0 *h, int nq, int w, const BatchLayout &L, double2 *chi, int bn,
-                        std::vector<gw::OzJob> &jobs)
-{
-    (void)nq;
-    jobs.clear();
-    for (const auto &sg : L.seg) {
-        const int ng = L.ng[sg.q];
-        gw::OzJob j;
-        gw_status s = oz_job(h, j, (uint16_t *)h->Zall + sg.zoff, sg.kpad, ng, h->Eall + sg.eoff,
-                             chi + L.coff[sg.q] + (int64_t)w * ng * ng, bn);
-        if (s) return s;
-        jobs.push_back(j);
-    }
-    return GW_OK;
-}
-
-// Time each launch-shape candidate of the contraction on the real data (into chi, which
-// is cleared afterwards by the real run) and keep the fastest.
-gw_status batch_autotune(gw_chi0 *h, int nq, const int *iq, int nw, const gw::OmegaList &om, const BatchLayout &L,
-                         double2 *chi)
-{
-    const std::string key = tune_key(h, L, nw);
-    auto it = h->tune_cache.find(key);
-    if (it != h->tune_cache.end()) {
-        h->tuned_bt = it->second[0];
-        h->tuned_waves = it->second[1];
-        h->tuned_bn = it->second[2];
-        return GW_OK;
-    }
-    gw_status s = batch_stage_a(h, nq, iq, om, L);
-    if (s) return s;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
-    std::array<int, 3> pick = {h->tuned_bt, h->tuned_waves, h->tuned_bn};
-    const bool saved_timing = h->timing;
-    h->timing = false;
-    if (h->d.prec == GW_PREC_FP64) {
-        for (int bt : {64, 32})
-            for (int waves : {2, 4, 8}) {
-                std::vector<gw::F64Job> jobs;
-                if ((s = batch_f64_jobs(h, nq, nw, L, chi, bt, jobs))) break;
-                cudaEventRecord(e0, h->st);
-                if ((s = launch_f64_jobs(h, jobs, bt, waves))) break;
-                cudaEventRecord(e1, h->st);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    pick = {bt, waves, h->tuned_bn};
-                }
-            }
-    } else if (!(s = batch_oz_split(h, nq, 0, L))) {
-        for (int bn : {256, 128}) {
-            std::vector<gw::OzJob> jobs;
-            if ((s = batch_oz_jobs(h, nq, 0, L, chi, bn, jobs))) break;
-            cudaEventRecord(e0, h->st);
-            if ((s = launch_oz_jobs(h, jobs, bn))) break;
-            cudaEventRecord(e1, h->st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                pick = {h->tuned_bt, h->tuned_waves, bn};
-            }
-        }
-    }
-    h->timing = saved_timing;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (s) return s;
-    h->tune_cache[key] = pick;
-    h->tuned_bt = pick[0];
-    h->tuned_waves = pick[1];
-    h->tuned_bn = pick[2];
-    return GW_OK;
-}
-
-gw_status compute_batch(gw_chi0 *h, int nq, const int *iq, int nw, const double *omega, const gw::OmegaList &om,
-                        double *chi, double *diag)
-{
-    const BatchLayout L = batch_layout(h, nq, iq, nw);
-    gw_status s;
-    if ((s = grow(h, (void **)&h->Mall, &h->Mall_cap, sizeof(double2) * L.Mtot, "resident M")) ||
-        (s = grow(h, (void **)&h->Dall, &h->Dall_cap, sizeof(double) * L.Dtot, "resident Delta")))
-        return s;
-    if (h->d.prec == GW_PREC_OZAKI_BF16 &&
-        ((s = grow(h, (void **)&h->SPall, &h->SPall_cap, sizeof(double) * L.Dtot, "resident scales")) ||
-         (s = grow(h, &h->Zall, &h->Zall_cap, sizeof(uint16_t) * L.Ztot, "resident slices")) ||
-         (s = grow(h, (void **)&h->Eall, &h->Eall_cap, sizeof(int) * L.Etot, "resident exponents"))))
-        return s;
-    if (!h->cap_st) CK(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking), "capture stream");
-    if ((s = batch_autotune(h, nq, iq, nw, om, L, (double2 *)chi))) return s;
-
-    const std::string key = batch_key(h, nq, iq, nw, omega, chi, diag) + "|" + std::to_string(h->tuned_bt) + "," +
-                            std::to_string(h->tuned_waves) + "," + std::to_string(h->tuned_bn);
-    gw_chi0::Graph *g = nullptr;
-    for (auto &x : h->graphs)
-        if (x.key == key) g = &x;
-    if (!g) {
-        // job tables first (outside the capture), in a buffer owned by the graph
-        std::vector<gw::F64Job> fj;
-        std::vector<std::vector<gw::OzJob>> oj(nw);
-        std::vector<unsigned char> blob;
-        std::vector<size_t> offs;
-        if (h->d.prec == GW_PREC_FP64) {
-            if ((s = batch_f64_jobs(h, nq, nw, L, (double2 *)chi, h->tuned_bt, fj))) return s;
-            f64_schedule(fj, h->tuned_waves);
-            offs.push_back(0);
-            blob.resize(sizeof(gw::F64Job) * fj.size());
-            std::memcpy(blob.data(), fj.data(), blob.size());
-        } else {
-            for (int w = 0; w < nw; ++w) {
-                if ((s = batch_oz_jobs(h, nq, w, L, (double2 *)chi, h->tuned_bn, oj[w]))) return s;
-                oz_schedule(oj[w]);
-                offs.push_back(blob.size());
-                blob.resize(blob.size() + sizeof(gw::OzJob) * oj[w].size());
-                std::memcpy(blob.data() + offs.back(), oj[w].data(), sizeof(gw::OzJob) * oj[w].size());
-            }
-        }
-        gw_chi0::Graph ng;
-        ng.key = key;
-        ng.jobs_bytes = blob.size();
-        if ((s = dalloc(h, &ng.jobs, ng.jobs_bytes, "graph job tables"))) return s;
-        CK(h, cudaMemcpy(ng.jobs, blob.data(), blob.size(), cudaMemcpyHostToDevice), "graph job tables");
-
-        cudaStream_t user = h->st;
-        const bool saved_timing = h->timing;
-        h->timing = false;
-        h->st = h->cap_st;
-        cudaGraph_t graph = nullptr;
-        cudaError_t ce = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed);
-        gw_status body = GW_OK;
-        if (ce == cudaSuccess) {
-            for (int i = 0; i < nq && !body; ++i) {
-                if (cudaMemsetAsync((double2 *)chi + L.coff[i], 0, sizeof(double2) * (size_t)nw * L.ng[i] * L.ng[i],
-                                    h->st) != cudaSuccess ||
-                    (diag && cudaMemsetAsync(diag + L.dgoff[i], 0, sizeof(double) * (size_t)nw * L.ng[i], h->st) !=
-                                 cudaSuccess))
-                    body = fail(h, GW_ERR_CUDA, "capture: memset");
-            }
-            if (!body) body = batch_stage_a(h, nq, iq, om, L);
-            if (!body && h->d.prec == GW_PREC_FP64) {
-                int nitems = 0;
-                for (auto &j : fj) nitems = std::max(nitems, j.item_start + (int)((int64_t)j.ksplit * j.ntile *
-                                                                                   (j.ntile + 1) / 2));
-                const int grid = std::max(1, std::min(nitems, 2 * num_sms()));
-                if (gw::launch_contract_f64_jobs(h->tuned_bt, (const gw::F64Job *)ng.jobs, (int)fj.size(), nitems,
-                                                 grid, h->status, h->st) != cudaSuccess)
-                    body = fail(h, GW_ERR_CUDA, "capture: contraction");
-            } else if (!body) {
-                for (int w = 0; w < nw && !body; ++w) {
-                    body = batch_oz_split(h, nq, w, L);
-                    if (body) break;
-                    int nitems = 0;
-                    for (auto &j : oj[w]) nitems = std::max(nitems, j.item_start + j.ntiles);
-                    const int grid = std::max(1, std::min(nitems, num_sms()));
-                    if (gw::launch_oz_gemm_jobs(h->tuned_bn, (const gw::OzJob *)((char *)ng.jobs + offs[w]),
-                                                (int)oj[w].size(), nitems, grid, h->status, h->st) != cudaSuccess)
-                        body = fail(h, GW_ERR_CUDA, "capture: split contraction");
-                }
-            }
-            for (int i = 0; i < nq && !body; ++i) {
-                const double2 *M = h->Mall + L.moff[i];
-                if (diag && gw::launch_diag(M, L.P[i], L.ng[i], h->Dall + L.doff[i], L.P[i], nw,
-                                            diag + L.dgoff[i], L.ng[i], h->st) != cudaSuccess)
-                    body = fail(h, GW_ERR_CUDA, "capture: diag");
-                if (!body && gw::launch_symmetrize((double2 *)chi + L.coff[i], L.ng[i], nw, h->st) != cudaSuccess)
-                    body = fail(h, GW_ERR_CUDA, "capture: symmetrize");
-            }
-            ce = cudaStreamEndCapture(h->st, &graph);
-        }
-        h->st = user;
-        h->timing = saved_timing;
-        if (body) {
-            if (graph) cudaGraphDestroy(graph);
-            dfree(h, ng.jobs, ng.jobs_bytes);
-            return body;
-        }
-        if (ce != cudaSuccess) {
-            dfree(h, ng.jobs, ng.jobs_bytes);
-            return cuda_fail(h, ce, "stream capture");
-        }
-        ce = cudaGraphInstantiate(&ng.exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) {
-            dfree(h, ng.jobs, ng.jobs_bytes);
-            return cuda_fail(h, ce, "graph instantiate");
-        }
-        h->graphs.push_back(ng);
-        g = &h->graphs.back();
-    }
-    Scope sc(h, "batch_graph");
-    CK(h, cudaGraphLaunch(g->exec, h->st), "graph launch");
-    return GW_OK;
-}
-
-} // namespace
-
+using namespace gwapi;
 // =================================================================== C ABI
 extern "C" {
 
@@ -1452,120 +962,6 @@ gw_status gw_chi0_contract(gw_chi0 *h, int nv, int nc, const double *ev, const d
     return GW_OK;
 }
 
-gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, double *L, double *dE_v, double *dE_c,
-                          double *dcoeff_v, double *dcoeff_c)
-{
-    if (!h) return GW_ERR_ARG;
-    gw_status s = check_slot(h, iq);
-    if (s) return s;
-    if (!W || !dE_v || !dE_c || !dcoeff_v || !dcoeff_c) return fail(h, GW_ERR_ARG, "null pointer");
-    if (!(omega >= 0.0) || !std::isfinite(omega)) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
-    const BandSet &v = h->val[iq];
-    const BandSet &c = h->cond;
-    const Sphere &sp = h->sph[iq];
-    const int nv = v.nb, nc = c.nb, ng = sp.ng;
-    const int64_t nr = h->nr;
-    const bool tf = h->d.mtxel_prec == GW_MTXEL_TWOFLOAT;
-    // valence bands per chunk: bounded by the pair chunk and by 2 GiB of back-projected grids
-    int64_t vch = std::max<int64_t>(1, h->d.pair_chunk / nc);
-    vch = std::min<int64_t>(vch, std::max<int64_t>(1, (int64_t(2) << 30) / ((int64_t)nc * nr * 16)));
-    vch = std::min<int64_t>(vch, nv);
-    const int64_t cmax = vch * nc;
-    // work buffers, held only for this call
-    double2 *Mb = nullptr, *Yb = nullptr, *Hb = nullptr, *pbv = nullptr, *pbc = nullptr;
-    double *Lacc = nullptr;
-    int *cs = nullptr, *cg = nullptr;
-    const int ncell = (int)sp.cstart.size() - 1;
-    size_t szM = sizeof(double2) * cmax * ng, szH = sizeof(double2) * cmax * nr;
-    size_t szV = sizeof(double2) * (size_t)nv * nr, szC = sizeof(double2) * (size_t)nc * nr;
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(h->st);
-        dfree(h, Mb, szM);
-        dfree(h, Yb, szM);
-        dfree(h, Hb, szH);
-        dfree(h, pbv, szV);
-        dfree(h, pbc, szC);
-        dfree(h, Lacc, sizeof(double));
-        dfree(h, cs, sizeof(int) * (ncell + 1));
-        dfree(h, cg, sizeof(int) * ng);
-    };
-#define ACK(x, what)                       \
-    do {                                   \
-        cudaError_t e_ = (x);              \
-        if (e_ != cudaSuccess) {           \
-            gw_status r_ = cuda_fail(h, e_, what); \
-            cleanup();                     \
-            return r_;                     \
-        }                                  \
-    } while (0)
-    if ((s = dalloc(h, (void **)&Mb, szM, "adjoint M")) || (s = dalloc(h, (void **)&Yb, szM, "adjoint Y")) ||
-        (s = dalloc(h, (void **)&Hb, szH, "adjoint grids")) || (s = dalloc(h, (void **)&pbv, szV, "valence adjoint")) ||
-        (s = dalloc(h, (void **)&pbc, szC, "conduction adjoint")) ||
-        (s = dalloc(h, (void **)&Lacc, sizeof(double), "L")) ||
-        (s = dalloc(h, (void **)&cs, sizeof(int) * (ncell + 1), "cells")) ||
-        (s = dalloc(h, (void **)&cg, sizeof(int) * ng, "cells"))) {
-        cleanup();
-        return s;
-    }
-    ACK(cudaMemcpyAsync(cs, sp.cstart.data(), sizeof(int) * (ncell + 1), cudaMemcpyHostToDevice, h->st), "cells");
-    ACK(cudaMemcpyAsync(cg, sp.cg.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, h->st), "cells");
-    ACK(cudaMemsetAsync(Lacc, 0, sizeof(double), h->st), "zero");
-    ACK(cudaMemsetAsync(dE_v, 0, sizeof(double) * nv, h->st), "zero");
-    ACK(cudaMemsetAsync(dE_c, 0, sizeof(double) * nc, h->st), "zero");
-    ACK(cudaMemsetAsync(pbv, 0, szV, h->st), "zero");
-    ACK(cudaMemsetAsync(pbc, 0, szC, h->st), "zero");
-    gw::PairPlan pp = pair_plan(h, sp);
-    // split precision: Y = M W as a split product, W's slices once per call
-    const bool split = h->d.prec == GW_PREC_OZAKI_BF16;
-    if (split && (s = oz_prepare_b(h, (const double2 *)W, ng, ng))) {
-        cleanup();
-        return s;
-    }
-    for (int v0 = 0; v0 < nv; v0 += (int)vch) {
-        const int nvc = (int)std::min<int64_t>(vch, nv - v0);
-        const int64_t p0 = (int64_t)v0 * nc, cnt = (int64_t)nvc * nc;
-        {
-            Scope sc(h, "pair_mtxel");
-            ACK(run_pair(h, v.psi, c.psi, nc, p0, cnt, pp, Mb), "pair kernel");
-        }
-        {
-            Scope sc(h, "adj_zgemm");
-            if (split) {
-                if ((s = oz_product(h, Mb, cnt, ng, ng, Yb))) {
-                    cleanup();
-                    return s;
-                }
-            } else {
-                ACK(gw::launch_zgemm(Mb, (const double2 *)W, Yb, cnt, ng, ng, h->st), "Y = M W");
-            }
-        }
-        {
-            Scope sc(h, "adj_rows");
-            ACK(gw::launch_adj_rows(Mb, Yb, cnt, ng, nc, p0, v.energy, c.energy, omega, Lacc, dE_v, dE_c, h->st),
-                "row reductions");
-        }
-        {
-            Scope sc(h, "adj_pair");
-            ACK(gw::launch_adj_pair(Yb, cnt, pp, cs, cg, ncell, Hb, h->st), "back-projection");
-        }
-        {
-            Scope sc(h, "adj_products");
-            ACK(gw::launch_adj_products(v.psi, c.psi, v0, nvc, nc, Hb, nr, tf, pbv, pbc, h->st), "products");
-        }
-    }
-    {
-        Scope sc(h, "adj_band");
-        ACK(gw::launch_band_adjoint(pbv, nv, h->d.n, h->ax, v.gofs, v.ngpsi, (double2 *)dcoeff_v, h->st),
-            "valence band adjoint");
-        ACK(gw::launch_band_adjoint(pbc, nc, h->d.n, h->ax, c.gofs, c.ngpsi, (double2 *)dcoeff_c, h->st),
-            "conduction band adjoint");
-    }
-    if (L) ACK(cudaMemcpyAsync(L, Lacc, sizeof(double), cudaMemcpyDeviceToHost, h->st), "L");
-#undef ACK
-    cleanup(); // synchronises: L is valid on return
-    return GW_OK;
-}
-
 gw_status gw_chi0_sync(gw_chi0 *h)
 {
     if (!h) return GW_ERR_ARG;
@@ -1616,333 +1012,4 @@ int gw_chi0_timing(gw_chi0 *h, int n, char (*names)[32], double *ms, int64_t *la
 size_t gw_chi0_device_bytes(const gw_chi0 *h) { return h ? h->bytes : 0; }
 
 } // extern "C"
-
-// ------------------------------------------------------------------ static subspace
-namespace {
-gw_status load_solver(gw_chi0 *h)
-{
-    if (h->sol.hdl) return GW_OK;
-    const char *names[] = {"libcusolver.so.12", "libcusolver.so.11", "libcusolver.so",
-                           "/usr/local/cuda/lib64/libcusolver.so.12", "/usr/local/cuda/lib64/libcusolver.so"};
-    for (const char *n : names)
-        if ((h->sol.lib = dlopen(n, RTLD_NOW | RTLD_LOCAL))) break;
-    if (!h->sol.lib) return fail(h, GW_ERR_UNSUPPORTED, "the dense eigensolver (libcusolver) was not found");
-    h->sol.create = (decltype(h->sol.create))dlsym(h->sol.lib, "cusolverDnCreate");
-    h->sol.destroy = (decltype(h->sol.destroy))dlsym(h->sol.lib, "cusolverDnDestroy");
-    h->sol.set_stream = (decltype(h->sol.set_stream))dlsym(h->sol.lib, "cusolverDnSetStream");
-    h->sol.buffer_size = (decltype(h->sol.buffer_size))dlsym(h->sol.lib, "cusolverDnZheevdx_bufferSize");
-    h->sol.heevdx = (decltype(h->sol.heevdx))dlsym(h->sol.lib, "cusolverDnZheevdx");
-    if (!h->sol.create || !h->sol.destroy || !h->sol.set_stream || !h->sol.buffer_size || !h->sol.heevdx)
-        return fail(h, GW_ERR_UNSUPPORTED, "libcusolver lacks the Hermitian eigensolver entry points");
-    if (h->sol.create(&h->sol.hdl) != CUSOLVER_STATUS_SUCCESS) {
-        h->sol.hdl = nullptr;
-        return fail(h, GW_ERR_CUDA, "cusolverDnCreate failed");
-    }
-    return GW_OK;
-}
-} // namespace
-
-gw_status gw_chi0_subspace_basis(gw_chi0 *h, int ng, const double *chi0, int neig, double *basis, double *evals)
-{
-    if (!h) return GW_ERR_ARG;
-    if (ng < 1 || neig < 1 || neig > ng) return fail(h, GW_ERR_ARG, "need 1 <= neig <= ng");
-    if (!chi0 || !basis) return fail(h, GW_ERR_ARG, "null pointer");
-    gw_status st = load_solver(h);
-    if (st) return st;
-    const size_t nn = (size_t)ng * ng;
-    if ((st = grow(h, (void **)&h->eigA, &h->eigA_cap, sizeof(double2) * nn, "eigensolver matrix")) ||
-        (st = grow(h, (void **)&h->eigW, &h->eigW_cap, sizeof(double) * (size_t)ng, "eigenvalues")) ||
-        (st = grow(h, (void **)&h->eigInfo, &h->eigInfo_cap, sizeof(int), "eigensolver status")))
-        return st;
-    // The row-major Hermitian chi0 read column-major is its transpose, conj(chi0): the solver
-    // returns the conjugated eigenvectors, which the transposing copy conjugates back.
-    CK(h, cudaMemcpyAsync(h->eigA, chi0, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, h->st), "copy chi0");
-    if (h->sol.set_stream(h->sol.hdl, h->st) != CUSOLVER_STATUS_SUCCESS) return fail(h, GW_ERR_CUDA, "solver stream");
-    int meig = 0, lwork = 0;
-    if (h->sol.buffer_size(h->sol.hdl, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, ng,
-                           (const cuDoubleComplex *)h->eigA, ng, 0.0, 0.0, 1, neig, &meig, h->eigW,
-                           &lwork) != CUSOLVER_STATUS_SUCCESS)
-        return fail(h, GW_ERR_CUDA, "eigensolver workspace query failed");
-    if ((st = grow(h, (void **)&h->eigWork, &h->eigWork_cap, sizeof(double2) * (size_t)std::max(lwork, 1),
-                   "eigensolver workspace")))
-        return st;
-    {
-        Scope sc(h, "subspace_eig");
-        if (h->sol.heevdx(h->sol.hdl, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, ng,
-                          (cuDoubleComplex *)h->eigA, ng, 0.0, 0.0, 1, neig, &meig, h->eigW,
-                          (cuDoubleComplex *)h->eigWork, lwork, h->eigInfo) != CUSOLVER_STATUS_SUCCESS)
-            return fail(h, GW_ERR_CUDA, "eigensolver failed");
-        CK(h, gw::launch_conj_transpose(h->eigA, ng, neig, (double2 *)basis, h->st), "basis");
-    }
-    if (evals)
-        CK(h, cudaMemcpyAsync(evals, h->eigW, sizeof(double) * neig, cudaMemcpyDeviceToDevice, h->st), "eigenvalues");
-    int info = 0;
-    CK(h, cudaMemcpyAsync(&info, h->eigInfo, sizeof(int), cudaMemcpyDeviceToHost, h->st), "solver status");
-    CK(h, cudaStreamSynchronize(h->st), "subspace basis sync");
-    if (info != 0) return fail(h, GW_ERR_CUDA, "eigensolver reported %d", info);
-    if (meig != neig) return fail(h, GW_ERR_CUDA, "eigensolver returned %d of %d vectors", meig, neig);
-    return GW_OK;
-}
-
-gw_status gw_chi0_compute_subspace(gw_chi0 *h, int iq, int neig, const double *basis, int nw, const double *omega,
-                                   double *chi_sub)
-{
-    if (!h) return GW_ERR_ARG;
-    if (nw < 1 || nw > gw::kMaxOmega || !omega || !basis || !chi_sub)
-        return fail(h, GW_ERR_ARG, "bad arguments (1 <= nw <= %d, non-null pointers)", gw::kMaxOmega);
-    gw::OmegaList om;
-    om.nw = nw;
-    for (int i = 0; i < nw; ++i) {
-        if (!(omega[i] >= 0.0) || !std::isfinite(omega[i])) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
-        om.w[i] = omega[i];
-    }
-    gw_status s = check_slot(h, iq);
-    if (s) return s;
-    const Sphere &sp = h->sph[iq];
-    const BandSet &v = h->val[iq];
-    const int ng = sp.ng;
-    if (neig < 1 || neig > ng) return fail(h, GW_ERR_ARG, "need 1 <= neig <= ng");
-    const int64_t P = (int64_t)v.nb * h->cond.nb;
-    const int64_t chunk = std::min<int64_t>(h->d.pair_chunk, P);
-    CK(h, cudaMemsetAsync(chi_sub, 0, sizeof(double2) * (size_t)nw * neig * neig, h->st), "zero chi");
-    if ((s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw)) ||
-        (s = grow(h, (void **)&h->MBbuf, &h->MBcap, sizeof(double2) * (size_t)chunk * neig, "projected M")))
-        return s;
-    const bool split = h->d.prec == GW_PREC_OZAKI_BF16;
-    if (split && (s = oz_prepare_b(h, (const double2 *)basis, ng, neig))) return s;
-    gw::PairPlan pp = pair_plan(h, sp);
-    for (int64_t p0 = 0; p0 < P; p0 += chunk) {
-        const int64_t cnt = std::min(chunk, P - p0);
-        {
-            Scope sc(h, "pair_mtxel");
-            CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
-        }
-        {
-            Scope sc(h, "subspace_projection");
-            if (split) {
-                if ((s = oz_product(h, h->Mbuf, cnt, ng, neig, h->MBbuf))) return s;
-            } else {
-                CK(h, gw::launch_zgemm(h->Mbuf, (const double2 *)basis, h->MBbuf, cnt, ng, neig, h->st), "projection");
-            }
-        }
-        {
-            Scope sc(h, "delta");
-            CK(h, gw::launch_delta(v.energy, h->cond.energy, h->cond.nb, p0, cnt, om, h->dbuf, h->st), "delta");
-        }
-        if ((s = contract_chunk(h, h->MBbuf, cnt, neig, h->dbuf, cnt, nw, (double2 *)chi_sub))) return s;
-    }
-    Scope sc(h, "symmetrize");
-    CK(h, gw::launch_symmetrize((double2 *)chi_sub, neig, nw, h->st), "symmetrize");
-    return GW_OK;
-}
-
-// ------------------------------------------------------------------ dielectric matrix inverse
-// Dense product C = A B of two [n][n] complex matrices in the handle's precision mode.
-static gw_status square_product(gw_chi0 *h, const double2 *A, const double2 *B, int n, double2 *C)
-{
-    if (h->d.prec == GW_PREC_OZAKI_BF16) {
-        gw_status st = oz_prepare_b(h, B, n, n);
-        if (st) return st;
-        return oz_product(h, A, n, n, n, C);
-    }
-    CK(h, gw::launch_zgemm(A, B, C, n, n, n, h->st), "product");
-    return GW_OK;
-}
-
-gw_status gw_chi0_epsilon_inverse(gw_chi0 *h, int ng, int nw, const double *chi, const double *vcoul,
-                                  double *epsinv)
-{
-    if (!h) return GW_ERR_ARG;
-    if (ng < 1 || nw < 1 || !chi || !vcoul || !epsinv) return fail(h, GW_ERR_ARG, "bad arguments");
-    {
-        std::vector<double> v(ng);
-        CK(h, cudaMemcpyAsync(v.data(), vcoul, sizeof(double) * ng, cudaMemcpyDeviceToHost, h->st), "read v");
-        CK(h, cudaStreamSynchronize(h->st), "read v");
-        for (int i = 0; i < ng; ++i)
-            if (!(v[i] > 0.0) || !std::isfinite(v[i])) return fail(h, GW_ERR_ARG, "v[%d] must be finite and > 0", i);
-    }
-    const size_t nn = (size_t)ng * ng;
-    gw_status st = grow(h, &h->epsbuf, &h->epscap, sizeof(double2) * 4 * nn + sizeof(double) * ng + 64,
-                        "dielectric work");
-    if (st) return st;
-    double2 *A = (double2 *)h->epsbuf, *X = A + nn, *T = X + nn, *Pm = T + nn;
-    double *sv = (double *)(Pm + nn);
-    unsigned long long *bmax = (unsigned long long *)(((uintptr_t)(sv + ng) + 15) & ~(uintptr_t)15);
-    CK(h, gw::launch_eps_sqrt(vcoul, ng, sv, h->st), "sqrt v");
-    for (int w = 0; w < nw; ++w) {
-        Scope sc(h, "epsilon_inverse");
-        CK(h, gw::launch_eps_sym((const double2 *)chi + (int64_t)w * nn, sv, ng, A, bmax, h->st), "I - s chi s");
-        unsigned long long bits = 0;
-        CK(h, cudaMemcpyAsync(&bits, bmax, sizeof bits, cudaMemcpyDeviceToHost, h->st), "bound");
-        CK(h, cudaStreamSynchronize(h->st), "bound");
-        double b;
-        std::memcpy(&b, &bits, sizeof b);
-        if (!(b >= 1.0) || !std::isfinite(b)) return fail(h, GW_ERR_ARG, "I - v chi is not positive (bound %g)", b);
-        // steps for (b - 1)/(b + 1) squared repeatedly to reach 1e-17, plus one for rounding
-        const double r = (b - 1.0) / (b + 1.0);
-        int steps = 1;
-        if (r > 0.0) steps = (int)std::ceil(std::log2(std::log(1e-17) / std::log(r))) + 1;
-        steps = std::max(steps, 1);
-        CK(h, gw::launch_eps_init(X, ng, bmax, h->st), "X0");
-        for (int k = 0; k < steps; ++k) {
-            if ((st = square_product(h, A, X, ng, T)) || (st = square_product(h, X, T, ng, Pm))) return st;
-            CK(h, gw::launch_eps_step(X, Pm, (int64_t)nn, h->st), "Newton-Schulz step");
-        }
-        CK(h, gw::launch_eps_unsym(X, sv, ng, (double2 *)epsinv + (int64_t)w * nn, h->st), "s X s^-1");
-    }
-    return GW_OK;
-}
-
-// ------------------------------------------------------------------ real frequencies
-gw_status gw_chi0_compute_real(gw_chi0 *h, int iq, int nw, const double *omega, double eta, double *chi)
-{
-    if (!h) return GW_ERR_ARG;
-    if (nw < 1 || 3 * nw > gw::kMaxOmega || !omega || !chi)
-        return fail(h, GW_ERR_ARG, "bad arguments (1 <= nw <= %d, non-null pointers)", gw::kMaxOmega / 3);
-    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(h, GW_ERR_ARG, "eta must be finite and > 0");
-    gw::OmegaList om;
-    om.nw = nw;
-    for (int i = 0; i < nw; ++i) {
-        if (!(omega[i] >= 0.0) || !std::isfinite(omega[i])) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
-        om.w[i] = omega[i];
-    }
-    gw_status s = check_slot(h, iq);
-    if (s) return s;
-    const Sphere &sp = h->sph[iq];
-    const BandSet &v = h->val[iq];
-    const int ng = sp.ng;
-    const int64_t nn = (int64_t)ng * ng;
-    const int64_t P = (int64_t)v.nb * h->cond.nb;
-    const int64_t chunk = std::min<int64_t>(h->d.pair_chunk, P);
-    if ((s = grow(h, (void **)&h->realbuf, &h->realcap, sizeof(double2) * 3 * nw * nn, "real-axis parts")) ||
-        (s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * 3 * nw)))
-        return s;
-    CK(h, cudaMemsetAsync(h->realbuf, 0, sizeof(double2) * 3 * nw * nn, h->st), "zero parts");
-    gw::PairPlan pp = pair_plan(h, sp);
-    for (int64_t p0 = 0; p0 < P; p0 += chunk) {
-        const int64_t cnt = std::min(chunk, P - p0);
-        {
-            Scope sc(h, "pair_mtxel");
-            CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
-        }
-        {
-            Scope sc(h, "delta");
-            CK(h, gw::launch_delta_real(v.energy, h->cond.energy, h->cond.nb, p0, cnt, om, eta, h->dbuf, h->st),
-               "real-axis delta");
-        }
-        if ((s = contract_chunk(h, h->Mbuf, cnt, ng, h->dbuf, cnt, 3 * nw, h->realbuf))) return s;
-    }
-    Scope sc(h, "symmetrize");
-    CK(h, gw::launch_symmetrize(h->realbuf, ng, 3 * nw, h->st), "symmetrize");
-    CK(h, gw::launch_combine_real(h->realbuf, nn, nw, (double2 *)chi, h->st), "combine");
-    return GW_OK;
-}
-
-// ------------------------------------------------------------------ forward derivative (JVP)
-// Real-space grids of caller coefficients on a stored band set's plane waves (the band
-// setup of gw_chi0_set_bands, into psi).
-static gw_status band_grids(gw_chi0 *h, const BandSet &b, const double *coeff, void *psi)
-{
-    CK(h, cudaMemsetAsync(psi, 0, sizeof(double2) * (size_t)b.nb * h->nr, h->st), "zero grids");
-    if (h->d.mtxel_prec == GW_MTXEL_TWOFLOAT) {
-        Scope sc(h, "band_setup_tf");
-        CK(h, gw::launch_band_setup_tf((const double2 *)coeff, b.gofs, b.nb, b.ngpsi, psi, h->d.n, h->ax, b.maxabs,
-                                       h->st),
-           "tangent band setup (two-float)");
-    } else {
-        CK(h, gw::launch_scatter((const double2 *)coeff, b.gofs, b.nb, b.ngpsi, h->nr, (double2 *)psi, h->st),
-           "tangent scatter");
-        CK(h, gw::launch_band_fft((double2 *)psi, b.nb, h->d.n, h->ax, h->st), "tangent band fft");
-    }
-    return GW_OK;
-}
-
-gw_status gw_chi0_jvp(gw_chi0 *h, int iq, int nw, const double *omega, const double *dcoeff_v,
-                      const double *dcoeff_c, const double *dE_v, const double *dE_c, double *dchi)
-{
-    if (!h) return GW_ERR_ARG;
-    if (nw < 1 || 2 * nw > gw::kMaxOmega || !omega || !dcoeff_v || !dcoeff_c || !dE_v || !dE_c || !dchi)
-        return fail(h, GW_ERR_ARG, "bad arguments (1 <= nw <= %d, non-null pointers)", gw::kMaxOmega / 2);
-    gw::OmegaList om;
-    om.nw = nw;
-    for (int i = 0; i < nw; ++i) {
-        if (!(omega[i] >= 0.0) || !std::isfinite(omega[i])) return fail(h, GW_ERR_ARG, "omega must be finite and >= 0");
-        om.w[i] = omega[i];
-    }
-    gw_status s = check_slot(h, iq);
-    if (s) return s;
-    const BandSet &v = h->val[iq];
-    const BandSet &c = h->cond;
-    const Sphere &sp = h->sph[iq];
-    const int ng = sp.ng, nc = c.nb;
-    const int64_t nn = (int64_t)ng * ng;
-    const int64_t P = (int64_t)v.nb * nc;
-    const int64_t chunk = std::min<int64_t>(h->d.pair_chunk, P);
-    // work held only for this call
-    void *gv = nullptr, *gc = nullptr;
-    double2 *X1 = nullptr, *X2 = nullptr, *T = nullptr;
-    double *wb = nullptr;
-    const size_t szv = sizeof(double2) * (size_t)v.nb * h->nr, szc = sizeof(double2) * (size_t)nc * h->nr;
-    const size_t szx = sizeof(double2) * (size_t)chunk * ng, szt = sizeof(double2) * 4 * nw * nn;
-    const size_t szw = sizeof(double) * 2 * nw * (size_t)chunk;
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(h->st);
-        dfree(h, gv, szv);
-        dfree(h, gc, szc);
-        dfree(h, X1, szx);
-        dfree(h, X2, szx);
-        dfree(h, T, szt);
-        dfree(h, wb, szw);
-    };
-    if ((s = dalloc(h, &gv, szv, "tangent valence grids")) || (s = dalloc(h, &gc, szc, "tangent conduction grids")) ||
-        (s = dalloc(h, (void **)&X1, szx, "tangent pairs")) || (s = dalloc(h, (void **)&X2, szx, "tangent pairs")) ||
-        (s = dalloc(h, (void **)&T, szt, "tangent parts")) || (s = dalloc(h, (void **)&wb, szw, "tangent weights")) ||
-        (s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * 2 * nw)) || (s = band_grids(h, v, dcoeff_v, gv)) ||
-        (s = band_grids(h, c, dcoeff_c, gc))) {
-        cleanup();
-        return s;
-    }
-#define JCK(x, what)                            \
-    do {                                        \
-        cudaError_t e_ = (x);                   \
-        if (e_ != cudaSuccess) {                \
-            gw_status r_ = cuda_fail(h, e_, what); \
-            cleanup();                          \
-            return r_;                          \
-        }                                       \
-    } while (0)
-    JCK(cudaMemsetAsync(T, 0, szt, h->st), "zero parts");
-    double2 *Tp = T, *Tm = T + (int64_t)nw * nn, *Tw = T + 2 * (int64_t)nw * nn;
-    gw::PairPlan pp = pair_plan(h, sp);
-    for (int64_t p0 = 0; p0 < P; p0 += chunk) {
-        const int64_t cnt = std::min(chunk, P - p0);
-        {
-            Scope sc(h, "pair_mtxel");
-            JCK(run_pair(h, v.psi, c.psi, nc, p0, cnt, pp, h->Mbuf), "pair kernel");
-            JCK(run_pair(h, gv, c.psi, nc, p0, cnt, pp, X1), "pair kernel (tangent valence)");
-            JCK(run_pair(h, v.psi, gc, nc, p0, cnt, pp, X2), "pair kernel (tangent conduction)");
-            JCK(gw::launch_jvp_mix(h->Mbuf, X1, X2, cnt * ng, h->st), "M +- dM");
-        }
-        {
-            Scope sc(h, "delta");
-            JCK(gw::launch_delta(v.energy, c.energy, nc, p0, cnt, om, h->dbuf, h->st), "delta");
-            JCK(gw::launch_delta_jvp(v.energy, c.energy, dE_v, dE_c, nc, p0, cnt, om, wb, h->st), "delta derivative");
-        }
-        // d chi = [chi(M + dM) - chi(M - dM)] / 2 + sum_p conj(M) dDelta M
-        if ((s = contract_chunk(h, X1, cnt, ng, h->dbuf, cnt, nw, Tp)) ||
-            (s = contract_chunk(h, X2, cnt, ng, h->dbuf, cnt, nw, Tm)) ||
-            (s = contract_chunk(h, h->Mbuf, cnt, ng, wb, cnt, 2 * nw, Tw))) {
-            cleanup();
-            return s;
-        }
-    }
-    {
-        Scope sc(h, "symmetrize");
-        JCK(gw::launch_symmetrize(T, ng, 4 * nw, h->st), "symmetrize");
-        JCK(gw::launch_combine_jvp(Tp, Tm, Tw, nn, nw, (double2 *)dchi, h->st), "combine");
-    }
-#undef JCK
-    cleanup();
-    return GW_OK;
-}
 
