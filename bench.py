@@ -178,6 +178,8 @@ def reference_arm(args):
 TRAFFIC = {
     "contract_f64": {"bytes_per_launch": 1.941011e9 + 0.034306e9,
                      "source": "ncu dram__bytes_read+write, contract_f64_kernel, p1_48cube_onechunk"},
+    "pair_mtxel": {"bytes_per_launch": 3.112e9 + 1.486e9,
+                   "source": "ncu dram__bytes_read+write, pair_kernel_tf_ct<48>, p1_48cube_onechunk"},
     "ozaki_gemm": {"bytes_per_launch": 7.32e9 + 0.219e9,
                    "source": "ncu dram__bytes_read+write, oz_gemm_kernel (s = 7), p1_48cube_onechunk"},
 }
