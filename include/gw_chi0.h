@@ -81,6 +81,10 @@ typedef struct {
     size_t mem_budget_bytes; /* cap on library-owned device memory; 0 = no cap */
     int device;              /* CUDA device ordinal; must be current on the calling thread */
     int mtxel_prec;          /* gw_mtxel_prec */
+    int single_stream;       /* 0: in split-precision streamed compute, the contraction of each chunk
+                                runs on a second, high-priority stream beside the pair elements of
+                                the next (tensor cores and FP32 pipes share the SMs); 1: every
+                                kernel on the handle's stream, one after the other */
 } gw_chi0_desc;
 
 /*

@@ -26,7 +26,7 @@ P, I, I64, D, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_doubl
 
 class Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("nq", I), ("prec", I), ("nslices", I), ("pair_chunk", I64),
-                ("mem_budget_bytes", SZ), ("device", I), ("mtxel_prec", I)]
+                ("mem_budget_bytes", SZ), ("device", I), ("mtxel_prec", I), ("single_stream", I)]
 
 
 SIGNATURES = {

@@ -38,7 +38,7 @@ class Chi0:
 
     def __init__(self, grid: Sequence[int], nq: int = 1, prec: str = "fp64", nslices: int = 6,
                  pair_chunk: int = 8192, mem_budget_bytes: int = 0, device: int | None = None,
-                 mtxel: str = "fp64"):
+                 mtxel: str = "fp64", single_stream: bool = False):
         self.lib = _lib.load()
         dev = torch.cuda.current_device() if device is None else device
         d = _lib.Desc()
@@ -47,6 +47,7 @@ class Chi0:
         d.nq, d.prec, d.nslices = int(nq), PREC[prec], int(nslices)
         d.pair_chunk, d.mem_budget_bytes, d.device = int(pair_chunk), int(mem_budget_bytes), int(dev)
         d.mtxel_prec = MTXEL[mtxel]
+        d.single_stream = 1 if single_stream else 0
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             st = self.lib.gw_chi0_create(ctypes.byref(h), ctypes.byref(d), _stream_handle())

@@ -479,6 +479,93 @@ void free_sphere(gw_chi0 *h, Sphere &s)
     dfree(h, s.cpts, sizeof(int2) * s.ng);
     s = Sphere();
 }
+// Split-precision streamed compute with the contraction of job j (chunk, frequency) on a
+// high-priority second stream while the user stream forms the pair elements and slices of
+// the jobs after it.  The split-precision contraction runs on the tensor cores and the pair
+// kernel on the FP32 pipes, so the two share the SMs: the contraction uses a 2-deep TMA ring
+// (99 KB of shared memory) to fit beside two pair-kernel blocks.  Slices, exponents and job
+// tables alternate between two buffer sets; job j waits for the contraction of job j - 2.
+bool overlap_enabled(gw_chi0 *h) { return h->d.prec == GW_PREC_OZAKI_BF16 && !h->d.single_stream; }
+
+gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *cq, double *dq)
+{
+    const Sphere &sp = h->sph[iq];
+    const BandSet &v = h->val[iq];
+    const int ng = sp.ng, nw = om.nw, s = h->d.nslices;
+    const int64_t P = (int64_t)v.nb * h->cond.nb;
+    const int64_t chunk = std::min<int64_t>(h->d.pair_chunk, P);
+    const int64_t kpad_max = (chunk + 63) / 64 * 64;
+    gw_status st = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw);
+    if (st) return st;
+    if ((st = grow(h, (void **)&h->spbuf, &h->spcap, sizeof(double) * (size_t)nw * chunk, "scale buffer"))) return st;
+    for (int b = 0; b < 2; ++b)
+        if ((st = grow(h, &h->ovZ[b], &h->ovZcap[b], (size_t)s * 2 * ng * kpad_max * 2, "slice buffer")) ||
+            (st = grow(h, (void **)&h->ovE[b], &h->ovEcap[b], sizeof(int) * (size_t)ng, "exponent buffer")) ||
+            (st = grow(h, &h->ovJ[b], &h->ovJcap[b], sizeof(gw::OzJob) * 256, "job table")))
+            return st;
+    if (!h->ov_st) {
+        int lo = 0, hi = 0;
+        CK(h, cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+        CK(h, cudaStreamCreateWithPriority(&h->ov_st, cudaStreamNonBlocking, hi), "contraction stream");
+        for (int b = 0; b < 2; ++b) {
+            CK(h, cudaEventCreateWithFlags(&h->ov_split[b], cudaEventDisableTiming), "event");
+            CK(h, cudaEventCreateWithFlags(&h->ov_gemm[b], cudaEventDisableTiming), "event");
+        }
+    }
+    const int bn = h->tuned_bn;
+    gw::PairPlan pp = pair_plan(h, sp);
+    bool used[2] = {false, false};
+    int64_t j = 0;
+    for (int64_t p0 = 0; p0 < P; p0 += chunk) {
+        const int64_t cnt = std::min(chunk, P - p0);
+        const int64_t kpad = (cnt + 63) / 64 * 64;
+        {
+            Scope sc(h, "pair_mtxel");
+            CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
+        }
+        {
+            Scope sc(h, "delta");
+            CK(h, gw::launch_delta(v.energy, h->cond.energy, h->cond.nb, p0, cnt, om, h->dbuf, h->st), "delta");
+        }
+        {
+            Scope sc(h, "oz_split");
+            CK(h, gw::launch_oz_sqrt(h->dbuf, (int64_t)nw * cnt, h->spbuf, h->st), "oz sqrt");
+        }
+        if (dq) {
+            Scope sc(h, "diag");
+            CK(h, gw::launch_diag(h->Mbuf, cnt, ng, h->dbuf, cnt, nw, dq, ng, h->st), "diag");
+        }
+        for (int w = 0; w < nw; ++w, ++j) {
+            const int b = (int)(j & 1);
+            if (used[b]) CK(h, cudaStreamWaitEvent(h->st, h->ov_gemm[b], 0), "wait contraction");
+            {
+                Scope sc(h, "oz_split");
+                const double *spw = h->spbuf + (int64_t)w * cnt;
+                CK(h, gw::launch_oz_colexp(h->Mbuf, cnt, ng, spw, h->ovE[b], h->st), "oz exponents");
+                CK(h, gw::launch_oz_slice(h->Mbuf, cnt, ng, spw, h->ovE[b], s, kpad, h->ovZ[b], h->st), "oz slices");
+            }
+            std::vector<gw::OzJob> jobs(1);
+            if ((st = oz_job(h, jobs[0], h->ovZ[b], kpad, ng, h->ovE[b], cq + (int64_t)w * ng * ng, bn))) return st;
+            const int nitems = oz_schedule(jobs);
+            CK(h, cudaMemcpyAsync(h->ovJ[b], jobs.data(), sizeof(gw::OzJob) * jobs.size(), cudaMemcpyHostToDevice,
+                                  h->st),
+               "job table");
+            CK(h, cudaEventRecord(h->ov_split[b], h->st), "record");
+            CK(h, cudaStreamWaitEvent(h->ov_st, h->ov_split[b], 0), "wait slices");
+            {
+                Scope sc(h, "ozaki_gemm", h->ov_st);
+                CK(h, gw::launch_oz_gemm_jobs(bn, (const gw::OzJob *)h->ovJ[b], (int)jobs.size(), nitems,
+                                              std::max(1, std::min(nitems, num_sms())), h->status, h->ov_st, 2),
+                   "oz gemm");
+            }
+            CK(h, cudaEventRecord(h->ov_gemm[b], h->ov_st), "record");
+            used[b] = true;
+        }
+    }
+    for (int b = 0; b < 2; ++b)
+        if (used[b]) CK(h, cudaStreamWaitEvent(h->st, h->ov_gemm[b], 0), "join");
+    return GW_OK;
+}
 } // namespace gwapi
 
 using namespace gwapi;
@@ -498,6 +585,7 @@ gw_status gw_chi0_create(gw_chi0 **out, const gw_chi0_desc *d, void *stream)
     if (h->d.prec != GW_PREC_FP64 && h->d.prec != GW_PREC_OZAKI_BF16) { delete h; return GW_ERR_ARG; }
     if (h->d.prec == GW_PREC_OZAKI_BF16 && (h->d.nslices < 3 || h->d.nslices > 8)) { delete h; return GW_ERR_ARG; }
     if (h->d.mtxel_prec != GW_MTXEL_FP64 && h->d.mtxel_prec != GW_MTXEL_TWOFLOAT) { delete h; return GW_ERR_ARG; }
+    if (h->d.single_stream != 0 && h->d.single_stream != 1) { delete h; return GW_ERR_ARG; }
     for (int a = 0; a < 3; ++a) {
         int n = h->d.n[a];
         if (n < 4 || n > 128 || !factor(n, h->ax[a])) { delete h; return GW_ERR_ARG; }
@@ -577,6 +665,14 @@ void gw_chi0_destroy(gw_chi0 *h)
     dfree(h, h->EBbuf, h->EBcap);
     dfree(h, h->ZBbuf, h->ZBcap);
     dfree(h, h->MBbuf, h->MBcap);
+    for (int b = 0; b < 2; ++b) {
+        dfree(h, h->ovZ[b], h->ovZcap[b]);
+        dfree(h, h->ovE[b], h->ovEcap[b]);
+        dfree(h, h->ovJ[b], h->ovJcap[b]);
+        if (h->ov_split[b]) cudaEventDestroy(h->ov_split[b]);
+        if (h->ov_gemm[b]) cudaEventDestroy(h->ov_gemm[b]);
+    }
+    if (h->ov_st) cudaStreamDestroy(h->ov_st);
     dfree(h, h->epsbuf, h->epscap);
     dfree(h, h->realbuf, h->realcap);
     dfree(h, h->eigA, h->eigA_cap);
@@ -861,6 +957,15 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
         double *dq = diag ? diag + doff : nullptr;
         CK(h, cudaMemsetAsync(cq, 0, sizeof(double2) * (size_t)nw * ng * ng, h->st), "zero chi");
         if (dq) CK(h, cudaMemsetAsync(dq, 0, sizeof(double) * (size_t)nw * ng, h->st), "zero diag");
+        if (overlap_enabled(h) && fault_chunk() < 0) {
+            gw_status s = compute_overlap(h, iq[i], om, cq, dq);
+            if (s) return s;
+            Scope sc(h, "symmetrize");
+            CK(h, gw::launch_symmetrize(cq, ng, nw, h->st), "symmetrize");
+            off += (size_t)nw * ng * ng;
+            doff += (size_t)nw * ng;
+            continue;
+        }
         gw_status s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw);
         if (s) return s;
         gw::PairPlan pp = pair_plan(h, sp);

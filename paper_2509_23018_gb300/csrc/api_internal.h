@@ -100,6 +100,15 @@ struct gw_chi0 {
     int *Eall = nullptr;
     size_t Eall_cap = 0;
     cudaStream_t cap_st = nullptr;
+    // overlapped streamed path: contractions on a high-priority second stream, buffers by parity
+    cudaStream_t ov_st = nullptr;
+    cudaEvent_t ov_split[2] = {nullptr, nullptr}, ov_gemm[2] = {nullptr, nullptr};
+    void *ovZ[2] = {nullptr, nullptr};
+    size_t ovZcap[2] = {0, 0};
+    int *ovE[2] = {nullptr, nullptr};
+    size_t ovEcap[2] = {0, 0};
+    void *ovJ[2] = {nullptr, nullptr};
+    size_t ovJcap[2] = {0, 0};
     struct Graph {
         std::string key;
         cudaGraphExec_t exec = nullptr;
@@ -161,19 +170,20 @@ cudaEvent_t ev_get(gw_chi0 *h);
 struct Scope {
     gw_chi0 *h;
     const char *name;
+    cudaStream_t s;
     cudaEvent_t a = nullptr;
-    Scope(gw_chi0 *h_, const char *n) : h(h_), name(n)
+    Scope(gw_chi0 *h_, const char *n, cudaStream_t s_ = nullptr) : h(h_), name(n), s(s_ ? s_ : h_->st)
     {
         if (h->timing) {
             a = ev_get(h);
-            cudaEventRecord(a, h->st);
+            cudaEventRecord(a, s);
         }
     }
     ~Scope()
     {
         if (h->timing) {
             cudaEvent_t b = ev_get(h);
-            cudaEventRecord(b, h->st);
+            cudaEventRecord(b, s);
             h->pending.push_back({name, a, b});
         }
     }
@@ -214,6 +224,10 @@ cudaError_t run_pair(gw_chi0 *h, const void *psiv, const void *psic, int nc, int
 gw::PairPlan pair_plan(gw_chi0 *h, const Sphere &s);
 void free_bands(gw_chi0 *h, BandSet &b);
 void free_sphere(gw_chi0 *h, Sphere &s);
+
+// overlapped split-precision streamed compute of one slot (api.cu)
+gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *cq, double *dq);
+bool overlap_enabled(gw_chi0 *h);
 
 // batched path (api_batch.cu)
 gw_status compute_batch(gw_chi0 *h, int nq, const int *iq, int nw, const double *omega, const gw::OmegaList &om,

@@ -125,8 +125,9 @@ struct __align__(128) OzJob {
     int64_t ldo;
     int rows_a, rows_b;
 };
+// stages: TMA ring depth, 4 (default) or 2 (room on the SM for pair-kernel blocks alongside)
 cudaError_t launch_oz_gemm_jobs(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
-                                cudaStream_t st);
+                                cudaStream_t st, int stages = 4);
 int oz_tiles(int ng, int bn);
 // General split product: Y[rows][nout] (complex, row-major, overwritten) = A[rows][ka] B[ka][nout]
 // (complex, row-major), A split by rows and B by columns into s six-bit BF16 slices.

@@ -223,8 +223,9 @@ __global__ void __launch_bounds__(256) oz_split_cols_kernel(const double2 *__res
 // beyond the mbarriers.  The tile width BN (128 or 256 real columns) is chosen by the
 // autotuner; two BN-column FP32 accumulators in TMEM alternate between slice groups so the
 // epilogue of group t overlaps the MMAs of group t+1.
-template <int BN>
+template <int BN, int ST = kOzStages>
 struct OzCfg {
+    static constexpr int Stages = ST;                        // TMA ring depth
     static constexpr int BM = kOzBM;
     static constexpr int BNC = BN / 2;                       // complex columns per tile
     static constexpr unsigned ABytes = kOzBM * kOzBK * 2, BBytes = BN * kOzBK * 2;
@@ -232,7 +233,7 @@ struct OzCfg {
     // idesc: D = F32, A = B = BF16, both K-major, N = BN, M = 128
     static constexpr uint32_t Idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(kOzBM >> 4) << 24);
-    static constexpr size_t Smem = 1024 + kOzStages * (size_t)(ABytes + BBytes) + (2 * kOzStages + 5) * 8 + 16;
+    static constexpr size_t Smem = 1024 + ST * (size_t)(ABytes + BBytes) + (2 * ST + 5) * 8 + 16;
 };
 
 // tile -> (I, J): J-major, rows I = 0 .. min((BNC (J+1) - 1)/64 + 1, nI) - 1
@@ -275,25 +276,26 @@ __device__ __forceinline__ int oz_find_job(const OzJob *jobs, int njobs, int ite
 
 // GEN = false: the Hermitian contraction above (upper tiles, chi epilogue).  GEN = true:
 // the general product out += A B (all tiles, each owned by one block, plain FP64 adds).
-template <int BN, bool GEN>
+// ST: depth of the TMA ring (2 leaves shared memory for other kernels' blocks on the SM).
+template <int BN, bool GEN, int ST = kOzStages>
 __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__restrict__ jobs, int njobs, int nitems,
                                                                int *status)
 {
-    using C = OzCfg<BN>;
+    using C = OzCfg<BN, ST>;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = sm;                                  // [stages][ABytes]
-    unsigned char *sB = sA + kOzStages * C::ABytes;          // [stages][BBytes]
-    uint64_t *full = (uint64_t *)(sB + kOzStages * C::BBytes);
-    uint64_t *empty = full + kOzStages;
-    uint64_t *tfull = empty + kOzStages;
+    unsigned char *sB = sA + ST * C::ABytes;          // [stages][BBytes]
+    uint64_t *full = (uint64_t *)(sB + ST * C::BBytes);
+    uint64_t *empty = full + ST;
+    uint64_t *tfull = empty + ST;
     uint64_t *tempty = tfull + 2;
     uint64_t *fin = tempty + 2;
     uint32_t *tslot = (uint32_t *)(fin + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kOzStages; ++i) {
+        for (int i = 0; i < ST; ++i) {
             bar_init(&full[i], 1);
             bar_init(&empty[i], 1);
         }
@@ -321,8 +323,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                 for (int t = 2; t <= jb.s + 1 && ok; ++t)
                     for (int i = 1; i < t && ok; ++i)
                         for (int kb = 0; kb < jb.nk; ++kb, ++it) {
-                            const int st = it % kOzStages;
-                            const uint32_t n = it / kOzStages;
+                            const int st = it % ST;
+                            const uint32_t n = it / ST;
                             if (!bar_wait(&empty[st], (n & 1) ^ 1)) { ok = false; break; }
                             bar_expect(&full[st], C::ABytes + C::BBytes);
                             tma3(sA + st * C::ABytes, &jb.tmA, &full[st], (jb.kb0 + kb) * kOzBK, I * kOzBM, i - 1);
@@ -344,8 +346,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                     bool first = true;
                     for (int i = 1; i < t && ok; ++i)
                         for (int kb = 0; kb < jb.nk; ++kb, ++it) {
-                            const int st = it % kOzStages;
-                            if (!bar_wait(&full[st], (it / kOzStages) & 1)) { ok = false; break; }
+                            const int st = it % ST;
+                            if (!bar_wait(&full[st], (it / ST) & 1)) { ok = false; break; }
                             tc_fence_after();
                             const uint32_t a0 = su32(sA + st * C::ABytes), b0 = su32(sB + st * C::BBytes);
 #pragma unroll
@@ -493,10 +495,23 @@ cudaError_t launch_oz_slice(const double2 *M, int64_t P, int ng, const double *s
     return cudaGetLastError();
 }
 
+template <int BN, int ST>
+static cudaError_t launch_oz_chi(const OzJob *jobs, int njobs, int nitems, int grid, int *status, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<BN, false, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)OzCfg<BN, ST>::Smem);
+    if (e != cudaSuccess) return e;
+    oz_gemm_kernel<BN, false, ST><<<grid, kOzThreads, OzCfg<BN, ST>::Smem, st>>>(jobs, njobs, nitems, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_oz_gemm_jobs(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
-                                cudaStream_t st)
+                                cudaStream_t st, int stages)
 {
     if (nitems == 0) return cudaSuccess;
+    if (stages == 2)
+        return bn == 128 ? launch_oz_chi<128, 2>(jobs, njobs, nitems, grid, status, st)
+                         : launch_oz_chi<256, 2>(jobs, njobs, nitems, grid, status, st);
     cudaError_t e;
     if (bn == 128) {
         e = cudaFuncSetAttribute(oz_gemm_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
