@@ -194,3 +194,49 @@ def coulomb(gchi, q=(0.0, 0.0, 0.0)) -> np.ndarray:
     k = np.asarray(gchi, np.float64) + np.asarray(q, np.float64)
     return 4.0 * np.pi / np.einsum("ij,ij->i", k, k)
 
+
+
+@dataclasses.dataclass
+class GppProblem:
+    """Inputs of the off-diagonal plasmon-pole self-energy: matrix elements between the summed
+    bands n and the self-energy bands l, band energies, plasmon-pole parameters, the Coulomb
+    diagonal and the energy grid."""
+    M: np.ndarray           # [nb, nsig, ng] complex128, M[n][l][G]
+    En: np.ndarray          # [nb] float64, eV
+    nocc: int               # bands n < nocc are occupied
+    omega2: np.ndarray      # [ng, ng] complex128, Omega^2_GG' (eV^2)
+    wtilde: np.ndarray      # [ng, ng] complex128, mode energies (eV)
+    vcoul: np.ndarray       # [ng] float64
+    E: np.ndarray           # [ne] float64, eV
+    gchi: np.ndarray        # [ng, 3] int32
+
+
+def make_gpp(nb: int, nocc: int, nsig: int, ng: int, ne: int, seed: int, wp: float = 16.6, eta: float = 0.25,
+             ewin=(-6.0, 6.0), q=(0.0, 0.0, 0.0)) -> GppProblem:
+    """Synthetic plasmon-pole inputs with the structure of the Hybertsen-Louie model:
+
+    * M: Re and Im i.i.d. N(0, 1/(2 ng)) (matrix elements of unit-norm band products);
+    * E_n: occupied uniform in [-10, -1] eV, empty uniform in [1, 30] eV (bands n < nocc occupied);
+    * Omega^2_GG' = wp^2 exp(-|G - G'|^2 / 8) e^{i(t_G - t_G')}: wp^2 on the diagonal (the
+      plasma frequency, 16.6 eV for silicon), decaying with |G - G'| like the charge density
+      rho(G - G') the model scales it by, Hermitian (t_G uniform phases);
+    * wtilde_GG' = wp (1 + (u_G + u_G') / 2) - i eta: mode energies between wp and 2 wp, symmetric,
+      with a damping eta so that no energy of the grid sits on a pole;
+    * v_G = 4 pi / |q + G|^2 on the sphere (G = 0 left out at q = 0);
+    * E: ne points spaced evenly over the window ``ewin`` (the energy range of the self-energy
+      bands, where the full-matrix solution of Dyson's equation needs Sigma)."""
+    rng = np.random.default_rng(seed)
+    gchi = gsphere(ng, q=q, exclude_zero=not np.any(np.asarray(q) != 0))
+    scale = 1.0 / math.sqrt(2.0 * ng)
+    M = (rng.standard_normal((nb, nsig, ng)) + 1j * rng.standard_normal((nb, nsig, ng))) * scale
+    En = np.concatenate([rng.uniform(-10.0, -1.0, nocc), rng.uniform(1.0, 30.0, nb - nocc)])
+    g = gchi.astype(np.float64) + np.asarray(q, np.float64)
+    g2 = np.einsum("ij,ij->i", g, g)
+    d2 = g2[:, None] + g2[None, :] - 2.0 * (g @ g.T)
+    t = rng.uniform(0.0, 2.0 * math.pi, ng)
+    omega2 = (wp * wp) * np.exp(-d2 / 8.0) * np.exp(1j * (t[:, None] - t[None, :]))
+    u = rng.uniform(0.0, 1.0, ng)
+    wtilde = wp * (1.0 + 0.5 * (u[:, None] + u[None, :])) - 1j * eta
+    E = np.linspace(ewin[0], ewin[1], ne) if ne > 1 else np.full(ne, 0.5 * (ewin[0] + ewin[1]))
+    return GppProblem(np.ascontiguousarray(M), En, int(nocc), np.ascontiguousarray(omega2),
+                      np.ascontiguousarray(wtilde), coulomb(gchi, q), E, gchi)

@@ -24,12 +24,19 @@ paper, "Overview of the Problem"):
 * ``epsilon_inverse`` -- Eq. epsilon_mat, [I - v chi]^-1 by a dense inverse;
 * ``subspace_basis`` / ``chi0_subspace`` -- the static subspace approximation
   (Eq. chi_mat_sub and the paragraph around it): the N_Eig most significant
-  eigenvectors of chi(0) as C_s, M^B = M C_s, chi_BB' from M^B as in Eq. chi_mat.
+  eigenvectors of chi(0) as C_s, M^B = M C_s, chi_BB' from M^B as in Eq. chi_mat;
+* ``gpp_pole_matrix`` / ``sigma_gpp`` -- the full-matrix (off-diagonal) plasmon-pole
+  self-energy on an energy grid (section on the off-diagonal GPP kernel, Eq.
+  flop_count_fullmat): the prep. step P^n(E) and the two products per (n, E).  The
+  pole factor is the Hybertsen-Louie model the paper cites for the frequency dependence
+  (its working equation is in a figure the text lacks).
 
 All functions are pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle.py``
 (two independent routes to M, orthonormality, Parseval, gauge and translation
 covariance, Hermiticity / semidefiniteness / rank / trace of chi0, the
-large-frequency limit, finite differences of L).
+large-frequency limit, finite differences of L; for the self-energy a numerical
+frequency integral of G W, the screened-exchange + Coulomb-hole decomposition by
+brute force, Hermiticity and phase covariance).
 """
 from __future__ import annotations
 
@@ -230,3 +237,31 @@ def jvp(gpsi, cv, ev, cc, ec, gchi, dcv, dcc, dev, dec, omega: float) -> np.ndar
     ddl = (-2.0 / (x - 1j * omega) ** 2 - 2.0 / (x + 1j * omega) ** 2).real * dx
     return (dM.conj().T * dl) @ M + (M.conj().T * dl) @ dM + (M.conj().T * ddl) @ M
 
+
+
+def gpp_pole_matrix(omega2, wtilde, vcoul, d: float, occupied: bool) -> np.ndarray:
+    """P^n_GG'(E) of the prep. step for one band n at one energy, d = E - E_n: the correlation
+    part of the plasmon-pole self-energy (Hybertsen-Louie model, cited by the paper for the
+    frequency dependence).  With B_GG' = v_G' Omega2_GG' / (2 wt_GG'), the residue of the
+    screened interaction's pole, P = B / (d + wt) for an occupied band and B / (d - wt) for an
+    empty one."""
+    s = -1.0 if occupied else 1.0
+    wt = np.asarray(wtilde, np.complex128)
+    return np.asarray(vcoul, np.float64)[None, :] * np.asarray(omega2, np.complex128) / (2.0 * wt * (d - s * wt))
+
+
+def sigma_gpp(M, En, nocc: int, omega2, wtilde, vcoul, E) -> np.ndarray:
+    """Full self-energy matrix on an energy grid (section on the off-diagonal GPP kernel;
+    the two products counted by Eq. flop_count_fullmat):
+    Sigma_lm(E_e) = sum_n sum_GG' conj(M_n[l][G]) P^n_GG'(E_e) M_n[m][G'],
+    for every (n, E_e) first X = conj(M_n) P (N_Sigma x N_G x N_G), then X M_n^T
+    (N_Sigma x N_G x N_Sigma).  Returns [ne][nsig][nsig] complex128."""
+    M = np.asarray(M, np.complex128)
+    nb, nsig, _ = M.shape
+    E = np.asarray(E, np.float64)
+    out = np.zeros((len(E), nsig, nsig), np.complex128)
+    for e, Ee in enumerate(E):
+        for n in range(nb):
+            P = gpp_pole_matrix(omega2, wtilde, vcoul, Ee - float(En[n]), n < nocc)
+            out[e] += (M[n].conj() @ P) @ M[n].T
+    return out

@@ -415,3 +415,83 @@ def test_jvp_central_differences(w):
 
     h = 1e-6
     assert rel(got, (chi(h) - chi(-h)) / (2 * h)) < 1e-7
+
+
+# ------------------------------------------------------------------ off-diagonal GPP self-energy
+
+def _sigma_by_frequency_integral(B, eps, occupied, wt, eta, E, n=400001, scale=10.0):
+    """(i/2pi) int dw G(E + w) W_c(w) for one band and one plane wave, by quadrature on the real
+    axis (w = scale tan(theta), trapezoid in theta).  G(z) = 1/(z - eps + i eta sgn), sgn = -1 for
+    an occupied band; W_c(w) = B [1/(w - wt + i eta) - 1/(w + wt - i eta)], the time-ordered
+    plasmon-pole screened interaction whose spectral weight B sits at +-wt."""
+    th = np.linspace(-np.pi / 2, np.pi / 2, n)[1:-1]
+    w = scale * np.tan(th)
+    jac = scale / np.cos(th) ** 2
+    sg = -1.0 if occupied else 1.0
+    G = 1.0 / (E + w - eps + 1j * eta * sg)
+    W = B * (1.0 / (w - wt + 1j * eta) - 1.0 / (w + wt - 1j * eta))
+    f = G * W * jac
+    return 1j / (2 * np.pi) * np.trapezoid(f, th)
+
+
+@pytest.mark.parametrize("occupied", [True, False])
+def test_gpp_pole_matches_frequency_integral(occupied):
+    """The pole factor is the frequency convolution of G and the plasmon-pole W: closing the contour
+    puts an empty band at E - eps - wt and an occupied one at E - eps + wt (with the damping
+    eta entering twice, wt -> wt - 2 i eta), both with residue B = v Omega^2 / (2 wt)."""
+    B, wt, eta = 2.5, 12.0, 0.3
+    eps = -3.0 if occupied else 4.0
+    wc = wt - 2j * eta
+    v = np.array([1.7])
+    om2 = np.array([[2.0 * wc * B / v[0]]])
+    for E in (-1.0, 0.5, 2.0, 9.0):
+        want = _sigma_by_frequency_integral(B, eps, occupied, wt, eta, E)
+        got = oracle.sigma_gpp(np.ones((1, 1, 1), complex), np.array([eps]), 1 if occupied else 0, om2,
+                               np.array([[wc]]), v, np.array([E]))[0, 0, 0]
+        assert abs(got - want) < 1e-6 * abs(want), (E, got, want)
+
+
+def test_gpp_screened_exchange_coulomb_hole_brute_force():
+    """Quadruple loop over (n, G, G') in the screened-exchange + Coulomb-hole form of the same model:
+    CH = (1/2) Omega^2 v / (wt (d - wt)) for every band, SX - X = -Omega^2 v / (d^2 - wt^2) for the
+    occupied ones.  Catches a wrong occupied/empty pole, a dropped 1/2, v on the wrong index and a
+    conjugate on the wrong side."""
+    p = gwgen.make_gpp(nb=3, nocc=1, nsig=2, ng=9, ne=2, seed=5)  # two |G| shells: v varies
+    nb, nsig, ng = p.M.shape
+    got = oracle.sigma_gpp(p.M, p.En, p.nocc, p.omega2, p.wtilde, p.vcoul, p.E)
+    for e in range(len(p.E)):
+        for l in range(nsig):
+            for m in range(nsig):
+                acc = 0j
+                for n in range(nb):
+                    d = p.E[e] - p.En[n]
+                    for G in range(ng):
+                        for Gp in range(ng):
+                            o2, wt, v = p.omega2[G, Gp], p.wtilde[G, Gp], p.vcoul[Gp]
+                            f = 0.5 * o2 * v / (wt * (d - wt))
+                            if n < p.nocc:
+                                f += -o2 * v / (d * d - wt * wt)
+                            acc += np.conj(p.M[n, l, G]) * f * p.M[n, m, Gp]
+                assert abs(got[e, l, m] - acc) < 1e-13 * max(1.0, abs(acc))
+
+
+def test_gpp_hermitian_and_phase_covariance():
+    """With a real symmetric mode energy and a Hermitian residue v_G' Omega^2_GG' / (2 wt), every
+    P^n(E) is Hermitian at real E, so Sigma(E) is Hermitian; a phase on band l of the self-energy
+    set multiplies Sigma_lm by e^{-i phi_l} e^{i phi_m}; a phase on a summed band n drops out."""
+    rng = np.random.default_rng(9)
+    p = gwgen.make_gpp(nb=5, nocc=2, nsig=4, ng=7, ne=3, seed=9)
+    ng = p.M.shape[2]
+    wt = p.wtilde.real.copy()
+    H = gwgen.hermitian(rng, ng)
+    om2 = 2.0 * wt * H / p.vcoul[None, :]
+    s = oracle.sigma_gpp(p.M, p.En, p.nocc, om2, wt, p.vcoul, p.E)
+    for e in range(len(p.E)):
+        assert np.abs(s[e] - s[e].conj().T).max() < 1e-13 * np.abs(s[e]).max()
+    s = oracle.sigma_gpp(p.M, p.En, p.nocc, p.omega2, p.wtilde, p.vcoul, p.E)
+    phi = rng.uniform(0, 2 * np.pi, p.M.shape[1])
+    th = rng.uniform(0, 2 * np.pi, p.M.shape[0])
+    M2 = p.M * np.exp(1j * phi)[None, :, None] * np.exp(1j * th)[:, None, None]
+    s2 = oracle.sigma_gpp(M2, p.En, p.nocc, p.omega2, p.wtilde, p.vcoul, p.E)
+    want = s * np.exp(-1j * phi)[None, :, None] * np.exp(1j * phi)[None, None, :]
+    assert np.abs(s2 - want).max() < 1e-13 * np.abs(s).max()
