@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--subspace", action="store_true")
     ap.add_argument("--epsilon", action="store_true")
     ap.add_argument("--extras", action="store_true", help="real-axis chi and the forward derivative")
+    ap.add_argument("--sigma", action="store_true", help="off-diagonal plasmon-pole self-energy")
+    ap.add_argument("--sigma-ng", type=int, default=11075)
+    ap.add_argument("--sigma-nsig", type=int, default=512)
+    ap.add_argument("--sigma-ne", type=int, default=16, help="energies per step (the default workload: 16)")
     return ap.parse_args()
 
 
@@ -147,6 +151,37 @@ def cpu_baseline(cfg, prob, sample_pairs):
             "seconds": dt}
 
 
+def oracle_block(cfg, prob, nsample=12, seed=3):
+    """Reference values for the error check, from the oracle on a bounded sample: the
+    nsample x nsample block of chi(0) at sampled G, all pairs.  Runs only with the CPU baseline."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(cfg.ng, nsample, replace=False))
+    M = oracle.m_conv(prob.gpsi, prob.cv, prob.gpsi, prob.cc, prob.gchi[idx])
+    ref = oracle.chi0(M, oracle.delta(prob.ev, prob.ec, 0.0))
+    return idx, ref, f"{nsample}x{nsample} sampled entries, all pairs"
+
+
+def block_error(chi, blk):
+    idx, ref, how = blk
+    got = chi[np.ix_(idx, idx)]
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), how
+
+
+def oracle_sigma_rows(p, n0, eidx, rows):
+    """Oracle Sigma rows for one (n, E) of the plasmon-pole workload (P formed once), timed as the
+    CPU baseline of that mode: the oracle's rate on this sample in the same flop convention."""
+    import oracle
+    t0 = time.perf_counter()
+    P = oracle.gpp_pole_matrix(p.omega2, p.wtilde, p.vcoul, float(p.E[eidx] - p.En[n0]), n0 < p.nocc)
+    ref = (p.M[n0][rows].conj() @ P) @ p.M[n0].T
+    dt = time.perf_counter() - t0
+    ng, nsig = P.shape[0], p.M.shape[1]
+    fl = 8.0 * (len(rows) * ng * ng + ng * len(rows) * nsig)
+    return ref, {"value": fl / dt * 1e-12, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+                 "sample": f"one (n, E): P^n(E) formed and {len(rows)} rows of Sigma, {dt:.1f} s"}
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -183,17 +218,6 @@ TRAFFIC = {
     "ozaki_gemm": {"bytes_per_launch": 7.32e9 + 0.219e9,
                    "source": "ncu dram__bytes_read+write, oz_gemm_kernel (s = 7), p1_48cube_onechunk"},
 }
-
-
-def sampled_error(cfg, prob, chi, nsample=12, seed=3):
-    """Relative Frobenius error of a sampled nsample x nsample block of chi against the oracle."""
-    import oracle
-    rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(cfg.ng, nsample, replace=False))
-    M = oracle.m_conv(prob.gpsi, prob.cv, prob.gpsi, prob.cc, prob.gchi[idx])
-    ref = oracle.chi0(M, oracle.delta(prob.ev, prob.ec, 0.0))
-    got = chi[np.ix_(idx, idx)]
-    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), f"{nsample}x{nsample} sampled entries, all pairs"
 
 
 def peak_for(prec):
@@ -438,9 +462,12 @@ def ours(args):
         a = run_mode(args, cfg, prob, dev, args.prec, args.nslices, mtxel, 2, 1, False, world, single_stream=True)
         alone = {"ms_per_step": a["ms_per_step"], "value": a["value"], "pair": roofline_pair(cfg, prob, a),
                  "contraction": roofline_for(cfg, args.prec, args.nslices, a)}
-    err = None
-    if rank == 0 and not args.no_check:
-        e, how = sampled_error(cfg, prob, main["chi"])
+    # the CPU baseline leg (rank 0): the oracle timed on a bounded sample, and its reference block
+    # for the error check
+    err, blk = None, None
+    if rank == 0 and not args.no_cpu_baseline and not args.no_check:
+        blk = oracle_block(cfg, prob)
+        e, how = block_error(main["chi"], blk)
         err = {"rel_frobenius_vs_oracle": e, "sample": how}
     # the native FP64 tensor-core path on the same input, for the FP64-vs-split comparison
     other = None
@@ -449,8 +476,8 @@ def ours(args):
         other = {"value": f["value"], "unit": "TFLOP/s", "ms_per_q": f["ms_per_step"], "mtxel": "fp64",
                  "roofline": roofline_for(cfg, "fp64", 0, f), "kernel_ms_per_step":
                      {k: v / max(1, min(2, args.steps)) for k, v in f["kernel_ms"].items()}}
-        if rank == 0 and not args.no_check:
-            other["rel_frobenius_vs_oracle"], _ = sampled_error(cfg, prob, f["chi"])
+        if blk is not None:
+            other["rel_frobenius_vs_oracle"], _ = block_error(f["chi"], blk)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, prob, args.cpu_sample_pairs)
@@ -479,15 +506,11 @@ def ours(args):
 def sweep(args):
     """Slice-count sweep on one 8192-pair chunk of the 72^3 workload (N_G = 6000)."""
     import torch
-    import oracle
     import paper_2509_23018_gb300 as gw
     cfg = gwgen.CONFIGS["p3_72cube_onechunk"]
     prob = gwgen.config_problem(cfg)
     dev = torch.device("cuda", 0)
-    rng = np.random.default_rng(3)
-    idx = np.sort(rng.choice(cfg.ng, 12, replace=False))
-    M = oracle.m_conv(prob.gpsi, prob.cv, prob.gpsi, prob.cc, prob.gchi[idx])
-    ref = oracle.chi0(M, oracle.delta(prob.ev, prob.ec, 0.0))
+    idx, ref, _ = oracle_block(cfg, prob)
     out = {"workload": f"{cfg.name}: grid 72^3, {cfg.nv}+{cfg.nc} bands, N_Gpsi={cfg.ngpsi}, N_G={cfg.ng}",
            "sample": "12x12 sampled entries vs the oracle, all pairs", "slices": {}}
     for s_ in (4, 5, 6, 7, 8):
@@ -694,6 +717,68 @@ def extras(args):
                       "jvp_hermitian": bool(torch.equal(d[0], d[0].conj().T))}), flush=True)
 
 
+def sigma(args):
+    """Off-diagonal plasmon-pole self-energy (section on the off-diagonal GPP kernel): N_Sigma = 512
+    self-energy bands (the paper's Si998 full-matrix runs), N_G = 11,075 (the Si214 dielectric
+    sphere of Table 2), per step 4 summed bands (2 occupied, 2 empty) x 16 energies of the grid.
+    TFLOP/s in the convention of Eq. flop_count_fullmat (the two products' ZGEMM flops only, the
+    whole kernel time including the prep. step).  Inputs from the seeded plasmon-pole recipe."""
+    import torch
+    import paper_2509_23018_gb300 as gw
+    ng, nsig, nb, nocc, ne = args.sigma_ng, args.sigma_nsig, 4, 2, args.sigma_ne
+    p = gwgen.make_gpp(nb, nocc, nsig, ng, ne, seed=gwgen.BASE_SEED + 50)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    M, o2, wt, v = t(p.M), t(p.omega2), t(p.wtilde), t(p.vcoul)
+    h = gw.Chi0((8, 8, 8), prec=args.prec, nslices=args.nslices)
+    out = torch.empty((ne, nsig, nsig), dtype=torch.complex128, device="cuda")
+    # one pair of products per (n, E): 8 (N_Sigma N_G^2 + N_G N_Sigma^2) ZGEMM flops each
+    flops = nb * ne * 8.0 * (nsig * ng * ng + ng * nsig * nsig)
+    steps, warm = max(1, min(args.steps, 3)), 1
+    for _ in range(warm):
+        h.sigma_gpp(M, p.En, nocc, o2, wt, v, p.E, out=out)
+    torch.cuda.synchronize()
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    h.set_timing(True)
+    h.timing(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h.sigma_gpp(M, p.En, nocc, o2, wt, v, p.E, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    kt = h.timing(reset=True)
+    h.set_timing(False)
+    clocks = clk.stop()
+    kms = {k: val[0] / steps for k, val in kt.items()}
+    s = args.nslices
+    issued_x = s * (s + 1) / 2 * 8.0 * nsig * ng * ng * nb * ne      # slice pairs x real flops, first product
+    pk, pk_src = peak_for("ozaki")
+    roof = None
+    if args.prec == "ozaki" and "gpp_gemm_x" in kms:
+        ach = issued_x / (kms["gpp_gemm_x"] * 1e-3) * 1e-12
+        roof = {"bound": "tensor", "kernel": "oz_gemm_kernel (X = conj(M_n) P)", "achieved": ach, "peak": pk,
+                "unit": "TFLOP/s", "frac": ach / pk, "peak_source": pk_src}
+    # error: one (n, E) against the oracle on 8 sampled rows l (P formed once on the host)
+    n0, eidx = 0, min(5, ne - 1)
+    one = h.sigma_gpp(M[n0:n0 + 1], p.En[n0:n0 + 1], 1 if n0 < nocc else 0, o2, wt, v, p.E[eidx:eidx + 1])
+    got = one[0].cpu().numpy()
+    h.sync()
+    rows = np.random.default_rng(1).choice(nsig, 8, replace=False)
+    err, cpu = None, None
+    if not args.no_cpu_baseline:
+        ref, cpu = oracle_sigma_rows(p, n0, eidx, rows)
+        err = float(np.linalg.norm(got[rows] - ref) / np.linalg.norm(ref))
+    print(json.dumps({
+        "metric": "gpp_offdiag_tflops", "value": flops / (ms * 1e-3) * 1e-12,
+        "unit": "TFLOP/s (Eq. flop_count_fullmat convention)", "ms_per_step": ms,
+        "workload": f"GPP off-diag. Sigma: N_Sigma={nsig}, N_G={ng}, {nb} summed bands ({nocc} occupied) x "
+                    f"{ne} energies per step, plasmon-pole recipe (wp = 16.6 eV, eta = 0.25 eV)",
+        "prec": args.prec, "nslices": s, "kernel_ms": kms, "roofline": roof, "clocks": clocks,
+        "rel_err_sampled_rows_one_nE": err, "cpu_baseline": cpu}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -708,6 +793,8 @@ def main():
         epsilon(args)
     elif args.extras:
         extras(args)
+    elif args.sigma:
+        sigma(args)
     elif args.adjoint:
         adjoint(args)
     else:

@@ -257,6 +257,35 @@ GW_API gw_status gw_chi0_epsilon_inverse(gw_chi0 *h, int ng, int nw, const doubl
                                          double *epsinv);
 
 /*
+ * Full-matrix (off-diagonal) self-energy of the plasmon-pole model on an energy grid -- the
+ * Sigma-module kernel of the section on the off-diagonal GPP kernel, whose work is the two
+ * products per (n, E) counted by Eq. flop_count_fullmat:
+ *   sigma[e][l][m] = sum_n sum_{G,G'} conj(M[n][l][G]) P^n_GG'(E[e]) M[n][m][G'],
+ *   P^n_GG'(E) = v[G'] Omega2[G][G'] / (2 wt[G][G'] (E - En[n] - s_n wt[G][G'])),
+ * s_n = -1 for an occupied band (n < nocc), +1 otherwise: the correlation part of the
+ * Hybertsen-Louie plasmon-pole model the paper cites for the frequency dependence (its working
+ * equation is in a figure).  P^n(E) is formed per (n, E) (the prep. step) and never leaves the
+ * device; in split-precision mode it goes straight into BF16 column slices.
+ *   nb, nocc  summed bands n and how many of them (the first nocc) are occupied; 0 <= nocc <= nb.
+ *   nsig, ng  self-energy bands l, m and plane waves G (the dielectric sphere).
+ *   M       device complex128 [nb][nsig][ng], M[n][l][G] (e.g. from gw_chi0_pair_elements).
+ *   En      host double [nb], band energies (eV).
+ *   omega2  device complex128 [ng][ng], Omega^2_GG' (eV^2).
+ *   wtilde  device complex128 [ng][ng], mode energies (eV); keep E - En[n] -+ wt away from 0
+ *           (a damping Im wt != 0 does).
+ *   vcoul   device float64 [ng], the Coulomb diagonal v_G.
+ *   ne, E   host double [ne], the energy grid (eV); ne = 0 is a no-op.
+ *   sigma   device complex128 [ne][nsig][nsig], written in full (zero when nb = 0).
+ * Work buffers: two [ng][ng] complex matrices plus, in split mode, the slices of up to 16
+ * energies' P (7 slices: 56 ng^2 bytes each), held by the handle until destroy.
+ * GW_ERR_ARG for sizes out of range, null or misaligned (16 bytes) complex pointers, non-finite
+ * energies; other errors as gw_chi0_compute.
+ */
+GW_API gw_status gw_chi0_sigma_gpp(gw_chi0 *h, int nb, int nocc, int nsig, int ng, const double *M, const double *En,
+                                   const double *omega2, const double *wtilde, const double *vcoul, int ne,
+                                   const double *E, double *sigma);
+
+/*
  * Adjoint of L = Re Tr(W chi0(iq, w)) for a Hermitian W (GWPT-style sensitivity,
  * Eq. gwpt motivates it).  Matrix elements are recomputed chunk by chunk; Y = M W runs as
  * a split product on the BF16 tensor cores in split-precision mode, on DMMA otherwise.

@@ -45,6 +45,7 @@ SIGNATURES = {
     "gw_chi0_subspace_basis": ([P, I, P, I, P, P], I),
     "gw_chi0_compute_subspace": ([P, I, I, P, I, P, P], I),
     "gw_chi0_epsilon_inverse": ([P, I, I, P, P, P], I),
+    "gw_chi0_sigma_gpp": ([P, I, I, I, I, P, P, P, P, P, I, P, P], I),
     "gw_chi0_compute_real": ([P, I, I, P, D, P], I),
     "gw_chi0_jvp": ([P, I, I, P, P, P, P, P, P], I),
     "gw_chi0_sync": ([P], I),

@@ -223,6 +223,31 @@ class Chi0:
         self._check(self.lib.gw_chi0_epsilon_inverse(self.h, ng, nw, _ptr(chi), _ptr(v), _ptr(out)))
         return out[0] if single else out
 
+    def sigma_gpp(self, M: torch.Tensor, En, nocc: int, omega2: torch.Tensor, wtilde: torch.Tensor,
+                  vcoul: torch.Tensor, E, out: torch.Tensor | None = None):
+        """Full self-energy matrix of the plasmon-pole model on the energy grid E:
+        M [nb, nsig, ng] (M[n][l][G]), En [nb] (host), the first nocc bands occupied, Omega^2 and
+        mode energies [ng, ng], v [ng].  Returns [ne, nsig, nsig] complex128."""
+        dev = f"cuda:{self.device}"
+        M = M.to(device=dev, dtype=torch.complex128).contiguous()
+        nb, nsig, ng = M.shape
+        o2 = omega2.to(device=dev, dtype=torch.complex128).contiguous()
+        wt = wtilde.to(device=dev, dtype=torch.complex128).contiguous()
+        v = vcoul.to(device=dev, dtype=torch.float64).contiguous()
+        en = [float(x) for x in En]
+        ee = [float(x) for x in E]
+        if len(en) != nb:
+            raise ValueError("En must have one energy per band")
+        ne = len(ee)
+        if out is None:
+            out = torch.empty((ne, nsig, nsig), dtype=torch.complex128, device=dev)
+        en_arr = (ctypes.c_double * max(nb, 1))(*en)
+        e_arr = (ctypes.c_double * max(ne, 1))(*ee)
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_sigma_gpp(self.h, nb, int(nocc), nsig, ng, _ptr(M), en_arr, _ptr(o2), _ptr(wt),
+                                               _ptr(v), ne, e_arr, _ptr(out)))
+        return out
+
     def sync(self):
         self._use_current_stream()
         self._check(self.lib.gw_chi0_sync(self.h))

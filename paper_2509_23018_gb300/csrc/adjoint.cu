@@ -29,6 +29,8 @@ __device__ __forceinline__ void dmma8(double &d0, double &d1, double a, double b
                  : "d"(a), "d"(b));
 }
 
+// CA: conj(A) in place of A.  TB: B given as its transpose, row-major [nc][kd].  ACC: C += A B.
+template <bool CA, bool TB, bool ACC>
 __global__ void __launch_bounds__(256) zgemm_kernel(const double2 *__restrict__ A, const double2 *__restrict__ B,
                                                     double2 *__restrict__ C, int64_t mr, int kd, int nc)
 {
@@ -44,12 +46,20 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const double2 *__restrict__ 
             int r = e / kGK, k = e % kGK;
             int64_t gm = m0 + r;
             int gk = k0 + k;
-            sa[r][k] = (gm < mr && gk < kd) ? A[gm * kd + gk] : make_double2(0.0, 0.0);
+            double2 x = (gm < mr && gk < kd) ? A[gm * kd + gk] : make_double2(0.0, 0.0);
+            if (CA) x.y = -x.y;
+            sa[r][k] = x;
         }
         for (int e = tid; e < kGK * kGT; e += blockDim.x) {
-            int k = e / kGT, n = e % kGT;
-            int gk = k0 + k, gn = n0 + n;
-            sb[k][n] = (gk < kd && gn < nc) ? B[(int64_t)gk * nc + gn] : make_double2(0.0, 0.0);
+            if (TB) {
+                int n = e / kGK, k = e % kGK;
+                int gk = k0 + k, gn = n0 + n;
+                sb[k][n] = (gk < kd && gn < nc) ? B[(int64_t)gn * kd + gk] : make_double2(0.0, 0.0);
+            } else {
+                int k = e / kGT, n = e % kGT;
+                int gk = k0 + k, gn = n0 + n;
+                sb[k][n] = (gk < kd && gn < nc) ? B[(int64_t)gk * nc + gn] : make_double2(0.0, 0.0);
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -91,7 +101,15 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const double2 *__restrict__ 
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int gn = n0 + wn * 16 + nt * 8 + 2 * (lane & 3) + q;
-                if (gn < nc) C[gm * nc + gn] = make_double2(cre[mt][nt][q], cim[mt][nt][q]);
+                if (gn < nc) {
+                    double2 v = make_double2(cre[mt][nt][q], cim[mt][nt][q]);
+                    if (ACC) {
+                        const double2 o = C[gm * nc + gn];
+                        v.x += o.x;
+                        v.y += o.y;
+                    }
+                    C[gm * nc + gn] = v;
+                }
             }
     }
 }
@@ -100,7 +118,19 @@ cudaError_t launch_zgemm(const double2 *A, const double2 *B, double2 *C, int64_t
 {
     if (mr == 0 || nc == 0) return cudaSuccess;
     dim3 grid((nc + kGT - 1) / kGT, (unsigned)((mr + kGT - 1) / kGT));
-    zgemm_kernel<<<grid, 256, 0, st>>>(A, B, C, mr, kd, nc);
+    zgemm_kernel<false, false, false><<<grid, 256, 0, st>>>(A, B, C, mr, kd, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zgemm_ex(const double2 *A, const double2 *B, double2 *C, int64_t mr, int kd, int nc, bool conj_a,
+                            bool trans_b, bool accumulate, cudaStream_t st)
+{
+    if (mr == 0 || nc == 0) return cudaSuccess;
+    dim3 grid((nc + kGT - 1) / kGT, (unsigned)((mr + kGT - 1) / kGT));
+    if (conj_a && !trans_b && !accumulate) zgemm_kernel<true, false, false><<<grid, 256, 0, st>>>(A, B, C, mr, kd, nc);
+    else if (!conj_a && trans_b && accumulate) zgemm_kernel<false, true, true><<<grid, 256, 0, st>>>(A, B, C, mr, kd, nc);
+    else if (!conj_a && !trans_b && !accumulate) zgemm_kernel<false, false, false><<<grid, 256, 0, st>>>(A, B, C, mr, kd, nc);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

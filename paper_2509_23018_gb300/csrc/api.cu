@@ -363,7 +363,8 @@ gw_status oz_prepare_b(gw_chi0 *h, const double2 *B, int ka, int nout)
     if ((st = grow(h, &h->ZBbuf, &h->ZBcap, (size_t)s * 2 * nout * kpad * 2, "product operand slices")) ||
         (st = grow(h, (void **)&h->EBbuf, &h->EBcap, sizeof(int) * (size_t)nout, "product operand exponents")))
         return st;
-    CK(h, gw::launch_oz_split_cols(B, ka, nout, s, kpad, h->ZBbuf, h->EBbuf, h->st), "oz column slices");
+    CK(h, gw::launch_oz_split_cols(B, ka, nout, nout, 1, false, s, kpad, h->ZBbuf, h->EBbuf, h->st),
+       "oz column slices");
     return GW_OK;
 }
 
@@ -674,6 +675,7 @@ void gw_chi0_destroy(gw_chi0 *h)
     }
     if (h->ov_st) cudaStreamDestroy(h->ov_st);
     dfree(h, h->epsbuf, h->epscap);
+    for (auto &b : h->gpp) dfree(h, b.p, b.cap);
     dfree(h, h->realbuf, h->realcap);
     dfree(h, h->eigA, h->eigA_cap);
     dfree(h, h->eigWork, h->eigWork_cap);

@@ -142,6 +142,11 @@ struct gw_chi0 {
     double *eigW = nullptr;
     int *eigInfo = nullptr;
     size_t eigA_cap = 0, eigWork_cap = 0, eigW_cap = 0, eigInfo_cap = 0;
+    // plasmon-pole self-energy work buffers (api_sigma.cu)
+    struct Buf {
+        void *p = nullptr;
+        size_t cap = 0;
+    } gpp[9];
     // scratch slots of the two-float pair kernel (sized in set_gsphere, outside any capture)
     float4 *pscr = nullptr;
     size_t pscr_cap = 0; // bytes

@@ -133,10 +133,23 @@ int oz_tiles(int ng, int bn);
 // (complex, row-major), A split by rows and B by columns into s six-bit BF16 slices.
 // ZA: s * rows * kpad bf16, ZB: s * 2 nout * kpad bf16, EA: rows ints, EB: nout ints,
 // kpad = ka rounded up to a multiple of 32 complex (64 real) entries.
+// conj: split the rows of conj(A) / the columns of conj(B).  B[g][b] is read at B[g sk + b sj]
+// (sk = nout, sj = 1: row-major [ka][nout]; sk = 1, sj = ka: a row-major [nout][ka] transpose).
 cudaError_t launch_oz_split_rows(const double2 *A, int64_t rows, int ka, int s, int64_t kpad, void *ZA, int *EA,
-                                 cudaStream_t st);
-cudaError_t launch_oz_split_cols(const double2 *B, int ka, int nout, int s, int64_t kpad, void *ZB, int *EB,
-                                 cudaStream_t st);
+                                 cudaStream_t st, bool conj = false);
+cudaError_t launch_oz_split_cols(const double2 *B, int ka, int nout, int64_t sk, int64_t sj, bool conj, int s,
+                                 int64_t kpad, void *ZB, int *EB, cudaStream_t st);
+// Plasmon-pole prep. step straight into row slices of P^T (the layout of launch_oz_split_rows with
+// rows = ka = ng): P[g][c] = A[g][c] / (d - sgn wt[g][c]) in two-float arithmetic, At / Wt = A
+// and wt transposed [c][g] as two-float (hi, lo) pairs (gpp_setup_tf), for cnt <= kGppMaxE
+// energies d[0..cnt) (host) at once: slices of energy j at Z + j zstride (bf16 elements),
+// exponents at E + j ng.
+constexpr int kGppMaxE = 16;
+struct GppEnergies {
+    double d[kGppMaxE];
+};
+cudaError_t launch_gpp_prep_split(const float4 *At, const float4 *Wt, int ng, const double *d, int cnt, float sgn,
+                                  int s, int64_t kpad, int64_t zstride, void *Z, int *E, cudaStream_t st);
 cudaError_t launch_oz_gemm_general(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
                                    cudaStream_t st);
 size_t oz_smem_bytes(int bn);
@@ -145,6 +158,22 @@ int oz_box_k();
 
 // ---- adjoint of L = Re Tr(W chi) (adjoint.cu)
 cudaError_t launch_zgemm(const double2 *A, const double2 *B, double2 *C, int64_t mr, int kd, int nc, cudaStream_t st);
+// C (+)= op(A) op(B): conj_a takes conj(A); trans_b reads B as its transpose, row-major [nc][kd];
+// accumulate adds into C.  Built for (conj_a), (trans_b, accumulate) and the plain product.
+cudaError_t launch_zgemm_ex(const double2 *A, const double2 *B, double2 *C, int64_t mr, int kd, int nc, bool conj_a,
+                            bool trans_b, bool accumulate, cudaStream_t st);
+// ---- plasmon-pole self-energy, prep. step (sigma.cu)
+// A[g][c] = v[c] Omega2[g][c] / (2 wt[g][c]) in FP64, stored [g][c]
+cudaError_t launch_gpp_setup(const double2 *omega2, const double2 *wtilde, const double *vcoul, int ng, double2 *A,
+                             cudaStream_t st);
+// the same A and wt, transposed [c][g], as two-float (hi, lo) pairs for the split path
+cudaError_t launch_gpp_setup_tf(const double2 *omega2, const double2 *wtilde, const double *vcoul, int ng, float4 *At,
+                                float4 *Wt, cudaStream_t st);
+// sigma[e][l][m] = ST[m][e nsig + l] (ST accumulated transposed by the split path)
+cudaError_t launch_gpp_untranspose(const double2 *ST, int ne, int nsig, double2 *sigma, cudaStream_t st);
+// P[g][c] = A[g][c] / (d - sgn wt[g][c]) (FP64, stored)
+cudaError_t launch_gpp_prep_f64(const double2 *A, const double2 *wtilde, int ng, double d, double sgn, double2 *P,
+                                cudaStream_t st);
 cudaError_t launch_adj_rows(const double2 *M, double2 *Y, int64_t P, int ng, int nc, int64_t p0, const double *ev,
                             const double *ec, double w, double *L, double *dEv, double *dEc, cudaStream_t st);
 cudaError_t launch_adj_pair(const double2 *Gb, int64_t P, const PairPlan &pp, const int *cell_start,

@@ -19,6 +19,7 @@
 // scaling, the recombination, the accumulation across chunks and the symmetrisation.
 #include "internal.h"
 #include "ptx.cuh"
+#include "fft_tf.cuh"
 #include <cuda_bf16.h>
 #include <algorithm>
 
@@ -29,6 +30,11 @@ constexpr int kOzBM = 128, kOzBN = 256, kOzBK = 64, kOzStages = 4;
 constexpr int kOzThreads = 192;
 constexpr unsigned kOzABytes = kOzBM * kOzBK * 2, kOzBBytes = kOzBN * kOzBK * 2;
 constexpr int kOzNoColumn = -400; // exponent of an all-zero column
+// K-steps of one accumulation segment: 128 x 64 = 8192 real K entries, the length over which a
+// slice group's FP32 sum is exact (|z_i z_k| <= 2^10, two products per entry for t = 3).  Longer
+// K (the general product with more than 4096 complex inner entries) is summed segment by segment,
+// each segment's groups recombined in FP64 by the epilogue.
+constexpr int kOzKSeg = 128;
 
 // ------------------------------------------------------------------ split, step 1: column exponents
 // E[g] = max_p ilogb(max(|Re A|, |Im A|)) + 2 over the chunk, A = s_p M[p][g].
@@ -160,7 +166,8 @@ __device__ __forceinline__ int oz_block_max(int e, int *red)
 }
 
 // One block per row p of A [rows][ka] (complex): E[p], then Z[i][p][k], k = 2 g + {Re, Im},
-// zero for k >= 2 ka.
+// zero for k >= 2 ka.  CONJ: the rows of conj(A).
+template <bool CONJ>
 __global__ void __launch_bounds__(256) oz_split_rows_kernel(const double2 *__restrict__ A, int64_t rows, int ka,
                                                             int s, int64_t kpad, uint16_t *__restrict__ Z,
                                                             int *__restrict__ E)
@@ -178,7 +185,7 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(const double2 *__res
     uint16_t *zr = Z + p * kpad;
     for (int64_t k = threadIdx.x; k < kpad; k += blockDim.x) {
         const int g = (int)(k >> 1);
-        const double x = g < ka ? ((k & 1) ? a[g].y : a[g].x) : 0.0;
+        const double x = g < ka ? ((k & 1) ? (CONJ ? -a[g].y : a[g].y) : a[g].x) : 0.0;
         oz_digits(x, e, s, zr + k, rows * kpad);
     }
 }
@@ -187,15 +194,18 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(const double2 *__res
 // and 2b + 1 (Im) of the real K-major operand B^T: row 2b = (Re B, -Im B), row 2b + 1 =
 // (Im B, Re B) interleaved by g, so that [Re A, Im A] interleaved times them gives Re and
 // Im of (A B)[p][b].
-__global__ void __launch_bounds__(256) oz_split_cols_kernel(const double2 *__restrict__ B, int ka, int nout, int s,
-                                                            int64_t kpad, uint16_t *__restrict__ Z,
-                                                            int *__restrict__ E)
+// B[g][b] is read at B[g sk + b sj] (sk = nout, sj = 1 for a row-major B; sk = 1, sj = ka for
+// the transpose of a row-major [nout][ka] matrix).  CONJ: the columns of conj(B).
+template <bool CONJ>
+__global__ void __launch_bounds__(256) oz_split_cols_kernel(const double2 *__restrict__ B, int ka, int nout,
+                                                            int64_t sk, int64_t sj, int s, int64_t kpad,
+                                                            uint16_t *__restrict__ Z, int *__restrict__ E)
 {
     __shared__ int red[8];
     const int b = blockIdx.x;
     int e = kOzNoColumn;
     for (int g = threadIdx.x; g < ka; g += blockDim.x) {
-        const double2 x = B[(int64_t)g * nout + b];
+        const double2 x = B[(int64_t)g * sk + (int64_t)b * sj];
         e = max(e, oz_expo(fmax(fabs(x.x), fabs(x.y))));
     }
     e = oz_block_max(e, red);
@@ -206,12 +216,158 @@ __global__ void __launch_bounds__(256) oz_split_cols_kernel(const double2 *__res
         const int g = (int)(k >> 1);
         double x0 = 0.0, x1 = 0.0;
         if (g < ka) {
-            const double2 x = B[(int64_t)g * nout + b];
+            double2 x = B[(int64_t)g * sk + (int64_t)b * sj];
+            if (CONJ) x.y = -x.y;
             x0 = (k & 1) ? -x.y : x.x;
             x1 = (k & 1) ? x.x : x.y;
         }
         oz_digits(x0, e, s, z0 + k, plane);
         oz_digits(x1, e, s, z1 + k, plane);
+    }
+}
+
+// ------------------------------------------------------------------ plasmon-pole prep. step, split
+// The A operand of X^T = P^T conj(M_n)^T straight from the pole parameters, P never stored:
+// P[g][c] = A[g][c] / (d - sgn wt[g][c]) with A = v Omega^2 / (2 wt) (gpp_setup_tf_kernel),
+// d = E - E_n, sgn = -1 for an occupied band n and +1 for an empty one.  At / Wt hold A and wt
+// transposed ([c][g]) in two-float form, so that row c of P^T is one contiguous row and the
+// pole runs on the FP32 pipes.  One block per row c and up to kGppMaxE energies per launch,
+// sharing each read of the row:
+//  * pass 1, the row exponent per energy, from P in FP32 after the exact two-float subtraction
+//    x = d - sgn wt (relative error ~2^-22 however close the pole), padded by 2^-10 so that the
+//    exponent is never below the one of the exact maximum;
+//  * pass 2, P = A conj(x) / |x|^2 in two-float arithmetic (the reciprocal by one Newton step,
+//    relative error near 2^-46, below the 2^-42 the seven slices keep), then the balanced
+//    base-64 digits of N = round(P 2^sh) in the layout of oz_split_rows_kernel, (Re P, Im P)
+//    interleaved by g.  The digits are taken in FP32, where every step is exact: v = hi 2^sh
+//    splits into t 2^24 + r (|r| <= 2^23), the low part L = rint(r) + rint(lo 2^sh) (|L| < 2^24)
+//    gives four digits by q = rint(L / 64), d = L - 64 q, and t + q the rest.  N differs from
+//    round((hi + lo) 2^sh) by one unit of the last digit at most; |d| <= 32 as before.
+__device__ __forceinline__ tf tf_recip(tf d)
+{
+    const float r0 = __frcp_rn(d.hi);
+    const tf p = tf_mul(d, tf{r0, 0.0f});
+    const tf e = tf_sub(tf{1.0f, 0.0f}, p); // 1 - d r0, of order 2^-23
+    return tf_fast2sum(r0, __fmul_rn(r0, e.hi));
+}
+
+__device__ __forceinline__ tcx gpp_pole_tf(float4 a4, float4 w4, tf d, float sgn)
+{
+    const tcx a{{a4.x, a4.y}, {a4.z, a4.w}};
+    // x = d - sgn wt (sgn = +-1: exact negation)
+    const tcx x{tf_sub(d, tf{sgn * w4.x, sgn * w4.y}), tf{-sgn * w4.z, -sgn * w4.w}};
+    const tf den = tf_add(tf_mul(x.re, x.re), tf_mul(x.im, x.im));
+    return tc_rmul(tc_mulc(x, a), tf_recip(den)); // conj(x) a / |x|^2
+}
+
+// max(|Re P|, |Im P|) in FP32 from the exact two-float x
+__device__ __forceinline__ float gpp_pole_mag(float4 a4, float4 w4, tf d, float sgn)
+{
+    const float xr = tf_sub(d, tf{sgn * w4.x, sgn * w4.y}).hi, xi = -sgn * w4.z;
+    const float r = __frcp_rn(__fmaf_rn(xr, xr, __fmul_rn(xi, xi)));
+    const float pr = __fmaf_rn(a4.x, xr, __fmul_rn(a4.z, xi)), pi = __fmaf_rn(a4.z, xr, -__fmul_rn(a4.x, xi));
+    return fmaxf(fabsf(pr), fabsf(pi)) * r;
+}
+
+__device__ __forceinline__ int tf_expo(float a)
+{
+    if (!(a > 0.0f)) return kOzNoColumn;
+    const int be = (int)((__float_as_uint(a) >> 23) & 0xff);
+    return (be == 0 ? -127 : be - 127) + 2;
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi)
+{
+    return (__float_as_uint(lo) >> 16) | (__float_as_uint(hi) & 0xffff0000u);
+}
+
+// Digits of round(v 2^sh) for v = Re P and Im P side by side (sc = (s1, s2), s1 s2 = 2^sh),
+// stored as they come: slice i of row zr (u32 pairs, slice planes plane32 apart), element g.
+__device__ __forceinline__ float tf_low(tf v, float s1, float s2, float &t)
+{
+    const float vh = __fmul_rn(__fmul_rn(v.hi, s1), s2);
+    t = rintf(__fmul_rn(vh, 0x1p-24f));
+    return __fadd_rn(rintf(__fmaf_rn(-0x1p24f, t, vh)), rintf(__fmul_rn(__fmul_rn(v.lo, s1), s2)));
+}
+
+__device__ __forceinline__ void tf_digits_store(tcx p, float s1, float s2, int s, uint32_t *zr, int64_t plane32,
+                                                int64_t g)
+{
+    float tr, ti;
+    float Lr = tf_low(p.re, s1, s2, tr), Li = tf_low(p.im, s1, s2, ti);
+    for (int i = s - 1; i >= 1; --i) {
+        if (i == s - 5) { // four digits taken from the low parts: carry into the high parts
+            Lr = __fadd_rn(Lr, tr);
+            Li = __fadd_rn(Li, ti);
+        }
+        const float qr = rintf(__fmul_rn(Lr, 0.015625f)), qi = rintf(__fmul_rn(Li, 0.015625f));
+        zr[i * plane32 + g] = bf16_pair(__fmaf_rn(-64.0f, qr, Lr), __fmaf_rn(-64.0f, qi, Li));
+        Lr = qr;
+        Li = qi;
+    }
+    if (s <= 5) { // at most four digits taken: the high parts join the top digit (zero for s <= 4)
+        Lr = __fadd_rn(Lr, tr);
+        Li = __fadd_rn(Li, ti);
+    }
+    zr[g] = bf16_pair(Lr, Li);
+}
+
+template <int NE>
+__global__ void __launch_bounds__(256, NE > 4 ? 3 : 4) gpp_prep_split_kernel(const float4 *__restrict__ At,
+                                                                const float4 *__restrict__ Wt, int ng, GppEnergies en,
+                                                                int cnt, float sgn, int s, int64_t kpad,
+                                                                int64_t zstride, uint16_t *__restrict__ Z,
+                                                                int *__restrict__ E)
+{
+    __shared__ int red[8][NE];
+    __shared__ float2 dsm[NE];
+    __shared__ float2 ssm[NE];
+    const int c = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < NE) {
+        const tf t = tf_from(threadIdx.x < cnt ? en.d[threadIdx.x] : 0.0);
+        dsm[threadIdx.x] = make_float2(t.hi, t.lo);
+    }
+    __syncthreads();
+    const float4 *a = At + (int64_t)c * ng, *w = Wt + (int64_t)c * ng;
+    float mx[NE];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) mx[j] = 0.0f;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const float4 a4 = a[g], w4 = w[g];
+#pragma unroll
+        for (int j = 0; j < NE; ++j)
+            if (j < cnt) mx[j] = fmaxf(mx[j], gpp_pole_mag(a4, w4, tf{dsm[j].x, dsm[j].y}, sgn));
+    }
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+        float v = mx[j];
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) red[wid][j] = __float_as_int(v);
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+        float v = 0.0f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v = fmaxf(v, __int_as_float(red[k][threadIdx.x]));
+        const int e = tf_expo(v * (1.0f + 0x1p-10f));
+        E[(int64_t)threadIdx.x * ng + c] = e;
+        // 2^sh in two factors, each inside the FP32 exponent range
+        const int sh = max(-250, min(250, kOzBeta * s - e));
+        ssm[threadIdx.x] = make_float2(__int_as_float((127 + sh / 2) << 23), __int_as_float((127 + sh - sh / 2) << 23));
+    }
+    __syncthreads();
+    const int64_t plane = (int64_t)ng * kpad;
+    for (int64_t g = threadIdx.x; g < kpad / 2; g += blockDim.x) {
+        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), w4 = make_float4(1.f, 0.f, 0.f, 0.f);
+        if (g < ng) {
+            a4 = a[g];
+            w4 = w[g];
+        }
+        for (int j = 0; j < cnt; ++j) {
+            // padding entries (g >= ng) have a = 0, so p = 0 there
+            const tcx p = gpp_pole_tf(a4, w4, tf{dsm[j].x, dsm[j].y}, sgn);
+            const float2 sc = ssm[j];
+            tf_digits_store(p, sc.x, sc.y, s, (uint32_t *)(Z + j * zstride + (int64_t)c * kpad), plane >> 1, g);
+        }
     }
 }
 
@@ -320,9 +476,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                 const OzJob &jb = jobs[oz_find_job(jobs, njobs, item)];
                 int I, J;
                 oz_tile<GEN, BN>(jb, item - jb.item_start, I, J);
+                for (int k0 = 0; k0 < jb.nk && ok; k0 += kOzKSeg)
                 for (int t = 2; t <= jb.s + 1 && ok; ++t)
                     for (int i = 1; i < t && ok; ++i)
-                        for (int kb = 0; kb < jb.nk; ++kb, ++it) {
+                        for (int kb = k0; kb < min(jb.nk, k0 + kOzKSeg); ++kb, ++it) {
                             const int st = it % ST;
                             const uint32_t n = it / ST;
                             if (!bar_wait(&empty[st], (n & 1) ^ 1)) { ok = false; break; }
@@ -338,6 +495,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
             uint32_t it = 0, grp = 0;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const OzJob &jb = jobs[oz_find_job(jobs, njobs, item)];
+                for (int k0 = 0; k0 < jb.nk && ok; k0 += kOzKSeg)
                 for (int t = 2; t <= jb.s + 1 && ok; ++t, ++grp) {
                     const uint32_t b = grp & 1, u = grp >> 1;
                     if (!bar_wait(&tempty[b], (u & 1) ^ 1)) { ok = false; break; }
@@ -345,7 +503,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                     const uint32_t d = tbase + b * BN;
                     bool first = true;
                     for (int i = 1; i < t && ok; ++i)
-                        for (int kb = 0; kb < jb.nk; ++kb, ++it) {
+                        for (int kb = k0; kb < min(jb.nk, k0 + kOzKSeg); ++kb, ++it) {
                             const int st = it % ST;
                             if (!bar_wait(&full[st], (it / ST) & 1)) { ok = false; break; }
                             tc_fence_after();
@@ -378,6 +536,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                 const int pr = I * kOzBM + r;     // output row
                 const int Ea = pr < jb.rows_a ? __ldg(jb.E + pr) : kOzNoColumn;
                 double *orow = jb.out + (int64_t)pr * jb.ldo;
+                for (int k0 = 0; k0 < jb.nk && ok; k0 += kOzKSeg)
                 for (int t = 2; t <= jb.s + 1; ++t, ++grp) {
                     const uint32_t b = grp & 1, u = grp >> 1;
                     const bool got = bar_wait(&tfull[b], u & 1);
@@ -416,6 +575,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                 const int g = I * 64 + (r >> 1);      // complex row G
                 const int Eg = g < ng ? __ldg(jb.E + g) : kOzNoColumn;
                 double *crow = jb.chi + 2 * ((int64_t)g * ng) + odd;
+                for (int k0 = 0; k0 < jb.nk && ok; k0 += kOzKSeg)
                 for (int t = 2; t <= jb.s + 1; ++t, ++grp) {
                     const uint32_t b = grp & 1, u = grp >> 1;
                     const bool got = bar_wait(&tfull[b], u & 1);
@@ -528,18 +688,36 @@ cudaError_t launch_oz_gemm_jobs(int bn, const OzJob *jobs, int njobs, int nitems
 }
 
 cudaError_t launch_oz_split_rows(const double2 *A, int64_t rows, int ka, int s, int64_t kpad, void *ZA, int *EA,
-                                 cudaStream_t st)
+                                 cudaStream_t st, bool conj)
 {
     if (rows == 0) return cudaSuccess;
-    oz_split_rows_kernel<<<(unsigned)rows, 256, 0, st>>>(A, rows, ka, s, kpad, (uint16_t *)ZA, EA);
+    if (conj) oz_split_rows_kernel<true><<<(unsigned)rows, 256, 0, st>>>(A, rows, ka, s, kpad, (uint16_t *)ZA, EA);
+    else oz_split_rows_kernel<false><<<(unsigned)rows, 256, 0, st>>>(A, rows, ka, s, kpad, (uint16_t *)ZA, EA);
     return cudaGetLastError();
 }
 
-cudaError_t launch_oz_split_cols(const double2 *B, int ka, int nout, int s, int64_t kpad, void *ZB, int *EB,
-                                 cudaStream_t st)
+cudaError_t launch_oz_split_cols(const double2 *B, int ka, int nout, int64_t sk, int64_t sj, bool conj, int s,
+                                 int64_t kpad, void *ZB, int *EB, cudaStream_t st)
 {
     if (nout == 0) return cudaSuccess;
-    oz_split_cols_kernel<<<(unsigned)nout, 256, 0, st>>>(B, ka, nout, s, kpad, (uint16_t *)ZB, EB);
+    if (conj) oz_split_cols_kernel<true><<<(unsigned)nout, 256, 0, st>>>(B, ka, nout, sk, sj, s, kpad, (uint16_t *)ZB, EB);
+    else oz_split_cols_kernel<false><<<(unsigned)nout, 256, 0, st>>>(B, ka, nout, sk, sj, s, kpad, (uint16_t *)ZB, EB);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gpp_prep_split(const float4 *At, const float4 *Wt, int ng, const double *d, int cnt, float sgn,
+                                  int s, int64_t kpad, int64_t zstride, void *Z, int *E, cudaStream_t st)
+{
+    if (ng == 0 || cnt == 0) return cudaSuccess;
+    if (cnt > kGppMaxE) return cudaErrorInvalidValue;
+    GppEnergies en{};
+    for (int j = 0; j < cnt; ++j) en.d[j] = d[j];
+    if (cnt <= 4)
+        gpp_prep_split_kernel<4><<<(unsigned)ng, 256, 0, st>>>(At, Wt, ng, en, cnt, sgn, s, kpad, zstride,
+                                                               (uint16_t *)Z, E);
+    else
+        gpp_prep_split_kernel<kGppMaxE><<<(unsigned)ng, 256, 0, st>>>(At, Wt, ng, en, cnt, sgn, s, kpad, zstride,
+                                                                      (uint16_t *)Z, E);
     return cudaGetLastError();
 }
 
