@@ -276,8 +276,10 @@ GW_API gw_status gw_chi0_epsilon_inverse(gw_chi0 *h, int ng, int nw, const doubl
  *   vcoul   device float64 [ng], the Coulomb diagonal v_G.
  *   ne, E   host double [ne], the energy grid (eV); ne = 0 is a no-op.
  *   sigma   device complex128 [ne][nsig][nsig], written in full (zero when nb = 0).
- * Work buffers: two [ng][ng] complex matrices plus, in split mode, the slices of up to 16
- * energies' P (7 slices: 56 ng^2 bytes each), held by the handle until destroy.
+ * Work buffers, held by the handle until destroy: FP64 mode two [ng][ng] complex128 matrices;
+ * split mode the pole parameters transposed in two-float form (32 ng^2 bytes), the BF16 slices
+ * of P^T for a batch of energies (28 ng^2 bytes each at 7 slices, at most 32 GiB or a quarter of
+ * mem_budget_bytes when set) and X^T for 16 energies (16 nsig ng complex128 plus its slices).
  * GW_ERR_ARG for sizes out of range, null or misaligned (16 bytes) complex pointers, non-finite
  * energies; other errors as gw_chi0_compute.
  */
