@@ -215,8 +215,11 @@ TRAFFIC = {
                      "source": "ncu dram__bytes_read+write, contract_f64_kernel, p1_48cube_onechunk"},
     "pair_mtxel": {"bytes_per_launch": 3.112e9 + 1.486e9,
                    "source": "ncu dram__bytes_read+write, pair_kernel_tf_ct<48>, p1_48cube_onechunk"},
-    "ozaki_gemm": {"bytes_per_launch": 7.32e9 + 0.219e9,
-                   "source": "ncu dram__bytes_read+write, oz_gemm_kernel (s = 7), p1_48cube_onechunk"},
+    # the overlapped step's launch (2-deep TMA ring, on the second stream); the single-stream
+    # launch (4-deep ring) has no capture of the kernel as it stands
+    "ozaki_gemm": {"bytes_per_launch": 8.033695e9 + 0.220375e9,
+                   "source": "ncu dram__bytes_read+write, oz_gemm_kernel (s = 7, 2-deep ring), p1_48cube_onechunk"},
+    "ozaki_gemm_single_stream": {"bytes_per_launch": None, "source": None},
 }
 
 
@@ -413,8 +416,9 @@ def roofline_pair(cfg, prob, res):
             "traffic_source": TRAFFIC.get("pair_mtxel", {}).get("source")}
 
 
-def roofline_for(cfg, prec, nslices, res):
+def roofline_for(cfg, prec, nslices, res, single_stream=False):
     kname = "contract_f64" if prec == "fp64" else "ozaki_gemm"
+    tkey = kname + ("_single_stream" if single_stream and prec != "fp64" else "")
     kms, kn = res["timing"].get(kname, (0.0, 0))
     nchunk = -(-cfg.npairs // cfg.pair_chunk)
     per_launch_flops = 4.0 * cfg.ng * (cfg.ng + 1) * cfg.npairs / nchunk
@@ -425,10 +429,10 @@ def roofline_for(cfg, prec, nslices, res):
     achieved = per_launch_flops / (kms / kn * 1e-3) * 1e-12 if kn else None
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": TRAFFIC.get(kname, {}).get("bytes_per_launch"), "kernel": kname,
+            "traffic": TRAFFIC.get(tkey, {}).get("bytes_per_launch"), "kernel": kname,
             "launches": kn, "ms_per_launch": kms / kn if kn else None, "flops_per_launch": per_launch_flops,
             "peak_source": peak_src, "share_of_step": kms / res["total_ms"] if res["total_ms"] else None,
-            "traffic_source": TRAFFIC.get(kname, {}).get("source"),
+            "traffic_source": TRAFFIC.get(tkey, {}).get("source"),
             "fp64_probe_peaks_tflops": {"dmma": 1.055, "dfma": 1.204}}
 
 
@@ -461,7 +465,7 @@ def ours(args):
     if args.prec == "ozaki" and args.path == "stream" and mtxel == "twofloat":
         a = run_mode(args, cfg, prob, dev, args.prec, args.nslices, mtxel, 2, 1, False, world, single_stream=True)
         alone = {"ms_per_step": a["ms_per_step"], "value": a["value"], "pair": roofline_pair(cfg, prob, a),
-                 "contraction": roofline_for(cfg, args.prec, args.nslices, a)}
+                 "contraction": roofline_for(cfg, args.prec, args.nslices, a, single_stream=True)}
     # the CPU baseline leg (rank 0): the oracle timed on a bounded sample, and its reference block
     # for the error check
     err, blk = None, None
