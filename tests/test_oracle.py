@@ -417,7 +417,7 @@ def test_jvp_central_differences(w):
     assert rel(got, (chi(h) - chi(-h)) / (2 * h)) < 1e-7
 
 
-# ------------------------------------------------------------------ off-diagonal GPP self-energy
+# ------------------------------------------------------------------ off-diagonal plasmon-pole self-energy
 
 def _sigma_by_frequency_integral(B, eps, occupied, wt, eta, E, n=400001, scale=10.0):
     """(i/2pi) int dw G(E + w) W_c(w) for one band and one plane wave, by quadrature on the real
