@@ -7,18 +7,20 @@
 
 namespace gw {
 
-// Threads per block: warps own whole slab lines, and 6 warps give every radix-4 stage of
-// a 48-point line a full round of lanes (8 lines x 12 butterflies = 3 x 32).
+// Threads per block: warps own whole slab lines.  6 warps give every radix-4 stage of a
+// 48-point line a full round of lanes (8 lines x 12 butterflies = 3 x 32); 5 warps of 8
+// 40-point lines give the radix-5 stage two full rounds (8 x 8 = 2 x 32) and measured 18 %
+// faster than 8 warps of 5 lines (27.5 vs 33.4 ms per 32768 pairs on 40^3).
 template <int N>
 constexpr int pair_threads()
 {
-    return N % 6 == 0 ? 192 : 256;
+    return N % 6 == 0 ? 192 : (N % 5 == 0 ? 160 : 256);
 }
 // Resident blocks per SM the register budget is sized for.
 template <int N>
 constexpr int pair_min_blocks()
 {
-    return N <= 48 ? (pair_threads<N>() == 192 ? 4 : 2) : 1;
+    return N <= 48 ? (pair_threads<N>() == 256 ? 2 : 4) : 1;
 }
 // The second full i2 stage (when the plan has one) runs in place when a lane's inputs for
 // all its butterflies fit in registers (at most 16 complex values).
