@@ -243,10 +243,82 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(const double2 *__restrict
     }
 }
 
+// The same back-projection in two-float arithmetic on the FP32 pipes (bands held in two-float
+// form): conj(g_p) converted once per pair, the i0 sums per cell and both line transforms in
+// hi + lo pairs; H is written in two-float form (16 bytes a point, as in FP64).
+__global__ void __launch_bounds__(256) adj_pair_tf_kernel(const double2 *__restrict__ Gb, PairPlan pp,
+                                                          const int *__restrict__ cell_start,
+                                                          const int *__restrict__ cell_g, int ncell, TfConsts kc,
+                                                          tf sc, float4 *__restrict__ H)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n0 = pp.n[0], n1 = pp.n[1], n2 = pp.n[2];
+    const int ns = n1 * n2;
+    float4 *a = (float4 *)smem, *b = a + ns;
+    float4 *tw0 = b + ns, *tw1 = tw0 + n0, *tw2 = tw1 + n1;
+    float4 *gs = tw2 + n2; // [ng] conj(g_p), two-float
+    int *kz = (int *)(gs + pp.ng);
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) tw0[i] = pp.ax[0].twf[i];
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = pp.ax[1].twf[i];
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = pp.ax[2].twf[i];
+    for (int i = threadIdx.x; i < pp.K2; i += blockDim.x) kz[i] = pp.kz[i];
+    const int64_t p = blockIdx.x;
+    for (int g = threadIdx.x; g < pp.ng; g += blockDim.x) {
+        const double2 x = Gb[p * pp.ng + g];
+        const tf re = tf_from(x.x), im = tf_from(-x.y);
+        gs[g] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    __syncthreads();
+    float4 *out = H + p * (int64_t)n0 * ns;
+    for (int i0 = 0; i0 < n0; ++i0) {
+        for (int i = threadIdx.x; i < pp.K2 * n1; i += blockDim.x) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        for (int cidx = threadIdx.x; cidx < ncell; cidx += blockDim.x) {
+            tcx acc{{0.f, 0.f}, {0.f, 0.f}};
+            int cell_pos = 0;
+            for (int t = cell_start[cidx]; t < cell_start[cidx + 1]; ++t) {
+                const int g = cell_g[t];
+                const int pk = pp.gpack[g];
+                const int k0 = pk & 255;
+                cell_pos = (pk >> 16) * n1 + ((pk >> 8) & 255);
+                acc = tc_add(acc, tc_mul(tc_load(gs + g), tc_load(tw0 + (k0 * i0) % n0)));
+            }
+            tc_store(a + cell_pos, acc);
+        }
+        __syncthreads();
+        float4 *r = tfft_lines(a, b, pp.K2, n1, 1, pp.ax[1], tw1, kc); // along i1, K2 lines
+        float4 *o = (r == a) ? b : a;
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) o[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        for (int i = threadIdx.x; i < pp.K2 * n1; i += blockDim.x) {
+            const int q = i / n1, i1 = i - q * n1;
+            o[i1 * n2 + kz[q]] = r[i];
+        }
+        __syncthreads();
+        const float4 *t = tfft_lines(o, r, n1, n2, 1, pp.ax[2], tw2, kc); // along i2
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            const tcx z = tc_load(t + i);
+            tc_store(out + (int64_t)i0 * ns + i, tcx{tf_mul(z.re, sc), tf_neg(tf_mul(z.im, sc))});
+        }
+        __syncthreads();
+    }
+}
+
 cudaError_t launch_adj_pair(const double2 *Gb, int64_t P, const PairPlan &pp, const int *cell_start,
-                            const int *cell_g, int ncell, double2 *H, cudaStream_t st)
+                            const int *cell_g, int ncell, double2 *H, bool twofloat, cudaStream_t st)
 {
     if (P == 0) return cudaSuccess;
+    if (twofloat) {
+        const size_t sm = sizeof(float4) * (2 * (size_t)pp.n[1] * pp.n[2] + pp.n[0] + pp.n[1] + pp.n[2] + pp.ng) +
+                          sizeof(int) * pp.K2;
+        cudaError_t e = cudaFuncSetAttribute(adj_pair_tf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        const double inv = 1.0 / ((double)pp.n[0] * pp.n[1] * pp.n[2]);
+        const float hi = (float)inv;
+        adj_pair_tf_kernel<<<(unsigned)P, 256, sm, st>>>(Gb, pp, cell_start, cell_g, ncell, tf_consts(),
+                                                         tf{hi, (float)(inv - (double)hi)}, (float4 *)H);
+        return cudaGetLastError();
+    }
     size_t sm = sizeof(double2) * (2 * (size_t)pp.n[1] * pp.n[2] + pp.n[0] + pp.n[1] + pp.n[2] + pp.ng) +
                 sizeof(int) * pp.K2;
     cudaError_t e = cudaFuncSetAttribute(adj_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -290,9 +362,46 @@ __global__ void adj_val_kernel(const void *__restrict__ psic, int v0, const doub
     pbv[(int64_t)(v0 + vl) * nr + i] = acc;
 }
 
+// Two-float forms of the two products (bands and H in two-float form): the sums over the
+// chunk's bands run on the FP32 pipes and are added once into the FP64 accumulators.
+__global__ void adj_cond_tf_kernel(const float4 *__restrict__ psiv, int v0, int nvc, const float4 *__restrict__ H,
+                                   int nc, int64_t nr, double2 *__restrict__ pbc)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= nr) return;
+    tcx acc{{0.f, 0.f}, {0.f, 0.f}};
+    for (int v = 0; v < nvc; ++v)
+        acc = tc_add(acc, tc_mul(tc_load(psiv + (int64_t)(v0 + v) * nr + i), tc_load(H + ((int64_t)v * nc + c) * nr + i)));
+    double2 &o = pbc[(int64_t)c * nr + i];
+    o = make_double2(o.x + tf_to_d(acc.re), o.y + tf_to_d(acc.im));
+}
+
+__global__ void adj_val_tf_kernel(const float4 *__restrict__ psic, int v0, const float4 *__restrict__ H, int nc,
+                                  int64_t nr, double2 *__restrict__ pbv)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int vl = blockIdx.y;
+    if (i >= nr) return;
+    tcx acc{{0.f, 0.f}, {0.f, 0.f}};
+    for (int c = 0; c < nc; ++c) // psi_c conj(H) = conj(conj(psi_c) H)
+        acc = tc_add(acc, tc_mulc(tc_load(psic + (int64_t)c * nr + i), tc_load(H + ((int64_t)vl * nc + c) * nr + i)));
+    double2 &o = pbv[(int64_t)(v0 + vl) * nr + i];
+    o = make_double2(o.x + tf_to_d(acc.re), o.y - tf_to_d(acc.im));
+}
+
 cudaError_t launch_adj_products(const void *psiv, const void *psic, int v0, int nvc, int nc, const double2 *H,
                                 int64_t nr, bool tf, double2 *pbv, double2 *pbc, cudaStream_t st)
 {
+    if (tf) {
+        dim3 gc((unsigned)((nr + 255) / 256), nc);
+        adj_cond_tf_kernel<<<gc, 256, 0, st>>>((const float4 *)psiv, v0, nvc, (const float4 *)H, nc, nr, pbc);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dim3 gv((unsigned)((nr + 255) / 256), nvc);
+        adj_val_tf_kernel<<<gv, 256, 0, st>>>((const float4 *)psic, v0, (const float4 *)H, nc, nr, pbv);
+        return cudaGetLastError();
+    }
     dim3 gc((unsigned)((nr + 255) / 256), nc);
     adj_cond_kernel<<<gc, 256, 0, st>>>(psiv, v0, nvc, H, nc, nr, tf, pbc);
     cudaError_t e = cudaGetLastError();

@@ -98,7 +98,7 @@ gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, dou
         }
         {
             Scope sc(h, "adj_pair");
-            ACK(gw::launch_adj_pair(Yb, cnt, pp, cs, cg, ncell, Hb, h->st), "back-projection");
+            ACK(gw::launch_adj_pair(Yb, cnt, pp, cs, cg, ncell, Hb, tf, h->st), "back-projection");
         }
         {
             Scope sc(h, "adj_products");

@@ -163,6 +163,7 @@ __device__ __forceinline__ void tc_store(float4 *p, tcx a) { *p = make_float4(a.
 struct TfConsts {
     tf sin60, c1, s1, c2, s2, rs2;
 };
+TfConsts tf_consts(); // host: the constants above from their FP64 values (mtxel.cu)
 __device__ __forceinline__ tf tf_from(double x)
 {
     float h = (float)x;
