@@ -182,6 +182,48 @@ def oracle_sigma_rows(p, n0, eidx, rows):
                  "sample": f"one (n, E): P^n(E) formed and {len(rows)} rows of Sigma, {dt:.1f} s"}
 
 
+def oracle_adjoint_sample(prob, W, nvs):
+    """The oracle adjoint on nvs valence bands x all conduction bands, scaled to every pair."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.adjoint(prob.gpsi, prob.cv[:nvs], prob.ev[:nvs], prob.gpsi, prob.cc, prob.ec, prob.gchi, W, 0.0)
+    dt = time.perf_counter() - t0
+    nv, nc = len(prob.ev), len(prob.ec)
+    return {"value": dt * nv / nvs, "unit": "s per adjoint", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{nvs} valence x {nc} conduction bands ({nvs * nc} of {nv * nc} pairs): {dt:.1f} s, "
+                      "scaled by the pair count"}
+
+
+def oracle_chi_sample(prob, npairs, omegas, basis=None, eta=None):
+    """The oracle on npairs pairs x the full sphere: M by the G-space convolution, then chi at the
+    given frequencies (in the subspace when basis is given, on the real axis when eta is given).
+    Returns (seconds for M, seconds per frequency, description)."""
+    import oracle
+    nc = len(prob.ec)
+    nvs = max(1, npairs // nc)
+    ncs = min(nc, npairs)
+    t0 = time.perf_counter()
+    M = oracle.m_conv(prob.gpsi, prob.cv[:nvs], prob.gpsi, prob.cc[:ncs], prob.gchi)
+    t1 = time.perf_counter()
+    for w in omegas:
+        if eta is not None:
+            oracle.chi0_real(M, oracle.delta_real(prob.ev[:nvs], prob.ec[:ncs], w, eta))
+        elif basis is not None:
+            oracle.chi0_subspace(M, oracle.delta(prob.ev[:nvs], prob.ec[:ncs], w), basis)
+        else:
+            oracle.chi0(M, oracle.delta(prob.ev[:nvs], prob.ec[:ncs], w))
+    t2 = time.perf_counter()
+    return (t1 - t0, (t2 - t1) / max(1, len(omegas)),
+            f"{nvs * ncs} pairs x the full sphere, {len(omegas)} frequencies", oracle.threads())
+
+
+def oracle_epsilon_sample(chi, v):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.epsilon_inverse(chi, v)
+    return time.perf_counter() - t0, oracle.threads()
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -400,6 +442,56 @@ def kept_columns(prob, n2):
 FP32_PEAK_TOPS = 152 * 128 * 2.070e9 * 1e-12  # lanes x max SM clock: FP32 operations per second, in T
 
 
+def _full_ops(n):
+    """A full two-float line transform of n points, every stage renormalised."""
+    ops, ns = 0, 1
+    for r in _rad_plan(n):
+        ops += (n // r) * _bfly_ops(r, ns > 1)
+        ns *= r
+    return ops
+
+
+def backprojection_ops_per_pair(cfg, k2):
+    """FP32 operations of the two-float adjoint back-projection per pair: per i0 slab the sphere's
+    sums per (k1, k2) cell (a complex product and a complex sum per point), K2 lines along i1,
+    N1 lines along i2, the scaled conjugate of the slab."""
+    n0, n1, n2 = cfg.grid
+    return n0 * (cfg.ng * (_CMUL + 22) + k2 * _full_ops(n1) + n1 * _full_ops(n2) + n1 * n2 * 14)
+
+
+def _hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    pk = json.load(open(path)) if os.path.exists(path) else {}
+    return (pk["hbm_gbs"], "measured") if "hbm_gbs" in pk else (6800.0, "fallback")
+
+
+def oz_kpad(ka):
+    """Real K extent of a general split product with ka complex inner entries (padded to 64)."""
+    return (2 * ka + 63) // 64 * 64
+
+
+def mode_roofline(bound, kernel, work, ms, unit_of_work, prec="ozaki"):
+    """Roofline object of one kernel in a side mode: work (FP32 operations, low-precision flops or
+    bytes) over its measured time."""
+    if not ms:
+        return None
+    if bound == "alu":
+        peak, unit, src = FP32_PEAK_TOPS, "FP32 Tops/s", "152 SMs x 128 FP32 lanes x 2070 MHz"
+        ach = work / (ms * 1e-3) * 1e-12
+    elif bound == "hbm":
+        peak, src = _hbm_peak()
+        unit, src = "GB/s", f"{src} copy bandwidth"
+        ach = work / (ms * 1e-3) * 1e-9
+    else:
+        peak, src = peak_for(prec)
+        unit = "TFLOP/s"
+        ach = work / (ms * 1e-3) * 1e-12
+    return {"bound": bound, "kernel": kernel, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "traffic": None, "ms": ms, "work": work, "unit_of_work": unit_of_work, "peak_source": src}
+
+
+
+
 def roofline_pair(cfg, prob, res):
     kms, kn = res["timing"].get("pair_mtxel", (0.0, 0))
     nchunk = -(-cfg.npairs // cfg.pair_chunk)
@@ -591,9 +683,26 @@ def adjoint(args):
         L, dEv, dEc, dcv, dcc = h.adjoint(0, Wd)
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / args.steps
+    kms = {k: v[0] / args.steps for k, v in h.timing().items()}
+    P, nr = cfg.nv * cfg.nc, cfg.grid[0] * cfg.grid[1] * cfg.grid[2]
+    s = args.nslices
+    roofs = {}
+    if (args.mtxel or "twofloat") == "twofloat":
+        roofs["back_projection"] = mode_roofline(
+            "alu", "adj_pair_tf_kernel", backprojection_ops_per_pair(cfg, kept_columns(prob, cfg.grid[2])) * P,
+            kms.get("adj_pair"), "FP32 operations of the two-float back-projection (bench.backprojection_ops_per_pair) x pairs")
+        roofs["products"] = mode_roofline("hbm", "adj_cond_tf_kernel + adj_val_tf_kernel", 2 * 16.0 * P * nr,
+                                          kms.get("adj_products"), "H read once by each product kernel, 16 B per point")
+    if args.prec == "ozaki":
+        roofs["y_mw"] = mode_roofline("tensor", "oz_gemm_kernel (general product Y = M W)",
+                                      s * (s + 1) / 2 * 2.0 * P * (2 * cfg.ng) * oz_kpad(cfg.ng), kms.get("adj_zgemm"),
+                                      "low-precision flops of the kept slice pairs")
+    dom = max(roofs, key=lambda k: roofs[k]["ms"] if roofs[k] else 0.0) if roofs else None
+    cpu = None if args.no_cpu_baseline else oracle_adjoint_sample(prob, W, 1)
     print(json.dumps({"workload": "L = Re Tr(W chi0), 40^3, 96+768 bands, N_Gpsi=4500, N_G=1500",
                       "prec": args.prec, "nslices": args.nslices, "s_per_adjoint": sec, "L": L,
-                      "timing_ms": {k: v[0] / args.steps for k, v in h.timing().items()}}), flush=True)
+                      "timing_ms": kms, "roofline": roofs.get(dom) if dom else None, "rooflines": roofs,
+                      "cpu_baseline": cpu}), flush=True)
 
 
 def subspace(args):
@@ -640,7 +749,27 @@ def subspace(args):
     dk = float(np.linalg.norm(sub[k].cpu().numpy() - proj) / np.linalg.norm(proj))
     approx = float(np.linalg.norm(Cn @ sub[k].cpu().numpy() @ Cn.conj().T - fk) / np.linalg.norm(fk))
     P = cfg.npairs
+    s = args.nslices
+    k2, k12 = kept_columns(prob, cfg.grid[2]), cells(prob, cfg.grid)
+    roofs = {"pair_elements": mode_roofline("alu", "pair_kernel_tf_ct<48>", twofloat_ops_per_pair(cfg, k2, k12) * P,
+                                            kms.get("pair_mtxel"), "FP32 operations of the pair kernel x pairs")}
+    if args.prec == "ozaki":
+        roofs["contraction"] = mode_roofline("tensor", "oz_gemm_kernel (N_Eig columns)",
+                                             s * (s + 1) / 2 * 4.0 * neig ** 2 * P * len(om19),
+                                             kms.get("ozaki_gemm"), "low-precision flops of the kept slice pairs")
+        roofs["projection"] = mode_roofline("tensor", "oz_gemm_kernel (general product M C_s)",
+                                            s * (s + 1) / 2 * 2.0 * P * (2 * neig) * oz_kpad(cfg.ng),
+                                            kms.get("subspace_projection"), "low-precision flops of the kept slice pairs")
+    cpu = None
+    if not args.no_cpu_baseline:
+        tm, tw, how, cores = oracle_chi_sample(prob, 1024, om19[:2], basis=Cn)
+        npair = (1024 // cfg.nc) * cfg.nc
+        cpu = {"value": 1e3 * (tm + tw * len(om19)) * P / npair, "unit": "ms for 19 frequencies in the subspace",
+               "cores": cores, "kind": "oracle",
+               "sample": f"{how}: M {tm:.1f} s, {tw:.1f} s per frequency, scaled by the pair count"}
     print(json.dumps({
+        "roofline": max((r for r in roofs.values() if r), key=lambda r: r["ms"], default=None), "rooflines": roofs,
+        "cpu_baseline": cpu,
         "workload": f"{cfg.name}: 48^3, {cfg.nv}+{cfg.nc} bands, N_G={cfg.ng}, N_Eig={neig} (20 %), "
                     "19 Gauss-Legendre imaginary frequencies on [0,100] eV",
         "prec": args.prec, "nslices": args.nslices, "mtxel": mtxel,
@@ -673,15 +802,33 @@ def epsilon(args):
     einv = h.epsilon_inverse(chi, v)
     e1.record()
     torch.cuda.synchronize()
-    kms = {k: val[0] for k, val in h.timing(reset=True).items()}
+    tm = h.timing(reset=True)
+    kms = {k: val[0] for k, val in tm.items()}
+    h_launches = {k: val[1] for k, val in tm.items()}
     ms = e0.elapsed_time(e1)
     eye = torch.eye(cfg.ng, dtype=torch.complex128, device="cuda")
     res = [float(torch.linalg.norm((eye - v[:, None] * chi[i]) @ einv[i] - eye) / cfg.ng ** 0.5)
            for i in range(len(om))]
+    steps = h_launches.get("eps_products", 0)
+    s = args.nslices
+    n = cfg.ng
+    if args.prec == "ozaki":
+        per_step = 2 * s * (s + 1) / 2 * 2.0 * n * (2 * n) * oz_kpad(n)
+        roof = mode_roofline("tensor", "oz_gemm_kernel (general products of the Newton-Schulz steps)",
+                             per_step * steps, kms.get("eps_products"), "low-precision flops of the kept slice pairs")
+    else:
+        roof = mode_roofline("tensor", "zgemm_kernel (DMMA)", 2 * 8.0 * n ** 3 * steps, kms.get("eps_products"),
+                             "FP64 flops of the two complex products per step", prec="fp64")
+    cpu = None
+    if not args.no_cpu_baseline:
+        dt, cores = oracle_epsilon_sample(chi[0].cpu().numpy(), v.cpu().numpy())
+        cpu = {"value": 1e3 * dt, "unit": "ms per frequency block", "cores": cores, "kind": "oracle",
+               "sample": f"one {n} x {n} block, dense inverse"}
     print(json.dumps({"workload": f"{cfg.name}: eps^-1 = [I - v chi(w)]^-1, N_G={cfg.ng}, w = {om} eV, "
                                   "v_G = 4 pi/|G|^2, chi from the 48^3 workload",
                       "prec": args.prec, "nslices": args.nslices, "ms_per_block": ms / len(om),
-                      "kernel_ms": kms, "residual_rms": res}), flush=True)
+                      "newton_schulz_steps": steps, "kernel_ms": kms, "residual_rms": res, "roofline": roof,
+                      "cpu_baseline": cpu}), flush=True)
 
 
 def extras(args):
@@ -709,14 +856,41 @@ def extras(args):
         torch.cuda.synchronize()
         return r, e0.elapsed_time(e1)
 
+    h.set_timing(True)
+    h.timing(reset=True)
     real, tr = timed(lambda: h.compute_real(0, [2.0, 15.0, 40.0], 0.1))
+    kr = h.timing(reset=True)  # warm-up call and timed call
     d, tj = timed(lambda: h.jvp(0, [0.0], dcv, dcc, dev, dec))
+    h.set_timing(False)
     (chi,), tc = timed(lambda: h.compute(0, [0.0]))
     h.sync()
     ci = (real[1] - real[1].conj().T) / 2j
+    s = args.nslices
+    P = cfg.npairs
+    nchunk = -(-P // cfg.pair_chunk)
+    k2, k12 = kept_columns(prob, cfg.grid[2]), cells(prob, cfg.grid)
+    half = lambda k: (kr[k][0] / 2, kr[k][1] // 2) if k in kr else (None, 0)
+    gms, gl = half("ozaki_gemm")
+    pms, _ = half("pair_mtxel")
+    roofs = {"pair_elements": mode_roofline("alu", "pair_kernel_tf_ct<48>", twofloat_ops_per_pair(cfg, k2, k12) * P,
+                                            pms, "FP32 operations of the pair kernel x pairs")}
+    if args.prec == "ozaki":
+        roofs["contraction"] = mode_roofline("tensor", "oz_gemm_kernel (sign-split real-axis contractions)",
+                                             s * (s + 1) / 2 * 4.0 * cfg.ng ** 2 * P / nchunk * gl, gms,
+                                             "low-precision flops of the kept slice pairs, per chunk contraction")
+    cpu = None
+    if not args.no_cpu_baseline:
+        tm, tw, how, cores = oracle_chi_sample(prob, 1024, [15.0], eta=0.1)
+        npair = (1024 // cfg.nc) * cfg.nc
+        cpu = {"value": 1e3 * (tm / 3 + tw) * P / npair, "unit": "ms per real-axis frequency (three share M)",
+               "cores": cores, "kind": "oracle",
+               "sample": f"{how}: M {tm:.1f} s, {tw:.1f} s per frequency, scaled by the pair count"}
     print(json.dumps({"workload": f"{cfg.name}: 48^3, {cfg.nv}+{cfg.nc} bands, N_G={cfg.ng}",
                       "prec": args.prec, "nslices": args.nslices, "ms_chi_imag_axis_1w": tc,
                       "ms_chi_real_axis_per_w": tr / 3, "ms_jvp_1w": tj,
+                      "kernel_ms_real_axis_3w": {k: v[0] / 2 for k, v in kr.items()},
+                      "roofline": max((r for r in roofs.values() if r), key=lambda r: r["ms"], default=None),
+                      "rooflines": roofs, "cpu_baseline": cpu,
                       "chi_I_max_eig_over_norm": float(torch.linalg.eigvalsh(ci).max() / torch.linalg.norm(ci)),
                       "jvp_hermitian": bool(torch.equal(d[0], d[0].conj().T))}), flush=True)
 

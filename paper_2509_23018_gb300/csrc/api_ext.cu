@@ -286,6 +286,7 @@ gw_status gw_chi0_epsilon_inverse(gw_chi0 *h, int ng, int nw, const double *chi,
         steps = std::max(steps, 1);
         CK(h, gw::launch_eps_init(X, ng, bmax, h->st), "X0");
         for (int k = 0; k < steps; ++k) {
+            Scope sp(h, "eps_products"); // two N_G^3 products per step: the launch count gives the steps
             if ((st = square_product(h, A, X, ng, T)) || (st = square_product(h, X, T, ng, Pm))) return st;
             CK(h, gw::launch_eps_step(X, Pm, (int64_t)nn, h->st), "Newton-Schulz step");
         }
