@@ -656,11 +656,30 @@ def batch(args):
     ms = e0.elapsed_time(e1) / args.steps
     P = cfg.nv * cfg.nc
     conv = sum(8.0 * n * n * P * 16 for n in ngs)
+    s = args.nslices
+    # a graph replay has no per-kernel timing: the contraction's rate over the whole call (stage (a)
+    # and the per-frequency slicing included) bounds it from below
+    roof = mode_roofline("tensor", "oz_gemm_kernel (16 per-frequency launches over all q), whole replay",
+                         sum(s * (s + 1) / 2 * 4.0 * n * n * P * 16 for n in ngs), ms,
+                         "low-precision flops of the kept slice pairs over the whole replay time")
+    cpu = None
+    if not args.no_cpu_baseline:
+        import types
+        q0 = types.SimpleNamespace(gpsi=b.gpsi, cv=b.cv[0], ev=b.ev[0], cc=b.cc, ec=b.ec, gchi=b.gchi[0])
+        tm, tw, how, cores = oracle_chi_sample(q0, 1024, list(b.omega[:2]))
+        npair = (1024 // cfg.nc) * cfg.nc
+        # M scales with pairs x N_G, chi with pairs x N_G^2: scale by the slots' sphere sizes
+        n0 = len(b.gchi[0])
+        est = sum((tm * n / n0 + tw * 16 * (n / n0) ** 2) * P / npair for n in ngs)
+        cpu = {"value": 1e3 * est, "unit": "ms per call", "cores": cores, "kind": "oracle",
+               "sample": f"q-point 0 (N_G = {n0}), {how}: M {tm:.1f} s, {tw:.1f} s per frequency, scaled by "
+                         "pairs, frequencies and each slot's N_G (M ~ N_G, chi ~ N_G^2)"}
     print(json.dumps({"workload": "64 q (4^3 grid) x 16 imaginary frequencies (Gauss-Legendre on [0,100] eV), "
                                   "40^3, 64+512 bands, N_Gpsi=8000, N_G in [300,3000]",
                       "prec": "ozaki", "nslices": args.nslices, "ms_per_call": ms, "ms_per_q": ms / len(b.qs),
                       "conv_tflops": conv / (ms * 1e-3) * 1e-12, "first_call_s": first,
-                      "tuning": h.tuning(), "timing_ms": {k: v[0] / args.steps for k, v in h.timing().items()}}),
+                      "tuning": h.tuning(), "timing_ms": {k: v[0] / args.steps for k, v in h.timing().items()},
+                      "roofline": roof, "cpu_baseline": cpu}),
           flush=True)
 
 
