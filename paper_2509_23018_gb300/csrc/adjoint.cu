@@ -246,13 +246,16 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(const double2 *__restrict
 // The same back-projection in two-float arithmetic on the FP32 pipes (bands held in two-float
 // form): conj(g_p) converted once per pair, the i0 sums per cell and both line transforms in
 // hi + lo pairs; H is written in two-float form (16 bytes a point, as in FP64).
+// N > 0: a cubic N^3 grid, the line transforms and index arithmetic specialised at compile time;
+// N = 0: any grid, runtime plans.
+template <int N>
 __global__ void __launch_bounds__(256) adj_pair_tf_kernel(const double2 *__restrict__ Gb, PairPlan pp,
                                                           const int *__restrict__ cell_start,
                                                           const int *__restrict__ cell_g, int ncell, TfConsts kc,
                                                           tf sc, float4 *__restrict__ H)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int n0 = pp.n[0], n1 = pp.n[1], n2 = pp.n[2];
+    const int n0 = N ? N : pp.n[0], n1 = N ? N : pp.n[1], n2 = N ? N : pp.n[2];
     const int ns = n1 * n2;
     float4 *a = (float4 *)smem, *b = a + ns;
     float4 *tw0 = b + ns, *tw1 = tw0 + n0, *tw2 = tw1 + n1;
@@ -286,7 +289,9 @@ __global__ void __launch_bounds__(256) adj_pair_tf_kernel(const double2 *__restr
             tc_store(a + cell_pos, acc);
         }
         __syncthreads();
-        float4 *r = tfft_lines(a, b, pp.K2, n1, 1, pp.ax[1], tw1, kc); // along i1, K2 lines
+        float4 *r;
+        if constexpr (N > 0) r = tfft_lines_ct<N>(a, b, pp.K2, n1, tw1, kc); // along i1, K2 lines
+        else r = tfft_lines(a, b, pp.K2, n1, 1, pp.ax[1], tw1, kc);
         float4 *o = (r == a) ? b : a;
         for (int i = threadIdx.x; i < ns; i += blockDim.x) o[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
@@ -295,7 +300,9 @@ __global__ void __launch_bounds__(256) adj_pair_tf_kernel(const double2 *__restr
             o[i1 * n2 + kz[q]] = r[i];
         }
         __syncthreads();
-        const float4 *t = tfft_lines(o, r, n1, n2, 1, pp.ax[2], tw2, kc); // along i2
+        const float4 *t;
+        if constexpr (N > 0) t = tfft_lines_ct<N>(o, r, n1, n2, tw2, kc); // along i2
+        else t = tfft_lines(o, r, n1, n2, 1, pp.ax[2], tw2, kc);
         for (int i = threadIdx.x; i < ns; i += blockDim.x) {
             const tcx z = tc_load(t + i);
             tc_store(out + (int64_t)i0 * ns + i, tcx{tf_mul(z.re, sc), tf_neg(tf_mul(z.im, sc))});
@@ -311,13 +318,21 @@ cudaError_t launch_adj_pair(const double2 *Gb, int64_t P, const PairPlan &pp, co
     if (twofloat) {
         const size_t sm = sizeof(float4) * (2 * (size_t)pp.n[1] * pp.n[2] + pp.n[0] + pp.n[1] + pp.n[2] + pp.ng) +
                           sizeof(int) * pp.K2;
-        cudaError_t e = cudaFuncSetAttribute(adj_pair_tf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
         const double inv = 1.0 / ((double)pp.n[0] * pp.n[1] * pp.n[2]);
         const float hi = (float)inv;
-        adj_pair_tf_kernel<<<(unsigned)P, 256, sm, st>>>(Gb, pp, cell_start, cell_g, ncell, tf_consts(),
-                                                         tf{hi, (float)(inv - (double)hi)}, (float4 *)H);
-        return cudaGetLastError();
+        const tf sc{hi, (float)(inv - (double)hi)};
+        const bool cubic = pp.n[0] == pp.n[1] && pp.n[1] == pp.n[2];
+        auto run = [&](auto kern) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            kern<<<(unsigned)P, 256, sm, st>>>(Gb, pp, cell_start, cell_g, ncell, tf_consts(), sc, (float4 *)H);
+            return cudaGetLastError();
+        };
+        if (cubic && pp.n[0] == 24) return run(adj_pair_tf_kernel<24>);
+        if (cubic && pp.n[0] == 40) return run(adj_pair_tf_kernel<40>);
+        if (cubic && pp.n[0] == 48) return run(adj_pair_tf_kernel<48>);
+        if (cubic && pp.n[0] == 72) return run(adj_pair_tf_kernel<72>);
+        return run(adj_pair_tf_kernel<0>);
     }
     size_t sm = sizeof(double2) * (2 * (size_t)pp.n[1] * pp.n[2] + pp.n[0] + pp.n[1] + pp.n[2] + pp.ng) +
                 sizeof(int) * pp.K2;

@@ -26,7 +26,9 @@ def dev(x):
 
 
 CASES = [((12, 12, 12), 3, 5, 93, 27, 0.0, 1000), ((16, 15, 18), 4, 9, 150, 64, 2.5, 12),
-         ((24, 24, 24), 16, 64, 600, 200, 0.0, 256)]
+         ((24, 24, 24), 16, 64, 600, 200, 0.0, 256),
+         # the grid-specialised back-projections of the 40^3 and 48^3 workloads
+         ((40, 40, 40), 2, 4, 600, 150, 1.0, 5), ((48, 48, 48), 2, 3, 900, 200, 0.0, 6)]
 
 
 @pytest.mark.parametrize("mtxel", ["fp64", "twofloat"])
