@@ -302,6 +302,14 @@ GW_API gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double 
                           double *dE_c, double *dcoeff_v, double *dcoeff_c);
 
 /*
+ * How many streams gw_chi0_compute uses for slot iq as it stands (bands and sphere set): 2 when
+ * each chunk's split contraction runs on a second stream beside the next chunk's pair elements
+ * (split precision, two-float stage (a), and room for two pair-kernel blocks beside a
+ * contraction block on an SM), else 1.  Negative (a gw_status, negated) on a bad handle or slot.
+ */
+GW_API int gw_chi0_streams(gw_chi0 *h, int iq);
+
+/*
  * Synchronise the handle's stream and report device-side status: GW_ERR_TIMEOUT if a
  * bounded wait inside a kernel gave up since the last gw_chi0_sync, GW_ERR_CUDA on a
  * CUDA error, else GW_OK.  Clears the device status word.

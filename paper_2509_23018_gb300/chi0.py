@@ -248,6 +248,13 @@ class Chi0:
                                                _ptr(v), ne, e_arr, _ptr(out)))
         return out
 
+    def streams(self, iq: int = 0) -> int:
+        """Streams compute() uses for slot iq: 2 with the contraction beside the pair kernel, else 1."""
+        r = int(self.lib.gw_chi0_streams(self.h, int(iq)))
+        if r < 0:
+            raise GwError(-r, self.lib.gw_chi0_last_error(self.h).decode())
+        return r
+
     def sync(self):
         self._use_current_stream()
         self._check(self.lib.gw_chi0_sync(self.h))

@@ -486,7 +486,24 @@ void free_sphere(gw_chi0 *h, Sphere &s)
 // kernel on the FP32 pipes, so the two share the SMs: the contraction uses a 2-deep TMA ring
 // (99 KB of shared memory) to fit beside two pair-kernel blocks.  Slices, exponents and job
 // tables alternate between two buffer sets; job j waits for the contraction of job j - 2.
-bool overlap_enabled(gw_chi0 *h) { return h->d.prec == GW_PREC_OZAKI_BF16 && !h->d.single_stream; }
+// The overlapped path pays off when two pair-kernel blocks fit on an SM beside a contraction
+// block (48^3: 180 vs 189 ms per q-point); with room for one (72^3, 112 KB pair blocks) the pair
+// kernel, the critical path, runs at half its occupancy (5.9 vs 4.8 s per q-point).
+bool overlap_enabled(gw_chi0 *h, const gw::PairPlan &pp)
+{
+    if (h->d.prec != GW_PREC_OZAKI_BF16 || h->d.single_stream || h->d.mtxel_prec != GW_MTXEL_TWOFLOAT) return false;
+    const size_t ps = gw::pair_tf_ct_smem_bytes(pp);
+    if (ps == 0) return false;
+    int dev = 0, sm_bytes = 0, resv = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t gs = gw::oz_smem_bytes(h->tuned_bn, 2);
+    return 2 * (ps + (size_t)resv) + gs + (size_t)resv <= (size_t)sm_bytes;
+}
 
 gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *cq, double *dq)
 {
@@ -644,6 +661,14 @@ gw_status gw_chi0_create(gw_chi0 **out, const gw_chi0_desc *d, void *stream)
     }
     *out = h;
     return GW_OK;
+}
+
+int gw_chi0_streams(gw_chi0 *h, int iq)
+{
+    if (!h) return -(int)GW_ERR_ARG;
+    gw_status s = check_slot(h, iq);
+    if (s) return -(int)s;
+    return overlap_enabled(h, pair_plan(h, h->sph[iq])) ? 2 : 1;
 }
 
 void gw_chi0_destroy(gw_chi0 *h)
@@ -959,7 +984,8 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
         double *dq = diag ? diag + doff : nullptr;
         CK(h, cudaMemsetAsync(cq, 0, sizeof(double2) * (size_t)nw * ng * ng, h->st), "zero chi");
         if (dq) CK(h, cudaMemsetAsync(dq, 0, sizeof(double) * (size_t)nw * ng, h->st), "zero diag");
-        if (overlap_enabled(h) && fault_chunk() < 0) {
+        gw::PairPlan pp = pair_plan(h, sp);
+        if (overlap_enabled(h, pp) && fault_chunk() < 0) {
             gw_status s = compute_overlap(h, iq[i], om, cq, dq);
             if (s) return s;
             Scope sc(h, "symmetrize");
@@ -970,7 +996,6 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
         }
         gw_status s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw);
         if (s) return s;
-        gw::PairPlan pp = pair_plan(h, sp);
         const int64_t fault_at = fault_chunk();
         for (int64_t p0 = 0, k = 0; p0 < P; p0 += chunk, ++k) {
             int64_t cnt = std::min(chunk, P - p0);

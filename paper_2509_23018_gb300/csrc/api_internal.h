@@ -232,7 +232,7 @@ void free_sphere(gw_chi0 *h, Sphere &s);
 
 // overlapped split-precision streamed compute of one slot (api.cu)
 gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *cq, double *dq);
-bool overlap_enabled(gw_chi0 *h);
+bool overlap_enabled(gw_chi0 *h, const gw::PairPlan &pp);
 
 // batched path (api_batch.cu)
 gw_status compute_batch(gw_chi0 *h, int nq, const int *iq, int nw, const double *omega, const gw::OmegaList &om,

@@ -39,6 +39,9 @@ struct PairPlan {
 // Scratch the two-float pair kernel needs for a plan: *nslots slots of *slot_elems float4
 // (0 slots: the plan runs on the runtime-shape kernel, which needs none).
 cudaError_t pair_tf_scratch(const PairPlan &pp, int *nslots, size_t *slot_elems);
+// Shared memory per block of the grid-specialised two-float pair kernel for this plan (0 when it
+// does not take the plan).
+size_t pair_tf_ct_smem_bytes(const PairPlan &pp);
 // M[p - p0][g] for p in [p0, p0 + count); pair p = v * nc + c.
 cudaError_t launch_pair(const double2 *psiv, const double2 *psic, int nc, int64_t p0, int64_t count,
                         const PairPlan &pp, double2 *M, cudaStream_t st);
@@ -152,7 +155,7 @@ cudaError_t launch_gpp_prep_split(const float4 *At, const float4 *Wt, int ng, co
                                   int s, int64_t kpad, int64_t zstride, void *Z, int *E, cudaStream_t st);
 cudaError_t launch_oz_gemm_general(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
                                    cudaStream_t st);
-size_t oz_smem_bytes(int bn);
+size_t oz_smem_bytes(int bn, int stages = 4);
 int oz_box_rows_a();
 int oz_box_k();
 

@@ -380,6 +380,18 @@ static cudaError_t launch_pair_tf_t(const float4 *psiv, const float4 *psic, int 
     return cudaGetLastError();
 }
 
+size_t pair_tf_ct_smem_bytes(const PairPlan &pp)
+{
+    if (!pair_tf_ct_fits(pp)) return 0;
+    switch (pp.n[0]) {
+    case 24: return pair_tf_ct_smem<24>(pp);
+    case 40: return pair_tf_ct_smem<40>(pp);
+    case 48: return pair_tf_ct_smem<48>(pp);
+    case 72: return pair_tf_ct_smem<72>(pp);
+    default: return 0;
+    }
+}
+
 cudaError_t pair_tf_scratch(const PairPlan &pp, int *nslots, size_t *slot_elems)
 {
     *nslots = 0;

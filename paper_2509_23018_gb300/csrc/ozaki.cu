@@ -625,7 +625,11 @@ int oz_tiles(int ng, int bn)
     return n;
 }
 
-size_t oz_smem_bytes(int bn) { return bn == 128 ? OzCfg<128>::Smem : OzCfg<256>::Smem; }
+size_t oz_smem_bytes(int bn, int stages)
+{
+    if (stages == 2) return bn == 128 ? OzCfg<128, 2>::Smem : OzCfg<256, 2>::Smem;
+    return bn == 128 ? OzCfg<128>::Smem : OzCfg<256>::Smem;
+}
 
 cudaError_t launch_oz_sqrt(const double *delta, int64_t n, double *sp, cudaStream_t st)
 {

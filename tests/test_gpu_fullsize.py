@@ -2,7 +2,8 @@
 
 48^3 grid, 128 + 1024 bands on 6000 plane waves, N_G = 2000, 8192-pair chunks: a sampled
 block of chi (all 131072 pairs contribute) and sampled rows of M against the oracle, plus
-properties that hold at any size (Hermitian, negative semidefinite at w = 0, trace).
+properties that hold at any size (Hermitian, negative semidefinite at w = 0, trace).  The same
+for the 72^3 workload (524288 pairs, N_G = 6000) in split precision.
 """
 import numpy as np
 import pytest
@@ -60,6 +61,32 @@ def test_c2_sampled(gw, c2, prec, nslices, mtxel, tol):
         mo = oracle.m_conv(p.gpsi, p.cv[v:v + 1], p.gpsi, p.cc[c:c + 1], p.gchi)[0]
         assert rel(m, mo) < 1e-12
     h.sync()
+    h.destroy()
+
+
+@pytest.fixture(scope="module")
+def c3():
+    cfg = gwgen.CONFIGS["c3_72cube"]
+    p = gwgen.config_problem(cfg)
+    rng = np.random.default_rng(19)
+    idx = np.sort(rng.choice(cfg.ng, 6, replace=False))
+    Mcols = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi[idx])   # all 524288 pairs, 6 columns
+    return cfg, p, idx, oracle.chi0(Mcols, oracle.delta(p.ev, p.ec, 0.0))
+
+
+def test_c3_sampled_split(gw, c3):
+    """72^3, 256 + 2048 bands on 20000 plane waves, N_G = 6000, 64 chunks of 8192 pairs, split
+    precision (s = 7) with two-float stage (a): a sampled block against the oracle, Hermitian and
+    trace at full size."""
+    cfg, p, idx, ref = c3
+    h = gw.from_problem(p, prec="ozaki", nslices=7, mtxel="twofloat", pair_chunk=cfg.pair_chunk)
+    (chi,), (dg,) = h.compute(0, [0.0], diag=True)
+    chi_d = chi[0]
+    assert torch.equal(chi_d, chi_d.conj().T)
+    assert abs(float(torch.trace(chi_d).real) - float(dg[0].sum())) <= 1e-9 * abs(float(dg[0].sum()))
+    got = chi_d.cpu().numpy()[np.ix_(idx, idx)]
+    h.sync()
+    assert rel(got, ref) <= 1e-9
     h.destroy()
 
 

@@ -92,3 +92,16 @@ def test_split_ragged(gw, ng):
     h.sync()
     Mo = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)
     assert rel(chi, oracle.chi0(Mo, oracle.delta(p.ev, p.ec, 0.0))) <= TOL_SPLIT
+
+
+def test_streams_query(gw):
+    """The overlapped path is taken for a 24^3 slot in split precision and not in
+    FP64 mode or with single_stream; an unset slot is an error."""
+    cfg = gwgen.CONFIGS["c1_24cube"]
+    p = gwgen.config_problem(cfg)
+    for prec, single, want in (("ozaki", False, 2), ("ozaki", True, 1), ("fp64", False, 1)):
+        h = gw.from_problem(p, prec=prec, nslices=7, mtxel="twofloat", single_stream=single)
+        assert h.streams(0) == want
+        with pytest.raises(gw.GwError):
+            h.streams(5)
+        h.destroy()
