@@ -20,16 +20,27 @@ constexpr int pair_threads()
 template <int N>
 constexpr int pair_min_blocks()
 {
-    return N <= 48 ? (pair_threads<N>() == 256 ? 2 : 4) : 1;
+    return N <= 48 ? (pair_threads<N>() == 256 ? 2 : 4) : 2;
 }
 // The second full i2 stage (when the plan has one) runs in place when a lane's inputs for
-// all its butterflies fit in registers (at most 16 complex values).
+// all its butterflies fit in registers (at most 16 complex values): over all of a warp's L
+// lines at once, or over the largest divisor of L that fits, subset by subset (the lines are
+// independent).  Returns the lines per in-place pass, 0 when none fits (the stage then goes
+// from A to a second slab buffer B).
 template <int N>
-constexpr bool pair_inplace()
+constexpr int pair_inplace_lines()
 {
     constexpr RadPlan P = make_prune_plan(N);
     constexpr int L = N / (pair_threads<N>() / 32);
-    return P.nst < 3 || ((L * (N / P.r[1]) + 31) / 32) * P.r[1] <= 16;
+    if (P.nst < 3) return L;
+    for (int ls = L; ls >= 1; --ls)
+        if (L % ls == 0 && ((ls * (N / P.r[1]) + 31) / 32) * P.r[1] <= 16) return ls;
+    return 0;
+}
+template <int N>
+constexpr bool pair_inplace()
+{
+    return pair_inplace_lines<N>() > 0;
 }
 
 // Lazy butterfly: outputs left unrenormalised where the radix has that form (they feed
@@ -177,8 +188,13 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         }
         __syncwarp();
         if constexpr (two) {
-            if constexpr (inplace) wstage_inplace<N, P.r[1], R0, L>(Aw, tw, kc);
-            else wstage_ct<N, P.r[1], R0, L>(Aw, Bw, tw, kc);
+            if constexpr (inplace) {
+                constexpr int LS = pair_inplace_lines<N>();
+#pragma unroll
+                for (int l0 = 0; l0 < L; l0 += LS) wstage_inplace<N, P.r[1], R0, LS>(Aw + l0 * N, tw, kc);
+            } else {
+                wstage_ct<N, P.r[1], R0, L>(Aw, Bw, tw, kc);
+            }
             __syncwarp();
         }
         // i2, pruned last stage: kept frequency kz[q] of line l -> C[q][warp L + l]
