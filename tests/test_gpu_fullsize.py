@@ -101,3 +101,52 @@ def test_adjoint_40cube_reduced_bands(gw):
     assert abs(L - Lo) <= 1e-10 * abs(Lo)
     for a, b in ((dEv, dEvo), (dEc, dEco), (dcv, dcvo), (dcc, dcco)):
         assert rel(a.cpu().numpy(), b) < 1e-10
+
+
+def test_adjoint_c5_central_differences(gw):
+    """The adjoint at the full 40^3 / 96 + 768 bands / 4500 / 1500 size in the launch configuration
+    the bench times (split precision, two-float stage (a)), against central differences of the
+    FP64 forward L = Re Tr(W chi) on the coefficients with the largest gradients and on two
+    energies."""
+    cfg = gwgen.CONFIGS["c5_adjoint"]
+    p = gwgen.config_problem(cfg)
+    W = gwgen.hermitian(np.random.default_rng(gwgen.BASE_SEED + 4), cfg.ng)
+    Wd = torch.as_tensor(W, device="cuda")
+    h = gw.from_problem(p, prec="ozaki", nslices=7, mtxel="twofloat", pair_chunk=cfg.pair_chunk)
+    L, dEv, dEc, dcv, dcc = h.adjoint(0, Wd)
+    h.sync()
+    h.destroy()
+    dcv, dcc, dEv = dcv.cpu().numpy(), dcc.cpu().numpy(), dEv.cpu().numpy()
+    hf = gw.from_problem(p, prec="fp64", mtxel="twofloat", pair_chunk=cfg.pair_chunk)
+    g = torch.as_tensor(p.gpsi, device="cuda")
+
+    def L_of(cv, cc, ev, ec):
+        hf.set_bands(0, 0, g, torch.as_tensor(cv, device="cuda"), torch.as_tensor(ev, device="cuda"))
+        hf.set_bands(0, 1, g, torch.as_tensor(cc, device="cuda"), torch.as_tensor(ec, device="cuda"))
+        (chi,) = hf.compute(0, [0.0])
+        return float(torch.real(torch.trace(Wd @ chi[0])).item())
+
+    L0 = L_of(p.cv, p.cc, p.ev, p.ec)
+    assert abs(L0 - L) <= 1e-12 * abs(L)
+    step = 1e-5
+    checks = []
+    for which, grad, base in (("v", dcv, p.cv), ("c", dcc, p.cc)):
+        for flat in np.argsort(-np.abs(grad).ravel())[:2]:
+            n, k = np.unravel_index(flat, grad.shape)
+            for part, unit in (("re", 1.0), ("im", 1j)):
+                cp, cm = base.copy(), base.copy()
+                cp[n, k] += step * unit
+                cm[n, k] -= step * unit
+                if which == "v":
+                    fd = (L_of(cp, p.cc, p.ev, p.ec) - L_of(cm, p.cc, p.ev, p.ec)) / (2 * step)
+                else:
+                    fd = (L_of(p.cv, cp, p.ev, p.ec) - L_of(p.cv, cm, p.ev, p.ec)) / (2 * step)
+                checks.append((fd, grad[n, k].real if part == "re" else grad[n, k].imag))
+    for v in np.argsort(-np.abs(dEv))[:2]:
+        ep, em = p.ev.copy(), p.ev.copy()
+        ep[v] += step
+        em[v] -= step
+        checks.append(((L_of(p.cv, p.cc, ep, p.ec) - L_of(p.cv, p.cc, em, p.ec)) / (2 * step), dEv[v]))
+    hf.destroy()
+    for fd, an in checks:
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
