@@ -133,3 +133,22 @@ def test_sigma_gpp_energy_batches_do_not_change_bits(gw):
         h.destroy()
     assert np.array_equal(outs[0], outs[1])
     assert rel(outs[0], want(p)) < 1e-9
+
+
+def test_sigma_gpp_from_stage_a(gw):
+    """The self-energy fed by stage (a): the summed bands n as the valence set and the self-energy
+    bands l as the conduction set give M[n][l][G] = sum_K conj(c_n(K)) c_l(K - G) from
+    gw_chi0_pair_elements (pair p = n N_Sigma + l), then Sigma from those elements."""
+    nb, nocc, nsig, ng, ne = 6, 3, 10, 150, 4
+    prob = gwgen.make_problem((24, 24, 24), nb, nsig, 400, ng, seed=gwgen.BASE_SEED + 46)
+    gp = gwgen.make_gpp(nb, nocc, nsig, ng, ne, seed=gwgen.BASE_SEED + 47)
+    h = gw.from_problem(prob, prec="ozaki", nslices=7, mtxel="twofloat")
+    M = h.pair_elements(0, 0, nb * nsig).view(nb, nsig, ng)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    En = np.concatenate([prob.ev, prob.ec])[:nb]
+    got = h.sigma_gpp(M, En, nocc, t(gp.omega2), t(gp.wtilde), t(gp.vcoul), gp.E).cpu().numpy()
+    h.sync()
+    Mo = oracle.m_conv(prob.gpsi, prob.cv, prob.gpsi, prob.cc, prob.gchi).reshape(nb, nsig, ng)
+    want = oracle.sigma_gpp(Mo, En, nocc, gp.omega2, gp.wtilde, gp.vcoul, gp.E)
+    assert rel(got, want) < 1e-9
+    h.destroy()
