@@ -16,6 +16,8 @@
 #include "fft.cuh"
 #include "fft_tf.cuh"
 
+#include <algorithm>
+
 namespace gw {
 
 // ------------------------------------------------------------------ Y = M W (FP64 DMMA)
@@ -244,12 +246,14 @@ __global__ void __launch_bounds__(256) adj_pair_kernel(const double2 *__restrict
 }
 
 // The same back-projection in two-float arithmetic on the FP32 pipes (bands held in two-float
-// form): conj(g_p) converted once per pair, the i0 sums per cell and both line transforms in
-// hi + lo pairs; H is written in two-float form (16 bytes a point, as in FP64).
+// form): conj(g_p) converted once per pair, in place over the block's own row of Gb (16 bytes
+// an entry either way; Gb is not read again), the i0 sums per cell reading it from L2, both line
+// transforms in hi + lo pairs; H is written in two-float form.  Keeping conj(g_p) out of shared
+// memory lets four blocks run per SM on 40^3 instead of two.
 // N > 0: a cubic N^3 grid, the line transforms and index arithmetic specialised at compile time;
 // N = 0: any grid, runtime plans.
 template <int N>
-__global__ void __launch_bounds__(256) adj_pair_tf_kernel(const double2 *__restrict__ Gb, PairPlan pp,
+__global__ void __launch_bounds__(256) adj_pair_tf_kernel(double2 *__restrict__ Gb, PairPlan pp,
                                                           const int *__restrict__ cell_start,
                                                           const int *__restrict__ cell_g, int ncell, TfConsts kc,
                                                           tf sc, float4 *__restrict__ H)
@@ -259,13 +263,13 @@ __global__ void __launch_bounds__(256) adj_pair_tf_kernel(const double2 *__restr
     const int ns = n1 * n2;
     float4 *a = (float4 *)smem, *b = a + ns;
     float4 *tw0 = b + ns, *tw1 = tw0 + n0, *tw2 = tw1 + n1;
-    float4 *gs = tw2 + n2; // [ng] conj(g_p), two-float
-    int *kz = (int *)(gs + pp.ng);
+    int *kz = (int *)(tw2 + n2);
     for (int i = threadIdx.x; i < n0; i += blockDim.x) tw0[i] = pp.ax[0].twf[i];
     for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = pp.ax[1].twf[i];
     for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = pp.ax[2].twf[i];
     for (int i = threadIdx.x; i < pp.K2; i += blockDim.x) kz[i] = pp.kz[i];
     const int64_t p = blockIdx.x;
+    float4 *gs = (float4 *)(Gb + p * pp.ng); // [ng] conj(g_p), two-float, over the row
     for (int g = threadIdx.x; g < pp.ng; g += blockDim.x) {
         const double2 x = Gb[p * pp.ng + g];
         const tf re = tf_from(x.x), im = tf_from(-x.y);
@@ -311,12 +315,12 @@ __global__ void __launch_bounds__(256) adj_pair_tf_kernel(const double2 *__restr
     }
 }
 
-cudaError_t launch_adj_pair(const double2 *Gb, int64_t P, const PairPlan &pp, const int *cell_start,
+cudaError_t launch_adj_pair(double2 *Gb, int64_t P, const PairPlan &pp, const int *cell_start,
                             const int *cell_g, int ncell, double2 *H, bool twofloat, cudaStream_t st)
 {
     if (P == 0) return cudaSuccess;
     if (twofloat) {
-        const size_t sm = sizeof(float4) * (2 * (size_t)pp.n[1] * pp.n[2] + pp.n[0] + pp.n[1] + pp.n[2] + pp.ng) +
+        const size_t sm = sizeof(float4) * (2 * (size_t)pp.n[1] * pp.n[2] + pp.n[0] + pp.n[1] + pp.n[2]) +
                           sizeof(int) * pp.K2;
         const double inv = 1.0 / ((double)pp.n[0] * pp.n[1] * pp.n[2]);
         const float hi = (float)inv;
@@ -377,10 +381,11 @@ __global__ void adj_val_kernel(const void *__restrict__ psic, int v0, const doub
     pbv[(int64_t)(v0 + vl) * nr + i] = acc;
 }
 
-// Two-float forms of the two products (bands and H in two-float form): the sums over the
-// chunk's bands run on the FP32 pipes and are added once into the FP64 accumulators.
+// Two-float forms of the two products (bands, H and the accumulators psibar in two-float form,
+// 16 bytes a point as in FP64): everything on the FP32 pipes -- adding into FP64 accumulators
+// took eight FP64 instructions a thread, which bounded the conduction product on this GPU.
 __global__ void adj_cond_tf_kernel(const float4 *__restrict__ psiv, int v0, int nvc, const float4 *__restrict__ H,
-                                   int nc, int64_t nr, double2 *__restrict__ pbc)
+                                   int nc, int64_t nr, float4 *__restrict__ pbc)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
@@ -388,12 +393,12 @@ __global__ void adj_cond_tf_kernel(const float4 *__restrict__ psiv, int v0, int 
     tcx acc{{0.f, 0.f}, {0.f, 0.f}};
     for (int v = 0; v < nvc; ++v)
         acc = tc_add(acc, tc_mul(tc_load(psiv + (int64_t)(v0 + v) * nr + i), tc_load(H + ((int64_t)v * nc + c) * nr + i)));
-    double2 &o = pbc[(int64_t)c * nr + i];
-    o = make_double2(o.x + tf_to_d(acc.re), o.y + tf_to_d(acc.im));
+    float4 *o = pbc + (int64_t)c * nr + i;
+    tc_store(o, tc_add(tc_load(o), acc));
 }
 
 __global__ void adj_val_tf_kernel(const float4 *__restrict__ psic, int v0, const float4 *__restrict__ H, int nc,
-                                  int64_t nr, double2 *__restrict__ pbv)
+                                  int64_t nr, float4 *__restrict__ pbv)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int vl = blockIdx.y;
@@ -401,8 +406,25 @@ __global__ void adj_val_tf_kernel(const float4 *__restrict__ psic, int v0, const
     tcx acc{{0.f, 0.f}, {0.f, 0.f}};
     for (int c = 0; c < nc; ++c) // psi_c conj(H) = conj(conj(psi_c) H)
         acc = tc_add(acc, tc_mulc(tc_load(psic + (int64_t)c * nr + i), tc_load(H + ((int64_t)vl * nc + c) * nr + i)));
-    double2 &o = pbv[(int64_t)(v0 + vl) * nr + i];
-    o = make_double2(o.x + tf_to_d(acc.re), o.y - tf_to_d(acc.im));
+    float4 *o = pbv + (int64_t)(v0 + vl) * nr + i;
+    tc_store(o, tc_add(tc_load(o), tcx{acc.re, tf_neg(acc.im)}));
+}
+
+// Two-float accumulators to FP64, in place (same 16 bytes per point).
+__global__ void tf_to_f64_kernel(void *__restrict__ x, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = ((const float4 *)x)[i];
+        ((double2 *)x)[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+}
+
+cudaError_t launch_tf_to_f64(void *x, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    tf_to_f64_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adj_products(const void *psiv, const void *psic, int v0, int nvc, int nc, const double2 *H,
@@ -410,11 +432,12 @@ cudaError_t launch_adj_products(const void *psiv, const void *psic, int v0, int 
 {
     if (tf) {
         dim3 gc((unsigned)((nr + 255) / 256), nc);
-        adj_cond_tf_kernel<<<gc, 256, 0, st>>>((const float4 *)psiv, v0, nvc, (const float4 *)H, nc, nr, pbc);
+        adj_cond_tf_kernel<<<gc, 256, 0, st>>>((const float4 *)psiv, v0, nvc, (const float4 *)H, nc, nr,
+                                               (float4 *)pbc);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         dim3 gv((unsigned)((nr + 255) / 256), nvc);
-        adj_val_tf_kernel<<<gv, 256, 0, st>>>((const float4 *)psic, v0, (const float4 *)H, nc, nr, pbv);
+        adj_val_tf_kernel<<<gv, 256, 0, st>>>((const float4 *)psic, v0, (const float4 *)H, nc, nr, (float4 *)pbv);
         return cudaGetLastError();
     }
     dim3 gc((unsigned)((nr + 255) / 256), nc);

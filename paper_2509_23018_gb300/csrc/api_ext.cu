@@ -107,6 +107,10 @@ gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, dou
     }
     {
         Scope sc(h, "adj_band");
+        if (tf) {
+            ACK(gw::launch_tf_to_f64(pbv, (int64_t)nv * nr, h->st), "valence adjoint to FP64");
+            ACK(gw::launch_tf_to_f64(pbc, (int64_t)nc * nr, h->st), "conduction adjoint to FP64");
+        }
         ACK(gw::launch_band_adjoint(pbv, nv, h->d.n, h->ax, v.gofs, v.ngpsi, (double2 *)dcoeff_v, h->st),
             "valence band adjoint");
         ACK(gw::launch_band_adjoint(pbc, nc, h->d.n, h->ax, c.gofs, c.ngpsi, (double2 *)dcoeff_c, h->st),

@@ -180,9 +180,13 @@ cudaError_t launch_gpp_prep_f64(const double2 *A, const double2 *wtilde, int ng,
 cudaError_t launch_adj_rows(const double2 *M, double2 *Y, int64_t P, int ng, int nc, int64_t p0, const double *ev,
                             const double *ec, double w, double *L, double *dEv, double *dEc, cudaStream_t st);
 // twofloat: the back-projection in two-float arithmetic (band grids in two-float form), H then
-// holds float4 (hi, lo) pairs and launch_adj_products reads it that way; else FP64
-cudaError_t launch_adj_pair(const double2 *Gb, int64_t P, const PairPlan &pp, const int *cell_start,
+// holds float4 (hi, lo) pairs and launch_adj_products reads it that way and accumulates pbv / pbc
+// in that form too (launch_tf_to_f64 converts them before the band adjoint), and Gb's rows are
+// overwritten with conj(g_p) in two-float form; else FP64, Gb read only
+cudaError_t launch_adj_pair(double2 *Gb, int64_t P, const PairPlan &pp, const int *cell_start,
                             const int *cell_g, int ncell, double2 *H, bool twofloat, cudaStream_t st);
+// two-float (float4 hi/lo pairs) to complex128, in place, n points
+cudaError_t launch_tf_to_f64(void *x, int64_t n, cudaStream_t st);
 cudaError_t launch_adj_products(const void *psiv, const void *psic, int v0, int nvc, int nc, const double2 *H,
                                 int64_t nr, bool tf, double2 *pbv, double2 *pbc, cudaStream_t st);
 cudaError_t launch_band_adjoint(double2 *pb, int nb, const int n[3], const FftAxis ax[3], const int32_t *gofs,
