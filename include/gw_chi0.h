@@ -302,10 +302,22 @@ GW_API gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double 
                           double *dE_c, double *dcoeff_v, double *dcoeff_c);
 
 /*
- * How many streams gw_chi0_compute uses for slot iq as it stands (bands and sphere set): 2 when
- * each chunk's split contraction runs on a second stream beside the next chunk's pair elements
- * (split precision, two-float stage (a), and room for two pair-kernel blocks beside a
- * contraction block on an SM), else 1.  Negative (a gw_status, negated) on a bad handle or slot.
+ * Keep pair elements resident (enable = 1): gw_chi0_compute then writes the M of each slot it
+ * computes into a library-owned buffer (P x N_G complex128, 4.2 GB on the 48^3 workload) instead
+ * of one chunk buffer, and gw_chi0_compute_subspace / gw_chi0_compute_real on the last slot
+ * computed reuse it and skip stage (a).  The buffer is taken only when it fits the handle's memory
+ * budget (when one is set) and half the free device memory; otherwise compute runs as without.
+ * gw_chi0_set_bands / gw_chi0_set_gsphere of that slot (or of the conduction set) drop the
+ * elements.  enable = 0 (the default) frees the buffer.  GW_ERR_ARG for other values.
+ */
+GW_API gw_status gw_chi0_keep_pair_elements(gw_chi0 *h, int enable);
+
+/*
+ * How many streams a single-frequency gw_chi0_compute uses for slot iq as it stands (bands and
+ * sphere set): 2 when each chunk's split contraction runs on a second stream beside the next
+ * chunk's pair elements (split precision, two-float stage (a), and room for two pair-kernel
+ * blocks beside a contraction block on an SM), else 1.  Calls with several frequencies always
+ * run on one stream.  Negative (a gw_status, negated) on a bad handle or slot.
  */
 GW_API int gw_chi0_streams(gw_chi0 *h, int iq);
 

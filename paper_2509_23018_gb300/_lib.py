@@ -49,6 +49,7 @@ SIGNATURES = {
     "gw_chi0_compute_real": ([P, I, I, P, D, P], I),
     "gw_chi0_jvp": ([P, I, I, P, P, P, P, P, P], I),
     "gw_chi0_streams": ([P, I], I),
+    "gw_chi0_keep_pair_elements": ([P, I], I),
     "gw_chi0_sync": ([P], I),
     "gw_chi0_check_watchdog": ([P, ctypes.c_longlong], I),
     "gw_chi0_set_timing": ([P, I], I),

@@ -248,6 +248,11 @@ class Chi0:
                                                _ptr(v), ne, e_arr, _ptr(out)))
         return out
 
+    def keep_pair_elements(self, enable: bool = True):
+        """Keep the pair elements of the last computed slot resident for compute_subspace and
+        compute_real on that slot (P x N_G complex128 of device memory)."""
+        self._check(self.lib.gw_chi0_keep_pair_elements(self.h, 1 if enable else 0))
+
     def streams(self, iq: int = 0) -> int:
         """Streams compute() uses for slot iq: 2 with the contraction beside the pair kernel, else 1."""
         r = int(self.lib.gw_chi0_streams(self.h, int(iq)))

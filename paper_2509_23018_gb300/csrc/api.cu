@@ -505,7 +505,27 @@ bool overlap_enabled(gw_chi0 *h, const gw::PairPlan &pp)
     return 2 * (ps + (size_t)resv) + gs + (size_t)resv <= (size_t)sm_bytes;
 }
 
-gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *cq, double *dq)
+gw_status resident_begin(gw_chi0 *h, int64_t P, int ng, bool *use)
+{
+    *use = false;
+    h->Mres_iq = -1;
+    if (!h->keep_m) return GW_OK;
+    const size_t need = sizeof(double2) * (size_t)P * ng;
+    if (h->d.mem_budget_bytes && h->bytes - h->Mres_cap + need > h->d.mem_budget_bytes) return GW_OK;
+    size_t free_b = 0, total_b = 0;
+    if (need > h->Mres_cap && (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || need - h->Mres_cap > free_b / 2)) {
+        cudaGetLastError();
+        return GW_OK; // keep at most half of what is free: the elements are an optimisation, not a need
+    }
+    gw_status s = grow(h, (void **)&h->Mres, &h->Mres_cap, need, "resident pair elements");
+    if (s) return s;
+    *use = true;
+    return GW_OK;
+}
+
+double2 *resident_for(gw_chi0 *h, int iq) { return h->keep_m && h->Mres_iq == iq ? h->Mres : nullptr; }
+
+gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *cq, double *dq, double2 *Mres)
 {
     const Sphere &sp = h->sph[iq];
     const BandSet &v = h->val[iq];
@@ -537,9 +557,10 @@ gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *
     for (int64_t p0 = 0; p0 < P; p0 += chunk) {
         const int64_t cnt = std::min(chunk, P - p0);
         const int64_t kpad = (cnt + 63) / 64 * 64;
+        double2 *Mc = Mres ? Mres + p0 * ng : h->Mbuf;
         {
             Scope sc(h, "pair_mtxel");
-            CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
+            CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, Mc), "pair kernel");
         }
         {
             Scope sc(h, "delta");
@@ -551,7 +572,7 @@ gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *
         }
         if (dq) {
             Scope sc(h, "diag");
-            CK(h, gw::launch_diag(h->Mbuf, cnt, ng, h->dbuf, cnt, nw, dq, ng, h->st), "diag");
+            CK(h, gw::launch_diag(Mc, cnt, ng, h->dbuf, cnt, nw, dq, ng, h->st), "diag");
         }
         for (int w = 0; w < nw; ++w, ++j) {
             const int b = (int)(j & 1);
@@ -559,8 +580,8 @@ gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *
             {
                 Scope sc(h, "oz_split");
                 const double *spw = h->spbuf + (int64_t)w * cnt;
-                CK(h, gw::launch_oz_colexp(h->Mbuf, cnt, ng, spw, h->ovE[b], h->st), "oz exponents");
-                CK(h, gw::launch_oz_slice(h->Mbuf, cnt, ng, spw, h->ovE[b], s, kpad, h->ovZ[b], h->st), "oz slices");
+                CK(h, gw::launch_oz_colexp(Mc, cnt, ng, spw, h->ovE[b], h->st), "oz exponents");
+                CK(h, gw::launch_oz_slice(Mc, cnt, ng, spw, h->ovE[b], s, kpad, h->ovZ[b], h->st), "oz slices");
             }
             std::vector<gw::OzJob> jobs(1);
             if ((st = oz_job(h, jobs[0], h->ovZ[b], kpad, ng, h->ovE[b], cq + (int64_t)w * ng * ng, bn))) return st;
@@ -700,6 +721,7 @@ void gw_chi0_destroy(gw_chi0 *h)
     }
     if (h->ov_st) cudaStreamDestroy(h->ov_st);
     dfree(h, h->epsbuf, h->epscap);
+    dfree(h, h->Mres, h->Mres_cap);
     for (auto &b : h->gpp) dfree(h, b.p, b.cap);
     dfree(h, h->realbuf, h->realcap);
     dfree(h, h->eigA, h->eigA_cap);
@@ -786,6 +808,7 @@ gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngpsi, con
             if (v.nb && !(*std::max_element(v.e.begin(), v.e.end()) < cmin))
                 return fail(h, GW_ERR_ARG, "a valence energy is not below every conduction energy");
     }
+    if (kind == 1 || iq == h->Mres_iq) h->Mres_iq = -1; // resident pair elements no longer match
     BandSet &dst = kind == 0 ? h->val[iq] : h->cond;
     if (dst.nb == nb && dst.ngpsi == ngpsi) {
         // same shape: reuse the device buffers (no allocation on repeated setup)
@@ -891,6 +914,7 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
         for (int m = s.cstart[d]; m < s.cstart[d + 1]; ++m) cpts[m] = make_int2(s.cg[m], (pack[s.cg[m]] & 255) | d << 8);
     }
     gw_status st;
+    if (iq == h->Mres_iq) h->Mres_iq = -1; // resident pair elements no longer match
     Sphere &old = h->sph[iq];
     if (old.ng == ng && old.K2 == s.K2 && old.K12 == s.K12) {
         s.kz = old.kz;
@@ -985,34 +1009,43 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
         CK(h, cudaMemsetAsync(cq, 0, sizeof(double2) * (size_t)nw * ng * ng, h->st), "zero chi");
         if (dq) CK(h, cudaMemsetAsync(dq, 0, sizeof(double) * (size_t)nw * ng, h->st), "zero diag");
         gw::PairPlan pp = pair_plan(h, sp);
-        if (overlap_enabled(h, pp) && fault_chunk() < 0) {
-            gw_status s = compute_overlap(h, iq[i], om, cq, dq);
+        bool keep = false;
+        gw_status s = resident_begin(h, P, ng, &keep);
+        if (s) return s;
+        double2 *Mres = keep ? h->Mres : nullptr;
+        // one frequency: a chunk's contraction is about as long as the next chunk's pair elements
+        // and hides behind them; with more, the contractions (the shallow-ring variant) queue up
+        // behind the two slice buffers and the single stream is faster
+        if (nw == 1 && overlap_enabled(h, pp) && fault_chunk() < 0) {
+            s = compute_overlap(h, iq[i], om, cq, dq, Mres);
             if (s) return s;
             Scope sc(h, "symmetrize");
             CK(h, gw::launch_symmetrize(cq, ng, nw, h->st), "symmetrize");
             off += (size_t)nw * ng * ng;
             doff += (size_t)nw * ng;
+            if (keep) h->Mres_iq = iq[i];
             continue;
         }
-        gw_status s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw);
+        s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw);
         if (s) return s;
         const int64_t fault_at = fault_chunk();
         for (int64_t p0 = 0, k = 0; p0 < P; p0 += chunk, ++k) {
             int64_t cnt = std::min(chunk, P - p0);
             if (k == fault_at) return fail(h, GW_ERR_CUDA, "injected host-side fault before chunk %lld", (long long)k);
+            double2 *Mc = Mres ? Mres + p0 * ng : h->Mbuf;
             {
                 Scope sc(h, "pair_mtxel");
-                CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
+                CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, Mc), "pair kernel");
             }
             {
                 Scope sc(h, "delta");
                 CK(h, gw::launch_delta(v.energy, h->cond.energy, h->cond.nb, p0, cnt, om, h->dbuf, h->st), "delta");
             }
-            s = contract_chunk(h, h->Mbuf, cnt, ng, h->dbuf, cnt, nw, cq);
+            s = contract_chunk(h, Mc, cnt, ng, h->dbuf, cnt, nw, cq);
             if (s) return s;
             if (dq) {
                 Scope sc(h, "diag");
-                CK(h, gw::launch_diag(h->Mbuf, cnt, ng, h->dbuf, cnt, nw, dq, ng, h->st), "diag");
+                CK(h, gw::launch_diag(Mc, cnt, ng, h->dbuf, cnt, nw, dq, ng, h->st), "diag");
             }
         }
         {
@@ -1021,6 +1054,22 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
         }
         off += (size_t)nw * ng * ng;
         doff += (size_t)nw * ng;
+        if (keep) h->Mres_iq = iq[i];
+    }
+    return GW_OK;
+}
+
+gw_status gw_chi0_keep_pair_elements(gw_chi0 *h, int enable)
+{
+    if (!h) return GW_ERR_ARG;
+    if (enable != 0 && enable != 1) return fail(h, GW_ERR_ARG, "enable must be 0 or 1");
+    h->keep_m = enable == 1;
+    h->Mres_iq = -1;
+    if (!h->keep_m && h->Mres) {
+        CK(h, cudaStreamSynchronize(h->st), "release resident pair elements");
+        dfree(h, h->Mres, h->Mres_cap);
+        h->Mres = nullptr;
+        h->Mres_cap = 0;
     }
     return GW_OK;
 }

@@ -216,18 +216,20 @@ gw_status gw_chi0_compute_subspace(gw_chi0 *h, int iq, int neig, const double *b
     const bool split = h->d.prec == GW_PREC_OZAKI_BF16;
     if (split && (s = oz_prepare_b(h, (const double2 *)basis, ng, neig))) return s;
     gw::PairPlan pp = pair_plan(h, sp);
+    const double2 *Mres = resident_for(h, iq); // kept by the last gw_chi0_compute of this slot
     for (int64_t p0 = 0; p0 < P; p0 += chunk) {
         const int64_t cnt = std::min(chunk, P - p0);
-        {
+        const double2 *Mc = Mres ? Mres + p0 * ng : h->Mbuf;
+        if (!Mres) {
             Scope sc(h, "pair_mtxel");
             CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
         }
         {
             Scope sc(h, "subspace_projection");
             if (split) {
-                if ((s = oz_product(h, h->Mbuf, cnt, ng, neig, h->MBbuf))) return s;
+                if ((s = oz_product(h, Mc, cnt, ng, neig, h->MBbuf))) return s;
             } else {
-                CK(h, gw::launch_zgemm(h->Mbuf, (const double2 *)basis, h->MBbuf, cnt, ng, neig, h->st), "projection");
+                CK(h, gw::launch_zgemm(Mc, (const double2 *)basis, h->MBbuf, cnt, ng, neig, h->st), "projection");
             }
         }
         {
@@ -325,9 +327,11 @@ gw_status gw_chi0_compute_real(gw_chi0 *h, int iq, int nw, const double *omega, 
         return s;
     CK(h, cudaMemsetAsync(h->realbuf, 0, sizeof(double2) * 3 * nw * nn, h->st), "zero parts");
     gw::PairPlan pp = pair_plan(h, sp);
+    const double2 *Mres = resident_for(h, iq); // kept by the last gw_chi0_compute of this slot
     for (int64_t p0 = 0; p0 < P; p0 += chunk) {
         const int64_t cnt = std::min(chunk, P - p0);
-        {
+        const double2 *Mc = Mres ? Mres + p0 * ng : h->Mbuf;
+        if (!Mres) {
             Scope sc(h, "pair_mtxel");
             CK(h, run_pair(h, v.psi, h->cond.psi, h->cond.nb, p0, cnt, pp, h->Mbuf), "pair kernel");
         }
@@ -336,7 +340,7 @@ gw_status gw_chi0_compute_real(gw_chi0 *h, int iq, int nw, const double *omega, 
             CK(h, gw::launch_delta_real(v.energy, h->cond.energy, h->cond.nb, p0, cnt, om, eta, h->dbuf, h->st),
                "real-axis delta");
         }
-        if ((s = contract_chunk(h, h->Mbuf, cnt, ng, h->dbuf, cnt, 3 * nw, h->realbuf))) return s;
+        if ((s = contract_chunk(h, Mc, cnt, ng, h->dbuf, cnt, 3 * nw, h->realbuf))) return s;
     }
     Scope sc(h, "symmetrize");
     CK(h, gw::launch_symmetrize(h->realbuf, ng, 3 * nw, h->st), "symmetrize");

@@ -142,6 +142,12 @@ struct gw_chi0 {
     double *eigW = nullptr;
     int *eigInfo = nullptr;
     size_t eigA_cap = 0, eigWork_cap = 0, eigW_cap = 0, eigInfo_cap = 0;
+    // pair elements of one slot kept resident between calls (gw_chi0_keep_pair_elements): written
+    // by gw_chi0_compute, reused by gw_chi0_compute_subspace / gw_chi0_compute_real
+    bool keep_m = false;
+    double2 *Mres = nullptr;
+    size_t Mres_cap = 0; // bytes
+    int Mres_iq = -1;    // slot whose elements the buffer holds; -1: none
     // plasmon-pole self-energy work buffers (api_sigma.cu)
     struct Buf {
         void *p = nullptr;
@@ -230,8 +236,13 @@ gw::PairPlan pair_plan(gw_chi0 *h, const Sphere &s);
 void free_bands(gw_chi0 *h, BandSet &b);
 void free_sphere(gw_chi0 *h, Sphere &s);
 
-// overlapped split-precision streamed compute of one slot (api.cu)
-gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *cq, double *dq);
+// resident pair elements: resident_begin makes room for slot iq's P x ng elements when keeping is
+// on and they fit (*use), invalidating what the buffer held; resident_for(h, iq) is the buffer when
+// it holds slot iq, else null
+gw_status resident_begin(gw_chi0 *h, int64_t P, int ng, bool *use);
+double2 *resident_for(gw_chi0 *h, int iq);
+// overlapped split-precision streamed compute of one slot (api.cu); Mres: resident output or null
+gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *cq, double *dq, double2 *Mres);
 bool overlap_enabled(gw_chi0 *h, const gw::PairPlan &pp);
 
 // batched path (api_batch.cu)

@@ -168,3 +168,38 @@ def test_jvp_matches_oracle(gw, case, prec, mtxel, tol):
         ref = oracle.jvp(p.gpsi, p.cv, p.ev, p.cc, p.ec, p.gchi, dcv, dcc, dev, dec, w)
         assert rel(got[i], ref) <= tol, (w, rel(got[i], ref))
         assert np.array_equal(got[i], got[i].conj().T)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_resident_pair_elements(gw, case, prec):
+    """With the pair elements kept resident, the subspace and real-axis calls that reuse them give
+    the same bits as the ones that recompute them; new bands drop them (results follow the new
+    bands)."""
+    p, M, chi_0, neig = case
+    C, _ = oracle.subspace_basis(chi_0, neig)
+    Cd = torch.as_tensor(C, device="cuda")
+    outs = {}
+    for keep in (False, True):
+        h = gw.from_problem(p, prec=prec, nslices=7, mtxel="twofloat")
+        if keep:
+            h.keep_pair_elements(True)
+        h.compute(0, [0.0])
+        sub = h.compute_subspace(0, Cd, OMEGA).cpu().numpy()
+        real = h.compute_real(0, [3.0], 0.2).cpu().numpy()
+        h.sync()
+        outs[keep] = (sub, real, h)
+    assert np.array_equal(outs[False][0], outs[True][0])
+    assert np.array_equal(outs[False][1], outs[True][1])
+    # new valence bands on the kept slot: the resident elements are dropped
+    h = outs[True][2]
+    q = gwgen.make_problem(p.grid, p.cv.shape[0], p.cc.shape[0], p.gpsi.shape[0], p.gchi.shape[0],
+                           seed=gwgen.BASE_SEED + 32)
+    h.set_bands(0, 0, torch.as_tensor(q.gpsi, device="cuda"), torch.as_tensor(q.cv, device="cuda"),
+                torch.as_tensor(q.ev, device="cuda"))
+    sub2 = h.compute_subspace(0, Cd, OMEGA).cpu().numpy()
+    h.sync()
+    Mq = oracle.m_conv(q.gpsi, q.cv, p.gpsi, p.cc, p.gchi)
+    want = oracle.chi0_subspace(Mq, oracle.delta(q.ev, p.ec, OMEGA[1]), C)
+    assert rel(sub2[1], want) < (1e-11 if prec == "fp64" else 1e-9)
+    for k in outs:
+        outs[k][2].destroy()
