@@ -885,6 +885,12 @@ def extras(args):
     d, tj = timed(lambda: h.jvp(0, [0.0], dcv, dcc, dev, dec))
     h.set_timing(False)
     (chi,), tc = timed(lambda: h.compute(0, [0.0]))
+    # the same calls reusing chi(0)'s resident pair elements
+    h.keep_pair_elements(True)
+    h.compute(0, [0.0])
+    _, trr = timed(lambda: h.compute_real(0, [2.0, 15.0, 40.0], 0.1))
+    _, tjr = timed(lambda: h.jvp(0, [0.0], dcv, dcc, dev, dec))
+    h.keep_pair_elements(False)
     h.sync()
     ci = (real[1] - real[1].conj().T) / 2j
     s = args.nslices
@@ -910,6 +916,7 @@ def extras(args):
     print(json.dumps({"workload": f"{cfg.name}: 48^3, {cfg.nv}+{cfg.nc} bands, N_G={cfg.ng}",
                       "prec": args.prec, "nslices": args.nslices, "ms_chi_imag_axis_1w": tc,
                       "ms_chi_real_axis_per_w": tr / 3, "ms_jvp_1w": tj,
+                      "ms_chi_real_axis_per_w_resident_m": trr / 3, "ms_jvp_1w_resident_m": tjr,
                       "kernel_ms_real_axis_3w": {k: v[0] / 2 for k, v in kr.items()},
                       "roofline": max((r for r in roofs.values() if r), key=lambda r: r["ms"], default=None),
                       "rooflines": roofs, "cpu_baseline": cpu,

@@ -304,8 +304,8 @@ GW_API gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double 
 /*
  * Keep pair elements resident (enable = 1): gw_chi0_compute then writes the M of each slot it
  * computes into a library-owned buffer (P x N_G complex128, 4.2 GB on the 48^3 workload) instead
- * of one chunk buffer, and gw_chi0_compute_subspace / gw_chi0_compute_real on the last slot
- * computed reuse it and skip stage (a).  The buffer is taken only when it fits the handle's memory
+ * of one chunk buffer, and gw_chi0_compute_subspace / gw_chi0_compute_real / gw_chi0_jvp on the
+ * last slot computed reuse it (stage (a) skipped; the JVP still forms its two tangent products).  The buffer is taken only when it fits the handle's memory
  * budget (when one is set) and half the free device memory; otherwise compute runs as without.
  * gw_chi0_set_bands / gw_chi0_set_gsphere of that slot (or of the conduction set) drop the
  * elements.  enable = 0 (the default) frees the buffer.  GW_ERR_ARG for other values.

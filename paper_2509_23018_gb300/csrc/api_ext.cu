@@ -424,14 +424,16 @@ gw_status gw_chi0_jvp(gw_chi0 *h, int iq, int nw, const double *omega, const dou
     JCK(cudaMemsetAsync(T, 0, szt, h->st), "zero parts");
     double2 *Tp = T, *Tm = T + (int64_t)nw * nn, *Tw = T + 2 * (int64_t)nw * nn;
     gw::PairPlan pp = pair_plan(h, sp);
+    const double2 *Mres = resident_for(h, iq); // kept by the last gw_chi0_compute of this slot
     for (int64_t p0 = 0; p0 < P; p0 += chunk) {
         const int64_t cnt = std::min(chunk, P - p0);
+        const double2 *Mc = Mres ? Mres + p0 * ng : h->Mbuf;
         {
             Scope sc(h, "pair_mtxel");
-            JCK(run_pair(h, v.psi, c.psi, nc, p0, cnt, pp, h->Mbuf), "pair kernel");
+            if (!Mres) JCK(run_pair(h, v.psi, c.psi, nc, p0, cnt, pp, h->Mbuf), "pair kernel");
             JCK(run_pair(h, gv, c.psi, nc, p0, cnt, pp, X1), "pair kernel (tangent valence)");
             JCK(run_pair(h, v.psi, gc, nc, p0, cnt, pp, X2), "pair kernel (tangent conduction)");
-            JCK(gw::launch_jvp_mix(h->Mbuf, X1, X2, cnt * ng, h->st), "M +- dM");
+            JCK(gw::launch_jvp_mix(Mc, X1, X2, cnt * ng, h->st), "M +- dM");
         }
         {
             Scope sc(h, "delta");
@@ -441,7 +443,7 @@ gw_status gw_chi0_jvp(gw_chi0 *h, int iq, int nw, const double *omega, const dou
         // d chi = [chi(M + dM) - chi(M - dM)] / 2 + sum_p conj(M) dDelta M
         if ((s = contract_chunk(h, X1, cnt, ng, h->dbuf, cnt, nw, Tp)) ||
             (s = contract_chunk(h, X2, cnt, ng, h->dbuf, cnt, nw, Tm)) ||
-            (s = contract_chunk(h, h->Mbuf, cnt, ng, wb, cnt, 2 * nw, Tw))) {
+            (s = contract_chunk(h, Mc, cnt, ng, wb, cnt, 2 * nw, Tw))) {
             cleanup();
             return s;
         }

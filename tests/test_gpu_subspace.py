@@ -172,12 +172,17 @@ def test_jvp_matches_oracle(gw, case, prec, mtxel, tol):
 
 @pytest.mark.parametrize("prec", ["fp64", "ozaki"])
 def test_resident_pair_elements(gw, case, prec):
-    """With the pair elements kept resident, the subspace and real-axis calls that reuse them give
-    the same bits as the ones that recompute them; new bands drop them (results follow the new
-    bands)."""
+    """With the pair elements kept resident, the subspace, real-axis and forward-derivative calls
+    that reuse them give the same bits as the ones that recompute them; new bands drop them
+    (results follow the new bands)."""
     p, M, chi_0, neig = case
     C, _ = oracle.subspace_basis(chi_0, neig)
     Cd = torch.as_tensor(C, device="cuda")
+    rng = np.random.default_rng(8)
+    tan = lambda shape: torch.as_tensor((rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * 1e-2,
+                                        device="cuda")
+    dcv, dcc = tan(p.cv.shape), tan(p.cc.shape)
+    dev_, dec_ = (torch.as_tensor(rng.standard_normal(n), device="cuda") for n in (len(p.ev), len(p.ec)))
     outs = {}
     for keep in (False, True):
         h = gw.from_problem(p, prec=prec, nslices=7, mtxel="twofloat")
@@ -186,10 +191,12 @@ def test_resident_pair_elements(gw, case, prec):
         h.compute(0, [0.0])
         sub = h.compute_subspace(0, Cd, OMEGA).cpu().numpy()
         real = h.compute_real(0, [3.0], 0.2).cpu().numpy()
+        jv = h.jvp(0, [1.0], dcv, dcc, dev_, dec_).cpu().numpy()
         h.sync()
-        outs[keep] = (sub, real, h)
+        outs[keep] = (sub, real, h, jv)
     assert np.array_equal(outs[False][0], outs[True][0])
     assert np.array_equal(outs[False][1], outs[True][1])
+    assert np.array_equal(outs[False][3], outs[True][3])
     # new valence bands on the kept slot: the resident elements are dropped
     h = outs[True][2]
     q = gwgen.make_problem(p.grid, p.cv.shape[0], p.cc.shape[0], p.gpsi.shape[0], p.gchi.shape[0],
