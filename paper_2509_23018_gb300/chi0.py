@@ -1,9 +1,19 @@
 """Python binding of the chi0 C ABI (argument marshalling only).
 
 Names follow include/gw_chi0.h: ``create``, ``set_bands``, ``set_gsphere``,
-``compute``, ``pair_elements``, ``contract``, ``adjoint``, ``sync``, ``destroy``.
+``compute``, ``compute_batch``, ``pair_elements``, ``contract``, ``adjoint``,
+``subspace_basis``, ``compute_subspace``, ``epsilon_inverse``, ``compute_real``,
+``jvp``, ``sigma_gpp``, ``keep_pair_elements``, ``streams``, ``sync``, ``destroy``.
 Torch supplies device memory and the stream; every arithmetic step runs in the
 CUDA library.  Complex tensors are complex128 (interleaved re/im doubles).
+
+Typical use (one q-point)::
+
+    h = Chi0((48, 48, 48), prec="ozaki", nslices=7, mtxel="twofloat")
+    h.set_bands(0, 0, gvec_psi, c_valence, e_valence)     # kind 0: valence at k+q
+    h.set_bands(0, 1, gvec_psi, c_conduction, e_conduction)
+    h.set_gsphere(0, gvec_chi)
+    (chi,) = h.compute(0, [0.0, 2.0])                    # [n_omega, N_G, N_G]
 """
 from __future__ import annotations
 
