@@ -304,38 +304,53 @@ gw_status contract_chunk_ozaki(gw_chi0 *h, const double2 *M, int64_t P, int ng, 
 {
     const int s = h->d.nslices;
     const int64_t kpad = (P + 63) / 64 * 64;
+    const size_t zper = (size_t)s * 2 * ng * kpad; // bf16 slices of one frequency
+    // several frequencies: slice a group at once (M read once per pass for the group), the group's
+    // slices within 4 GiB
+    const int wg = nw == 1 ? 1 : std::max(1, std::min({nw, gw::oz_group_w(), (int)(4294967296.0 / (2.0 * zper))}));
     gw_status st;
-    if ((st = grow(h, &h->Zbuf, &h->Zcap, (size_t)s * 2 * ng * kpad * 2, "slice buffer")) ||
+    if ((st = grow(h, &h->Zbuf, &h->Zcap, zper * 2 * wg, "slice buffer")) ||
         (st = grow(h, (void **)&h->spbuf, &h->spcap, sizeof(double) * (size_t)nw * dstride, "scale buffer")) ||
-        (st = grow(h, (void **)&h->Ebuf, &h->Ecap, sizeof(int) * (size_t)ng, "exponent buffer")))
+        (st = grow(h, (void **)&h->Ebuf, &h->Ecap, sizeof(int) * (size_t)ng * wg, "exponent buffer")))
         return st;
     {
         Scope sc(h, "oz_split");
         CK(h, gw::launch_oz_sqrt(delta, (int64_t)nw * dstride, h->spbuf, h->st), "oz sqrt");
     }
     const int bn = h->tuned_bn;
-    for (int w = 0; w < nw; ++w) {
-        const double *sp = h->spbuf + (int64_t)w * dstride;
+    for (int w0 = 0; w0 < nw; w0 += wg) {
+        const int cnt = std::min(wg, nw - w0);
+        const double *sp = h->spbuf + (int64_t)w0 * dstride;
         {
             Scope sc(h, "oz_split");
-            CK(h, gw::launch_oz_colexp(M, P, ng, sp, h->Ebuf, h->st), "oz exponents");
-            CK(h, gw::launch_oz_slice(M, P, ng, sp, h->Ebuf, s, kpad, h->Zbuf, h->st), "oz slices");
-        }
-        std::vector<gw::OzJob> jobs(1);
-        if ((st = oz_job(h, jobs[0], h->Zbuf, kpad, ng, h->Ebuf, chi + (int64_t)w * ng * ng, bn))) return st;
-        // few tiles (small N_G): split K over jobs so that about one wave of blocks runs,
-        // at least 8 K-steps each; the atomic epilogue adds the parts
-        const int nk = jobs[0].nk;
-        const int ks = std::max(1, std::min(num_sms() / std::max(1, jobs[0].ntiles), nk / 8));
-        if (ks > 1) {
-            const gw::OzJob base = jobs[0];
-            jobs.assign(ks, base);
-            for (int i = 0; i < ks; ++i) {
-                jobs[i].kb0 = (int)((int64_t)nk * i / ks);
-                jobs[i].nk = (int)((int64_t)nk * (i + 1) / ks) - jobs[i].kb0;
+            if (cnt == 1) {
+                CK(h, gw::launch_oz_colexp(M, P, ng, sp, h->Ebuf, h->st), "oz exponents");
+                CK(h, gw::launch_oz_slice(M, P, ng, sp, h->Ebuf, s, kpad, h->Zbuf, h->st), "oz slices");
+            } else {
+                CK(h, gw::launch_oz_split_multi(M, P, ng, sp, dstride, cnt, h->Ebuf, s, kpad, h->Zbuf, (int64_t)zper,
+                                                h->st),
+                   "oz slices (frequency group)");
             }
         }
-        if ((st = launch_oz_jobs(h, jobs, bn))) return st;
+        for (int j = 0; j < cnt; ++j) {
+            std::vector<gw::OzJob> jobs(1);
+            if ((st = oz_job(h, jobs[0], (uint16_t *)h->Zbuf + zper * j, kpad, ng, h->Ebuf + (size_t)ng * j,
+                             chi + (int64_t)(w0 + j) * ng * ng, bn)))
+                return st;
+            // few tiles (small N_G): split K over jobs so that about one wave of blocks runs,
+            // at least 8 K-steps each; the atomic epilogue adds the parts
+            const int nk = jobs[0].nk;
+            const int ks = std::max(1, std::min(num_sms() / std::max(1, jobs[0].ntiles), nk / 8));
+            if (ks > 1) {
+                const gw::OzJob base = jobs[0];
+                jobs.assign(ks, base);
+                for (int i = 0; i < ks; ++i) {
+                    jobs[i].kb0 = (int)((int64_t)nk * i / ks);
+                    jobs[i].nk = (int)((int64_t)nk * (i + 1) / ks) - jobs[i].kb0;
+                }
+            }
+            if ((st = launch_oz_jobs(h, jobs, bn))) return st;
+        }
     }
     return GW_OK;
 }

@@ -110,6 +110,11 @@ size_t contract_f64_smem(int bt);
 cudaError_t launch_oz_sqrt(const double *delta, int64_t n, double *sp, cudaStream_t st);
 // E[g] = column exponent of s_p M[p][g] over the chunk
 cudaError_t launch_oz_colexp(const double2 *M, int64_t P, int ng, const double *sp, int *E, cudaStream_t st);
+// A group of nw <= oz_group_w() frequencies at once (scales sp + w dstride): exponents E[w][ng],
+// slices of frequency w at Z + w zstride (bf16 elements); M read once per pass for the group.
+int oz_group_w();
+cudaError_t launch_oz_split_multi(const double2 *M, int64_t P, int ng, const double *sp, int64_t dstride, int nw,
+                                  int *E, int s, int64_t kpad, void *Z, int64_t zstride, cudaStream_t st);
 // Z[i][j][p] bf16 slices, rows p in [P, kpad) zero
 cudaError_t launch_oz_slice(const double2 *M, int64_t P, int ng, const double *sp, const int *E, int s,
                             int64_t kpad, void *Z, cudaStream_t st);

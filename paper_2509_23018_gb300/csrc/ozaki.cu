@@ -126,6 +126,111 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double2 *__restrict
     }
 }
 
+// ------------------------------------------------------------------ split for several frequencies
+// The scale s_p(w) = sqrt(-Delta_p(w)) is the only thing that changes with the frequency, so a
+// group of up to kOzGroupW frequencies shares one read of M: exponents E[w][g] in one pass,
+// slices Z_w in another (each frequency's slices at Z + w zstride), the digits as in
+// oz_slice_kernel.
+constexpr int kOzGroupW = 8;
+
+__global__ void __launch_bounds__(256) oz_colexp_multi_kernel(const double2 *__restrict__ M, int64_t P, int ng,
+                                                              const double *__restrict__ sp, int64_t dstride,
+                                                              int nw, int *__restrict__ E)
+{
+    __shared__ int red[8][32][kOzGroupW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int g = blockIdx.x * 32 + lane;
+    int e[kOzGroupW];
+#pragma unroll
+    for (int w = 0; w < kOzGroupW; ++w) e[w] = kOzNoColumn;
+    if (g < ng) {
+        for (int64_t p = (int64_t)blockIdx.y * 8 + wid; p < P; p += (int64_t)gridDim.y * 8) {
+            const double2 m = M[p * ng + g];
+            const double a0 = fmax(fabs(m.x), fabs(m.y));
+#pragma unroll
+            for (int w = 0; w < kOzGroupW; ++w)
+                if (w < nw) {
+                    const double a = a0 * sp[(int64_t)w * dstride + p];
+                    if (a > 0.0) {
+                        const int be = (int)((__double_as_longlong(a) >> 52) & 0x7ff);
+                        e[w] = max(e[w], (be == 0 ? -1023 : be - 1023) + 2);
+                    }
+                }
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < kOzGroupW; ++w) red[wid][lane][w] = e[w];
+    __syncthreads();
+    if (wid == 0 && g < ng) {
+#pragma unroll
+        for (int w = 0; w < kOzGroupW; ++w)
+            if (w < nw) {
+                int v = red[0][lane][w];
+                for (int k = 1; k < 8; ++k) v = max(v, red[k][lane][w]);
+                atomicMax(E + (int64_t)w * ng + g, v);
+            }
+    }
+}
+
+__global__ void __launch_bounds__(256) oz_slice_multi_kernel(const double2 *__restrict__ M, int64_t P, int ng,
+                                                             const double *__restrict__ spv, int64_t dstride, int nw,
+                                                             const int *__restrict__ E, int s, int64_t kpad,
+                                                             int64_t zstride, __nv_bfloat16 *__restrict__ Z)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint16_t *zs = (uint16_t *)smem; // [s][64 rows j][64 + 8 pairs] (padded)
+    constexpr int LD = 72;
+    const int64_t p0 = (int64_t)blockIdx.y * 64;
+    const int g0 = blockIdx.x * 32;
+    const int nrows = 2 * ng;
+    // the block's 64 x 32 tile of M, read once for every frequency of the group
+    double2 m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int e = threadIdx.x + u * 256, pl = e >> 5, gl = e & 31;
+        const int64_t p = p0 + pl;
+        const int g = g0 + gl;
+        m[u] = (p < P && g < ng) ? M[p * ng + g] : make_double2(0.0, 0.0);
+    }
+    for (int w = 0; w < nw; ++w) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = threadIdx.x + u * 256, pl = e >> 5, gl = e & 31;
+            const int64_t p = p0 + pl;
+            const int g = g0 + gl;
+            double2 a = make_double2(0.0, 0.0);
+            int Eg = kOzNoColumn;
+            if (p < P && g < ng) {
+                const double sp = spv[(int64_t)w * dstride + p];
+                a = make_double2(m[u].x * sp, m[u].y * sp);
+                Eg = E[(int64_t)w * ng + g];
+            }
+            const int sh = kOzBeta * s - Eg;
+            const double sc = __longlong_as_double((long long)(1023 + max(-1022, min(1023, sh))) << 52);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                long long N = __double2ll_rn((c ? a.y : a.x) * sc);
+                for (int i = s - 1; i >= 1; --i) {
+                    int d = (int)((N + 32) & 63) - 32;
+                    N = (N - d) >> 6;
+                    zs[(i * 64 + 2 * gl + c) * LD + pl] = (uint16_t)(__float_as_uint((float)d) >> 16);
+                }
+                zs[(0 * 64 + 2 * gl + c) * LD + pl] = (uint16_t)(__float_as_uint((float)N) >> 16);
+            }
+        }
+        __syncthreads();
+        __nv_bfloat16 *Zw = Z + w * zstride;
+        for (int e = threadIdx.x; e < s * 64 * 8; e += blockDim.x) {
+            const int i = e / (64 * 8), r = (e >> 3) & 63, v = e & 7;
+            const int j = 2 * g0 + r;
+            if (j >= nrows) continue;
+            const uint4 val = *(const uint4 *)(zs + (i * 64 + r) * LD + v * 8);
+            *(uint4 *)(Zw + ((int64_t)i * nrows + j) * kpad + p0 + v * 8) = val;
+        }
+        __syncthreads(); // before the next frequency rewrites zs
+    }
+}
+
 // ------------------------------------------------------------------ general product: slices
 // Y = A B with A split by rows and B by columns: x = 2^E sum_{i=1..s} 2^(-6 i) z_i, the same
 // balanced base-64 digits as oz_slice_kernel, with E = max(ilogb) + 2 over a row of A or a
@@ -645,6 +750,28 @@ cudaError_t launch_oz_colexp(const double2 *M, int64_t P, int ng, const double *
     if (e != cudaSuccess || P == 0) return e;
     int gy = (int)std::min<int64_t>((P + 63) / 64, 256);
     oz_colexp_kernel<<<dim3((ng + 31) / 32, gy), 256, 0, st>>>(M, P, ng, sp, E);
+    return cudaGetLastError();
+}
+
+int oz_group_w() { return kOzGroupW; }
+
+cudaError_t launch_oz_split_multi(const double2 *M, int64_t P, int ng, const double *sp, int64_t dstride, int nw,
+                                  int *E, int s, int64_t kpad, void *Z, int64_t zstride, cudaStream_t st)
+{
+    if (nw < 1 || nw > kOzGroupW) return cudaErrorInvalidValue;
+    oz_fill_kernel<<<(unsigned)(((int64_t)nw * ng + 255) / 256), 256, 0, st>>>(E, nw * ng, kOzNoColumn);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (P > 0) {
+        const int gy = (int)std::min<int64_t>((P + 63) / 64, 256);
+        oz_colexp_multi_kernel<<<dim3((ng + 31) / 32, gy), 256, 0, st>>>(M, P, ng, sp, dstride, nw, E);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const size_t sm = (size_t)s * 64 * 72 * sizeof(uint16_t);
+    e = cudaFuncSetAttribute(oz_slice_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    oz_slice_multi_kernel<<<dim3((ng + 31) / 32, (unsigned)(kpad / 64)), 256, sm, st>>>(
+        M, P, ng, sp, dstride, nw, E, s, kpad, zstride, (__nv_bfloat16 *)Z);
     return cudaGetLastError();
 }
 

@@ -105,3 +105,23 @@ def test_streams_query(gw):
         with pytest.raises(gw.GwError):
             h.streams(5)
         h.destroy()
+
+
+@pytest.mark.parametrize("mtxel", ["twofloat", "fp64"])
+def test_frequency_group_slicing(gw, mtxel):
+    """Nine frequencies in one call (sliced in groups of up to eight from one read of M) against
+    nine single-frequency calls (sliced one by one), and against the oracle."""
+    cfg = gwgen.CONFIGS["c1_24cube"]
+    p = gwgen.config_problem(cfg)
+    om = [0.0, 0.5, 1.0, 2.0, 3.5, 5.0, 8.0, 13.0, 21.0]
+    h = gw.from_problem(p, prec="ozaki", nslices=7, mtxel=mtxel, pair_chunk=300)
+    (many,) = h.compute(0, om)
+    many = many.cpu().numpy()
+    one = np.stack([h.compute(0, [w])[0][0].cpu().numpy() for w in om])
+    h.sync()
+    assert np.abs(many - one).max() <= 1e-14 * np.abs(one).max()
+    M = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)
+    for i in (0, 4, 8):
+        ref = oracle.chi0(M, oracle.delta(p.ev, p.ec, om[i]))
+        assert np.linalg.norm(many[i] - ref) <= 1e-9 * np.linalg.norm(ref)
+    h.destroy()
