@@ -224,6 +224,12 @@ def oracle_epsilon_sample(chi, v):
     return time.perf_counter() - t0, oracle.threads()
 
 
+def workload_name(cfg):
+    """The workload both arms name in their config."""
+    return (f"{cfg.name}: grid {cfg.grid[0]}^3, {cfg.nv}+{cfg.nc} bands, N_Gpsi={cfg.ngpsi}, N_G={cfg.ng}, "
+            f"chunks of {cfg.pair_chunk} pairs, omega=0")
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -241,7 +247,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "ms_per_step": 1e3 * statistics.median(secs), "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg.name, "grid": list(cfg.grid), "nv": cfg.nv, "nc": cfg.nc,
+            "config": {"workload": workload_name(cfg), "grid": list(cfg.grid), "nv": cfg.nv, "nc": cfg.nc,
                        "ngpsi": cfg.ngpsi, "ng": cfg.ng, "sample_pairs": args.cpu_sample_pairs},
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
@@ -583,8 +589,7 @@ def ours(args):
                 "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "ms_per_q": main["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.prec == "fp64" else "bf16-split/f64", "data": "synthetic",
-                "config": {"workload": f"{cfg.name}: grid {cfg.grid[0]}^3, {cfg.nv}+{cfg.nc} bands, "
-                                       f"N_Gpsi={cfg.ngpsi}, N_G={cfg.ng}, chunks of {cfg.pair_chunk} pairs, omega=0",
+                "config": {"workload": workload_name(cfg),
                            "prec": args.prec, "nslices": args.nslices if args.prec == "ozaki" else None,
                            "mtxel": mtxel, "path": args.path, "pairs": cfg.npairs,
                            "conv_tflop_per_step": conv_flops(cfg) * 1e-12,
