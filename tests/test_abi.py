@@ -52,6 +52,7 @@ def test_create_rejects_bad_descriptors():
     from paper_2509_23018_gb300 import _lib
     lib = _lib.load()
     for grid, nq, prec, ns in [((24, 24, 7), 1, 0, 0), ((24, 24, 24), 0, 0, 0), ((24, 24, 24), 1, 9, 0),
+                               ((24, 24, 24), 1, 2, 7),  # no third (integer-sliced) precision
                                ((24, 24, 24), 1, 1, 2), ((256, 24, 24), 1, 0, 0)]:
         d = _lib.Desc()
         for a in range(3):
