@@ -3,7 +3,8 @@
 48^3 grid, 128 + 1024 bands on 6000 plane waves, N_G = 2000, 8192-pair chunks: a sampled
 block of chi (all 131072 pairs contribute) and sampled rows of M against the oracle, plus
 properties that hold at any size (Hermitian, negative semidefinite at w = 0, trace).  The same
-for the 72^3 workload (524288 pairs, N_G = 6000) in split precision.
+for the 72^3 workload (524288 pairs, N_G = 6000) in split precision, and for the batched
+workload (64 q-points x 16 frequencies, uneven spheres) in one graph-captured call.
 """
 import numpy as np
 import pytest
@@ -150,3 +151,45 @@ def test_adjoint_c5_central_differences(gw):
     hf.destroy()
     for fd, an in checks:
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+@pytest.fixture(scope="module")
+def c4():
+    cfg = gwgen.CONFIGS["c4_batch"]
+    b = gwgen.make_batch(cfg.grid, cfg.nv, cfg.nc, cfg.ngpsi, 300, 3000, 4, cfg.nw, seed=gwgen.BASE_SEED + cfg.index)
+    ngs = np.array([len(x) for x in b.gchi])
+    rng = np.random.default_rng(23)
+    refs = {}
+    for iq in dict.fromkeys([0, int(np.argmin(ngs)), int(np.argmax(ngs))]):  # q = 0, smallest, largest sphere
+        idx = np.sort(rng.choice(int(ngs[iq]), 8, replace=False))
+        Mcols = oracle.m_conv(b.gpsi, b.cv[iq], b.gpsi, b.cc, b.gchi[iq][idx])   # all 32768 pairs, 8 columns
+        refs[iq] = (idx, [oracle.chi0(Mcols, oracle.delta(b.ev[iq], b.ec, w)) for w in b.omega])
+    return cfg, b, refs
+
+
+def test_c4_sampled_batch(gw, c4):
+    """64 q-points (N_G uniform in [300, 3000]) x 16 imaginary frequencies on 40^3, 64 + 512 bands
+    on 8000 plane waves, all in one graph-captured persistent call in split precision (s = 7) with
+    two-float stage (a), as the batched benchmark runs it: sampled blocks of three slots (q = 0 and
+    the smallest and largest spheres) at every frequency against the oracle, every block Hermitian."""
+    cfg, b, refs = c4
+    h = gw.Chi0(cfg.grid, nq=len(b.qs), prec="ozaki", nslices=7, mtxel="twofloat")
+    t = lambda x: torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+    g = t(b.gpsi)
+    h.set_bands(0, 1, g, t(b.cc), t(b.ec))
+    for iq in range(len(b.qs)):
+        h.set_bands(iq, 0, g, t(b.cv[iq]), t(b.ev[iq]))
+        h.set_gsphere(iq, t(b.gchi[iq]))
+    slots = list(range(len(b.qs)))
+    res = h.compute_batch(slots, list(b.omega))
+    for r in res:
+        assert torch.equal(r, r.conj().transpose(-1, -2))
+    got = {}
+    for iq, (idx, _) in refs.items():
+        it = torch.as_tensor(idx, device="cuda")
+        got[iq] = res[iq].index_select(1, it).index_select(2, it).cpu().numpy()
+    h.sync()
+    for iq, (idx, ref) in refs.items():
+        for w in range(len(b.omega)):
+            assert rel(got[iq][w], ref[w]) <= 1e-9, (iq, w)
+    h.destroy()
