@@ -153,6 +153,31 @@ def test_adjoint_c5_central_differences(gw):
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
 
 
+def test_adjoint_c5_sampled_bands_vs_oracle(gw):
+    """The full-size adjoint (40^3, 96 + 768 bands on 4500 plane waves, N_G = 1500, split precision
+    with two-float stage (a), as the bench runs it) against the oracle adjoint on sampled bands.
+    L is a sum over pairs, so one valence band's gradient (coefficients and energy) involves only
+    its pairs with every conduction band, and one conduction band's only its pairs with every
+    valence band: the oracle runs those one-band problems, whose gradient rows are the full
+    problem's."""
+    cfg = gwgen.CONFIGS["c5_adjoint"]
+    p = gwgen.config_problem(cfg)
+    W = gwgen.hermitian(np.random.default_rng(gwgen.BASE_SEED + 4), cfg.ng)
+    h = gw.from_problem(p, prec="ozaki", nslices=7, mtxel="twofloat", pair_chunk=cfg.pair_chunk)
+    _, dEv, dEc, dcv, dcc = h.adjoint(0, torch.as_tensor(W, device="cuda"))
+    h.sync()
+    h.destroy()
+    dEv, dEc, dcv, dcc = (x.cpu().numpy() for x in (dEv, dEc, dcv, dcc))
+    v = int(np.random.default_rng(29).integers(cfg.nv))
+    _, dEvo, _, dcvo, _ = oracle.adjoint(p.gpsi, p.cv[v:v + 1], p.ev[v:v + 1], p.gpsi, p.cc, p.ec, p.gchi, W, 0.0)
+    assert rel(dcv[v], dcvo[0]) <= 1e-9
+    assert abs(dEv[v] - dEvo[0]) <= 1e-9 * float(np.abs(dEv).max())  # against the largest energy derivative
+    for c in np.random.default_rng(31).choice(cfg.nc, 2, replace=False):
+        _, _, dEco, _, dcco = oracle.adjoint(p.gpsi, p.cv, p.ev, p.gpsi, p.cc[c:c + 1], p.ec[c:c + 1], p.gchi,
+                                             W, 0.0)
+        assert rel(dcc[c], dcco[0]) <= 1e-9
+        assert abs(dEc[c] - dEco[0]) <= 1e-9 * float(np.abs(dEc).max())
+
 @pytest.fixture(scope="module")
 def c4():
     cfg = gwgen.CONFIGS["c4_batch"]

@@ -293,6 +293,22 @@ def test_adjoint_finite_differences(adj_case, w):
         assert abs((Lp - Lm) / (2 * h) - dEc[i]) < 1e-6 * max(1, abs(dEc[i]))
 
 
+def test_adjoint_rows_from_one_band_problems():
+    """L = Re Tr(W chi) is a sum over pairs, so a valence band's gradient row (coefficients and
+    energy) is that of the problem with this valence band alone and every conduction band, and a
+    conduction band's that of the problem with it alone; the full-size GPU adjoint is checked on
+    sampled bands through exactly these one-band problems."""
+    p = gwgen.make_problem((12, 12, 12), 3, 5, 60, 30, seed=7)
+    W = gwgen.hermitian(np.random.default_rng(3), 30)
+    _, dEv, dEc, dcv, dcc = oracle.adjoint(p.gpsi, p.cv, p.ev, p.gpsi, p.cc, p.ec, p.gchi, W, 0.0)
+    for v in range(3):
+        _, a, _, b, _ = oracle.adjoint(p.gpsi, p.cv[v:v + 1], p.ev[v:v + 1], p.gpsi, p.cc, p.ec, p.gchi, W, 0.0)
+        assert abs(a[0] - dEv[v]) <= 1e-13 * abs(dEv[v]) and np.allclose(b[0], dcv[v], rtol=0, atol=1e-13 * abs(dcv).max())
+    for c in range(5):
+        _, _, e, _, f = oracle.adjoint(p.gpsi, p.cv, p.ev, p.gpsi, p.cc[c:c + 1], p.ec[c:c + 1], p.gchi, W, 0.0)
+        assert abs(e[0] - dEc[c]) <= 1e-13 * abs(dEc[c]) and np.allclose(f[0], dcc[c], rtol=0, atol=1e-13 * abs(dcc).max())
+
+
 def test_adjoint_identity_W_energy_closed_form(adj_case):
     """W = I: L = sum_p Delta_p |m_p|^2 and dL/dE_v = sum_c |m_vc|^2 4(w^2-x^2)/(x^2+w^2)^2."""
     p, _ = adj_case
