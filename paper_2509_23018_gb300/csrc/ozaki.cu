@@ -20,6 +20,7 @@
 #include "internal.h"
 #include "ptx.cuh"
 #include "fft_tf.cuh"
+#include "oz_digits.cuh"
 #include <cuda_bf16.h>
 #include <algorithm>
 
@@ -53,13 +54,9 @@ __global__ void oz_colexp_kernel(const double2 *__restrict__ M, int64_t P, int n
     int e = kOzNoColumn;
     if (g < ng) {
         for (int64_t p = (int64_t)blockIdx.y * 8 + wid; p < P; p += (int64_t)gridDim.y * 8) {
-            double2 m = M[p * ng + g];
-            double a = fmax(fabs(m.x), fabs(m.y)) * sp[p];
-            if (a > 0.0) {
-                int be = (int)((__double_as_longlong(a) >> 52) & 0x7ff);
-                int x = (be == 0 ? -1023 : be - 1023) + 2;
-                e = max(e, x);
-            }
+            const double2 m = M[p * ng + g];
+            const double a = oz_bits_d(oz_absmax_bits(m.x, m.y)) * sp[p];
+            e = max(e, oz_expo_pos(a, kOzNoColumn));
         }
     }
     red[wid][lane] = e;
@@ -87,6 +84,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double2 *__restrict
     constexpr int LD = 72;
     const int64_t p0 = (int64_t)blockIdx.y * 64;
     const int g0 = blockIdx.x * 32;
+    const long long bias = oz_digit_bias(s);
     for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
         const int pl = e >> 5, gl = e & 31;
         const int64_t p = p0 + pl;
@@ -99,20 +97,11 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double2 *__restrict
             a = make_double2(m.x * sp, m.y * sp);
             Eg = E[g];
         }
-        // N = round(a 2^(6 s - E)): an exact power-of-two scaling, then round to nearest
+        // N = round(a 2^(6 s - E)) and its balanced base-64 digits, in integer arithmetic
         const int sh = kOzBeta * s - Eg;
-        const double sc = __longlong_as_double((long long)(1023 + max(-1022, min(1023, sh))) << 52);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            long long N = __double2ll_rn((c ? a.y : a.x) * sc);
-            // balanced base-64 digits, least significant first; the top digit keeps the rest
-            for (int i = s - 1; i >= 1; --i) {
-                int d = (int)((N + 32) & 63) - 32;
-                N = (N - d) >> 6;
-                zs[(i * 64 + 2 * gl + c) * LD + pl] = (uint16_t)(__float_as_uint((float)d) >> 16);
-            }
-            zs[(0 * 64 + 2 * gl + c) * LD + pl] = (uint16_t)(__float_as_uint((float)N) >> 16);
-        }
+        for (int c = 0; c < 2; ++c)
+            oz_store_digits(oz_round_scaled(c ? a.y : a.x, sh), s, bias, zs + (2 * gl + c) * LD + pl, 64 * LD);
     }
     __syncthreads();
     // rows j = 2 g0 .. 2 g0 + 63 of each slice, 64 consecutive pairs = 128 bytes
@@ -146,15 +135,12 @@ __global__ void __launch_bounds__(256) oz_colexp_multi_kernel(const double2 *__r
     if (g < ng) {
         for (int64_t p = (int64_t)blockIdx.y * 8 + wid; p < P; p += (int64_t)gridDim.y * 8) {
             const double2 m = M[p * ng + g];
-            const double a0 = fmax(fabs(m.x), fabs(m.y));
+            const double a0 = oz_bits_d(oz_absmax_bits(m.x, m.y));
 #pragma unroll
             for (int w = 0; w < kOzGroupW; ++w)
                 if (w < nw) {
                     const double a = a0 * sp[(int64_t)w * dstride + p];
-                    if (a > 0.0) {
-                        const int be = (int)((__double_as_longlong(a) >> 52) & 0x7ff);
-                        e[w] = max(e[w], (be == 0 ? -1023 : be - 1023) + 2);
-                    }
+                    e[w] = max(e[w], oz_expo_pos(a, kOzNoColumn));
                 }
         }
     }
@@ -183,6 +169,7 @@ __global__ void __launch_bounds__(256) oz_slice_multi_kernel(const double2 *__re
     const int64_t p0 = (int64_t)blockIdx.y * 64;
     const int g0 = blockIdx.x * 32;
     const int nrows = 2 * ng;
+    const long long bias = oz_digit_bias(s);
     // the block's 64 x 32 tile of M, read once for every frequency of the group
     double2 m[8];
 #pragma unroll
@@ -206,17 +193,9 @@ __global__ void __launch_bounds__(256) oz_slice_multi_kernel(const double2 *__re
                 Eg = E[(int64_t)w * ng + g];
             }
             const int sh = kOzBeta * s - Eg;
-            const double sc = __longlong_as_double((long long)(1023 + max(-1022, min(1023, sh))) << 52);
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                long long N = __double2ll_rn((c ? a.y : a.x) * sc);
-                for (int i = s - 1; i >= 1; --i) {
-                    int d = (int)((N + 32) & 63) - 32;
-                    N = (N - d) >> 6;
-                    zs[(i * 64 + 2 * gl + c) * LD + pl] = (uint16_t)(__float_as_uint((float)d) >> 16);
-                }
-                zs[(0 * 64 + 2 * gl + c) * LD + pl] = (uint16_t)(__float_as_uint((float)N) >> 16);
-            }
+            for (int c = 0; c < 2; ++c)
+                oz_store_digits(oz_round_scaled(c ? a.y : a.x, sh), s, bias, zs + (2 * gl + c) * LD + pl, 64 * LD);
         }
         __syncthreads();
         __nv_bfloat16 *Zw = Z + w * zstride;
@@ -235,24 +214,15 @@ __global__ void __launch_bounds__(256) oz_slice_multi_kernel(const double2 *__re
 // Y = A B with A split by rows and B by columns: x = 2^E sum_{i=1..s} 2^(-6 i) z_i, the same
 // balanced base-64 digits as oz_slice_kernel, with E = max(ilogb) + 2 over a row of A or a
 // column of B (both parts of a complex entry).
-__device__ __forceinline__ int oz_expo(double a)
+// exponent of a complex entry: ilogb(max(|Re|, |Im|)) + 2
+__device__ __forceinline__ int oz_expo(double2 x)
 {
-    if (!(a > 0.0)) return kOzNoColumn;
-    const int be = (int)((__double_as_longlong(a) >> 52) & 0x7ff);
-    return (be == 0 ? -1023 : be - 1023) + 2;
+    return oz_expo_bits(oz_absmax_bits(x.x, x.y), kOzNoColumn);
 }
 
 __device__ __forceinline__ void oz_digits(double x, int E, int s, uint16_t *out, int64_t plane)
 {
-    const int sh = kOzBeta * s - E;
-    const double sc = __longlong_as_double((long long)(1023 + max(-1022, min(1023, sh))) << 52);
-    long long N = __double2ll_rn(x * sc);
-    for (int i = s - 1; i >= 1; --i) {
-        const int d = (int)((N + 32) & 63) - 32;
-        N = (N - d) >> 6;
-        out[i * plane] = (uint16_t)(__float_as_uint((float)d) >> 16);
-    }
-    out[0] = (uint16_t)(__float_as_uint((float)N) >> 16);
+    oz_store_digits(oz_round_scaled(x, kOzBeta * s - E), s, oz_digit_bias(s), out, plane);
 }
 
 __device__ __forceinline__ int oz_block_max(int e, int *red)
@@ -283,7 +253,7 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(const double2 *__res
     int e = kOzNoColumn;
     for (int g = threadIdx.x; g < ka; g += blockDim.x) {
         const double2 x = a[g];
-        e = max(e, oz_expo(fmax(fabs(x.x), fabs(x.y))));
+        e = max(e, oz_expo(x));
     }
     e = oz_block_max(e, red);
     if (threadIdx.x == 0) E[p] = e;
@@ -311,7 +281,7 @@ __global__ void __launch_bounds__(256) oz_split_cols_kernel(const double2 *__res
     int e = kOzNoColumn;
     for (int g = threadIdx.x; g < ka; g += blockDim.x) {
         const double2 x = B[(int64_t)g * sk + (int64_t)b * sj];
-        e = max(e, oz_expo(fmax(fabs(x.x), fabs(x.y))));
+        e = max(e, oz_expo(x));
     }
     e = oz_block_max(e, red);
     if (threadIdx.x == 0) E[b] = e;
