@@ -33,6 +33,10 @@
  *     a message is kept for gw_chi0_last_error and the handle stays usable.
  *   - Plane-wave vectors G are integer Miller triples (int32 [n][3]); a cubic cell with
  *     reciprocal vectors equal to the identity.
+ *   - A handle serves one host thread at a time; calls on one handle from several threads
+ *     must be serialised by the caller.  Separate handles share no state and may be used
+ *     from separate threads (gw_chi0_contract_noalloc, which has no handle, excepted: see
+ *     there).
  */
 #ifndef GW_CHI0_H
 #define GW_CHI0_H
