@@ -66,6 +66,12 @@ typedef enum {
     GW_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up (reported by gw_chi0_sync) */
 } gw_status;
 
+/*
+ * Contraction precision.  The value 2 (an Ozaki split on INT8 tensor cores, GW_PREC_OZAKI_INT8
+ * in the method's statement) is deliberately absent: this GPU runs INT8 tensor instructions at
+ * a small fraction of its BF16 rate (gw_chi0_probe measures both), so integer slices would
+ * carry more work per useful bit on a slower pipe.  gw_chi0_create rejects it with GW_ERR_ARG.
+ */
 typedef enum {
     GW_PREC_FP64 = 0,      /* FP64 FFT + FP64 tensor-core (DMMA) contraction */
     GW_PREC_OZAKI_BF16 = 1 /* FP64 FFT + split-precision contraction on BF16 tensor cores */
@@ -292,10 +298,13 @@ GW_API gw_status gw_chi0_sigma_gpp(gw_chi0 *h, int nb, int nocc, int nsig, int n
                                    const double *E, double *sigma);
 
 /*
- * Adjoint of L = Re Tr(W chi0(iq, w)) for a Hermitian W (GWPT-style sensitivity,
- * Eq. gwpt motivates it).  Matrix elements are recomputed chunk by chunk; Y = M W runs as
- * a split product on the BF16 tensor cores in split-precision mode, on DMMA otherwise.
- *   W        device complex128 [ng][ng], Hermitian (only its values are read).
+ * Adjoint of L = Re Tr(W chi0(iq, w)) (GWPT-style sensitivity, Eq. gwpt motivates it).
+ * Matrix elements are recomputed chunk by chunk; Y = M W_h runs as a split product on the
+ * BF16 tensor cores in split-precision mode, on DMMA otherwise.
+ *   W        device complex128 [ng][ng], any complex matrix (read only).  chi0 is Hermitian, so
+ *            L depends on W only through its Hermitian part W_h = (W + W^H)/2, which the call
+ *            forms itself: an upstream gradient dL/dchi in torch's convention (dL/dRe + i dL/dIm,
+ *            equal to W^H for this L) can be passed as it is.
  *   L        host double* or NULL: the value of L (synchronous when non-NULL).
  *   dE_v     device float64 [nv]; dE_c device float64 [nc]: dL/dE.
  *   dcoeff_v device complex128 [nv][ngpsi_v]; dcoeff_c [nc][ngpsi_c]:
@@ -354,15 +363,40 @@ GW_API int gw_chi0_timing(gw_chi0 *h, int n, char (*names)[32], double *ms, int6
 GW_API size_t gw_chi0_device_bytes(const gw_chi0 *h);
 
 /*
+ * Peak-rate probes (measurement helper; no counterpart in the paper).  Enqueues one launch on
+ * the given stream (a cudaStream_t, NULL = legacy default) that fills every SM of the current
+ * device with independent chains of one instruction kind, `iters` instructions per chain, and
+ * returns in *ops the arithmetic operations it performs (an FMA counts 2, a tensor instruction
+ * 2 m n k).  The caller times the launch (CUDA events) and divides.  These rates are the
+ * denominators of the roofline fractions of kernels bound by those pipes: FP32 FMA (scalar and
+ * packed two-lane), FP64 FMA, FP64 tensor (DMMA), and the warp-level BF16 / INT8 tensor
+ * instructions.  sink: device float32 [256], written only if a chain takes an impossible value
+ * (it keeps the chains from being optimised away).  GW_ERR_ARG for an unknown kind, iters < 1 or
+ * null pointers; GW_ERR_CUDA if the launch fails.
+ */
+typedef enum {
+    GW_PROBE_FFMA = 0,           /* fma.rn.f32 */
+    GW_PROBE_FFMA2 = 1,          /* fma.rn.f32x2 (two lanes per instruction) */
+    GW_PROBE_FADD2 = 2,          /* add.rn.f32x2 */
+    GW_PROBE_DFMA = 3,           /* fma.rn.f64 */
+    GW_PROBE_DMMA_M8N8K4 = 4,    /* mma.sync m8n8k4 f64 */
+    GW_PROBE_DMMA_M16N8K16 = 5,  /* mma.sync m16n8k16 f64 */
+    GW_PROBE_BF16_MMA_SYNC = 6,  /* mma.sync m16n8k16 bf16 -> f32 (warp-level, not tcgen05) */
+    GW_PROBE_INT8_MMA_SYNC = 7   /* mma.sync m16n8k32 s8 -> s32 (warp-level, not tcgen05) */
+} gw_probe_kind;
+GW_API gw_status gw_chi0_probe(int kind, long long iters, void *cuda_stream, float *sink, double *ops);
+
+/*
  * gw_chi0_contract_noalloc -- stage (b) in FP64 without any device allocation.
  *
  * The paper has no counterpart to this call.  It serves callers that cannot call
- * cudaMalloc: code that records its work into a CUDA graph under stream capture
- * (allocation is not capturable), plugins whose host framework owns every device
- * allocation through its own pool, and services that forbid allocator calls on their
- * hot path.  It computes what gw_chi0_contract computes in GW_PREC_FP64 mode (same
- * kernels, same arguments and layouts, chi written in full), without a handle, on the
- * given stream (a cudaStream_t; NULL = legacy default stream), for the current device.
+ * cudaMalloc: plugins whose host framework owns every device allocation through its own
+ * pool (an allocation behind the pool's back fragments it, or fails once the pool holds the
+ * free memory), and services that forbid allocator calls on their hot path (cudaMalloc and
+ * cudaFree can synchronise the device and take unbounded time).  It computes what
+ * gw_chi0_contract computes in GW_PREC_FP64 mode (same kernels, same arguments and layouts,
+ * chi written in full), without a handle, on the given stream (a cudaStream_t; NULL =
+ * legacy default stream), for the current device.
  *
  * Its only scratch -- the energy factors Delta of every pair and frequency, the kernel's
  * job table and a status word -- lives in one fixed device array compiled into the library
@@ -370,9 +404,14 @@ GW_API size_t gw_chi0_device_bytes(const gw_chi0 *h);
  *   - Limit: nw * nv * nc <= 524288; larger requests return GW_ERR_ARG and do nothing.
  *   - The first call on a device looks up that array's device address (once per device,
  *     with the device current); make that first call before any stream capture.
- *   - Every call shares the array: calls that overlap on the GPU (other streams, other
- *     host threads) race on it and must be serialised by the caller.
- *   - Device-side timeouts of bounded waits are not reported by this call.
+ *   - The job table goes up with one cudaMemcpyAsync from host memory of the calling
+ *     thread (staged by the driver; the call returns after the host side of the copy).
+ *   - Every call shares the array and finds the previous call's contents there: calls that
+ *     overlap on the GPU (other streams, other host threads) race on it and must be
+ *     serialised by the caller.  The status word is cleared at the start of each call.
+ *   - A bounded device-side wait that gives up cannot be reported through the return
+ *     value (the call returns before the kernels run); the call then writes NaN on the
+ *     diagonal of every chi block, so a partial result cannot pass as a valid one.
  * Calls no cudaMalloc, cudaFree or allocating library routine.  Returns GW_OK,
  * GW_ERR_ARG (null pointers, sizes out of range, M not 16-byte aligned, bad omega),
  * GW_ERR_CUDA, or GW_ERR_UNSUPPORTED (device ordinal >= 64).

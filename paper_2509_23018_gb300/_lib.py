@@ -19,6 +19,9 @@ STATUS_NAMES = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_STATE", 3: "GW_ERR_OOM",
                 5: "GW_ERR_UNSUPPORTED", 6: "GW_ERR_TIMEOUT"}
 GW_PREC_FP64, GW_PREC_OZAKI_BF16 = 0, 1
 GW_MTXEL_FP64, GW_MTXEL_TWOFLOAT = 0, 1
+# gw_probe_kind
+PROBES = {"ffma": 0, "ffma2": 1, "fadd2": 2, "dfma": 3, "dmma_m8n8k4": 4, "dmma_m16n8k16": 5,
+          "bf16_mma_sync": 6, "int8_mma_sync": 7}
 
 # Every entry point declared in include/gw_chi0.h, with its ctypes signature.
 P, I, I64, D, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
@@ -56,6 +59,7 @@ SIGNATURES = {
     "gw_chi0_timing": ([P, I, P, P, P, I], I),
     "gw_chi0_device_bytes": ([P], SZ),
     "gw_chi0_contract_noalloc": ([I, I, P, P, I, P, I, P, P, P], I),
+    "gw_chi0_probe": ([I, ctypes.c_longlong, P, P, ctypes.POINTER(D)], I),
 }
 
 

@@ -312,12 +312,33 @@ def contract_noalloc(ev: torch.Tensor, ec: torch.Tensor, M: torch.Tensor, omega:
                      out: torch.Tensor) -> torch.Tensor:
     """FP64 contraction through gw_chi0_contract_noalloc: no device allocation inside the call.
 
-    All tensors must already be on the current device (complex128 M [nv*nc, ng],
-    float64 ev/ec, complex128 out [nw, ng, ng]); the call uses the library's fixed
-    scratch array, so calls must not overlap on the GPU.
+    For callers that cannot allocate device memory (a host framework that owns every
+    allocation through its own pool, or a hot path where allocator calls are forbidden).
+    All tensors must already be on the current device, contiguous: float64 ev [nv] and
+    ec [nc], complex128 M [nv*nc, ng], complex128 out [nw, ng, ng] (1 <= nw <= 64).  The
+    call uses the library's fixed scratch array, so calls must not overlap on the GPU.
+    Raises ValueError before anything reaches the library when a tensor does not match.
     """
-    lib = _lib.load()
     nw = len(omega)
+    cur = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None
+    for name, t, dt in (("ev", ev, torch.float64), ("ec", ec, torch.float64), ("M", M, torch.complex128),
+                        ("out", out, torch.complex128)):
+        if not isinstance(t, torch.Tensor) or cur is None or t.device != cur:
+            raise ValueError(f"{name} must be a tensor on the current CUDA device")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if ev.dim() != 1 or ec.dim() != 1 or M.dim() != 2:
+        raise ValueError("ev, ec must be 1-D and M 2-D")
+    if not 1 <= nw <= 64:
+        raise ValueError("need 1 <= len(omega) <= 64")
+    ng = M.shape[1]
+    if M.shape[0] != ev.numel() * ec.numel():
+        raise ValueError(f"M has {M.shape[0]} rows, expected nv * nc = {ev.numel() * ec.numel()}")
+    if tuple(out.shape) != (nw, ng, ng):
+        raise ValueError(f"out must have shape {(nw, ng, ng)}, got {tuple(out.shape)}")
+    lib = _lib.load()
     om_arr = (ctypes.c_double * nw)(*[float(w) for w in omega])
     st = lib.gw_chi0_contract_noalloc(ev.shape[0], ec.shape[0], _ptr(ev), _ptr(ec), M.shape[1], _ptr(M), nw,
                                       om_arr, _ptr(out), _stream_handle())
@@ -331,8 +352,8 @@ class Chi0Fn(torch.autograd.Function):
 
     forward(handle, gvec, cv, ev, cc, ec, gchi, omega) loads the bands into slot 0 of
     ``handle`` and returns chi [ng, ng] (complex128).  backward receives dL/dchi for a
-    real L; because chi is Hermitian only the Hermitian part W of that gradient matters,
-    L = Re Tr(W chi) locally, and the gradients come from gw_chi0_adjoint (torch's
+    real L and passes it unchanged to gw_chi0_adjoint, which uses its Hermitian part W (chi is
+    Hermitian, so L = Re Tr(W chi) locally) and returns the gradients (torch's
     convention for complex inputs: dL/dRe + i dL/dIm).
     """
 
@@ -347,8 +368,8 @@ class Chi0Fn(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gchi_out):
-        W = 0.5 * (gchi_out + gchi_out.conj().transpose(0, 1))
-        _, dEv, dEc, dcv, dcc = ctx.handle.adjoint(0, W.contiguous(), omega=ctx.omega, want_L=False)
+        # the library takes the Hermitian part of the upstream gradient itself
+        _, dEv, dEc, dcv, dcc = ctx.handle.adjoint(0, gchi_out.contiguous(), omega=ctx.omega, want_L=False)
         return None, None, dcv, dEv, dcc, dEc, None, None
 
 

@@ -24,14 +24,16 @@ gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, dou
     vch = std::min<int64_t>(vch, nv);
     const int64_t cmax = vch * nc;
     // work buffers, held only for this call
-    double2 *Mb = nullptr, *Yb = nullptr, *Hb = nullptr, *pbv = nullptr, *pbc = nullptr;
+    double2 *Mb = nullptr, *Yb = nullptr, *Hb = nullptr, *pbv = nullptr, *pbc = nullptr, *Wh = nullptr;
     double *Lacc = nullptr;
     int *cs = nullptr, *cg = nullptr;
     const int ncell = (int)sp.cstart.size() - 1;
     size_t szM = sizeof(double2) * cmax * ng, szH = sizeof(double2) * cmax * nr;
     size_t szV = sizeof(double2) * (size_t)nv * nr, szC = sizeof(double2) * (size_t)nc * nr;
+    const size_t szW = sizeof(double2) * (size_t)ng * ng;
     auto cleanup = [&]() {
         cudaStreamSynchronize(h->st);
+        dfree(h, Wh, szW);
         dfree(h, Mb, szM);
         dfree(h, Yb, szM);
         dfree(h, Hb, szH);
@@ -55,10 +57,13 @@ gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, dou
         (s = dalloc(h, (void **)&pbc, szC, "conduction adjoint")) ||
         (s = dalloc(h, (void **)&Lacc, sizeof(double), "L")) ||
         (s = dalloc(h, (void **)&cs, sizeof(int) * (ncell + 1), "cells")) ||
-        (s = dalloc(h, (void **)&cg, sizeof(int) * ng, "cells"))) {
+        (s = dalloc(h, (void **)&cg, sizeof(int) * ng, "cells")) ||
+        (s = dalloc(h, (void **)&Wh, szW, "Hermitian part of W"))) {
         cleanup();
         return s;
     }
+    // L sees W only through its Hermitian part (chi is Hermitian)
+    ACK(gw::launch_herm_part((const double2 *)W, ng, Wh, h->st), "Hermitian part of W");
     ACK(cudaMemcpyAsync(cs, sp.cstart.data(), sizeof(int) * (ncell + 1), cudaMemcpyHostToDevice, h->st), "cells");
     ACK(cudaMemcpyAsync(cg, sp.cg.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, h->st), "cells");
     ACK(cudaMemsetAsync(Lacc, 0, sizeof(double), h->st), "zero");
@@ -69,7 +74,7 @@ gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, dou
     gw::PairPlan pp = pair_plan(h, sp);
     // split precision: Y = M W as a split product, W's slices once per call
     const bool split = h->d.prec == GW_PREC_OZAKI_BF16;
-    if (split && (s = oz_prepare_b(h, (const double2 *)W, ng, ng))) {
+    if (split && (s = oz_prepare_b(h, Wh, ng, ng))) {
         cleanup();
         return s;
     }
@@ -88,7 +93,7 @@ gw_status gw_chi0_adjoint(gw_chi0 *h, int iq, double omega, const double *W, dou
                     return s;
                 }
             } else {
-                ACK(gw::launch_zgemm(Mb, (const double2 *)W, Yb, cnt, ng, ng, h->st), "Y = M W");
+                ACK(gw::launch_zgemm(Mb, Wh, Yb, cnt, ng, ng, h->st), "Y = M W");
             }
         }
         {

@@ -88,6 +88,8 @@ cudaError_t launch_eps_unsym(const double2 *X, const double *sv, int ng, double2
 cudaError_t launch_conj_transpose(const double2 *V, int n, int neig, double2 *out, cudaStream_t st);
 // a bounded wait that is never satisfied: sets kStatusTimeout in *status after iters tries
 cudaError_t launch_watchdog(long long iters, int *status, cudaStream_t st);
+// out = (W + W^H) / 2 for a row-major n x n complex matrix (out must not alias W)
+cudaError_t launch_herm_part(const double2 *W, int n, double2 *out, cudaStream_t st);
 // lower triangle <- conj(upper), Im diag <- 0, for nw consecutive ng x ng blocks
 cudaError_t launch_symmetrize(double2 *chi, int ng, int nw, cudaStream_t st);
 

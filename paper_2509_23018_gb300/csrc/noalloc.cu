@@ -1,12 +1,13 @@
 // gw_chi0_contract_noalloc: the FP64 contraction for callers that must not allocate.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA graph that is
-// being captured (allocation is not a capturable operation), plugins that run under a
-// host framework which owns every device allocation through its own pool, and
-// real-time services that forbid allocator calls on their hot path.  This entry point
-// computes the same result as gw_chi0_contract in GW_PREC_FP64 mode, but the one
-// piece of scratch it needs (the energy factors Delta, and a status word) lives in a
-// fixed, file-scope device array instead of memory obtained from an allocator.
+// Some callers cannot call cudaMalloc: plugins that run under a host framework which owns
+// every device allocation through its own pool (a stray cudaMalloc there fragments the
+// pool or fails once the pool has reserved the free memory), and services that forbid
+// allocator calls on their hot path because cudaMalloc and cudaFree can synchronise the
+// device and take unbounded time.  This entry point computes the same result as
+// gw_chi0_contract in GW_PREC_FP64 mode, but the one piece of scratch it needs (the energy
+// factors Delta, the kernel's job table and a status word) lives in a fixed, file-scope
+// device array instead of memory obtained from an allocator.
 #include "../../include/gw_chi0.h"
 #include "internal.h"
 
@@ -60,6 +61,18 @@ gw_status setup(int dev, double **out)
     }
     *out = g_scratch[dev];
     return GW_OK;
+}
+
+// A bounded wait that gave up leaves its tile out of chi; mark such a result unusable by
+// writing NaN on the diagonal of every block (the caller cannot read the status word).
+__global__ void noalloc_poison_kernel(const int *status, double2 *chi, int ng, int nw)
+{
+    if (*status == 0) return;
+    const int64_t n = (int64_t)ng * nw;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = i / ng, g = i - w * ng;
+        chi[w * ng * ng + g * ng + g] = make_double2(__longlong_as_double(0x7ff8000000000000LL), 0.0);
+    }
 }
 
 } // namespace
@@ -138,5 +151,8 @@ extern "C" gw_status gw_chi0_contract_noalloc(int nv, int nc, const double *ev, 
         cudaGetLastError();
         return GW_ERR_CUDA;
     }
+    noalloc_poison_kernel<<<(unsigned)std::min<int64_t>(((int64_t)ng * nw + 255) / 256, 1024), 256, 0, st>>>(
+        status, (double2 *)chi, ng, nw);
+    if (cudaGetLastError() != cudaSuccess) return GW_ERR_CUDA;
     return GW_OK;
 }

@@ -1,0 +1,225 @@
+// Peak-rate probes of the arithmetic pipes the library's kernels run on (gw_chi0_probe).
+//
+// Each probe launches enough warps to fill every SM and runs independent dependency chains
+// of one instruction kind, so the pipe, not latency, bounds the rate: FP32 FMA (scalar and
+// the packed two-lane form the two-float transforms can use), FP64 FMA, the FP64 tensor
+// instructions (DMMA m8n8k4 and m16n8k16), and the warp-level BF16 and INT8 tensor
+// instructions.  The caller times the launch; the call returns the operations it performs
+// (an FMA counts as 2, a tensor instruction as 2 m n k).  These rates are the denominators
+// of the roofline fractions of the kernels that run on those pipes.
+#include "../../include/gw_chi0.h"
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace {
+
+constexpr int kChains = 8;     // independent chains per thread
+constexpr int kThreads = 256;  // threads per block
+constexpr int kBlocksPerSm = 4;
+
+template <typename T>
+__device__ __forceinline__ void sink(T v, float *out)
+{
+    // never true for the probes' bounded values; keeps the chains alive
+    if ((float)v == 1234.5f) out[threadIdx.x] = (float)v;
+}
+
+__global__ void __launch_bounds__(kThreads) probe_ffma(float *out, long long iters)
+{
+    float a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = 1e-3f * (threadIdx.x + k);
+    const float m = 0.9999999f, c = 1e-9f;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = __fmaf_rn(a[k], m, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += a[k];
+    sink(s, out);
+}
+
+__global__ void __launch_bounds__(kThreads) probe_ffma2(float *out, long long iters)
+{
+    float2 a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = make_float2(1e-3f * (threadIdx.x + k), 2e-3f * (threadIdx.x + k));
+    const float2 m = make_float2(0.9999999f, 0.9999998f), c = make_float2(1e-9f, 2e-9f);
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = __ffma2_rn(a[k], m, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += a[k].x + a[k].y;
+    sink(s, out);
+}
+
+__global__ void __launch_bounds__(kThreads) probe_fadd2(float *out, long long iters)
+{
+    float2 a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = make_float2(1e-3f * (threadIdx.x + k), 2e-3f * (threadIdx.x + k));
+    const float2 c = make_float2(1e-9f, -2e-9f);
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = __fadd2_rn(a[k], c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += a[k].x + a[k].y;
+    sink(s, out);
+}
+
+__global__ void __launch_bounds__(kThreads) probe_dfma(float *out, long long iters)
+{
+    double a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = 1e-3 * (threadIdx.x + k);
+    const double m = 0.9999999999, c = 1e-15;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = __fma_rn(a[k], m, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += a[k];
+    sink(s, out);
+}
+
+__global__ void __launch_bounds__(kThreads) probe_dmma884(float *out, long long iters)
+{
+    double d[kChains][2];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) d[k][0] = d[k][1] = 0.0;
+    const double a = 1e-9 * (threadIdx.x & 7), b = 1e-9;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                         : "+d"(d[k][0]), "+d"(d[k][1])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += d[k][0] + d[k][1];
+    sink(s, out);
+}
+
+__global__ void __launch_bounds__(kThreads) probe_dmma16816(float *out, long long iters)
+{
+    constexpr int K = 4;
+    double d[K][4];
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k][0] = d[k][1] = d[k][2] = d[k][3] = 0.0;
+    const double a = 1e-9 * (threadIdx.x & 7), b = 1e-9;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            asm volatile("mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
+                         "{%4,%4,%4,%4,%4,%4,%4,%4}, {%5,%5,%5,%5}, {%0,%1,%2,%3};"
+                         : "+d"(d[k][0]), "+d"(d[k][1]), "+d"(d[k][2]), "+d"(d[k][3])
+                         : "d"(a), "d"(b));
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) s += d[k][0] + d[k][1] + d[k][2] + d[k][3];
+    sink(s, out);
+}
+
+__global__ void __launch_bounds__(kThreads) probe_bf16_mma(float *out, long long iters)
+{
+    float d[kChains][4];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) d[k][0] = d[k][1] = d[k][2] = d[k][3] = 0.f;
+    const uint32_t a = 0x3c003c00u + (threadIdx.x & 1), b = 0x3c003c00u; // small bf16 pairs
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k)
+            asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%4,%4,%4}, "
+                         "{%5,%5}, {%0,%1,%2,%3};"
+                         : "+f"(d[k][0]), "+f"(d[k][1]), "+f"(d[k][2]), "+f"(d[k][3])
+                         : "r"(a), "r"(b));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += d[k][0] + d[k][1] + d[k][2] + d[k][3];
+    sink(s, out);
+}
+
+__global__ void __launch_bounds__(kThreads) probe_int8_mma(float *out, long long iters)
+{
+    int d[kChains][4];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) d[k][0] = d[k][1] = d[k][2] = d[k][3] = 0;
+    const uint32_t a = 0x01010101u * (threadIdx.x & 1), b = 0x01010101u;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k)
+            asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%4,%4,%4}, "
+                         "{%5,%5}, {%0,%1,%2,%3};"
+                         : "+r"(d[k][0]), "+r"(d[k][1]), "+r"(d[k][2]), "+r"(d[k][3])
+                         : "r"(a), "r"(b));
+    }
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += d[k][0] + d[k][1] + d[k][2] + d[k][3];
+    if (s == 123456789) out[threadIdx.x] = (float)s;
+}
+
+} // namespace
+
+extern "C" gw_status gw_chi0_probe(int kind, long long iters, void *cuda_stream, float *sink_buf, double *ops)
+{
+    if (iters < 1 || !sink_buf || !ops) return GW_ERR_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess) {
+        cudaGetLastError();
+        return GW_ERR_CUDA;
+    }
+    const int blocks = sms * kBlocksPerSm;
+    const double threads = (double)blocks * kThreads, warps = threads / 32.0;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    switch (kind) {
+    case GW_PROBE_FFMA:
+        probe_ffma<<<blocks, kThreads, 0, st>>>(sink_buf, iters);
+        *ops = 2.0 * threads * kChains * (double)iters;
+        break;
+    case GW_PROBE_FFMA2:
+        probe_ffma2<<<blocks, kThreads, 0, st>>>(sink_buf, iters);
+        *ops = 4.0 * threads * kChains * (double)iters;
+        break;
+    case GW_PROBE_FADD2:
+        probe_fadd2<<<blocks, kThreads, 0, st>>>(sink_buf, iters);
+        *ops = 2.0 * threads * kChains * (double)iters;
+        break;
+    case GW_PROBE_DFMA:
+        probe_dfma<<<blocks, kThreads, 0, st>>>(sink_buf, iters);
+        *ops = 2.0 * threads * kChains * (double)iters;
+        break;
+    case GW_PROBE_DMMA_M8N8K4:
+        probe_dmma884<<<blocks, kThreads, 0, st>>>(sink_buf, iters);
+        *ops = 2.0 * 8 * 8 * 4 * warps * kChains * (double)iters;
+        break;
+    case GW_PROBE_DMMA_M16N8K16:
+        probe_dmma16816<<<blocks, kThreads, 0, st>>>(sink_buf, iters);
+        *ops = 2.0 * 16 * 8 * 16 * warps * 4 * (double)iters;
+        break;
+    case GW_PROBE_BF16_MMA_SYNC:
+        probe_bf16_mma<<<blocks, kThreads, 0, st>>>(sink_buf, iters);
+        *ops = 2.0 * 16 * 8 * 16 * warps * kChains * (double)iters;
+        break;
+    case GW_PROBE_INT8_MMA_SYNC:
+        probe_int8_mma<<<blocks, kThreads, 0, st>>>(sink_buf, iters);
+        *ops = 2.0 * 16 * 8 * 32 * warps * kChains * (double)iters;
+        break;
+    default:
+        return GW_ERR_ARG;
+    }
+    if (cudaGetLastError() != cudaSuccess) return GW_ERR_CUDA;
+    return GW_OK;
+}

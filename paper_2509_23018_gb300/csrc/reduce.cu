@@ -210,6 +210,33 @@ cudaError_t launch_symmetrize(double2 *chi, int ng, int nw, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Hermitian part of a square complex matrix: out[i][j] = (W[i][j] + conj(W[j][i])) / 2.  Tile
+// (bi, bj) and its transpose pass through shared memory so reads and writes are row-contiguous.
+__global__ void herm_part_kernel(const double2 *__restrict__ W, int n, double2 *__restrict__ out)
+{
+    __shared__ double2 t[32][33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) { // the transposed tile W[j0 + r][i0 + x]
+        const int j = j0 + r, i = i0 + threadIdx.x;
+        if (j < n && i < n) t[r][threadIdx.x] = W[(int64_t)j * n + i];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r, j = j0 + threadIdx.x;
+        if (i < n && j < n) {
+            const double2 a = W[(int64_t)i * n + j], b = t[threadIdx.x][r]; // W[i][j], W[j][i]
+            out[(int64_t)i * n + j] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+        }
+    }
+}
+
+cudaError_t launch_herm_part(const double2 *W, int n, double2 *out, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    herm_part_kernel<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, st>>>(W, n, out);
+    return cudaGetLastError();
+}
+
 // out[g][b] = conj(V[b n + g]): a column-major n x neig block (an eigensolver's vectors of the
 // conjugated matrix) to a row-major [n][neig] basis.  32 x 32 tiles through shared memory.
 __global__ void conj_transpose_kernel(const double2 *__restrict__ V, int n, int neig, double2 *__restrict__ out)

@@ -61,3 +61,14 @@ def test_create_rejects_bad_descriptors():
         h = ctypes.c_void_p()
         assert lib.gw_chi0_create(ctypes.byref(h), ctypes.byref(d), None) == _lib.GW_ERR_ARG
         assert not h.value
+
+
+def test_noalloc_binding_rejects_host_tensors():
+    """The binding refuses tensors that are not on the current CUDA device before any call."""
+    torch = pytest.importorskip("torch")
+    import paper_2509_23018_gb300 as gw
+    ev = torch.full((2,), -5.0, dtype=torch.float64)
+    ec = torch.full((3,), 5.0, dtype=torch.float64)
+    M = torch.zeros((6, 4), dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        gw.contract_noalloc(ev, ec, M, [0.0], torch.zeros((1, 4, 4), dtype=torch.complex128))

@@ -47,6 +47,23 @@ def test_adjoint_matches_oracle(gw, mtxel, grid, nv, nc, ngpsi, ng, w, chunk):
     assert rel(dcc.cpu().numpy(), dcco) < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "ozaki"])
+def test_adjoint_takes_hermitian_part_of_w(gw, prec):
+    """A non-Hermitian W: the library uses (W + W^H)/2, which is all Re Tr(W chi) sees."""
+    p = gwgen.make_problem((16, 15, 18), 4, 9, 150, 64, seed=33)
+    rng = np.random.default_rng(8)
+    W = rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))
+    Wh = 0.5 * (W + W.conj().T)
+    Lo, dEvo, dEco, dcvo, dcco = oracle.adjoint(p.gpsi, p.cv, p.ev, p.gpsi, p.cc, p.ec, p.gchi, Wh, 1.5)
+    h = gw.from_problem(p, prec=prec, nslices=7, pair_chunk=12)
+    L, dEv, dEc, dcv, dcc = h.adjoint(0, dev(W), omega=1.5)
+    h.sync()
+    tol = 1e-10 if prec == "fp64" else 1e-9
+    assert abs(L - Lo) <= tol * abs(Lo)
+    for a, b in ((dEv, dEvo), (dEc, dEco), (dcv, dcvo), (dcc, dcco)):
+        assert rel(a.cpu().numpy(), b) < tol
+
+
 def _L_forward(gw, p, W, cv, cc, ev, ec, w):
     """L = Re Tr(W chi) with chi from the forward path."""
     pp = gwgen.Problem(p.grid, p.gpsi, cv, cc, ev, ec, p.gchi, np.array([w]))
@@ -131,3 +148,20 @@ def test_autograd_function(gw):
     assert rel(cc.grad.cpu().numpy(), dcco) < 1e-10
     assert rel(ev.grad.cpu().numpy(), dEvo) < 1e-10
     assert rel(ec.grad.cpu().numpy(), dEco) < 1e-10
+
+
+def test_autograd_function_non_hermitian_w(gw):
+    """The upstream gradient of L = Re Tr(W chi) for a non-Hermitian W reaches the library as it
+    is (W^H in torch's convention); the gradients are those of the Hermitian part of W."""
+    p = gwgen.make_problem((16, 15, 18), 4, 9, 150, 64, seed=12)
+    rng = np.random.default_rng(4)
+    W = rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))
+    h = gw.Chi0(p.grid)
+    cv = dev(p.cv).requires_grad_(True)
+    ev = dev(p.ev).requires_grad_(True)
+    chi = gw.Chi0Fn.apply(h, dev(p.gpsi), cv, ev, dev(p.cc), dev(p.ec), dev(p.gchi), 0.7)
+    torch.real(torch.trace(dev(W) @ chi)).backward()
+    _, dEvo, _, dcvo, _ = oracle.adjoint(p.gpsi, p.cv, p.ev, p.gpsi, p.cc, p.ec, p.gchi,
+                                         0.5 * (W + W.conj().T), 0.7)
+    assert rel(cv.grad.cpu().numpy(), dcvo) < 1e-10
+    assert rel(ev.grad.cpu().numpy(), dEvo) < 1e-10
