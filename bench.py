@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-pairs", type=int, default=4096)
     ap.add_argument("--no-check", action="store_true", help="skip the sampled error check against the oracle")
+    ap.add_argument("--peaks", action="store_true", help="measure the pipe peaks, write profiles/peaks_gb300.json")
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--adjoint", action="store_true")
@@ -284,17 +285,87 @@ TRAFFIC = {
 }
 
 
+# ---------------------------------------------------------------- pipe peaks
+# Rates of the arithmetic pipes, measured by the library's probes (gw_chi0_probe) on this GPU:
+# filled by measure_peaks() at the start of a run; profiles/peaks_gb300.json (written by
+# `bench.py --peaks`) is the record of one such measurement and the fallback.
+PEAKS_JSON = os.path.join(ROOT, "profiles", "peaks_gb300.json")
+PROBE_KINDS = ["ffma", "ffma2", "fadd2", "dfma", "dmma_m8n8k4", "dmma_m16n8k16", "bf16_mma_sync", "int8_mma_sync"]
+LIVE_PEAKS = {}
+
+
+def probe_rates(kinds, target_ms=25.0, reps=3):
+    """Peak rate (T operations/s; an FMA counts 2) of each probe kind: one calibration launch
+    sizes the chain length for about target_ms, then the best of `reps` timed launches (CUDA
+    events on the launching stream)."""
+    import ctypes
+
+    import torch
+    from paper_2509_23018_gb300 import _lib
+
+    lib = _lib.load()
+    sink = torch.zeros(256, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    out = {}
+    for k in kinds:
+        iters, best = 16, 0.0
+        for rep in range(reps + 2):
+            ops = ctypes.c_double()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            rc = lib.gw_chi0_probe(_lib.PROBES[k], iters, ctypes.c_void_p(st.cuda_stream),
+                                   ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops))
+            e1.record(st)
+            torch.cuda.synchronize()
+            if rc != 0:
+                raise RuntimeError(f"gw_chi0_probe({k}) failed: {rc}")
+            ms = e0.elapsed_time(e1)
+            if rep == 0:  # calibration
+                iters = max(16, int(iters * target_ms / max(ms, 1e-3)))
+                continue
+            best = max(best, ops.value / (ms * 1e-3) * 1e-12)
+        out[k] = {"tops": best, "iters": iters}
+    return out
+
+
+def measure_peaks(kinds=("ffma", "ffma2", "dfma", "dmma_m8n8k4", "dmma_m16n8k16")):
+    """Fill LIVE_PEAKS from the probes on this GPU (falls back to the committed record)."""
+    try:
+        LIVE_PEAKS.update({k: v["tops"] for k, v in probe_rates(list(kinds)).items()})
+        LIVE_PEAKS["_source"] = "measured in this run (gw_chi0_probe)"
+    except Exception as e:  # noqa: BLE001
+        if os.path.exists(PEAKS_JSON):
+            rec = json.load(open(PEAKS_JSON))
+            LIVE_PEAKS.update({k: v["tops"] for k, v in rec.get("probes", {}).items()})
+            LIVE_PEAKS["_source"] = f"profiles/peaks_gb300.json ({rec.get('when')}); live probe failed: {e}"
+
+
+def fp64_tensor_peak():
+    """FP64 tensor peak (TFLOP/s): the faster of the two measured DMMA shapes."""
+    r = [LIVE_PEAKS.get(k) for k in ("dmma_m8n8k4", "dmma_m16n8k16") if LIVE_PEAKS.get(k)]
+    if r:
+        return max(r), f"measured DMMA (gw_chi0_probe; {LIVE_PEAKS.get('_source')})"
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    pk = json.load(open(path)) if os.path.exists(path) else {}
+    return pk.get("bf16_tflops_sustained", 1700.0) * 1.25 / 2250.0, "bf16 sustained x nominal fp64/bf16 ratio"
+
+
+def fp32_lane_peak():
+    """FP32 operations per second (T; one FMA = one operation) of the FP32 pipes: the faster of
+    the scalar and the packed two-lane FMA probes, else lanes x max clock."""
+    r = [LIVE_PEAKS.get(k) for k in ("ffma", "ffma2") if LIVE_PEAKS.get(k)]
+    if r:
+        return max(r) / 2.0, f"measured FFMA/FFMA2 (gw_chi0_probe; {LIVE_PEAKS.get('_source')})"
+    return FP32_PEAK_TOPS, "152 SMs x 128 FP32 lanes x 2070 MHz (one operation per lane per clock)"
+
+
 def peak_for(prec):
+    if prec == "fp64":
+        return fp64_tensor_peak()
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     pk = json.load(open(path)) if os.path.exists(path) else {}
     src = "measured" if pk else "fallback"
-    bf16_burst = pk.get("bf16_tflops", 1900.0)
-    bf16_sus = pk.get("bf16_tflops_sustained", 1700.0)
-    if prec == "fp64":
-        # FP64 tensor peak = measured bf16 (sustained: the kernel runs inside a long step)
-        # x nominal FP64/bf16 dense ratio 1.25 / 2250
-        return bf16_sus * 1.25 / 2250.0, f"of {src} bf16 sustained x nominal fp64/bf16 ratio (1.25/2250)"
-    return bf16_sus, f"of {src} bf16 sustained"
+    return pk.get("bf16_tflops_sustained", 1700.0), f"of {src} bf16 sustained (cuBLAS)"
 
 
 def run_mode(args, cfg, prob, dev, prec, nslices, mtxel, steps, warmup, with_e2e, world, single_stream=False):
@@ -495,7 +566,8 @@ def mode_roofline(bound, kernel, work, ms, unit_of_work, prec="ozaki"):
     if not ms:
         return None
     if bound == "alu":
-        peak, unit, src = FP32_PEAK_TOPS, "FP32 Tops/s", "152 SMs x 128 FP32 lanes x 2070 MHz"
+        peak, src = fp32_lane_peak()
+        unit = "FP32 Tops/s"
         ach = work / (ms * 1e-3) * 1e-12
     elif bound == "hbm":
         peak, src = _hbm_peak()
@@ -511,20 +583,50 @@ def mode_roofline(bound, kernel, work, ms, unit_of_work, prec="ozaki"):
 
 
 
+def method_stage_a(cfg):
+    """Stage (a)'s method-level work per step: the algorithmic bytes (read every band grid once,
+    write M once) and the FFT flops of the pruned transforms (half of 5 N_r log2 N_r per pair)
+    plus the pair product (6 flops per point)."""
+    n0, n1, n2 = cfg.grid
+    nr = n0 * n1 * n2
+    nbytes = (cfg.nv + cfg.nc) * nr * 16 + cfg.npairs * cfg.ng * 16
+    flops = cfg.npairs * (0.5 * 5 * nr * np.log2(nr) + 6 * nr)
+    return float(nbytes), float(flops)
+
+
 def roofline_pair(cfg, prob, res):
     kms, kn = res["timing"].get("pair_mtxel", (0.0, 0))
     nchunk = -(-cfg.npairs // cfg.pair_chunk)
     per_pair = twofloat_ops_per_pair(cfg, kept_columns(prob, cfg.grid[2]), cells(prob, cfg.grid))
     per_launch = per_pair * cfg.npairs / nchunk
-    achieved = per_launch / (kms / kn * 1e-3) * 1e-12 if kn else None
-    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS, "unit": "FP32 Tops/s",
-            "frac": achieved / FP32_PEAK_TOPS if achieved else None,
-            "traffic": TRAFFIC.get("pair_mtxel", {}).get("bytes_per_launch"), "kernel": "pair_kernel_tf_ct",
-            "launches": kn, "ms_per_launch": kms / kn if kn else None, "ops_per_launch": per_launch,
-            "ops_per_pair": per_pair,
-            "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (one operation per lane per clock)",
+    ms_launch = kms / kn if kn else None
+    achieved = per_launch / (ms_launch * 1e-3) * 1e-12 if kn else None
+    peak, peak_src = fp32_lane_peak()
+    # the method-level bound of SURVEY-style stage (a): max(HBM bytes, FP64 ALU flops)
+    mbytes, mflops = method_stage_a(cfg)
+    hbm, hbm_src = _hbm_peak()
+    dfma = LIVE_PEAKS.get("dfma")
+    t_step = kms * 1e-3 * nchunk / kn if kn else None
+    traffic = TRAFFIC.get("pair_mtxel", {}).get("bytes_per_launch")
+    method = {"bytes_per_step": mbytes, "flops_per_step": mflops,
+              "hbm_frac": (mbytes / t_step * 1e-9 / hbm) if t_step else None, "hbm_peak_gbs": hbm,
+              "hbm_peak_source": hbm_src,
+              "fp64_equiv_tflops": (mflops / t_step * 1e-12) if t_step else None,
+              "fp64_alu_peak_tflops": dfma, "fp64_alu_frac": (mflops / t_step * 1e-12 / dfma) if t_step and dfma
+              else None,
+              "dram_bytes_per_step_ncu": traffic * nchunk if traffic else None,
+              "dram_over_method_bytes": traffic * nchunk / mbytes if traffic else None,
+              "note": "bytes: every band grid read once + M written once; flops: half of 5 N_r log2 N_r per "
+                      "pair (output-pruned FFT) + 6 N_r for the product, FP64 arithmetic"}
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "FP32 Tops/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": traffic, "kernel": "pair_kernel_tf_ct",
+            "launches": kn, "ms_per_launch": ms_launch, "ops_per_launch": per_launch,
+            "ops_per_pair": per_pair, "peak_source": peak_src,
+            "unit_of_work": "FP32 operations of the two-float transforms as implemented (issue efficiency)",
             "share_of_step": kms / res["total_ms"] if res["total_ms"] else None,
-            "traffic_source": TRAFFIC.get("pair_mtxel", {}).get("source")}
+            "traffic_source": TRAFFIC.get("pair_mtxel", {}).get("source"), "method": method,
+            "method_bytes": mbytes, "method_flops": mflops, "hbm_frac": method["hbm_frac"]}
 
 
 def roofline_for(cfg, prec, nslices, res, single_stream=False):
@@ -544,7 +646,7 @@ def roofline_for(cfg, prec, nslices, res, single_stream=False):
             "launches": kn, "ms_per_launch": kms / kn if kn else None, "flops_per_launch": per_launch_flops,
             "peak_source": peak_src, "share_of_step": kms / res["total_ms"] if res["total_ms"] else None,
             "traffic_source": TRAFFIC.get(tkey, {}).get("source"),
-            "fp64_probe_peaks_tflops": {"dmma": 1.055, "dfma": 1.204}}
+            "probe_peaks_tops": {k: v for k, v in LIVE_PEAKS.items() if not k.startswith("_")}}
 
 
 def ours(args):
@@ -1005,11 +1107,69 @@ def sigma(args):
         "rel_err_sampled_rows_one_nE": err, "cpu_baseline": cpu}), flush=True)
 
 
+def peaks(args):
+    """Measure the pipe peaks of this GPU (the library's probes, cuBLAS bf16, cuBLASLt int8, a
+    device copy) and write them to profiles/peaks_gb300.json; one JSON line on stdout."""
+    import torch
+
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    rates = probe_rates(PROBE_KINDS)
+    lib = {}
+
+    def best_of(fn, flops, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        b = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            b = max(b, flops / (e0.elapsed_time(e1) * 1e-3) * 1e-12)
+        return b
+
+    n = 8192
+    a = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    lib["bf16_cublas_tflops"] = best_of(lambda: a @ a, 2.0 * n ** 3)
+    try:
+        i8 = torch.randint(-8, 8, (n, n), device="cuda", dtype=torch.int8)
+        lib["int8_cublaslt_tops"] = best_of(lambda: torch._int_mm(i8, i8), 2.0 * n ** 3)
+    except Exception as e:  # noqa: BLE001
+        lib["int8_cublaslt_tops"] = None
+        lib["int8_error"] = str(e)[:200]
+    del a
+    x = torch.empty(1 << 30, dtype=torch.bfloat16, device="cuda")
+    y = torch.empty_like(x)
+    lib["hbm_copy_gbs"] = best_of(lambda: y.copy_(x), 4.0 * (1 << 30)) * 1e3  # 2 GiB read + 2 GiB written
+    del x, y
+    clocks = clk.stop()
+    rec = {"what": "peak rates of this GPU's pipes (T operations/s, an FMA counts 2)",
+           "command": "python bench.py --peaks", "gpu": torch.cuda.get_device_name(),
+           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+           "probes": rates, "library": lib, "clocks": clocks,
+           "notes": {"ffma2": "fma.rn.f32x2: two FP32 lanes per instruction",
+                     "dmma": "FP64 tensor rate; the FP64 contraction issues m8n8k4",
+                     "bf16_mma_sync/int8_mma_sync": "warp-level (legacy) tensor instructions, not tcgen05"}}
+    os.makedirs(os.path.dirname(PEAKS_JSON), exist_ok=True)
+    with open(PEAKS_JSON, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
-    elif args.sweep:
+        return
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if args.peaks:
+        peaks(args)
+        return
+    measure_peaks()
+    if args.sweep:
         sweep(args)
     elif args.batch:
         batch(args)
