@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the sampled error check against the oracle")
     ap.add_argument("--peaks", action="store_true", help="measure the pipe peaks, write profiles/peaks_gb300.json")
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--sweep-fp64", action="store_true", help="with --sweep --config c3_72cube: also native FP64")
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--subspace", action="store_true")
@@ -307,24 +308,31 @@ def probe_rates(kinds, target_ms=25.0, reps=3):
     sink = torch.zeros(256, dtype=torch.float32, device="cuda")
     st = torch.cuda.current_stream()
     out = {}
+    def launch(k, iters):
+        ops = ctypes.c_double()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rc = lib.gw_chi0_probe(_lib.PROBES[k], iters, ctypes.c_void_p(st.cuda_stream),
+                               ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops))
+        e1.record(st)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise RuntimeError(f"gw_chi0_probe({k}) failed: {rc}")
+        return e0.elapsed_time(e1), ops.value
+
     for k in kinds:
-        iters, best = 16, 0.0
-        for rep in range(reps + 2):
-            ops = ctypes.c_double()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            rc = lib.gw_chi0_probe(_lib.PROBES[k], iters, ctypes.c_void_p(st.cuda_stream),
-                                   ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops))
-            e1.record(st)
-            torch.cuda.synchronize()
-            if rc != 0:
-                raise RuntimeError(f"gw_chi0_probe({k}) failed: {rc}")
-            ms = e0.elapsed_time(e1)
-            if rep == 0:  # calibration
-                iters = max(16, int(iters * target_ms / max(ms, 1e-3)))
-                continue
-            best = max(best, ops.value / (ms * 1e-3) * 1e-12)
-        out[k] = {"tops": best, "iters": iters}
+        iters, ms = 64, 0.0
+        while True:  # calibration: grow the chains until a launch takes a good part of target_ms
+            ms, _ = launch(k, iters)
+            if ms >= 0.3 * target_ms or iters > (1 << 30):
+                break
+            iters = int(iters * min(64.0, max(2.0, target_ms / max(ms, 1e-3))))
+        iters = max(64, int(iters * target_ms / max(ms, 1e-3)))
+        best = 0.0
+        for _ in range(reps):
+            ms, ops = launch(k, iters)
+            best = max(best, ops / (ms * 1e-3) * 1e-12)
+        out[k] = {"tops": best, "iters": iters, "ms": ms}
     return out
 
 
@@ -719,29 +727,54 @@ def ours(args):
         dist.destroy_process_group()
 
 
+# Pairs per chunk of the precision workload: chunks sized to 40 GB of M (N_G = 6000 complex128
+# rows of 96 kB), a whole number of conduction rows: 204 x 2048 = 417792 pairs (40.1 GB).
+C3_CHUNK_40GB = 204 * 2048
+
+
 def sweep(args):
-    """Slice-count sweep on one 8192-pair chunk of the 72^3 workload (N_G = 6000)."""
+    """Slice-count sweep with the error against the oracle per slice count.  --config c3_72cube:
+    the precision workload as configured (72^3, 256 + 2048 bands, N_G = 6000, pair chunks sized to
+    40 GB of M, s = 4..7, one q-point per step); otherwise one 8192-pair chunk of it (s = 4..8 and
+    native FP64)."""
+    import dataclasses
+
     import torch
-    import paper_2509_23018_gb300 as gw
-    cfg = gwgen.CONFIGS["p3_72cube_onechunk"]
+    import paper_2509_23018_gb300 as gw  # noqa: F401
+    full = args.config == "c3_72cube"
+    cfg = gwgen.CONFIGS["c3_72cube" if full else "p3_72cube_onechunk"]
+    if full:
+        cfg = dataclasses.replace(cfg, pair_chunk=C3_CHUNK_40GB)
     prob = gwgen.config_problem(cfg)
     dev = torch.device("cuda", 0)
-    idx, ref, _ = oracle_block(cfg, prob)
-    out = {"workload": f"{cfg.name}: grid 72^3, {cfg.nv}+{cfg.nc} bands, N_Gpsi={cfg.ngpsi}, N_G={cfg.ng}",
-           "sample": "12x12 sampled entries vs the oracle, all pairs", "slices": {}}
-    for s_ in (4, 5, 6, 7, 8):
-        r = run_mode(args, cfg, prob, dev, "ozaki", s_, "twofloat", 2, 1, False, 1)
+    idx, ref, how = oracle_block(cfg, prob)
+    out = {"metric": METRIC, "mode": "slice-count sweep",
+           "workload": f"{cfg.name}: grid 72^3, {cfg.nv}+{cfg.nc} bands, N_Gpsi={cfg.ngpsi}, N_G={cfg.ng}, "
+                       f"pair chunks of {cfg.pair_chunk} pairs ({cfg.pair_chunk * cfg.ng * 16 / 1e9:.1f} GB of M)",
+           "unit": "TFLOP/s (8 N_G^2 P convention) and ms per q-point", "sample": how + " vs the oracle",
+           "slices": {}}
+    steps, warm = (1, 1) if full else (2, 1)
+    for s_ in ((4, 5, 6, 7) if full else (4, 5, 6, 7, 8)):
+        r = run_mode(args, cfg, prob, dev, "ozaki", s_, "twofloat", steps, warm, False, 1)
         rf = roofline_for(cfg, "ozaki", s_, r)
         got = r["chi"][np.ix_(idx, idx)]
         out["slices"][s_] = {"rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-                             "gemm_tflops": rf["achieved"], "gemm_frac": rf["frac"], "gemm_ms": rf["ms_per_launch"],
-                             "ms_per_step": r["ms_per_step"]}
-    r = run_mode(args, cfg, prob, dev, "fp64", 0, "fp64", 1, 1, False, 1)
-    got = r["chi"][np.ix_(idx, idx)]
-    rf = roofline_for(cfg, "fp64", 0, r)
-    out["fp64_dmma"] = {"rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-                        "contract_tflops": rf["achieved"], "contract_ms": rf["ms_per_launch"],
-                        "ms_per_step": r["ms_per_step"]}
+                             "ms_per_q": r["ms_per_step"], "value": r["value"], "gemm_tflops": rf["achieved"],
+                             "gemm_frac": rf["frac"], "gemm_ms": rf["ms_per_launch"], "clocks": r["clocks"]}
+        if s_ == 7:
+            out["roofline"] = rf
+            out["roofline_pair"] = roofline_pair(cfg, prob, r)
+    if not full or args.sweep_fp64:
+        r = run_mode(args, cfg, prob, dev, "fp64", 0, "fp64", 1, 1 if not full else 0, False, 1)
+        got = r["chi"][np.ix_(idx, idx)]
+        rf = roofline_for(cfg, "fp64", 0, r)
+        out["fp64_dmma"] = {"rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                            "contract_tflops": rf["achieved"], "contract_ms": rf["ms_per_launch"],
+                            "ms_per_q": r["ms_per_step"], "value": r["value"], "roofline": rf}
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg, prob, args.cpu_sample_pairs)
+        cpu.pop("seconds", None)
+        out["cpu_baseline"] = cpu
     print(json.dumps(out), flush=True)
 
 

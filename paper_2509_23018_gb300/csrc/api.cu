@@ -370,9 +370,9 @@ int64_t oz_kpad(int ka) { return ((int64_t)2 * ka + 63) / 64 * 64; }
 
 // B operand of a general split product: the columns of B [ka][nout] (complex, row-major)
 // into the handle's ZB / EB buffers.
-gw_status oz_prepare_b(gw_chi0 *h, const double2 *B, int ka, int nout)
+gw_status oz_prepare_b(gw_chi0 *h, const double2 *B, int ka, int nout, int nslices)
 {
-    const int s = h->d.nslices;
+    const int s = nslices > 0 ? nslices : h->d.nslices;
     const int64_t kpad = oz_kpad(ka);
     gw_status st;
     if ((st = grow(h, &h->ZBbuf, &h->ZBcap, (size_t)s * 2 * nout * kpad * 2, "product operand slices")) ||
@@ -386,9 +386,9 @@ gw_status oz_prepare_b(gw_chi0 *h, const double2 *B, int ka, int nout)
 // Y[rows][nout] = A[rows][ka] B[ka][nout] (complex, row-major) in split precision, B prepared
 // by oz_prepare_b.  A's slices reuse the contraction's slice buffer (stream order separates
 // the two uses).
-gw_status oz_product(gw_chi0 *h, const double2 *A, int64_t rows, int ka, int nout, double2 *Y)
+gw_status oz_product(gw_chi0 *h, const double2 *A, int64_t rows, int ka, int nout, double2 *Y, int nslices)
 {
-    const int s = h->d.nslices;
+    const int s = nslices > 0 ? nslices : h->d.nslices;
     const int64_t kpad = oz_kpad(ka);
     const int bn = 2 * nout >= 256 ? 256 : 128;
     gw_status st;
@@ -495,6 +495,72 @@ void free_sphere(gw_chi0 *h, Sphere &s)
     dfree(h, s.cpts, sizeof(int2) * s.ng);
     s = Sphere();
 }
+// ------------------------------------------------------------------ stage (a) on the tensor cores
+// The last-axis transform of the pair products as a split product per grid line (zdft.cu) for
+// two-float stage (a) on the 48^3 grid; chunks are all valence bands x a block of conduction
+// bands, rows r = cl nv + v.  GW_CHI0_STAGE_A=fft selects the FFT pair kernel instead.
+bool zd_route(gw_chi0 *h, int iq, bool resident)
+{
+    static const bool fft_only = [] {
+        const char *e = getenv("GW_CHI0_STAGE_A");
+        return e && strcmp(e, "fft") == 0;
+    }();
+    if (fft_only || resident || h->d.mtxel_prec != GW_MTXEL_TWOFLOAT) return false;
+    const Sphere &sp = h->sph[iq];
+    const int n = h->d.n[0];
+    if (h->d.n[1] != n || h->d.n[2] != n || sp.nslots <= 0 || !h->pscr) return false;
+    return gw::zd_supported(n, sp.K2, h->val[iq].nb) && h->d.pair_chunk >= h->val[iq].nb;
+}
+
+int zd_chunk_bands(gw_chi0 *h, int iq)
+{
+    const int nv = h->val[iq].nb;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(h->cond.nb, h->d.pair_chunk / nv));
+}
+
+gw_status zd_prepare(gw_chi0 *h, int iq, CUtensorMap *tmA)
+{
+    const BandSet &v = h->val[iq];
+    const Sphere &sp = h->sph[iq];
+    const int n = h->d.n[0], nv = v.nb, cb = zd_chunk_bands(h, iq);
+    const int64_t lines = (int64_t)n * n;
+    const size_t abytes = (size_t)gw::kZdSlices * lines * nv * 2 * n * 2;
+    const size_t fbytes = sizeof(float4) * (size_t)lines * nv * cb * sp.K2;
+    gw_status s;
+    if ((s = grow(h, &h->zdA, &h->zdAcap, abytes, "valence slices")) ||
+        (s = grow(h, (void **)&h->zdF, &h->zdFcap, fbytes, "last-axis transform")))
+        return s;
+    {
+        Scope sc(h, "zd_aslices");
+        CK(h, gw::launch_zd_aslices(v.psi, nv, n, (uint16_t *)h->zdA, h->st), "valence slices");
+    }
+    cuuint64_t dims[4] = {(cuuint64_t)2 * n, (cuuint64_t)nv, (cuuint64_t)lines, (cuuint64_t)gw::kZdSlices};
+    cuuint64_t strides[3] = {(cuuint64_t)2 * n * 2, (cuuint64_t)2 * n * 2 * nv, (cuuint64_t)2 * n * 2 * nv * lines};
+    cuuint32_t box[4] = {32, 128, 1, (cuuint32_t)gw::kZdSlices};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = h->encode(tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, h->zdA, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, GW_ERR_CUDA, "cuTensorMapEncodeTiled (valence slices) failed (%d)", (int)r);
+    return GW_OK;
+}
+
+gw_status zd_stage_a(gw_chi0 *h, int iq, const CUtensorMap &tmA, int c0, int cb, const gw::PairPlan &pp, double2 *M)
+{
+    const BandSet &v = h->val[iq];
+    const Sphere &sp = h->sph[iq];
+    const int n = h->d.n[0];
+    {
+        Scope sc(h, "zdft");
+        CK(h, gw::launch_zd_gemm(tmA, h->cond.psi, sp.kz, pp.ax[2].twf, n, v.nb, c0, cb, sp.K2, h->zdF, h->status,
+                                 h->st),
+           "last-axis transform");
+    }
+    Scope sc(h, "pair_mtxel");
+    CK(h, gw::launch_pair_tf_from_f(h->zdF, (int64_t)v.nb * cb, pp, M, h->st), "pair elements from F");
+    return GW_OK;
+}
+
 // Split-precision streamed compute with the contraction of job j (chunk, frequency) on a
 // high-priority second stream while the user stream forms the pair elements and slices of
 // the jobs after it.  The split-precision contraction runs on the tensor cores and the pair
@@ -727,6 +793,8 @@ void gw_chi0_destroy(gw_chi0 *h)
     dfree(h, h->EBbuf, h->EBcap);
     dfree(h, h->ZBbuf, h->ZBcap);
     dfree(h, h->MBbuf, h->MBcap);
+    dfree(h, h->zdA, h->zdAcap);
+    dfree(h, h->zdF, h->zdFcap);
     for (int b = 0; b < 2; ++b) {
         dfree(h, h->ovZ[b], h->ovZcap[b]);
         dfree(h, h->ovE[b], h->ovEcap[b]);
@@ -1031,7 +1099,7 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
         // one frequency: a chunk's contraction is about as long as the next chunk's pair elements
         // and hides behind them; with more, the contractions (the shallow-ring variant) queue up
         // behind the two slice buffers and the single stream is faster
-        if (nw == 1 && overlap_enabled(h, pp) && fault_chunk() < 0) {
+        if (nw == 1 && overlap_enabled(h, pp) && fault_chunk() < 0 && !zd_route(h, iq[i], keep)) {
             s = compute_overlap(h, iq[i], om, cq, dq, Mres);
             if (s) return s;
             Scope sc(h, "symmetrize");
@@ -1039,6 +1107,32 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
             off += (size_t)nw * ng * ng;
             doff += (size_t)nw * ng;
             if (keep) h->Mres_iq = iq[i];
+            continue;
+        }
+        if (zd_route(h, iq[i], keep) && fault_chunk() < 0) {
+            const int nv = v.nb, cb = zd_chunk_bands(h, iq[i]);
+            s = ensure_work(h, (size_t)nv * cb * ng, (size_t)nv * cb * nw);
+            if (s) return s;
+            CUtensorMap tmA;
+            if ((s = zd_prepare(h, iq[i], &tmA))) return s;
+            for (int c0 = 0; c0 < h->cond.nb; c0 += cb) {
+                const int cbc = std::min(cb, h->cond.nb - c0);
+                const int64_t cnt = (int64_t)nv * cbc;
+                if ((s = zd_stage_a(h, iq[i], tmA, c0, cbc, pp, h->Mbuf))) return s;
+                {
+                    Scope sc(h, "delta");
+                    CK(h, gw::launch_delta_block(v.energy, h->cond.energy, nv, c0, cbc, om, h->dbuf, h->st), "delta");
+                }
+                if ((s = contract_chunk(h, h->Mbuf, cnt, ng, h->dbuf, cnt, nw, cq))) return s;
+                if (dq) {
+                    Scope sc(h, "diag");
+                    CK(h, gw::launch_diag(h->Mbuf, cnt, ng, h->dbuf, cnt, nw, dq, ng, h->st), "diag");
+                }
+            }
+            Scope sc(h, "symmetrize");
+            CK(h, gw::launch_symmetrize(cq, ng, nw, h->st), "symmetrize");
+            off += (size_t)nw * ng * ng;
+            doff += (size_t)nw * ng;
             continue;
         }
         s = ensure_work(h, (size_t)chunk * ng, (size_t)chunk * nw);

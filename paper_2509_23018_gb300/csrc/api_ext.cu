@@ -250,16 +250,19 @@ gw_status gw_chi0_compute_subspace(gw_chi0 *h, int iq, int neig, const double *b
 
 // ------------------------------------------------------------------ dielectric matrix inverse
 // Dense product C = A B of two [n][n] complex matrices in the handle's precision mode.
-static gw_status square_product(gw_chi0 *h, const double2 *A, const double2 *B, int n, double2 *C)
+static gw_status square_product(gw_chi0 *h, const double2 *A, const double2 *B, int n, double2 *C, int nslices = 0)
 {
     if (h->d.prec == GW_PREC_OZAKI_BF16) {
-        gw_status st = oz_prepare_b(h, B, n, n);
+        gw_status st = oz_prepare_b(h, B, n, n, nslices);
         if (st) return st;
-        return oz_product(h, A, n, n, n, C);
+        return oz_product(h, A, n, n, n, C, nslices);
     }
     CK(h, gw::launch_zgemm(A, B, C, n, n, n, h->st), "product");
     return GW_OK;
 }
+
+// Slices of the split products of the last Newton-Schulz steps (the most the digit step takes).
+constexpr int kEpsFinalSlices = 8;
 
 gw_status gw_chi0_epsilon_inverse(gw_chi0 *h, int ng, int nw, const double *chi, const double *vcoul,
                                   double *epsinv)
@@ -296,9 +299,12 @@ gw_status gw_chi0_epsilon_inverse(gw_chi0 *h, int ng, int nw, const double *chi,
         if (r > 0.0) steps = (int)std::ceil(std::log2(std::log(1e-17) / std::log(r))) + 1;
         steps = std::max(steps, 1);
         CK(h, gw::launch_eps_init(X, ng, bmax, h->st), "X0");
+        // The error of the converged iterate is the rounding of the last steps' products (earlier
+        // errors are squared away), so in split precision the last two steps take the most slices.
         for (int k = 0; k < steps; ++k) {
             Scope sp(h, "eps_products"); // two N_G^3 products per step: the launch count gives the steps
-            if ((st = square_product(h, A, X, ng, T)) || (st = square_product(h, X, T, ng, Pm))) return st;
+            const int s = (h->d.prec == GW_PREC_OZAKI_BF16 && k >= steps - 2) ? kEpsFinalSlices : 0;
+            if ((st = square_product(h, A, X, ng, T, s)) || (st = square_product(h, X, T, ng, Pm, s))) return st;
             CK(h, gw::launch_eps_step(X, Pm, (int64_t)nn, h->st), "Newton-Schulz step");
         }
         CK(h, gw::launch_eps_unsym(X, sv, ng, (double2 *)epsinv + (int64_t)w * nn, h->st), "s X s^-1");

@@ -153,6 +153,12 @@ struct gw_chi0 {
         void *p = nullptr;
         size_t cap = 0;
     } gpp[9];
+    // stage (a) with the last-axis transform on the tensor cores (zdft.cu): valence slices of the
+    // slot being computed and the transform output F of one chunk
+    void *zdA = nullptr;
+    size_t zdAcap = 0;  // bytes
+    float4 *zdF = nullptr;
+    size_t zdFcap = 0;  // bytes
     // scratch slots of the two-float pair kernel (sized in set_gsphere, outside any capture)
     float4 *pscr = nullptr;
     size_t pscr_cap = 0; // bytes
@@ -226,8 +232,9 @@ gw_status contract_chunk_ozaki(gw_chi0 *h, const double2 *M, int64_t P, int ng, 
 gw_status contract_chunk(gw_chi0 *h, const double2 *M, int64_t P, int ng, const double *delta, int64_t dstride,
                          int nw, double2 *chi);
 int64_t oz_kpad(int ka);
-gw_status oz_prepare_b(gw_chi0 *h, const double2 *B, int ka, int nout);
-gw_status oz_product(gw_chi0 *h, const double2 *A, int64_t rows, int ka, int nout, double2 *Y);
+// nslices > 0 overrides the handle's slice count (both calls of one product must agree)
+gw_status oz_prepare_b(gw_chi0 *h, const double2 *B, int ka, int nout, int nslices = 0);
+gw_status oz_product(gw_chi0 *h, const double2 *A, int64_t rows, int ka, int nout, double2 *Y, int nslices = 0);
 bool alias_free(const gw_chi0 *h, const BandSet &v, const BandSet &c, const Sphere &s, int *axis);
 gw_status check_slot(gw_chi0 *h, int iq);
 cudaError_t run_pair(gw_chi0 *h, const void *psiv, const void *psic, int nc, int64_t p0, int64_t cnt,
@@ -243,6 +250,13 @@ gw_status resident_begin(gw_chi0 *h, int64_t P, int ng, bool *use);
 double2 *resident_for(gw_chi0 *h, int iq);
 // overlapped split-precision streamed compute of one slot (api.cu); Mres: resident output or null
 gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *cq, double *dq, double2 *Mres);
+// Stage (a) with the last-axis transform on the tensor cores: whether slot iq takes it, the
+// conduction bands per chunk, the valence slices (once per call), and one chunk's pair
+// elements M[cl nv + v] for the conduction bands c0 .. c0 + cb - 1.
+bool zd_route(gw_chi0 *h, int iq, bool resident);
+int zd_chunk_bands(gw_chi0 *h, int iq);
+gw_status zd_prepare(gw_chi0 *h, int iq, CUtensorMap *tmA);
+gw_status zd_stage_a(gw_chi0 *h, int iq, const CUtensorMap &tmA, int c0, int cb, const gw::PairPlan &pp, double2 *M);
 bool overlap_enabled(gw_chi0 *h, const gw::PairPlan &pp);
 
 // batched path (api_batch.cu)

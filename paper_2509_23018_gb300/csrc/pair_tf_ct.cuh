@@ -267,23 +267,6 @@ inline cudaError_t launch_pair_tf_cube(const float4 *psiv, const float4 *psic, i
     return cudaGetLastError();
 }
 
-// Scratch slots the kernel needs for this plan: SMs x resident blocks + 32.
-template <int N>
-inline cudaError_t pair_tf_cube_slots(const PairPlan &pp, int *nslots)
-{
-    const size_t sm = pair_tf_ct_smem<N>(pp);
-    cudaError_t e = cudaFuncSetAttribute(pair_kernel_tf_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    int occ = 0, dev = 0, nsm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_kernel_tf_ct<N>, pair_threads<N>(), sm)) !=
-            cudaSuccess ||
-        (e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-        return e;
-    *nslots = nsm * (occ > 0 ? occ : 1) + 32;
-    return cudaSuccess;
-}
-
 // Whether the grid-specialised kernel takes this plan: a cubic 24/40/48/72 grid and a
 // shared-memory footprint within the 227 KB a block may opt into.
 inline bool pair_tf_ct_fits(const PairPlan &pp)
@@ -299,6 +282,157 @@ inline bool pair_tf_ct_fits(const PairPlan &pp)
     default: return false;
     }
     return sm <= 227 * 1024 - 64;
+}
+
+// The middle and first axes of the pair transform from the last-axis output F of the tensor-core
+// stage (zdft.cu): one block per pair row r of the chunk.  Per i0 slab the block loads
+// F[i0 N + i1][r][q] (the K2 kept last-axis frequencies of every line of the slab) into C,
+// transforms the columns along i1 and stores the K12 cells in its scratch slot; phase 2 is
+// that of pair_kernel_tf_ct.  The next slab's F is loaded into registers while the current
+// one is transformed.
+template <int N>
+__global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
+    pair_kernel_tf_from_f(const float4 *__restrict__ F, int64_t R, PairPlan pp, TfConsts kc, tf inv_nr,
+                          double2 *__restrict__ M)
+{
+    constexpr int NT = pair_threads<N>();
+    constexpr int CS = N + 1;
+    constexpr int NPF = 6; // F entries per thread and slab held in flight (K2 N <= NT NPF)
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int slot_s;
+    const int K2 = pp.K2, K12 = pp.K12;
+    const int sizeAB = K2 * CS > 31 * CS ? K2 * CS : 31 * CS;
+    float4 *A = (float4 *)smem, *C = A + sizeAB;
+    float4 *tw = C + K2 * CS;
+    int *cell = (int *)(tw + N);
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = pp.ax[0].twf[i];
+    for (int i = threadIdx.x; i < K12; i += NT) cell[i] = pp.cell[i];
+    if (threadIdx.x == 0) {
+        int got = -1;
+        int c = (int)((blockIdx.x * 2654435761u) % (unsigned)pp.nslots);
+        for (int t = 0; t < pp.nslots; ++t) {
+            if (atomicCAS(pp.slot_flags + c, 0, 1) == 0) {
+                got = c;
+                break;
+            }
+            if (++c == pp.nslots) c = 0;
+        }
+        slot_s = got;
+    }
+    __syncthreads();
+    const int slot = slot_s;
+    if (slot < 0) {
+        if (threadIdx.x == 0) atomicOr(pp.status, kStatusNoSlot);
+        return;
+    }
+    float4 *S = pp.scr + (size_t)slot * N * K12;
+    const int64_t row = blockIdx.x;
+    const int nld = N * K2; // entries of F per slab
+    float4 buf[NPF];
+    auto load = [&](int i0) {
+#pragma unroll
+        for (int u = 0; u < NPF; ++u) {
+            const int e = threadIdx.x + u * NT;
+            if (e < nld) {
+                const int i1 = e / K2, q = e - i1 * K2;
+                buf[u] = F[(((int64_t)i0 * N + i1) * R + row) * K2 + q];
+            }
+        }
+    };
+    load(0);
+    for (int i0 = 0; i0 < N; ++i0) {
+#pragma unroll
+        for (int u = 0; u < NPF; ++u) {
+            const int e = threadIdx.x + u * NT;
+            if (e < nld) {
+                const int i1 = e / K2, q = e - i1 * K2;
+                C[q * CS + i1] = buf[u];
+            }
+        }
+        __syncthreads(); // C complete
+        if (i0 + 1 < N) load(i0 + 1);
+        const float4 *y1 = tstages_ct<N, 0, 1, true>(C, A, K2, CS, tw, kc, 1);
+        float4 *Si = S + (size_t)i0 * K12;
+        for (int d = threadIdx.x; d < K12; d += NT) {
+            const int cl = cell[d];
+            tc_store(Si + d, tprune_ct<N>(y1 + (cl >> 8) * CS, cl & 255, tw));
+        }
+        __syncthreads(); // i1 done with C and A
+    }
+
+    // Phase 2 (as in pair_kernel_tf_ct)
+    const int NB = (sizeAB + K2 * CS) / (2 * CS);
+    float4 *X = A, *Y = A + NB * CS;
+    double2 *out = M + row * pp.ng;
+    for (int d0 = 0; d0 < K12; d0 += NB) {
+        const int nbat = K12 - d0 < NB ? K12 - d0 : NB;
+        for (int i = threadIdx.x; i < nbat * N; i += NT) {
+            const int x = i / nbat, dl = i - x * nbat;
+            X[dl * CS + x] = S[(size_t)x * K12 + d0 + dl];
+        }
+        __syncthreads();
+        const float4 *y0 = tstages_ct<N, 0, 1, true>(X, Y, nbat, CS, tw, kc, 1);
+        const int m1 = pp.cstart[d0 + nbat];
+        for (int m = pp.cstart[d0] + threadIdx.x; m < m1; m += NT) {
+            const int2 pt = pp.cpts[m];
+            const tcx f = tprune_ct<N>(y0 + ((pt.y >> 8) - d0) * CS, pt.y & 255, tw);
+            out[pt.x] = make_double2(tf_to_d(tf_mul(f.re, inv_nr)), tf_to_d(tf_mul(f.im, inv_nr)));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(pp.slot_flags + slot, 0);
+    }
+}
+
+template <int N>
+inline size_t pair_tf_from_f_smem(const PairPlan &pp)
+{
+    const size_t cs = N + 1;
+    const size_t ab = (size_t)pp.K2 * cs > 31 * cs ? (size_t)pp.K2 * cs : 31 * cs;
+    return sizeof(float4) * (ab + (size_t)pp.K2 * cs + N) + sizeof(int) * (size_t)pp.K12;
+}
+
+template <int N>
+inline cudaError_t launch_pair_tf_from_f_cube(const float4 *F, int64_t R, const PairPlan &pp, const TfConsts &kc,
+                                             tf inv_nr, double2 *M, cudaStream_t st)
+{
+    if ((int64_t)N * pp.K2 > (int64_t)pair_threads<N>() * 6) return cudaErrorInvalidValue;
+    const size_t sm = pair_tf_from_f_smem<N>(pp);
+    cudaError_t e =
+        cudaFuncSetAttribute(pair_kernel_tf_from_f<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(pp.slot_flags, 0, sizeof(int) * pp.nslots, st)) != cudaSuccess) return e;
+    pair_kernel_tf_from_f<N><<<(unsigned)R, pair_threads<N>(), sm, st>>>(F, R, pp, kc, inv_nr, M);
+    return cudaGetLastError();
+}
+
+// Scratch slots the kernel needs for this plan: SMs x resident blocks + 32.
+template <int N>
+inline cudaError_t pair_tf_cube_slots(const PairPlan &pp, int *nslots)
+{
+    const size_t sm = pair_tf_ct_smem<N>(pp);
+    cudaError_t e = cudaFuncSetAttribute(pair_kernel_tf_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0, dev = 0, nsm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pair_kernel_tf_ct<N>, pair_threads<N>(), sm)) !=
+            cudaSuccess ||
+        (e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if constexpr (N == 48) { // the pool also serves the kernel that starts from the tensor-core output
+        const size_t sm2 = pair_tf_from_f_smem<N>(pp);
+        int occ2 = 0;
+        if ((e = cudaFuncSetAttribute(pair_kernel_tf_from_f<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm2)) != cudaSuccess ||
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, pair_kernel_tf_from_f<N>, pair_threads<N>(),
+                                                               sm2)) != cudaSuccess)
+            return e;
+        occ = occ > occ2 ? occ : occ2;
+    }
+    *nslots = nsm * (occ > 0 ? occ : 1) + 32;
+    return cudaSuccess;
 }
 
 // Band setup in two-float arithmetic for a cubic N^3 grid: the (band, i0) slab kernel
@@ -381,5 +515,7 @@ cudaError_t pair_tf_slots_g48(const PairPlan &, int *);
 cudaError_t launch_pair_tf_g72(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,
                                const TfConsts &, tf, double2 *, cudaStream_t);
 cudaError_t pair_tf_slots_g72(const PairPlan &, int *);
+cudaError_t launch_pair_tf_from_f_g48(const float4 *, int64_t, const PairPlan &, const TfConsts &, tf, double2 *,
+                                      cudaStream_t);
 
 } // namespace gw

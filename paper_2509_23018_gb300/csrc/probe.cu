@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kThreads) probe_ffma(float *out, long long ite
 #pragma unroll
     for (int k = 0; k < kChains; ++k) a[k] = 1e-3f * (threadIdx.x + k);
     const float m = 0.9999999f, c = 1e-9f;
+#pragma unroll 4
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k) a[k] = __fmaf_rn(a[k], m, c);
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(kThreads) probe_ffma2(float *out, long long it
 #pragma unroll
     for (int k = 0; k < kChains; ++k) a[k] = make_float2(1e-3f * (threadIdx.x + k), 2e-3f * (threadIdx.x + k));
     const float2 m = make_float2(0.9999999f, 0.9999998f), c = make_float2(1e-9f, 2e-9f);
+#pragma unroll 4
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k) a[k] = __ffma2_rn(a[k], m, c);
@@ -64,6 +66,7 @@ __global__ void __launch_bounds__(kThreads) probe_fadd2(float *out, long long it
 #pragma unroll
     for (int k = 0; k < kChains; ++k) a[k] = make_float2(1e-3f * (threadIdx.x + k), 2e-3f * (threadIdx.x + k));
     const float2 c = make_float2(1e-9f, -2e-9f);
+#pragma unroll 4
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k) a[k] = __fadd2_rn(a[k], c);
@@ -80,6 +83,7 @@ __global__ void __launch_bounds__(kThreads) probe_dfma(float *out, long long ite
 #pragma unroll
     for (int k = 0; k < kChains; ++k) a[k] = 1e-3 * (threadIdx.x + k);
     const double m = 0.9999999999, c = 1e-15;
+#pragma unroll 4
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k) a[k] = __fma_rn(a[k], m, c);
@@ -96,6 +100,7 @@ __global__ void __launch_bounds__(kThreads) probe_dmma884(float *out, long long 
 #pragma unroll
     for (int k = 0; k < kChains; ++k) d[k][0] = d[k][1] = 0.0;
     const double a = 1e-9 * (threadIdx.x & 7), b = 1e-9;
+#pragma unroll 4
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k)
@@ -116,6 +121,7 @@ __global__ void __launch_bounds__(kThreads) probe_dmma16816(float *out, long lon
 #pragma unroll
     for (int k = 0; k < K; ++k) d[k][0] = d[k][1] = d[k][2] = d[k][3] = 0.0;
     const double a = 1e-9 * (threadIdx.x & 7), b = 1e-9;
+#pragma unroll 4
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < K; ++k)
@@ -136,6 +142,7 @@ __global__ void __launch_bounds__(kThreads) probe_bf16_mma(float *out, long long
 #pragma unroll
     for (int k = 0; k < kChains; ++k) d[k][0] = d[k][1] = d[k][2] = d[k][3] = 0.f;
     const uint32_t a = 0x3c003c00u + (threadIdx.x & 1), b = 0x3c003c00u; // small bf16 pairs
+#pragma unroll 4
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k)
@@ -156,6 +163,7 @@ __global__ void __launch_bounds__(kThreads) probe_int8_mma(float *out, long long
 #pragma unroll
     for (int k = 0; k < kChains; ++k) d[k][0] = d[k][1] = d[k][2] = d[k][3] = 0;
     const uint32_t a = 0x01010101u * (threadIdx.x & 1), b = 0x01010101u;
+#pragma unroll 4
     for (long long i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k)

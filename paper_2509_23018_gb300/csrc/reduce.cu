@@ -19,6 +19,31 @@ __global__ void delta_kernel(const double *__restrict__ ev, const double *__rest
     }
 }
 
+// The same for a chunk of all valence bands x conduction bands c0 .. c0 + cb - 1, rows in the
+// order r = cl nv + v of the tensor-core pair elements.
+__global__ void delta_block_kernel(const double *__restrict__ ev, const double *__restrict__ ec, int nv, int c0,
+                                   int cb, OmegaList om, double *__restrict__ delta)
+{
+    const int64_t count = (int64_t)nv * cb;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int cl = (int)(i / nv), v = (int)(i - (int64_t)cl * nv);
+    const double x = ev[v] - ec[c0 + cl];
+    for (int w = 0; w < om.nw; ++w) {
+        const double ww = om.w[w];
+        delta[(int64_t)w * count + i] = 4.0 * x / fma(x, x, ww * ww);
+    }
+}
+
+cudaError_t launch_delta_block(const double *ev, const double *ec, int nv, int c0, int cb, const OmegaList &om,
+                               double *delta, cudaStream_t st)
+{
+    const int64_t count = (int64_t)nv * cb;
+    if (count == 0) return cudaSuccess;
+    delta_block_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(ev, ec, nv, c0, cb, om, delta);
+    return cudaGetLastError();
+}
+
 // Real-axis energy factor with broadening: Delta = 2/(x - w - i eta) + 2/(x + w + i eta),
 // x = E_v - E_c < 0, split into three non-positive weights per frequency (block 3 w + k):
 // k = 0: min(Re Delta, 0); k = 1: -max(Re Delta, 0); k = 2: Im Delta (<= 0 for w >= 0, x < 0).

@@ -1,0 +1,424 @@
+// Stage (a), last-axis transform of the pair products on the BF16 tensor cores.
+//
+// For a line l = (i0, i1) of the grid and a pair (v, c), the pruned transform of the pair
+// product along the last axis at the kept frequencies kz[q] is
+//     F[v][c][l][q] = sum_{i2} conj(psi_v[l][i2]) W_q[i2] psi_c[l][i2],   W_q[i2] = e^{+2 pi i kz[q] i2 / N},
+// the first stage of the forward transform of the product (the definition after Eq. ff-ch).
+// Over the pairs of a chunk it is, line by line, a complex matrix product whose operands
+// belong to one band each: rows conj(psi_v[l]) (valence), columns W_q psi_c[l] (conduction).
+// Written in real form (K = 2 N: Re and Im of each point interleaved), it runs as an
+// Ozaki-style split product (the scheme of stage (b)):
+//   * each operand row / column is scaled by its own power of two 2^E (|x| < 2^E) and cut into
+//     six balanced base-256 digits, x = 2^E sum_{i<6} d_i 2^(-7-8i), |d_i| <= 128; a digit
+//     times its scale is exact in BF16 (eight significant bits), so the slices carry their
+//     scales and the tensor cores accumulate true values;
+//   * the slice products i + j <= 5 are kept (the rest lies below 2^-48 of the operands'
+//     scales); the products with i + j = 0, 1, 2 go to three FP32 accumulators of their own:
+//     each of their terms is a multiple of one unit of that group with |sum| <= 3 * 96 * 2^14
+//     < 2^24, so those sums are exact; i + j = 3..5 share a fourth accumulator (its rounding
+//     lies 2^-48 below the leading group);
+//   * the four accumulators are summed in two-float arithmetic (two-sums for the exact groups)
+//     into F, which the pair kernel's remaining stages (middle and first axis) take from there.
+// The valence slices are formed once per call (band setup); the conduction columns are formed
+// per tile on the chip, from psi_c and the twiddles, by producer warps.
+#include "internal.h"
+#include "ptx.cuh"
+#include "fft_tf.cuh"
+
+#include <algorithm>
+
+namespace gw {
+
+// ------------------------------------------------------------------ digits
+// Balanced base-256 digits of y = (h + l) 2^(7 - E), |y| < 128 (two-float value, exponent E):
+// N = round(y 2^40) = T 2^24 + U with T, U exact FP32 integers, digits taken from the low end,
+// each digit times its weight 2^(E - 7 - 8i) returned as the BF16 bits of slice i.
+__device__ __forceinline__ void zd_digits(float h, float l, int E, uint16_t out[kZdSlices])
+{
+    // 2^(47 - E) in two factors so that each stays a normal FP32 for any E in [-100, 100]
+    const int sh = 47 - E;
+    const float s1 = __int_as_float((127 + sh / 2) << 23), s2 = __int_as_float((127 + sh - sh / 2) << 23);
+    const float Y = __fmul_rn(__fmul_rn(h, s1), s2), L = __fmul_rn(__fmul_rn(l, s1), s2);
+    const float T = rintf(__fmul_rn(Y, 0x1p-24f));
+    float U = __fadd_rn(rintf(__fmaf_rn(-0x1p24f, T, Y)), rintf(L)); // |U| <= 2^24
+    float d[kZdSlices];
+#pragma unroll
+    for (int i = kZdSlices - 1; i >= 3; --i) {
+        const float q = rintf(__fmul_rn(U, 0.00390625f));
+        d[i] = __fmaf_rn(-256.0f, q, U);
+        U = q;
+    }
+    float V = __fadd_rn(T, U); // |V| < 2^23 + 2
+#pragma unroll
+    for (int i = 2; i >= 1; --i) {
+        const float q = rintf(__fmul_rn(V, 0.00390625f));
+        d[i] = __fmaf_rn(-256.0f, q, V);
+        V = q;
+    }
+    d[0] = V;
+    // weights: slice i holds d_i 2^(E - 7 - 8 i)
+#pragma unroll
+    for (int i = 0; i < kZdSlices; ++i) {
+        const int e = E - 7 - 8 * i;
+        const float w = __int_as_float((127 + max(-126, e)) << 23);
+        out[i] = (uint16_t)(__float_as_uint(__fmul_rn(d[i], w)) >> 16);
+    }
+}
+
+// exponent E with |x| < 2^E for a line's largest component magnitude m (E = -126 for m = 0)
+__device__ __forceinline__ int zd_expo(float m)
+{
+    if (!(m > 0.0f)) return -126;
+    const int be = (int)((__float_as_uint(m) >> 23) & 0xff);
+    return (be == 0 ? -126 : be - 127) + 1;
+}
+
+// ------------------------------------------------------------------ valence slices
+// A[i][l][v][k] (BF16, k = 2 i2 + {Re, Im}) of the rows psi_v[l][.]: one warp per (v, l).
+__global__ void __launch_bounds__(256) zd_aslices_kernel(const float4 *__restrict__ psi, int nv, int n, int nlines,
+                                                         uint16_t *__restrict__ A)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= nv * nlines) return;
+    const int v = warp % nv, l = warp / nv;
+    const float4 *row = psi + ((int64_t)v * nlines + l) * n;
+    float m = 0.0f;
+    for (int i = lane; i < n; i += 32) {
+        const float4 x = row[i];
+        m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.z)) * (1.0f + 0x1p-20f));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int E = zd_expo(m);
+    const int64_t plane = (int64_t)nlines * nv * 2 * n;
+    uint16_t *dst = A + ((int64_t)l * nv + v) * 2 * n;
+    for (int i = lane; i < n; i += 32) {
+        const float4 x = row[i];
+        uint16_t dr[kZdSlices], di[kZdSlices];
+        zd_digits(x.x, x.y, E, dr);
+        zd_digits(x.z, x.w, E, di);
+#pragma unroll
+        for (int s = 0; s < kZdSlices; ++s)
+            *(uint32_t *)(dst + s * plane + 2 * i) = (uint32_t)dr[s] | ((uint32_t)di[s] << 16);
+    }
+}
+
+cudaError_t launch_zd_aslices(const void *psiv, int nv, int n, uint16_t *A, cudaStream_t st)
+{
+    const int nlines = n * n;
+    const int64_t warps = (int64_t)nv * nlines;
+    zd_aslices_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>((const float4 *)psiv, nv, n, nlines, A);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ the product
+// One block per SM, persistent over units u = (line l, row tile mt); per unit the block keeps
+// the valence slices of its 128 rows resident (three K-chunks of 32 real entries, TMA) and
+// runs over the conduction tiles ct of the chunk (CT bands, 2 K2 real columns each, padded to
+// 64 columns): producer warps form the tile's column slices per K-chunk into a 2-deep ring,
+// one thread issues the tcgen05 products into four accumulators (two buffers of 4 x 64 TMEM
+// columns alternate between tiles), and the epilogue warps sum the accumulators into F.
+//  warp 0: TMA; warp 1: MMA (and TMEM); warps 2..5: epilogue (TMEM lane quadrant warp % 4);
+//  warps 6..11: producers.
+constexpr int kZdN = 64;                               // columns per tile
+constexpr int kZdKC = 32;                              // real K entries per K-chunk
+constexpr int kZdThreads = 384;
+constexpr int kZdProducers = 6;                        // producer warps
+constexpr unsigned kZdASlice = 128 * kZdKC * 2;        // one slice of one K-chunk: 8 KB
+constexpr unsigned kZdAChunk = kZdSlices * kZdASlice;  // 48 KB
+constexpr unsigned kZdBSlice = kZdN * kZdKC * 2;       // 4 KB
+constexpr unsigned kZdBStage = kZdSlices * kZdBSlice;  // 24 KB
+// idesc: D = F32, A = B = BF16, both K-major, N = 64, M = 128
+constexpr uint32_t kZdIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kZdN >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+// K-major operand tile with 64-byte swizzling: row r of 64 bytes (32 BF16), 8-row atoms of
+// 512 bytes, 16-byte chunk j of row r stored at chunk j ^ ((r % 8) >> 1).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+__device__ __forceinline__ uint32_t sw64_off(int r, int k) // byte offset of element k of row r
+{
+    return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((k >> 3) ^ ((r & 7) >> 1)) & 3) << 4) + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void tma4(void *dst, const CUtensorMap *m, uint64_t *b, int x, int y, int z, int w)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+                 "%5}], [%6];" ::"r"(su32(dst)),
+                 "l"(m), "r"(x), "r"(y), "r"(z), "r"(w), "r"(su32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// two-sum with the sum's rounding error
+__device__ __forceinline__ float zd_2sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+struct ZdArgs {
+    CUtensorMap tmA;        // A slices [6][lines][nv][2N] bf16, box {32, 128, 1, 6}, 64-byte swizzle
+    const float4 *psic;     // conduction band grids (two-float), [nc][N^3]
+    const int *kz;          // [K2] kept last-axis frequencies
+    float4 *F;              // [lines][R][K2] two-float, R = rows of the chunk = nv * cb, r = cl * nv + v
+    int *status;
+    int n, nv, c0, cb, K2, CT, nunits, nmt;
+};
+
+__global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_constant__ ZdArgs a,
+                                                                const float4 *__restrict__ twf)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = sm;                               // 3 K-chunks x 48 KB
+    unsigned char *sB = sA + 3 * kZdAChunk;               // 2 stages x 24 KB
+    float4 *tw = (float4 *)(sB + 2 * kZdBStage);          // [N] twiddles e^{+2 pi i t / N}
+    int *kzs = (int *)(tw + a.n);                         // [K2]
+    uint64_t *bar = (uint64_t *)(((uintptr_t)(kzs + 64) + 7) & ~(uintptr_t)7);
+    uint64_t *aFull = bar, *aEmpty = bar + 1, *bFull = bar + 2, *bEmpty = bar + 4, *tFull = bar + 6,
+             *tEmpty = bar + 8, *fin = bar + 10;
+    uint32_t *tslot = (uint32_t *)(bar + 11);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) tw[i] = twf[i];
+    for (int i = threadIdx.x; i < a.K2; i += blockDim.x) kzs[i] = a.kz[i];
+    if (threadIdx.x == 0) {
+        bar_init(aFull, 1);
+        bar_init(aEmpty, 1);
+        for (int i = 0; i < 2; ++i) {
+            bar_init(&bFull[i], kZdProducers);
+            bar_init(&bEmpty[i], 1);
+            bar_init(&tFull[i], 1);
+            bar_init(&tEmpty[i], 128);
+        }
+        bar_init(fin, 1);
+        bar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(tslot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    const int nct = (a.cb + a.CT - 1) / a.CT; // conduction tiles per unit
+    const int ncol = 2 * a.K2;                // real columns per conduction band
+    bool ok = true;
+
+    if (warp == 0) {
+        // ---- TMA: the unit's valence slices, once the previous unit's products are done
+        if (lane == 0) {
+            uint32_t u = 0;
+            for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x, ++u) {
+                const int l = unit / a.nmt, mt = unit - l * a.nmt;
+                if (!bar_wait(aEmpty, (u & 1) ^ 1)) { ok = false; break; }
+                bar_expect(aFull, 3 * kZdAChunk);
+                for (int kc = 0; kc < 3; ++kc) tma4(sA + kc * kZdAChunk, &a.tmA, aFull, kc * kZdKC, mt * 128, l, 0);
+            }
+            // the last load has landed before the block may leave
+            if (u > 0 && ok && !bar_wait(aFull, (u - 1) & 1)) ok = false;
+            if (!ok) atomicOr(a.status, kStatusTimeout);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issue
+        if (lane == 0) {
+            uint32_t u = 0, it = 0, tile = 0;
+            for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x, ++u) {
+                if (!bar_wait(aFull, u & 1)) { ok = false; break; }
+                for (int ct = 0; ct < nct && ok; ++ct, ++tile) {
+                    const uint32_t buf = tile & 1;
+                    if (!bar_wait(&tEmpty[buf], ((tile >> 1) & 1) ^ 1)) { ok = false; break; }
+                    tc_fence_after();
+                    unsigned written = 0;
+                    for (int kc = 0; kc < 3 && ok; ++kc, ++it) {
+                        const uint32_t st = it & 1;
+                        if (!bar_wait(&bFull[st], (it >> 1) & 1)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t a0 = su32(sA + kc * kZdAChunk), b0 = su32(sB + st * kZdBStage);
+                        for (int i = 0; i < kZdSlices; ++i)
+                            for (int j = 0; i + j < kZdSlices; ++j) {
+                                const int g = min(i + j, 3);
+                                const uint32_t d = tbase + buf * 256 + g * kZdN;
+#pragma unroll
+                                for (int s16 = 0; s16 < 2; ++s16) {
+                                    const uint32_t acc = (written >> g) & 1u;
+                                    umma_f16(d, sdesc_sw64(a0 + i * kZdASlice + s16 * 32),
+                                             sdesc_sw64(b0 + j * kZdBSlice + s16 * 32), kZdIdesc, acc);
+                                    written |= 1u << g;
+                                }
+                            }
+                        umma_commit(&bEmpty[st]);
+                    }
+                    umma_commit(&tFull[buf]);
+                }
+                umma_commit(aEmpty);
+            }
+            umma_commit(fin);
+            bar_wait(fin, 0);
+            if (!ok) atomicOr(a.status, kStatusTimeout);
+        }
+    } else if (warp < 6) {
+        // ---- epilogue: one tile row (valence band) per thread
+        const int q4 = warp & 3, r = q4 * 32 + lane;
+        uint32_t tile = 0;
+        for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x) {
+            const int l = unit / a.nmt, mt = unit - l * a.nmt;
+            const int v = mt * 128 + r;
+            for (int ct = 0; ct < nct; ++ct, ++tile) {
+                const uint32_t buf = tile & 1;
+                const bool got = bar_wait(&tFull[buf], (tile >> 1) & 1);
+                if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t ta = tbase + ((uint32_t)(q4 * 32) << 16) + buf * 256;
+#pragma unroll 1
+                for (int c0 = 0; c0 < kZdN; c0 += 32) {
+                    uint32_t g0[32], g1[32], g2[32], g3[32];
+                    GW_TMEM_LD32(ta + 0 * kZdN + c0, g0);
+                    GW_TMEM_LD32(ta + 1 * kZdN + c0, g1);
+                    GW_TMEM_LD32(ta + 2 * kZdN + c0, g2);
+                    GW_TMEM_LD32(ta + 3 * kZdN + c0, g3);
+                    tmem_wait_ld();
+                    if (v < a.nv) {
+#pragma unroll
+                        for (int cc = 0; cc < 32; cc += 2) {
+                            const int col = c0 + cc; // Re column; col + 1 is the Im column
+                            const int cl = col / ncol, q = (col - cl * ncol) >> 1;
+                            const int cbd = ct * a.CT + cl;
+                            if (cl < a.CT && cbd < a.cb) {
+                                float x[2], y[2];
+#pragma unroll
+                                for (int p = 0; p < 2; ++p) {
+                                    float e1, e2;
+                                    const float s1 = zd_2sum(__uint_as_float(g0[cc + p]), __uint_as_float(g1[cc + p]), e1);
+                                    const float s2 = zd_2sum(s1, __uint_as_float(g2[cc + p]), e2);
+                                    const float t = __fadd_rn(__fadd_rn(e1, e2), __uint_as_float(g3[cc + p]));
+                                    x[p] = __fadd_rn(s2, t);
+                                    y[p] = __fsub_rn(t, __fsub_rn(x[p], s2));
+                                }
+                                const int64_t row = (int64_t)cbd * a.nv + v;
+                                a.F[((int64_t)l * ((int64_t)a.cb * a.nv) + row) * a.K2 + q] =
+                                    make_float4(x[0], y[0], x[1], y[1]);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                bar_arrive(&tEmpty[buf]);
+            }
+        }
+        if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
+    } else {
+        // ---- producers: column slices of the conduction tile, K-chunk by K-chunk
+        const int pt = threadIdx.x - 6 * 32; // 0 .. 191
+        uint32_t it = 0;
+        for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x) {
+            const int l = unit / a.nmt;
+            for (int ct = 0; ct < nct && ok; ++ct) {
+                // column exponents of the tile's bands: |Re b|, |Im b| <= |psi_c| on the line
+                int Ec[4] = {-126, -126, -126, -126};
+                for (int cl = 0; cl < a.CT; ++cl) {
+                    const int c = ct * a.CT + cl;
+                    float m = 0.0f;
+                    if (c < a.cb) {
+                        const float4 *row = a.psic + ((int64_t)(a.c0 + c) * a.n * a.n + l) * a.n;
+                        for (int i = lane; i < a.n; i += 32) {
+                            const float4 x = row[i];
+                            m = fmaxf(m, (fabsf(x.x) + fabsf(x.z)) * (1.0f + 0x1p-20f));
+                        }
+                    }
+                    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    Ec[cl] = zd_expo(m);
+                }
+                for (int kc = 0; kc < 3 && ok; ++kc, ++it) {
+                    const uint32_t st = it & 1;
+                    const bool got = bar_wait(&bEmpty[st], ((it >> 1) & 1) ^ 1);
+                    if (!__all_sync(0xffffffffu, got)) { ok = false; break; } // warp-uniform exit
+                    unsigned char *B = sB + st * kZdBStage;
+                    // zero the padding columns (their products never reach F, but must be finite)
+                    for (int e = pt; e < (kZdN - a.CT * ncol) * (kZdKC / 2) * kZdSlices; e += kZdProducers * 32) {
+                        const int s = e / ((kZdN - a.CT * ncol) * (kZdKC / 2)), rem = e % ((kZdN - a.CT * ncol) * (kZdKC / 2));
+                        const int col = a.CT * ncol + rem / (kZdKC / 2), k = 2 * (rem % (kZdKC / 2));
+                        *(uint32_t *)(B + s * kZdBSlice + sw64_off(col, k)) = 0u;
+                    }
+                    // items (cl, q, k2): b = W^{kz[q] i2} psi_c[l][i2], i2 = 16 kc + k2
+                    const int nitem = a.CT * a.K2 * 16;
+                    for (int w = pt; w < nitem; w += kZdProducers * 32) {
+                        const int k2 = w & 15, rest = w >> 4;
+                        const int q = rest % a.K2, cl = rest / a.K2;
+                        const int c = ct * a.CT + cl;
+                        const int i2 = kc * 16 + k2;
+                        uint16_t dr[kZdSlices], di[kZdSlices];
+                        if (c < a.cb) {
+                            const tcx x = tc_load(a.psic + ((int64_t)(a.c0 + c) * a.n * a.n + l) * a.n + i2);
+                            const int e = (kzs[q] * i2) % a.n;
+                            const tcx b = tc_mul(x, tc_load(tw + e));
+                            zd_digits(b.re.hi, b.re.lo, Ec[cl], dr);
+                            zd_digits(b.im.hi, b.im.lo, Ec[cl], di);
+                        } else {
+#pragma unroll
+                            for (int s = 0; s < kZdSlices; ++s) dr[s] = di[s] = 0;
+                        }
+                        const int colr = cl * ncol + 2 * q, k = 2 * k2;
+#pragma unroll
+                        for (int s = 0; s < kZdSlices; ++s) {
+                            // Re column: (Re b, Im b); Im column: (Im b, -Re b)
+                            *(uint32_t *)(B + s * kZdBSlice + sw64_off(colr, k)) = (uint32_t)dr[s] | ((uint32_t)di[s] << 16);
+                            *(uint32_t *)(B + s * kZdBSlice + sw64_off(colr + 1, k)) =
+                                (uint32_t)di[s] | ((uint32_t)(dr[s] ^ 0x8000u) << 16);
+                        }
+                    }
+                    fence_async_shared();
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(&bFull[st]);
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tbase, 512);
+}
+
+size_t zd_smem_bytes() { return 1024 + 3 * kZdAChunk + 2 * kZdBStage + 16 * 128 + 64 * 4 + 16 * 8 + 64; }
+
+bool zd_supported(int n, int K2, int nv)
+{
+    return n == 48 && K2 >= 1 && 2 * K2 <= kZdN && nv >= 1 && 2 * n == 3 * kZdKC;
+}
+
+int zd_conduction_per_tile(int K2) { return std::min(4, kZdN / (2 * K2)); }
+
+cudaError_t launch_zd_gemm(const CUtensorMap &tmA, const void *psic, const int *kz, const float4 *twf, int n, int nv,
+                           int c0, int cb, int K2, float4 *F, int *status, cudaStream_t st)
+{
+    ZdArgs a;
+    a.tmA = tmA;
+    a.psic = (const float4 *)psic;
+    a.kz = kz;
+    a.F = F;
+    a.status = status;
+    a.n = n;
+    a.nv = nv;
+    a.c0 = c0;
+    a.cb = cb;
+    a.K2 = K2;
+    a.CT = zd_conduction_per_tile(K2);
+    a.nmt = (nv + 127) / 128;
+    a.nunits = n * n * a.nmt;
+    const size_t sm = zd_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(zd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const int grid = std::min(a.nunits, sms);
+    zd_gemm_kernel<<<grid, kZdThreads, sm, st>>>(a, twf);
+    return cudaGetLastError();
+}
+
+} // namespace gw

@@ -65,6 +65,24 @@ def test_c2_sampled(gw, c2, prec, nslices, mtxel, tol):
     h.destroy()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("ozaki", 1e-9)])
+def test_c2_epsilon_inverse_full_size(gw, c2, prec, tol):
+    """[I - v chi(w)]^-1 at N_G = 2000 for chi(0), chi(5 eV) and chi(20 eV) of the 48^3 workload
+    (the bench's --epsilon workload), element by element against the oracle's dense inverse of
+    the same chi blocks, v_G = 4 pi / |G|^2."""
+    cfg, p, _, _, _ = c2
+    h = gw.from_problem(p, prec="ozaki", nslices=7, mtxel="twofloat", pair_chunk=cfg.pair_chunk)
+    (chi,) = h.compute(0, [0.0, 5.0, 20.0])
+    h.destroy()
+    v = torch.as_tensor(gwgen.coulomb(p.gchi), device="cuda")
+    he = gw.Chi0(cfg.grid, prec=prec, nslices=7)
+    einv = he.epsilon_inverse(chi, v).cpu().numpy()
+    he.sync()
+    chis, vv = chi.cpu().numpy(), v.cpu().numpy()
+    for i in range(3):
+        assert rel(einv[i], oracle.epsilon_inverse(chis[i], vv)) <= tol
+
+
 @pytest.fixture(scope="module")
 def c3():
     cfg = gwgen.CONFIGS["c3_72cube"]

@@ -125,3 +125,24 @@ def test_frequency_group_slicing(gw, mtxel):
         ref = oracle.chi0(M, oracle.delta(p.ev, p.ec, om[i]))
         assert np.linalg.norm(many[i] - ref) <= 1e-9 * np.linalg.norm(ref)
     h.destroy()
+
+
+@pytest.mark.parametrize("spread", [0.0, 1e-3])
+def test_split_correlated_rows(gw, spread):
+    """Correlated inputs, the worst case for the FP32 sums of the slice groups: every pair
+    carries (nearly) the same row, so the digits of all 8192 pairs of a chunk share their signs
+    and the group sums reach their largest magnitudes (t >= 4 may then round in FP32; the
+    rounding sits at least 2^-36 below the leading group).  The result must still meet the
+    split bar against the oracle."""
+    rng = np.random.default_rng(23)
+    ng, nv, nc = 160, 8, 1024
+    m0 = rng.standard_normal(ng) + 1j * rng.standard_normal(ng)
+    noise = rng.standard_normal((nv * nc, ng)) + 1j * rng.standard_normal((nv * nc, ng))
+    M = m0[None, :] * (1.0 + spread * noise)
+    ev = rng.uniform(-10, -1, nv)
+    ec = rng.uniform(1, 30, nc)
+    h = gw.Chi0((8, 8, 8), prec="ozaki", nslices=7, pair_chunk=8192)
+    for w in (0.0, 4.0):
+        chi = h.contract(dev(ev), dev(ec), dev(M), [w]).cpu().numpy()[0]
+        assert rel(chi, oracle.chi0(M, oracle.delta(ev, ec, w))) <= TOL_SPLIT
+    h.sync()
