@@ -602,6 +602,71 @@ def method_stage_a(cfg):
     return float(nbytes), float(flops)
 
 
+ZD_SLICES, ZD_TILE_N, ZD_TILE_M = 6, 64, 128
+
+
+def zd_ops(cfg, prob):
+    """Work of stage (a) on the tensor-core route per chunk: the low-precision flops the last-axis
+    split product executes (21 kept slice products of 128 x 64 x 2N tiles, padding included) and
+    the useful share, and the FP32 operations of the middle/first-axis kernel per pair."""
+    n0, n1, n2 = cfg.grid
+    k2 = kept_columns(prob, n2)
+    ct = min(4, ZD_TILE_N // (2 * k2))
+    cb = max(1, cfg.pair_chunk // cfg.nv)
+    tiles = n0 * n1 * -(-cfg.nv // ZD_TILE_M) * -(-cb // ct)
+    prods = ZD_SLICES * (ZD_SLICES + 1) // 2
+    flops = prods * 2.0 * ZD_TILE_M * ZD_TILE_N * 2 * n2 * tiles
+    useful = prods * 8.0 * n2 * k2 * cfg.nv * cb * n0 * n1  # complex MACs of the kept outputs
+    k12 = cells(prob, cfg.grid)
+    i1 = k2 * _head_ops(n1, lazy=True) + k12 * _prune_out_ops(n1)
+    i0 = k12 * _head_ops(n0, lazy=True) + cfg.ng * _prune_out_ops(n0)
+    return flops, useful, n0 * i1 + i0, cb
+
+
+def roofline_zd(cfg, prob, res):
+    """Rooflines of the tensor-core stage (a): the last-axis split product (tensor) and the
+    middle/first-axis kernel (FP32 issue), each per launch; plus the method-level stage (a)
+    numbers over both."""
+    flops, useful, ops_pair, cb = zd_ops(cfg, prob)
+    out = {}
+    kms, kn = res["timing"].get("zdft", (0.0, 0))
+    if kn:
+        peak, src = peak_for("ozaki")
+        ach = flops / (kms / kn * 1e-3) * 1e-12
+        out["zdft"] = {"bound": "tensor", "kernel": "zd_gemm_kernel", "achieved": ach, "peak": peak,
+                       "unit": "TFLOP/s", "frac": ach / peak, "traffic": TRAFFIC.get("zdft", {}).get("bytes_per_launch"),
+                       "traffic_source": TRAFFIC.get("zdft", {}).get("source"), "launches": kn,
+                       "ms_per_launch": kms / kn, "flops_per_launch": flops, "useful_share": useful / flops,
+                       "peak_source": src, "share_of_step": kms / res["total_ms"],
+                       "unit_of_work": "BF16 flops of the 21 kept slice products (128 x 64 tiles, K = 2N)"}
+    kms2, kn2 = res["timing"].get("pair_from_f", (0.0, 0))
+    if kn2:
+        peak, src = fp32_lane_peak()
+        per_launch = ops_pair * cfg.nv * cb
+        ach = per_launch / (kms2 / kn2 * 1e-3) * 1e-12
+        out["pair_from_f"] = {"bound": "alu", "kernel": "pair_kernel_tf_from_f", "achieved": ach, "peak": peak,
+                              "unit": "FP32 Tops/s", "frac": ach / peak,
+                              "traffic": TRAFFIC.get("pair_from_f", {}).get("bytes_per_launch"),
+                              "traffic_source": TRAFFIC.get("pair_from_f", {}).get("source"), "launches": kn2,
+                              "ms_per_launch": kms2 / kn2, "ops_per_launch": per_launch, "ops_per_pair": ops_pair,
+                              "peak_source": src, "share_of_step": kms2 / res["total_ms"],
+                              "unit_of_work": "FP32 operations of the two-float i1 and i0 transforms as implemented"}
+    if kn and kn2:
+        mbytes, mflops = method_stage_a(cfg)
+        hbm, hbm_src = _hbm_peak()
+        nchunk = -(-cfg.nc // cb)
+        t_step = (kms / kn + kms2 / kn2) * 1e-3 * nchunk
+        dfma = LIVE_PEAKS.get("dfma")
+        out["stage_a_method"] = {"bytes_per_step": mbytes, "flops_per_step": mflops,
+                                 "hbm_frac": mbytes / t_step * 1e-9 / hbm, "hbm_peak_gbs": hbm,
+                                 "hbm_peak_source": hbm_src, "fp64_equiv_tflops": mflops / t_step * 1e-12,
+                                 "fp64_alu_peak_tflops": dfma,
+                                 "fp64_alu_frac": mflops / t_step * 1e-12 / dfma if dfma else None,
+                                 "note": "bytes: every band grid read once + M written once; flops: half of "
+                                         "5 N_r log2 N_r per pair (output-pruned FFT) + 6 N_r for the product"}
+    return out
+
+
 def roofline_pair(cfg, prob, res):
     kms, kn = res["timing"].get("pair_mtxel", (0.0, 0))
     nchunk = -(-cfg.npairs // cfg.pair_chunk)
@@ -673,19 +738,26 @@ def ours(args):
     main = run_mode(args, cfg, prob, dev, args.prec, args.nslices, mtxel, args.steps, args.warmup,
                     not args.no_e2e, world)
     roofline = roofline_for(cfg, args.prec, args.nslices, main)
-    # the dominant kernel of the step carries the "roofline" key; the other is kept beside it
-    pair_ms = main["timing"].get("pair_mtxel", (0.0, 0))[0]
-    contr_ms = main["timing"].get(roofline["kernel"], (0.0, 0))[0]
-    roofline_other = None
-    if mtxel == "twofloat" and pair_ms > contr_ms:
-        roofline_other, roofline = roofline, roofline_pair(cfg, prob, main)
+    # the dominant kernel of the step carries the "roofline" key; every kernel's is under "rooflines"
+    rooflines = {roofline["kernel"]: roofline}
+    if "zdft" in main["timing"]:
+        rooflines.update(roofline_zd(cfg, prob, main))
+    elif mtxel == "twofloat":
+        rooflines["pair_mtxel"] = roofline_pair(cfg, prob, main)
+    kernel_ms = {"ozaki_gemm": "ozaki_gemm", "contract_f64": "contract_f64", "zdft": "zdft",
+                 "pair_from_f": "pair_from_f", "pair_mtxel": "pair_mtxel"}
+    dom = max((k for k in rooflines if k in kernel_ms),
+              key=lambda k: main["timing"].get(kernel_ms[k], (0.0, 0))[0])
+    roofline = rooflines[dom]
+    roofline_other = rooflines.get("ozaki_gemm") if dom != "ozaki_gemm" else None
     # In split precision the step runs each chunk's contraction on a second stream beside the
     # next chunk's pair elements, so the kernels above share the SMs; a short single-stream
     # pass gives each kernel's rate when it runs alone.
     alone = None
     if args.prec == "ozaki" and args.path == "stream" and mtxel == "twofloat" and main.get("streams", 1) == 2:
         a = run_mode(args, cfg, prob, dev, args.prec, args.nslices, mtxel, 2, 1, False, world, single_stream=True)
-        alone = {"ms_per_step": a["ms_per_step"], "value": a["value"], "pair": roofline_pair(cfg, prob, a),
+        alone = {"ms_per_step": a["ms_per_step"], "value": a["value"],
+                 "pair": roofline_zd(cfg, prob, a) if "zdft" in a["timing"] else roofline_pair(cfg, prob, a),
                  "contraction": roofline_for(cfg, args.prec, args.nslices, a, single_stream=True)}
     # the CPU baseline leg (rank 0): the oracle timed on a bounded sample, and its reference block
     # for the error check
@@ -719,7 +791,7 @@ def ours(args):
                            "l2": "inputs larger than L2 (psi grids 2.0 GB, M chunks 262 MB)",
                            "parallelism": f"replicas x{world} (independent q-points)",
                            "streams": main.get("streams", 1)},
-                "error": err, "roofline": roofline, "roofline_contraction": roofline_other,
+                "error": err, "roofline": roofline, "roofline_contraction": roofline_other, "rooflines": rooflines,
                 "single_stream": alone, "fp64_dmma": other, "cpu_baseline": cpu, "e2e": main["e2e"],
                 "gpu_launches": main["launches"], "kernel_ms": main["kernel_ms"], "clocks": main["clocks"]}
         print(json.dumps(line), flush=True)

@@ -181,6 +181,19 @@ GW_API int gw_chi0_tuning(const gw_chi0 *h, int *tile_f64, int *waves_f64, int *
 GW_API gw_status gw_chi0_pair_elements(gw_chi0 *h, int iq, int64_t pair_begin, int64_t pair_count, double *M);
 
 /*
+ * Stage (a) alone for all valence bands of slot iq and the conduction bands c0 .. c0 + cb - 1,
+ * on the route gw_chi0_compute takes for two-float stage (a) on the 48^3 grid: the last-axis
+ * transform of the pair products as a split product on the BF16 tensor cores (the grid line's
+ * valence points against the conduction points times the kept twiddles, six BF16 slices each,
+ * FP32 group sums combined in two-float arithmetic), the middle and first axes as in the FFT
+ * pair kernel.  Rows in that route's order: M[(c - c0) nv + v][g], device complex128
+ * [cb nv][ng].  GW_ERR_UNSUPPORTED when the slot does not take the route (another grid, FP64
+ * stage (a), resident pair elements kept); GW_ERR_ARG for a block outside [0, nc).  Uses the
+ * handle's work buffers (the last-axis output of cb nv pairs, 16 * 48^2 * K2 bytes per pair).
+ */
+GW_API gw_status gw_chi0_pair_elements_block(gw_chi0 *h, int iq, int c0, int cb, double *M);
+
+/*
  * Stage (b) alone (steps a5-a7) on caller-given matrix elements, using the handle's
  * precision mode:  chi[w][G][G'] = sum_p conj(M[p][G]) Delta_p(w) M[p][G'],
  * p = v*nc + c, Delta from ev [nv] and ec [nc] (device float64, eV).
@@ -331,8 +344,9 @@ GW_API gw_status gw_chi0_keep_pair_elements(gw_chi0 *h, int enable);
 /*
  * How many streams a single-frequency gw_chi0_compute uses for slot iq as it stands (bands and
  * sphere set): 2 when each chunk's split contraction runs on a second stream beside the next
- * chunk's pair elements (split precision, two-float stage (a), and room for two pair-kernel
- * blocks beside a contraction block on an SM), else 1.  Calls with several frequencies always
+ * chunk's pair elements (split precision, two-float stage (a) by the FFT pair kernel, and room for
+ * two pair-kernel blocks beside a contraction block on an SM), else 1 (always 1 on the
+ * tensor-core route of stage (a), see gw_chi0_pair_elements_block).  Calls with several frequencies always
  * run on one stream.  Negative (a gw_status, negated) on a bad handle or slot.
  */
 GW_API int gw_chi0_streams(gw_chi0 *h, int iq);

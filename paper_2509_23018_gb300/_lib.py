@@ -43,6 +43,7 @@ SIGNATURES = {
     "gw_chi0_compute_batch": ([P, I, P, I, P, P, P], I),
     "gw_chi0_tuning": ([P, P, P, P], I),
     "gw_chi0_pair_elements": ([P, I, I64, I64, P], I),
+    "gw_chi0_pair_elements_block": ([P, I, I, I, P], I),
     "gw_chi0_contract": ([P, I, I, P, P, I, P, I, P, P], I),
     "gw_chi0_adjoint": ([P, I, D, P, P, P, P, P, P], I),
     "gw_chi0_subspace_basis": ([P, I, P, I, P, P], I),

@@ -141,6 +141,16 @@ class Chi0:
         self._check(self.lib.gw_chi0_pair_elements(self.h, int(iq), int(begin), int(count), _ptr(out)))
         return out
 
+    def pair_elements_block(self, iq: int, c0: int, cb: int, out: torch.Tensor | None = None):
+        """M rows [(c - c0) nv + v] of all valence bands x conduction bands c0 .. c0 + cb - 1 on the
+        tensor-core route of stage (a) (gw_chi0_pair_elements_block)."""
+        n, nv = self.ng[iq], self.nb[("v", iq)]
+        if out is None:
+            out = torch.empty((cb * nv, n), dtype=torch.complex128, device=f"cuda:{self.device}")
+        self._use_current_stream()
+        self._check(self.lib.gw_chi0_pair_elements_block(self.h, int(iq), int(c0), int(cb), _ptr(out)))
+        return out
+
     def contract(self, ev: torch.Tensor, ec: torch.Tensor, M: torch.Tensor, omega: Sequence[float],
                  out: torch.Tensor | None = None):
         ev = ev.to(device=f"cuda:{self.device}", dtype=torch.float64).contiguous()

@@ -495,10 +495,27 @@ void free_sphere(gw_chi0 *h, Sphere &s)
     dfree(h, s.cpts, sizeof(int2) * s.ng);
     s = Sphere();
 }
+// The high-priority second stream and the events of the overlapped paths (created on first use).
+gw_status ensure_overlap_stream(gw_chi0 *h)
+{
+    if (h->ov_st) return GW_OK;
+    int lo = 0, hi = 0;
+    CK(h, cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+    CK(h, cudaStreamCreateWithPriority(&h->ov_st, cudaStreamNonBlocking, hi), "contraction stream");
+    for (int b = 0; b < 2; ++b) {
+        CK(h, cudaEventCreateWithFlags(&h->ov_split[b], cudaEventDisableTiming), "event");
+        CK(h, cudaEventCreateWithFlags(&h->ov_gemm[b], cudaEventDisableTiming), "event");
+    }
+    return GW_OK;
+}
+
 // ------------------------------------------------------------------ stage (a) on the tensor cores
 // The last-axis transform of the pair products as a split product per grid line (zdft.cu) for
 // two-float stage (a) on the 48^3 grid; chunks are all valence bands x a block of conduction
-// bands, rows r = cl nv + v.  GW_CHI0_STAGE_A=fft selects the FFT pair kernel instead.
+// bands, rows r = cl nv + v, on one stream (the last-axis product and the split contraction each
+// need whole SMs' shared memory: running the contraction on a second stream beside the next
+// chunk's FP32 stages measured slower, 163 against 142 ms per 48^3 q-point).
+// GW_CHI0_STAGE_A=fft selects the FFT pair kernel instead.
 bool zd_route(gw_chi0 *h, int iq, bool resident)
 {
     static const bool fft_only = [] {
@@ -518,7 +535,7 @@ int zd_chunk_bands(gw_chi0 *h, int iq)
     return (int)std::max<int64_t>(1, std::min<int64_t>(h->cond.nb, h->d.pair_chunk / nv));
 }
 
-gw_status zd_prepare(gw_chi0 *h, int iq, CUtensorMap *tmA)
+gw_status zd_prepare(gw_chi0 *h, int iq, CUtensorMap *tmA, CUtensorMap *tmC)
 {
     const BandSet &v = h->val[iq];
     const Sphere &sp = h->sph[iq];
@@ -542,21 +559,30 @@ gw_status zd_prepare(gw_chi0 *h, int iq, CUtensorMap *tmA)
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, GW_ERR_CUDA, "cuTensorMapEncodeTiled (valence slices) failed (%d)", (int)r);
+    // the conduction grids, line by line: box of one line of CT bands
+    cuuint64_t cd[3] = {(cuuint64_t)4 * n, (cuuint64_t)lines, (cuuint64_t)h->cond.nb};
+    cuuint64_t cst[2] = {(cuuint64_t)4 * n * 4, (cuuint64_t)16 * lines * n};
+    cuuint32_t cbox[3] = {(cuuint32_t)(4 * n), 1, (cuuint32_t)gw::zd_conduction_per_tile(sp.K2)};
+    cuuint32_t ces[3] = {1, 1, 1};
+    r = h->encode(tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->cond.psi, cd, cst, cbox, ces, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, GW_ERR_CUDA, "cuTensorMapEncodeTiled (conduction grids) failed (%d)", (int)r);
     return GW_OK;
 }
 
-gw_status zd_stage_a(gw_chi0 *h, int iq, const CUtensorMap &tmA, int c0, int cb, const gw::PairPlan &pp, double2 *M)
+gw_status zd_stage_a(gw_chi0 *h, int iq, const CUtensorMap &tmA, const CUtensorMap &tmC, int c0, int cb,
+                     const gw::PairPlan &pp, double2 *M)
 {
     const BandSet &v = h->val[iq];
     const Sphere &sp = h->sph[iq];
     const int n = h->d.n[0];
     {
         Scope sc(h, "zdft");
-        CK(h, gw::launch_zd_gemm(tmA, h->cond.psi, sp.kz, pp.ax[2].twf, n, v.nb, c0, cb, sp.K2, h->zdF, h->status,
-                                 h->st),
+        CK(h, gw::launch_zd_gemm(tmA, tmC, h->cond.psi, sp.kz, pp.ax[2].twf, n, v.nb, c0, cb, sp.K2, h->zdF,
+                                 h->status, h->st),
            "last-axis transform");
     }
-    Scope sc(h, "pair_mtxel");
+    Scope sc(h, "pair_from_f");
     CK(h, gw::launch_pair_tf_from_f(h->zdF, (int64_t)v.nb * cb, pp, M, h->st), "pair elements from F");
     return GW_OK;
 }
@@ -622,15 +648,7 @@ gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *
             (st = grow(h, (void **)&h->ovE[b], &h->ovEcap[b], sizeof(int) * (size_t)ng, "exponent buffer")) ||
             (st = grow(h, &h->ovJ[b], &h->ovJcap[b], sizeof(gw::OzJob) * 256, "job table")))
             return st;
-    if (!h->ov_st) {
-        int lo = 0, hi = 0;
-        CK(h, cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
-        CK(h, cudaStreamCreateWithPriority(&h->ov_st, cudaStreamNonBlocking, hi), "contraction stream");
-        for (int b = 0; b < 2; ++b) {
-            CK(h, cudaEventCreateWithFlags(&h->ov_split[b], cudaEventDisableTiming), "event");
-            CK(h, cudaEventCreateWithFlags(&h->ov_gemm[b], cudaEventDisableTiming), "event");
-        }
-    }
+    if ((st = ensure_overlap_stream(h))) return st;
     const int bn = h->tuned_bn;
     gw::PairPlan pp = pair_plan(h, sp);
     bool used[2] = {false, false};
@@ -770,6 +788,7 @@ int gw_chi0_streams(gw_chi0 *h, int iq)
     if (!h) return -(int)GW_ERR_ARG;
     gw_status s = check_slot(h, iq);
     if (s) return -(int)s;
+    if (zd_route(h, iq, h->keep_m)) return 1; // the tensor-core stage (a) leaves no room beside it
     return overlap_enabled(h, pair_plan(h, h->sph[iq])) ? 2 : 1;
 }
 
@@ -1047,6 +1066,28 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
     return GW_OK;
 }
 
+gw_status gw_chi0_pair_elements_block(gw_chi0 *h, int iq, int c0, int cb, double *M)
+{
+    if (!h) return GW_ERR_ARG;
+    gw_status s = check_slot(h, iq);
+    if (s) return s;
+    if (c0 < 0 || cb < 0 || c0 + cb > h->cond.nb)
+        return fail(h, GW_ERR_ARG, "conduction block [%d, %d) outside [0, %d)", c0, c0 + cb, h->cond.nb);
+    if (cb && !M) return fail(h, GW_ERR_ARG, "null M");
+    if (!zd_route(h, iq, h->keep_m)) return fail(h, GW_ERR_UNSUPPORTED, "slot %d does not take the tensor-core route", iq);
+    if (cb == 0) return GW_OK;
+    const int nv = h->val[iq].nb, cbmax = zd_chunk_bands(h, iq);
+    CUtensorMap tmA, tmC;
+    if ((s = zd_prepare(h, iq, &tmA, &tmC))) return s;
+    const gw::PairPlan pp = pair_plan(h, h->sph[iq]);
+    const int ng = h->sph[iq].ng;
+    for (int b0 = 0; b0 < cb; b0 += cbmax) {
+        const int n = std::min(cbmax, cb - b0);
+        if ((s = zd_stage_a(h, iq, tmA, tmC, c0 + b0, n, pp, (double2 *)M + (int64_t)b0 * nv * ng))) return s;
+    }
+    return GW_OK;
+}
+
 gw_status gw_chi0_pair_elements(gw_chi0 *h, int iq, int64_t pair_begin, int64_t pair_count, double *M)
 {
     if (!h) return GW_ERR_ARG;
@@ -1113,12 +1154,12 @@ gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, const doubl
             const int nv = v.nb, cb = zd_chunk_bands(h, iq[i]);
             s = ensure_work(h, (size_t)nv * cb * ng, (size_t)nv * cb * nw);
             if (s) return s;
-            CUtensorMap tmA;
-            if ((s = zd_prepare(h, iq[i], &tmA))) return s;
+            CUtensorMap tmA, tmC;
+            if ((s = zd_prepare(h, iq[i], &tmA, &tmC))) return s;
             for (int c0 = 0; c0 < h->cond.nb; c0 += cb) {
                 const int cbc = std::min(cb, h->cond.nb - c0);
                 const int64_t cnt = (int64_t)nv * cbc;
-                if ((s = zd_stage_a(h, iq[i], tmA, c0, cbc, pp, h->Mbuf))) return s;
+                if ((s = zd_stage_a(h, iq[i], tmA, tmC, c0, cbc, pp, h->Mbuf))) return s;
                 {
                     Scope sc(h, "delta");
                     CK(h, gw::launch_delta_block(v.energy, h->cond.energy, nv, c0, cbc, om, h->dbuf, h->st), "delta");

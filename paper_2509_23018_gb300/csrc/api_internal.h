@@ -254,9 +254,11 @@ gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *
 // conduction bands per chunk, the valence slices (once per call), and one chunk's pair
 // elements M[cl nv + v] for the conduction bands c0 .. c0 + cb - 1.
 bool zd_route(gw_chi0 *h, int iq, bool resident);
+gw_status ensure_overlap_stream(gw_chi0 *h);
 int zd_chunk_bands(gw_chi0 *h, int iq);
-gw_status zd_prepare(gw_chi0 *h, int iq, CUtensorMap *tmA);
-gw_status zd_stage_a(gw_chi0 *h, int iq, const CUtensorMap &tmA, int c0, int cb, const gw::PairPlan &pp, double2 *M);
+gw_status zd_prepare(gw_chi0 *h, int iq, CUtensorMap *tmA, CUtensorMap *tmC);
+gw_status zd_stage_a(gw_chi0 *h, int iq, const CUtensorMap &tmA, const CUtensorMap &tmC, int c0, int cb,
+                     const gw::PairPlan &pp, double2 *M);
 bool overlap_enabled(gw_chi0 *h, const gw::PairPlan &pp);
 
 // batched path (api_batch.cu)

@@ -62,12 +62,14 @@ constexpr int kZdSlices = 6; // BF16 slices per operand (balanced base-256 digit
 cudaError_t launch_zd_aslices(const void *psiv, int nv, int n, uint16_t *A, cudaStream_t st);
 bool zd_supported(int n, int K2, int nv);
 int zd_conduction_per_tile(int K2);
-size_t zd_smem_bytes();
+size_t zd_smem_bytes(int n, int K2);
 // F[l][cl nv + v][q] (two-float) = sum_i2 conj(psi_v[l][i2]) W^{kz[q] i2} psi_c[l][i2] for the
 // conduction bands c = c0 + cl, cl < cb; tmA maps the valence slices (box {32, 128, 1, 6},
 // 64-byte swizzle)
-cudaError_t launch_zd_gemm(const CUtensorMap &tmA, const void *psic, const int *kz, const float4 *twf, int n, int nv,
-                           int c0, int cb, int K2, float4 *F, int *status, cudaStream_t st);
+// tmC maps the conduction grids as FP32 [nc][n^2 lines][4n], box {4n, 1, zd_conduction_per_tile(K2)}
+cudaError_t launch_zd_gemm(const CUtensorMap &tmA, const CUtensorMap &tmC, const void *psic, const int *kz,
+                           const float4 *twf, int n, int nv, int c0, int cb, int K2, float4 *F, int *status,
+                           cudaStream_t st);
 // M[r][g] of the chunk's R pairs from F (middle and first axis of the pair transform)
 cudaError_t launch_pair_tf_from_f(const float4 *F, int64_t R, const PairPlan &pp, double2 *M, cudaStream_t st);
 // delta[w][cl nv + v] = 4x/(x^2 + w^2), x = ev[v] - ec[c0 + cl], the row order of the chunks above

@@ -285,25 +285,35 @@ inline bool pair_tf_ct_fits(const PairPlan &pp)
 }
 
 // The middle and first axes of the pair transform from the last-axis output F of the tensor-core
-// stage (zdft.cu): one block per pair row r of the chunk.  Per i0 slab the block loads
-// F[i0 N + i1][r][q] (the K2 kept last-axis frequencies of every line of the slab) into C,
-// transforms the columns along i1 and stores the K12 cells in its scratch slot; phase 2 is
-// that of pair_kernel_tf_ct.  The next slab's F is loaded into registers while the current
-// one is transformed.
+// stage (zdft.cu): one block per pair row r of the chunk.  The slabs go in pairs: the block
+// transforms the 2 K2 columns of slabs i0 and i0 + 1 (F[i0 N + i1][r][q], the kept last-axis
+// frequencies of every line) along i1 at once, two butterflies per thread per stage, and stores
+// the K12 cells of each slab in its scratch slot.  Two buffers alternate: the i1 stages run X -> Y
+// -> X, after which Y is free and receives the next pair of slabs (cp.async) while the pruned
+// stage reads X; the next step starts from Y.  Phase 2 is that of pair_kernel_tf_ct.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int N>
 __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
     pair_kernel_tf_from_f(const float4 *__restrict__ F, int64_t R, PairPlan pp, TfConsts kc, tf inv_nr,
                           double2 *__restrict__ M)
 {
+    static_assert(N % 2 == 0, "slabs go in pairs");
+    static_assert(make_prune_plan(N).nst == 3, "two full i1 stages: the result returns to the input buffer");
     constexpr int NT = pair_threads<N>();
     constexpr int CS = N + 1;
-    constexpr int NPF = 6; // F entries per thread and slab held in flight (K2 N <= NT NPF)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int slot_s;
     const int K2 = pp.K2, K12 = pp.K12;
-    const int sizeAB = K2 * CS > 31 * CS ? K2 * CS : 31 * CS;
-    float4 *A = (float4 *)smem, *C = A + sizeAB;
-    float4 *tw = C + K2 * CS;
+    const int ncols = 2 * K2;                  // columns of a slab pair
+    float4 *Xb = (float4 *)smem;               // [2][ncols][CS]
+    float4 *tw = Xb + 2 * ncols * CS;
     int *cell = (int *)(tw + N);
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = pp.ax[0].twf[i];
     for (int i = threadIdx.x; i < K12; i += NT) cell[i] = pp.cell[i];
@@ -327,42 +337,33 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
     }
     float4 *S = pp.scr + (size_t)slot * N * K12;
     const int64_t row = blockIdx.x;
-    const int nld = N * K2; // entries of F per slab
-    float4 buf[NPF];
-    auto load = [&](int i0) {
-#pragma unroll
-        for (int u = 0; u < NPF; ++u) {
-            const int e = threadIdx.x + u * NT;
-            if (e < nld) {
-                const int i1 = e / K2, q = e - i1 * K2;
-                buf[u] = F[(((int64_t)i0 * N + i1) * R + row) * K2 + q];
-            }
+    const int nld = 2 * N * K2; // F entries of a slab pair
+    auto fetch = [&](int i0, float4 *C) {
+        for (int e = threadIdx.x; e < nld; e += NT) {
+            const int sl = e / (N * K2), rem = e - sl * (N * K2);
+            const int i1 = rem / K2, q = rem - i1 * K2;
+            cp_async16(C + (sl * K2 + q) * CS + i1, F + (((int64_t)(i0 + sl) * N + i1) * R + row) * K2 + q);
         }
+        cp_async_commit();
     };
-    load(0);
-    for (int i0 = 0; i0 < N; ++i0) {
-#pragma unroll
-        for (int u = 0; u < NPF; ++u) {
-            const int e = threadIdx.x + u * NT;
-            if (e < nld) {
-                const int i1 = e / K2, q = e - i1 * K2;
-                C[q * CS + i1] = buf[u];
-            }
+    fetch(0, Xb);
+    for (int i0 = 0, b = 0; i0 < N; i0 += 2, b ^= 1) {
+        float4 *X = Xb + b * ncols * CS, *Y = Xb + (b ^ 1) * ncols * CS;
+        cp_async_wait_all();
+        __syncthreads(); // X complete
+        const float4 *y1 = tstages_ct<N, 0, 1, true>(X, Y, ncols, CS, tw, kc, 1); // ends in X, then a barrier
+        if (i0 + 2 < N) fetch(i0 + 2, Y);
+        for (int d = threadIdx.x; d < 2 * K12; d += NT) {
+            const int sl = d >= K12, dd = d - sl * K12;
+            const int cl = cell[dd];
+            tc_store(S + (size_t)(i0 + sl) * K12 + dd, tprune_ct<N>(y1 + (sl * K2 + (cl >> 8)) * CS, cl & 255, tw));
         }
-        __syncthreads(); // C complete
-        if (i0 + 1 < N) load(i0 + 1);
-        const float4 *y1 = tstages_ct<N, 0, 1, true>(C, A, K2, CS, tw, kc, 1);
-        float4 *Si = S + (size_t)i0 * K12;
-        for (int d = threadIdx.x; d < K12; d += NT) {
-            const int cl = cell[d];
-            tc_store(Si + d, tprune_ct<N>(y1 + (cl >> 8) * CS, cl & 255, tw));
-        }
-        __syncthreads(); // i1 done with C and A
+        __syncthreads(); // X read before the next step's first stage writes it
     }
 
-    // Phase 2 (as in pair_kernel_tf_ct)
-    const int NB = (sizeAB + K2 * CS) / (2 * CS);
-    float4 *X = A, *Y = A + NB * CS;
+    // Phase 2 (as in pair_kernel_tf_ct) in the two buffers
+    const int NB = ncols;
+    float4 *X = Xb, *Y = Xb + NB * CS;
     double2 *out = M + row * pp.ng;
     for (int d0 = 0; d0 < K12; d0 += NB) {
         const int nbat = K12 - d0 < NB ? K12 - d0 : NB;
@@ -389,16 +390,14 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
 template <int N>
 inline size_t pair_tf_from_f_smem(const PairPlan &pp)
 {
-    const size_t cs = N + 1;
-    const size_t ab = (size_t)pp.K2 * cs > 31 * cs ? (size_t)pp.K2 * cs : 31 * cs;
-    return sizeof(float4) * (ab + (size_t)pp.K2 * cs + N) + sizeof(int) * (size_t)pp.K12;
+    const size_t cs = N + 1, ncols = 2 * (size_t)pp.K2;
+    return sizeof(float4) * (2 * ncols * cs + N) + sizeof(int) * (size_t)pp.K12;
 }
 
 template <int N>
 inline cudaError_t launch_pair_tf_from_f_cube(const float4 *F, int64_t R, const PairPlan &pp, const TfConsts &kc,
                                              tf inv_nr, double2 *M, cudaStream_t st)
 {
-    if ((int64_t)N * pp.K2 > (int64_t)pair_threads<N>() * 6) return cudaErrorInvalidValue;
     const size_t sm = pair_tf_from_f_smem<N>(pp);
     cudaError_t e =
         cudaFuncSetAttribute(pair_kernel_tf_from_f<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -65,6 +65,33 @@ __device__ __forceinline__ void zd_digits(float h, float l, int E, uint16_t out[
     }
 }
 
+// The same digits with the line's scale sc = 2^(47 - E) and the slice weights w[i] = 2^(E - 7 - 8i)
+// precomputed (-70 <= E <= 60, so that both stay normal FP32 numbers).
+__device__ __forceinline__ void zd_digits_w(float h, float l, float sc, const float w[kZdSlices],
+                                            uint16_t out[kZdSlices])
+{
+    const float Y = __fmul_rn(h, sc), L = __fmul_rn(l, sc);
+    const float T = rintf(__fmul_rn(Y, 0x1p-24f));
+    float U = __fadd_rn(rintf(__fmaf_rn(-0x1p24f, T, Y)), rintf(L));
+    float d[kZdSlices];
+#pragma unroll
+    for (int i = kZdSlices - 1; i >= 3; --i) {
+        const float q = rintf(__fmul_rn(U, 0.00390625f));
+        d[i] = __fmaf_rn(-256.0f, q, U);
+        U = q;
+    }
+    float V = __fadd_rn(T, U);
+#pragma unroll
+    for (int i = 2; i >= 1; --i) {
+        const float q = rintf(__fmul_rn(V, 0.00390625f));
+        d[i] = __fmaf_rn(-256.0f, q, V);
+        V = q;
+    }
+    d[0] = V;
+#pragma unroll
+    for (int i = 0; i < kZdSlices; ++i) out[i] = (uint16_t)(__float_as_uint(__fmul_rn(d[i], w[i])) >> 16);
+}
+
 // exponent E with |x| < 2^E for a line's largest component magnitude m (E = -126 for m = 0)
 __device__ __forceinline__ int zd_expo(float m)
 {
@@ -110,6 +137,12 @@ cudaError_t launch_zd_aslices(const void *psiv, int nv, int n, uint16_t *A, cuda
     return cudaGetLastError();
 }
 
+__host__ __device__ __forceinline__ int zd_conduction_per_tile_d(int K2)
+{
+    const int ct = 64 / (2 * K2);
+    return ct < 4 ? ct : 4;
+}
+
 // ------------------------------------------------------------------ the product
 // One block per SM, persistent over units u = (line l, row tile mt); per unit the block keeps
 // the valence slices of its 128 rows resident (three K-chunks of 32 real entries, TMA) and
@@ -117,6 +150,8 @@ cudaError_t launch_zd_aslices(const void *psiv, int nv, int n, uint16_t *A, cuda
 // 64 columns): producer warps form the tile's column slices per K-chunk into a 2-deep ring,
 // one thread issues the tcgen05 products into four accumulators (two buffers of 4 x 64 TMEM
 // columns alternate between tiles), and the epilogue warps sum the accumulators into F.
+// (128-column tiles with one accumulator buffer, 16-entry column stages and a 32-byte swizzle
+// measured slower: 3.02 against 2.86 ms per 48^3 chunk, the epilogue no longer hidden.)
 //  warp 0: TMA; warp 1: MMA (and TMEM); warps 2..5: epilogue (TMEM lane quadrant warp % 4);
 //  warps 6..11: producers.
 constexpr int kZdN = 64;                               // columns per tile
@@ -160,9 +195,11 @@ __device__ __forceinline__ float zd_2sum(float a, float b, float &e)
     return s;
 }
 
+constexpr int kZdPsiSlots = 4; // ring of conduction-band line tiles
+
 struct ZdArgs {
     CUtensorMap tmA;        // A slices [6][lines][nv][2N] bf16, box {32, 128, 1, 6}, 64-byte swizzle
-    const float4 *psic;     // conduction band grids (two-float), [nc][N^3]
+    CUtensorMap tmC;        // conduction grids as FP32 [nc][lines][4N], box {4N, 1, CT}
     const int *kz;          // [K2] kept last-axis frequencies
     float4 *F;              // [lines][R][K2] two-float, R = rows of the chunk = nv * cb, r = cl * nv + v
     int *status;
@@ -176,16 +213,28 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = sm;                               // 3 K-chunks x 48 KB
     unsigned char *sB = sA + 3 * kZdAChunk;               // 2 stages x 24 KB
-    float4 *tw = (float4 *)(sB + 2 * kZdBStage);          // [N] twiddles e^{+2 pi i t / N}
-    int *kzs = (int *)(tw + a.n);                         // [K2]
-    uint64_t *bar = (uint64_t *)(((uintptr_t)(kzs + 64) + 7) & ~(uintptr_t)7);
+    float4 *ring = (float4 *)(sB + 2 * kZdBStage);        // [slots][4][N] conduction line tiles
+    float4 *wt = ring + kZdPsiSlots * 4 * a.n;            // [K2][N] twiddles W^{kz[q] i2}
+    uint64_t *bar = (uint64_t *)(wt + a.K2 * a.n);
     uint64_t *aFull = bar, *aEmpty = bar + 1, *bFull = bar + 2, *bEmpty = bar + 4, *tFull = bar + 6,
-             *tEmpty = bar + 8, *fin = bar + 10;
-    uint32_t *tslot = (uint32_t *)(bar + 11);
+             *tEmpty = bar + 8, *fin = bar + 10, *pFull = bar + 11, *pEmpty = pFull + kZdPsiSlots;
+    uint32_t *tslot = (uint32_t *)(pEmpty + kZdPsiSlots);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < a.n; i += blockDim.x) tw[i] = twf[i];
-    for (int i = threadIdx.x; i < a.K2; i += blockDim.x) kzs[i] = a.kz[i];
+    for (int i = threadIdx.x; i < a.K2 * a.n; i += blockDim.x) {
+        const int q = i / a.n, i2 = i - q * a.n;
+        wt[i] = twf[(a.kz[q] * i2) % a.n];
+    }
+    {
+        // the padding columns of both stages stay zero (their products never reach F)
+        const int ncol = 2 * a.K2, npad = kZdN - zd_conduction_per_tile_d(a.K2) * ncol;
+        for (int e = threadIdx.x; e < 2 * kZdSlices * npad * (kZdKC / 2); e += blockDim.x) {
+            const int st = e / (kZdSlices * npad * (kZdKC / 2)), r1 = e % (kZdSlices * npad * (kZdKC / 2));
+            const int sl = r1 / (npad * (kZdKC / 2)), r2 = r1 % (npad * (kZdKC / 2));
+            const int col = kZdN - npad + r2 / (kZdKC / 2), k = 2 * (r2 % (kZdKC / 2));
+            *(uint32_t *)(sB + st * kZdBStage + sl * kZdBSlice + sw64_off(col, k)) = 0u;
+        }
+    }
     if (threadIdx.x == 0) {
         bar_init(aFull, 1);
         bar_init(aEmpty, 1);
@@ -196,6 +245,10 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
             bar_init(&tEmpty[i], 128);
         }
         bar_init(fin, 1);
+        for (int i = 0; i < kZdPsiSlots; ++i) {
+            bar_init(&pFull[i], 1);
+            bar_init(&pEmpty[i], kZdProducers);
+        }
         bar_fence_init();
     }
     if (warp == 1) tmem_alloc(tslot, 512);
@@ -210,15 +263,24 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     if (warp == 0) {
         // ---- TMA: the unit's valence slices, once the previous unit's products are done
         if (lane == 0) {
-            uint32_t u = 0;
+            uint32_t u = 0, tile = 0;
+            const unsigned pbytes = (unsigned)a.CT * a.n * 16; // CT lines of N two-float points
             for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x, ++u) {
                 const int l = unit / a.nmt, mt = unit - l * a.nmt;
                 if (!bar_wait(aEmpty, (u & 1) ^ 1)) { ok = false; break; }
                 bar_expect(aFull, 3 * kZdAChunk);
                 for (int kc = 0; kc < 3; ++kc) tma4(sA + kc * kZdAChunk, &a.tmA, aFull, kc * kZdKC, mt * 128, l, 0);
+                for (int ct = 0; ct < nct && ok; ++ct, ++tile) {
+                    const uint32_t ps = tile % kZdPsiSlots, pn = tile / kZdPsiSlots;
+                    if (!bar_wait(&pEmpty[ps], (pn & 1) ^ 1)) { ok = false; break; }
+                    bar_expect(&pFull[ps], pbytes);
+                    tma3(ring + ps * 4 * a.n, &a.tmC, &pFull[ps], 0, l, a.c0 + ct * a.CT);
+                }
             }
-            // the last load has landed before the block may leave
+            // every load has landed before the block may leave
             if (u > 0 && ok && !bar_wait(aFull, (u - 1) & 1)) ok = false;
+            for (uint32_t t = tile > kZdPsiSlots ? tile - kZdPsiSlots : 0; t < tile && ok; ++t)
+                if (!bar_wait(&pFull[t % kZdPsiSlots], (t / kZdPsiSlots) & 1)) ok = false;
             if (!ok) atomicOr(a.status, kStatusTimeout);
         }
     } else if (warp == 1) {
@@ -310,63 +372,68 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
         }
         if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
     } else {
-        // ---- producers: column slices of the conduction tile, K-chunk by K-chunk
-        const int pt = threadIdx.x - 6 * 32; // 0 .. 191
-        uint32_t it = 0;
+        // ---- producers: column slices of the conduction tile, K-chunk by K-chunk.  A lane owns
+        // the points (cl, i2 = 16 kc + k2) of one or two (cl, k2) combinations, loaded once per
+        // tile for the three K-chunks; producer warp pw forms the frequencies q = pw, pw + 6, ...
+        const int pw = warp - 6;
+        const int ncomb = a.CT * 16; // (cl, k2) combinations, at most 64
+        uint32_t it = 0, tile = 0;
         for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x) {
-            const int l = unit / a.nmt;
-            for (int ct = 0; ct < nct && ok; ++ct) {
-                // column exponents of the tile's bands: |Re b|, |Im b| <= |psi_c| on the line
-                int Ec[4] = {-126, -126, -126, -126};
-                for (int cl = 0; cl < a.CT; ++cl) {
-                    const int c = ct * a.CT + cl;
+            for (int ct = 0; ct < nct && ok; ++ct, ++tile) {
+                // the tile's conduction lines, staged by the TMA warp
+                const uint32_t ps = tile % kZdPsiSlots, pn = tile / kZdPsiSlots;
+                const bool pgot = bar_wait(&pFull[ps], pn & 1);
+                if (!__all_sync(0xffffffffu, pgot)) { ok = false; break; }
+                const float4 *pl = ring + ps * 4 * a.n;
+                float4 x[2][3];
+                float sc[2], w[2][kZdSlices];
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int comb = lane + 32 * h2;
+                    const int cl = comb >> 4, k2 = comb & 15, c = ct * a.CT + cl;
                     float m = 0.0f;
-                    if (c < a.cb) {
-                        const float4 *row = a.psic + ((int64_t)(a.c0 + c) * a.n * a.n + l) * a.n;
-                        for (int i = lane; i < a.n; i += 32) {
-                            const float4 x = row[i];
-                            m = fmaxf(m, (fabsf(x.x) + fabsf(x.z)) * (1.0f + 0x1p-20f));
-                        }
+#pragma unroll
+                    for (int kc = 0; kc < 3; ++kc) {
+                        x[h2][kc] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (comb < ncomb && c < a.cb) x[h2][kc] = pl[cl * a.n + kc * 16 + k2];
+                        m = fmaxf(m, (fabsf(x[h2][kc].x) + fabsf(x[h2][kc].z)) * (1.0f + 0x1p-20f));
                     }
-                    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                    Ec[cl] = zd_expo(m);
+                    // the 16 lanes of one band hold its whole line: the band's maximum
+                    for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    const int E = max(-70, zd_expo(m)); // keeps the scale and every weight normal
+                    sc[h2] = __int_as_float((127 + 47 - E) << 23);
+#pragma unroll
+                    for (int i = 0; i < kZdSlices; ++i) w[h2][i] = __int_as_float((127 + E - 7 - 8 * i) << 23);
                 }
-                for (int kc = 0; kc < 3 && ok; ++kc, ++it) {
+                __syncwarp();
+                if (lane == 0) bar_arrive(&pEmpty[ps]); // the slot's values are in registers
+#pragma unroll
+                for (int kc = 0; kc < 3; ++kc, ++it) {
+                    if (!ok) continue;
                     const uint32_t st = it & 1;
                     const bool got = bar_wait(&bEmpty[st], ((it >> 1) & 1) ^ 1);
-                    if (!__all_sync(0xffffffffu, got)) { ok = false; break; } // warp-uniform exit
+                    if (!__all_sync(0xffffffffu, got)) { ok = false; continue; } // warp-uniform exit
                     unsigned char *B = sB + st * kZdBStage;
-                    // zero the padding columns (their products never reach F, but must be finite)
-                    for (int e = pt; e < (kZdN - a.CT * ncol) * (kZdKC / 2) * kZdSlices; e += kZdProducers * 32) {
-                        const int s = e / ((kZdN - a.CT * ncol) * (kZdKC / 2)), rem = e % ((kZdN - a.CT * ncol) * (kZdKC / 2));
-                        const int col = a.CT * ncol + rem / (kZdKC / 2), k = 2 * (rem % (kZdKC / 2));
-                        *(uint32_t *)(B + s * kZdBSlice + sw64_off(col, k)) = 0u;
-                    }
-                    // items (cl, q, k2): b = W^{kz[q] i2} psi_c[l][i2], i2 = 16 kc + k2
-                    const int nitem = a.CT * a.K2 * 16;
-                    for (int w = pt; w < nitem; w += kZdProducers * 32) {
-                        const int k2 = w & 15, rest = w >> 4;
-                        const int q = rest % a.K2, cl = rest / a.K2;
-                        const int c = ct * a.CT + cl;
-                        const int i2 = kc * 16 + k2;
-                        uint16_t dr[kZdSlices], di[kZdSlices];
-                        if (c < a.cb) {
-                            const tcx x = tc_load(a.psic + ((int64_t)(a.c0 + c) * a.n * a.n + l) * a.n + i2);
-                            const int e = (kzs[q] * i2) % a.n;
-                            const tcx b = tc_mul(x, tc_load(tw + e));
-                            zd_digits(b.re.hi, b.re.lo, Ec[cl], dr);
-                            zd_digits(b.im.hi, b.im.lo, Ec[cl], di);
-                        } else {
 #pragma unroll
-                            for (int s = 0; s < kZdSlices; ++s) dr[s] = di[s] = 0;
-                        }
-                        const int colr = cl * ncol + 2 * q, k = 2 * k2;
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int comb = lane + 32 * h2;
+                        if (comb >= ncomb) continue;
+                        const int cl = comb >> 4, k2 = comb & 15;
+                        const tcx xv = {{x[h2][kc].x, x[h2][kc].y}, {x[h2][kc].z, x[h2][kc].w}};
+                        const float4 *wrow = wt + kc * 16 + k2;
+                        for (int q = pw; q < a.K2; q += kZdProducers) {
+                            const tcx b = tc_mul(xv, tc_load(wrow + q * a.n));
+                            uint16_t dr[kZdSlices], di[kZdSlices];
+                            zd_digits_w(b.re.hi, b.re.lo, sc[h2], w[h2], dr);
+                            zd_digits_w(b.im.hi, b.im.lo, sc[h2], w[h2], di);
+                            const int colr = cl * ncol + 2 * q;
+                            unsigned char *pr = B + sw64_off(colr, 2 * k2), *pi = B + sw64_off(colr + 1, 2 * k2);
 #pragma unroll
-                        for (int s = 0; s < kZdSlices; ++s) {
-                            // Re column: (Re b, Im b); Im column: (Im b, -Re b)
-                            *(uint32_t *)(B + s * kZdBSlice + sw64_off(colr, k)) = (uint32_t)dr[s] | ((uint32_t)di[s] << 16);
-                            *(uint32_t *)(B + s * kZdBSlice + sw64_off(colr + 1, k)) =
-                                (uint32_t)di[s] | ((uint32_t)(dr[s] ^ 0x8000u) << 16);
+                            for (int sl = 0; sl < kZdSlices; ++sl) {
+                                // Re column: (Re b, Im b); Im column: (Im b, -Re b)
+                                *(uint32_t *)(pr + sl * kZdBSlice) = (uint32_t)dr[sl] | ((uint32_t)di[sl] << 16);
+                                *(uint32_t *)(pi + sl * kZdBSlice) = (uint32_t)di[sl] | ((uint32_t)(dr[sl] ^ 0x8000u) << 16);
+                            }
                         }
                     }
                     fence_async_shared();
@@ -383,21 +450,25 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     if (warp == 1) tmem_dealloc(tbase, 512);
 }
 
-size_t zd_smem_bytes() { return 1024 + 3 * kZdAChunk + 2 * kZdBStage + 16 * 128 + 64 * 4 + 16 * 8 + 64; }
+size_t zd_smem_bytes(int n, int K2)
+{
+    return 1024 + 3 * kZdAChunk + 2 * kZdBStage + 16 * (size_t)kZdPsiSlots * 4 * n + 16 * (size_t)K2 * n + 8 * 24 + 64;
+}
 
 bool zd_supported(int n, int K2, int nv)
 {
     return n == 48 && K2 >= 1 && 2 * K2 <= kZdN && nv >= 1 && 2 * n == 3 * kZdKC;
 }
 
-int zd_conduction_per_tile(int K2) { return std::min(4, kZdN / (2 * K2)); }
+int zd_conduction_per_tile(int K2) { return zd_conduction_per_tile_d(K2); }
 
-cudaError_t launch_zd_gemm(const CUtensorMap &tmA, const void *psic, const int *kz, const float4 *twf, int n, int nv,
-                           int c0, int cb, int K2, float4 *F, int *status, cudaStream_t st)
+cudaError_t launch_zd_gemm(const CUtensorMap &tmA, const CUtensorMap &tmC, const void *, const int *kz,
+                           const float4 *twf, int n, int nv, int c0, int cb, int K2, float4 *F, int *status,
+                           cudaStream_t st)
 {
     ZdArgs a;
     a.tmA = tmA;
-    a.psic = (const float4 *)psic;
+    a.tmC = tmC;
     a.kz = kz;
     a.F = F;
     a.status = status;
@@ -409,7 +480,7 @@ cudaError_t launch_zd_gemm(const CUtensorMap &tmA, const void *psic, const int *
     a.CT = zd_conduction_per_tile(K2);
     a.nmt = (nv + 127) / 128;
     a.nunits = n * n * a.nmt;
-    const size_t sm = zd_smem_bytes();
+    const size_t sm = zd_smem_bytes(n, K2);
     cudaError_t e = cudaFuncSetAttribute(zd_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
