@@ -276,13 +276,22 @@ def reference_arm(args):
 TRAFFIC = {
     "contract_f64": {"bytes_per_launch": 1.941011e9 + 0.034306e9,
                      "source": "ncu dram__bytes_read+write, contract_f64_kernel, p1_48cube_onechunk"},
+    # the FFT route of stage (a) (fp64 and pre-tensor-core paths): taken before the tensor-core
+    # route existed; the kernel is unchanged since
     "pair_mtxel": {"bytes_per_launch": 3.112e9 + 1.486e9,
                    "source": "ncu dram__bytes_read+write, pair_kernel_tf_ct<48>, p1_48cube_onechunk"},
-    # the overlapped step's launch (2-deep TMA ring, on the second stream); the single-stream
-    # launch (4-deep ring) has no capture of the kernel as it stands
-    "ozaki_gemm": {"bytes_per_launch": 8.033695e9 + 0.220375e9,
-                   "source": "ncu dram__bytes_read+write, oz_gemm_kernel (s = 7, 2-deep ring), p1_48cube_onechunk"},
-    "ozaki_gemm_single_stream": {"bytes_per_launch": None, "source": None},
+    # the tensor-core route of the 48^3 workload: one 8192-pair chunk (128 valence x 64
+    # conduction bands), the launch shape the bench's step repeats 16 times
+    "zdft": {"bytes_per_launch": 0.489212e9 + 4.488817e9,
+             "source": "ncu dram__bytes_read+write, zd_gemm_kernel, p2_48cube_chunk"},
+    "pair_from_f": {"bytes_per_launch": 5.626491e9 + 1.483600e9,
+                    "source": "ncu dram__bytes_read+write, pair_kernel_tf_from_f<48>, p2_48cube_chunk"},
+    # the single-stream launch (4-deep TMA ring) the tensor-core route runs
+    "ozaki_gemm": {"bytes_per_launch": 7.620381e9 + 0.217023e9,
+                   "source": "ncu dram__bytes_read+write, oz_gemm_kernel<256,0,4> (s = 7), p2_48cube_chunk"},
+    "ozaki_gemm_single_stream": {"bytes_per_launch": 7.620381e9 + 0.217023e9,
+                                 "source": "ncu dram__bytes_read+write, oz_gemm_kernel<256,0,4> (s = 7), "
+                                           "p2_48cube_chunk"},
 }
 
 
@@ -291,7 +300,8 @@ TRAFFIC = {
 # filled by measure_peaks() at the start of a run; profiles/peaks_gb300.json (written by
 # `bench.py --peaks`) is the record of one such measurement and the fallback.
 PEAKS_JSON = os.path.join(ROOT, "profiles", "peaks_gb300.json")
-PROBE_KINDS = ["ffma", "ffma2", "fadd2", "dfma", "dmma_m8n8k4", "dmma_m16n8k16", "bf16_mma_sync", "int8_mma_sync"]
+PROBE_KINDS = ["ffma", "ffma2", "fadd2", "dfma", "dmma_m8n8k4", "dmma_m16n8k16", "bf16_mma_sync", "int8_mma_sync",
+               "tcgen05_n64", "tcgen05_n128", "tcgen05_n256"]
 LIVE_PEAKS = {}
 
 

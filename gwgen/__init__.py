@@ -117,6 +117,9 @@ CONFIGS = {
     "c5_adjoint": Config("c5_adjoint", (40, 40, 40), 96, 768, 4500, 1500, index=4),
     # one 8192-pair chunk of the 48^3 workload: the small case kernel profiles are taken on
     "p1_48cube_onechunk": Config("p1_48cube_onechunk", (48, 48, 48), 8, 1024, 6000, 2000, index=1),
+    # one 8192-pair chunk of the 48^3 workload as the tensor-core stage (a) forms it (all 128
+    # valence bands x 64 conduction bands): the small case its kernel profiles are taken on
+    "p2_48cube_chunk": Config("p2_48cube_chunk", (48, 48, 48), 128, 64, 6000, 2000, index=1),
     # one 8192-pair chunk of the 72^3 workload (slice-count sweep)
     "p3_72cube_onechunk": Config("p3_72cube_onechunk", (72, 72, 72), 4, 2048, 20000, 6000, index=2),
 }

@@ -399,7 +399,10 @@ typedef enum {
     GW_PROBE_DMMA_M8N8K4 = 4,    /* mma.sync m8n8k4 f64 */
     GW_PROBE_DMMA_M16N8K16 = 5,  /* mma.sync m16n8k16 f64 */
     GW_PROBE_BF16_MMA_SYNC = 6,  /* mma.sync m16n8k16 bf16 -> f32 (warp-level, not tcgen05) */
-    GW_PROBE_INT8_MMA_SYNC = 7   /* mma.sync m16n8k32 s8 -> s32 (warp-level, not tcgen05) */
+    GW_PROBE_INT8_MMA_SYNC = 7,  /* mma.sync m16n8k32 s8 -> s32 (warp-level, not tcgen05) */
+    GW_PROBE_TCGEN05_N64 = 8,    /* tcgen05.mma kind::f16 BF16 M=128 N=64 K=16 from shared memory */
+    GW_PROBE_TCGEN05_N128 = 9,   /* the same, N = 128 */
+    GW_PROBE_TCGEN05_N256 = 10   /* the same, N = 256 */
 } gw_probe_kind;
 GW_API gw_status gw_chi0_probe(int kind, long long iters, void *cuda_stream, float *sink, double *ops);
 

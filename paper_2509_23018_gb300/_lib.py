@@ -21,7 +21,7 @@ GW_PREC_FP64, GW_PREC_OZAKI_BF16 = 0, 1
 GW_MTXEL_FP64, GW_MTXEL_TWOFLOAT = 0, 1
 # gw_probe_kind
 PROBES = {"ffma": 0, "ffma2": 1, "fadd2": 2, "dfma": 3, "dmma_m8n8k4": 4, "dmma_m16n8k16": 5,
-          "bf16_mma_sync": 6, "int8_mma_sync": 7}
+          "bf16_mma_sync": 6, "int8_mma_sync": 7, "tcgen05_n64": 8, "tcgen05_n128": 9, "tcgen05_n256": 10}
 
 # Every entry point declared in include/gw_chi0.h, with its ctypes signature.
 P, I, I64, D, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
@@ -65,17 +65,21 @@ SIGNATURES = {
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if os.environ.get("GW_CHI0_DEBUG") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load libgwchi0.so; build it first if it is missing or stale and nvcc exists."""
+    """Load libgwchi0.so (the bounds-checked build with GW_CHI0_DEBUG=1); build it first if it is
+    missing or stale and nvcc exists."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
-        if build_if_missing and not _build.up_to_date():
+        path = library_path()
+        if os.environ.get("GW_CHI0_DEBUG") == "1":
+            if build_if_missing and not os.path.exists(path):
+                _build.build(debug=True)
+        elif build_if_missing and not _build.up_to_date():
             _build.build()
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")

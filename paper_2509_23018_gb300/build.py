@@ -12,6 +12,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgwchi0.so")
+# the bounds-checked build (-DGW_DEBUG): kernels check the indices they derive from the plans and
+# record a violation in the status word instead of accessing out of range
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libgwchi0_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
@@ -40,9 +44,15 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list | None = None, debug: bool = False) -> str:
+    if debug:
+        return _build_into(BUILD_DEBUG, LIB_DEBUG, verbose, (extra or []) + ["-DGW_DEBUG"])
     if not force and up_to_date():
         return LIB
+    return _build_into(BUILD, LIB, verbose, extra)
+
+
+def _build_into(BUILD, LIB, verbose, extra):
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     objs = []

@@ -969,52 +969,26 @@ gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec)
     s.g.resize((size_t)3 * ng);
     CK(h, cudaMemcpyAsync(s.g.data(), gvec, sizeof(int32_t) * 3 * ng, cudaMemcpyDeviceToHost, h->st), "copy sphere");
     CK(h, cudaStreamSynchronize(h->st), "set_gsphere sync");
-    std::vector<int> present(h->d.n[2], 0);
     for (int i = 0; i < ng; ++i)
         for (int a = 0; a < 3; ++a) {
             int g = s.g[3 * i + a];
             if (2 * std::abs(g) >= h->d.n[a]) return fail(h, GW_ERR_ARG, "G %d: component %d outside (-n/2, n/2)", i, g);
             s.maxabs[a] = std::max(s.maxabs[a], std::abs(g));
         }
-    for (int i = 0; i < ng; ++i) present[mod(s.g[3 * i + 2], h->d.n[2])] = 1;
-    std::vector<int> kz, pos(h->d.n[2], -1);
-    for (int k = 0; k < h->d.n[2]; ++k)
-        if (present[k]) {
-            pos[k] = (int)kz.size();
-            kz.push_back(k);
-        }
-    std::vector<int32_t> pack(ng);
-    for (int i = 0; i < ng; ++i) {
-        int k0 = mod(s.g[3 * i], h->d.n[0]), k1 = mod(s.g[3 * i + 1], h->d.n[1]);
-        int k2 = pos[mod(s.g[3 * i + 2], h->d.n[2])];
-        pack[i] = k0 | (k1 << 8) | (k2 << 16);
-    }
+    gw::SpherePlanHost plan;
+    gw::build_sphere_plan(h->d.n, ng, s.g.data(), plan);
     // alias check against whatever bands are already stored
     int ax;
     if (h->val[iq].nb && h->cond.nb && !alias_free(h, h->val[iq], h->cond, s, &ax))
         return fail(h, GW_ERR_ARG, "max|K_v| + max|K_c| + max|G| >= n on axis %d (aliasing)", ax);
-    s.K2 = (int)kz.size();
-    {
-        // group sphere points by their (k2 column, k1) cell
-        std::vector<std::pair<int, int>> key(ng);
-        for (int i = 0; i < ng; ++i) key[i] = {(pack[i] >> 16) * h->d.n[1] + ((pack[i] >> 8) & 255), i};
-        std::sort(key.begin(), key.end());
-        s.cg.resize(ng);
-        for (int i = 0; i < ng; ++i) {
-            if (i == 0 || key[i].first != key[i - 1].first) s.cstart.push_back(i);
-            s.cg[i] = key[i].second;
-        }
-        s.cstart.push_back(ng);
-    }
-    // cell table of the pruned i1 stage and the sphere points grouped by cell
-    s.K12 = (int)s.cstart.size() - 1;
-    std::vector<int32_t> cell(s.K12);
+    s.K2 = plan.K2;
+    s.K12 = plan.K12;
+    s.cstart = plan.cstart;
+    s.cg = plan.cg;
+    const std::vector<int> &kz = plan.kz;
+    const std::vector<int32_t> &pack = plan.pack, &cell = plan.cell;
     std::vector<int2> cpts(ng);
-    for (int d = 0; d < s.K12; ++d) {
-        const int i = s.cg[s.cstart[d]];
-        cell[d] = (pack[i] >> 16) << 8 | ((pack[i] >> 8) & 255);
-        for (int m = s.cstart[d]; m < s.cstart[d + 1]; ++m) cpts[m] = make_int2(s.cg[m], (pack[s.cg[m]] & 255) | d << 8);
-    }
+    for (int m = 0; m < ng; ++m) cpts[m] = make_int2(plan.cpts[m].first, plan.cpts[m].second);
     gw_status st;
     if (iq == h->Mres_iq) h->Mres_iq = -1; // resident pair elements no longer match
     Sphere &old = h->sph[iq];
@@ -1302,6 +1276,7 @@ gw_status gw_chi0_sync(gw_chi0 *h)
     CK(h, cudaMemset(h->status, 0, sizeof(int)), "status reset");
     if (st & gw::kStatusTimeout) return fail(h, GW_ERR_TIMEOUT, "a bounded device-side wait gave up");
     if (st & gw::kStatusNoSlot) return fail(h, GW_ERR_CUDA, "a pair block found no free scratch slot");
+    if (st & gw::kStatusBounds) return fail(h, GW_ERR_CUDA, "an index outside its buffer (bounds-checked build)");
     return GW_OK;
 }
 

@@ -5,6 +5,7 @@
 #pragma once
 #include "../../include/gw_chi0.h"
 #include "internal.h"
+#include "sphere_plan.h"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>

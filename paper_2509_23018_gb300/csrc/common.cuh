@@ -38,5 +38,21 @@ struct FftAxis {
 // Device-side status word bits (written by bounded waits that gave up).
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusNoSlot = 2; // a pair block found no free scratch slot
+constexpr int kStatusBounds = 4; // an index outside its buffer (bounds-checked build only)
+
+// Bounds checks of the bounds-checked build (compiled with -DGW_DEBUG, see build.py): an index
+// outside [0, n) records kStatusBounds in the status word and the access is skipped; in the
+// normal build the check compiles to true.
+#ifdef GW_DEBUG
+__device__ __forceinline__ bool gw_in_range(long long i, long long n, int *status)
+{
+    if (i >= 0 && i < n) return true;
+    if (status) atomicOr(status, kStatusBounds);
+    return false;
+}
+#define GW_IN(i, n, status) ::gw::gw_in_range((long long)(i), (long long)(n), (status))
+#else
+#define GW_IN(i, n, status) true
+#endif
 
 } // namespace gw

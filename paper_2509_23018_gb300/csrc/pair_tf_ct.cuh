@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         float4 *Si = S + (size_t)i0 * K12;
         for (int d = threadIdx.x; d < K12; d += NT) {
             const int cl = cell[d];
+            if (!GW_IN((cl >> 8), K2, pp.status)) continue;
             tc_store(Si + d, tprune_ct<N>(y1 + (cl >> 8) * CS, cl & 255, tw));
         }
         __syncthreads(); // i1 done with C and A
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         const int m1 = pp.cstart[d0 + nbat];
         for (int m = pp.cstart[d0] + threadIdx.x; m < m1; m += NT) {
             const int2 pt = pp.cpts[m]; // point index, k0 | cell << 8
+            if (!GW_IN(pt.x, pp.ng, pp.status) || !GW_IN((pt.y >> 8) - d0, nbat, pp.status)) continue;
             const tcx f = tprune_ct<N>(y0 + ((pt.y >> 8) - d0) * CS, pt.y & 255, tw);
             out[pt.x] = make_double2(tf_to_d(tf_mul(f.re, inv_nr)), tf_to_d(tf_mul(f.im, inv_nr)));
         }
@@ -342,7 +344,9 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         for (int e = threadIdx.x; e < nld; e += NT) {
             const int sl = e / (N * K2), rem = e - sl * (N * K2);
             const int i1 = rem / K2, q = rem - i1 * K2;
-            cp_async16(C + (sl * K2 + q) * CS + i1, F + (((int64_t)(i0 + sl) * N + i1) * R + row) * K2 + q);
+            const int64_t fi = (((int64_t)(i0 + sl) * N + i1) * R + row) * K2 + q;
+            if (!GW_IN(fi, (int64_t)N * N * R * K2, pp.status)) continue;
+            cp_async16(C + (sl * K2 + q) * CS + i1, F + fi);
         }
         cp_async_commit();
     };
@@ -356,6 +360,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         for (int d = threadIdx.x; d < 2 * K12; d += NT) {
             const int sl = d >= K12, dd = d - sl * K12;
             const int cl = cell[dd];
+            if (!GW_IN(cl >> 8, K2, pp.status)) continue;
             tc_store(S + (size_t)(i0 + sl) * K12 + dd, tprune_ct<N>(y1 + (sl * K2 + (cl >> 8)) * CS, cl & 255, tw));
         }
         __syncthreads(); // X read before the next step's first stage writes it
@@ -376,6 +381,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         const int m1 = pp.cstart[d0 + nbat];
         for (int m = pp.cstart[d0] + threadIdx.x; m < m1; m += NT) {
             const int2 pt = pp.cpts[m];
+            if (!GW_IN(pt.x, pp.ng, pp.status) || !GW_IN((pt.y >> 8) - d0, nbat, pp.status)) continue;
             const tcx f = tprune_ct<N>(y0 + ((pt.y >> 8) - d0) * CS, pt.y & 255, tw);
             out[pt.x] = make_double2(tf_to_d(tf_mul(f.re, inv_nr)), tf_to_d(tf_mul(f.im, inv_nr)));
         }

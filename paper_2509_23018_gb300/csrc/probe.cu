@@ -8,6 +8,7 @@
 // (an FMA counts as 2, a tensor instruction as 2 m n k).  These rates are the denominators
 // of the roofline fractions of the kernels that run on those pipes.
 #include "../../include/gw_chi0.h"
+#include "ptx.cuh"
 
 #include <cuda_runtime.h>
 
@@ -178,6 +179,54 @@ __global__ void __launch_bounds__(kThreads) probe_int8_mma(float *out, long long
     if (s == 123456789) out[threadIdx.x] = (float)s;
 }
 
+// tcgen05 BF16 products of one shape (M = 128, N = BN, K = 16) back to back from shared memory
+// into one TMEM accumulator: one block per SM, one thread issues, 4 K-steps of a 64-wide chunk
+// per iteration.  The operands are zero (the rate does not depend on the values).
+template <int BN>
+__global__ void __launch_bounds__(128, 1) probe_tcgen05(float *out, long long iters)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = sm, *sB = sm + 128 * 64 * 2;
+    __shared__ uint64_t done;
+    __shared__ uint32_t tslot;
+    for (int i = threadIdx.x; i < (128 + BN) * 64 * 2 / 16; i += blockDim.x) ((uint4 *)sm)[i] = make_uint4(0, 0, 0, 0);
+    if (threadIdx.x == 0) {
+        gw::bar_init(&done, 1);
+        gw::bar_fence_init();
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x < 32) gw::tmem_alloc(&tslot, BN < 32 ? 32 : BN);
+    gw::tc_fence_before();
+    __syncthreads();
+    gw::tc_fence_after();
+    const uint32_t d = tslot;
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    if (threadIdx.x == 0) {
+        const uint64_t ad = gw::sdesc_sw128(gw::su32(sA)), bd = gw::sdesc_sw128(gw::su32(sB));
+        for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) gw::umma_f16(d, ad + kk * 2, bd + kk * 2, idesc, (i | kk) ? 1u : 0u);
+        }
+        gw::umma_commit(&done);
+        if (!gw::bar_wait(&done, 0)) out[0] = 1.0f; // bounded: report instead of hanging
+    }
+    gw::tc_fence_before();
+    __syncthreads();
+    gw::tc_fence_after();
+    if (threadIdx.x < 32) gw::tmem_dealloc(d, BN < 32 ? 32 : BN);
+}
+
+template <int BN>
+static cudaError_t launch_probe_tcgen05(float *out, long long iters, int sms, cudaStream_t st)
+{
+    const size_t smem = 1024 + (size_t)(128 + BN) * 64 * 2;
+    cudaError_t e = cudaFuncSetAttribute(probe_tcgen05<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    probe_tcgen05<BN><<<sms, 128, smem, st>>>(out, iters);
+    return cudaGetLastError();
+}
+
 } // namespace
 
 extern "C" gw_status gw_chi0_probe(int kind, long long iters, void *cuda_stream, float *sink_buf, double *ops)
@@ -225,6 +274,17 @@ extern "C" gw_status gw_chi0_probe(int kind, long long iters, void *cuda_stream,
         probe_int8_mma<<<blocks, kThreads, 0, st>>>(sink_buf, iters);
         *ops = 2.0 * 16 * 8 * 32 * warps * kChains * (double)iters;
         break;
+    case GW_PROBE_TCGEN05_N64:
+    case GW_PROBE_TCGEN05_N128:
+    case GW_PROBE_TCGEN05_N256: {
+        const int bn = kind == GW_PROBE_TCGEN05_N64 ? 64 : (kind == GW_PROBE_TCGEN05_N128 ? 128 : 256);
+        const cudaError_t e = bn == 64    ? launch_probe_tcgen05<64>(sink_buf, iters, sms, st)
+                              : bn == 128 ? launch_probe_tcgen05<128>(sink_buf, iters, sms, st)
+                                          : launch_probe_tcgen05<256>(sink_buf, iters, sms, st);
+        if (e != cudaSuccess) return GW_ERR_CUDA;
+        *ops = 2.0 * 128 * bn * 16 * 4 * (double)iters * sms;
+        return GW_OK;
+    }
     default:
         return GW_ERR_ARG;
     }

@@ -360,8 +360,9 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                                     y[p] = __fsub_rn(t, __fsub_rn(x[p], s2));
                                 }
                                 const int64_t row = (int64_t)cbd * a.nv + v;
-                                a.F[((int64_t)l * ((int64_t)a.cb * a.nv) + row) * a.K2 + q] =
-                                    make_float4(x[0], y[0], x[1], y[1]);
+                                const int64_t fi = ((int64_t)l * ((int64_t)a.cb * a.nv) + row) * a.K2 + q;
+                                if (!GW_IN(fi, (int64_t)a.n * a.n * a.cb * a.nv * a.K2, a.status)) continue;
+                                a.F[fi] = make_float4(x[0], y[0], x[1], y[1]);
                             }
                         }
                     }
@@ -427,6 +428,7 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                             zd_digits_w(b.re.hi, b.re.lo, sc[h2], w[h2], dr);
                             zd_digits_w(b.im.hi, b.im.lo, sc[h2], w[h2], di);
                             const int colr = cl * ncol + 2 * q;
+                            if (!GW_IN(colr + 1, kZdN, a.status)) continue;
                             unsigned char *pr = B + sw64_off(colr, 2 * k2), *pi = B + sw64_off(colr + 1, 2 * k2);
 #pragma unroll
                             for (int sl = 0; sl < kZdSlices; ++sl) {
