@@ -342,21 +342,41 @@ constexpr RadPlan plan_of()
     return PR ? make_prune_plan(N) : make_rad_plan(N);
 }
 
+// Work split of a block-level stage over its butterflies (line l, index j).  By default j runs
+// fastest over the threads: consecutive lanes read consecutive points of a line, right for lines
+// at an even stride.  With lines fastest consecutive lanes take consecutive lines, which keeps a
+// warp's 16-byte accesses in distinct bank groups when the line stride is odd (N + 1) or the
+// lines are contiguous (element stride N); the thread's first butterfly and its step are
+// computed once per transform.
+struct LMap {
+    int j0, l0, dj, dl;
+};
+__device__ __forceinline__ LMap lmap_lines_fastest(int nlines)
+{
+    LMap m{1 << 30, 0, 0, 0};
+    if (nlines > 0) {
+        m.j0 = (int)threadIdx.x / nlines;
+        m.l0 = (int)threadIdx.x - m.j0 * nlines;
+        m.dj = (int)blockDim.x / nlines;
+        m.dl = (int)blockDim.x - m.dj * nlines;
+    }
+    return m;
+}
+
 // lines of N points, line l at x + l * ls, element stride es; LAZY leaves radix-4 outputs
 // unrenormalised (for stages whose outputs feed another lazy stage)
 // lmax >= 0 skips the lines l whose signed index (l, or l - N above N/2) exceeds lmax in
 // magnitude (all-zero lines whose outputs stay zero in both ping-pong buffers).
-template <int N, int R, int NS, bool LAZY = false>
+// LF: lines fastest over the threads, in the split lm (see LMap).
+template <int N, int R, int NS, bool LAZY = false, bool LF = false>
 __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *__restrict__ y, int nlines, int ls,
                                           const float4 *__restrict__ tw, const TfConsts &k, int es = 1,
-                                          int lmax = -1)
+                                          int lmax = -1, LMap lm = LMap{})
 {
     constexpr int nb = N / R;
     constexpr int tstride = N / (NS * R); // r * kk * tstride < N: no reduction needed
-    const int total = nlines * nb;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        const int l = b / nb, j = b - l * nb;
-        if (lmax >= 0 && (l <= N / 2 ? l : N - l) > lmax) continue;
+    auto bfly = [&](int l, int j) {
+        if (lmax >= 0 && (l <= N / 2 ? l : N - l) > lmax) return;
         const int kk = j % NS;
         const float4 *xl = x + l * ls;
         tcx v[R];
@@ -373,34 +393,54 @@ __device__ __forceinline__ void tstage_ct(const float4 *__restrict__ x, float4 *
         const int o = (j / NS) * (NS * R) + kk;
 #pragma unroll
         for (int r = 0; r < R; ++r) tc_store(yl + (o + r * NS) * es, v[r]);
+    };
+    if constexpr (LF) {
+        int l = lm.l0, j = lm.j0;
+        while (j < nb) {
+            bfly(l, j);
+            l += lm.dl;
+            j += lm.dj;
+            if (l >= nlines) {
+                l -= nlines;
+                ++j;
+            }
+        }
+    } else {
+        const int total = nlines * nb;
+        for (int b = threadIdx.x; b < total; b += blockDim.x) {
+            const int l = b / nb;
+            bfly(l, b - l * nb);
+        }
     }
 }
 
 // Stages S.. of the plan (all of make_rad_plan(N), or all but the pruned last one of
 // make_prune_plan(N)), block-wide with a barrier after each; returns the result buffer.
 // With PR the stages are lazy: their outputs only feed the pruned stage's lazy sums.
-template <int N, int S, int NS, bool PR = false>
+// LF: lines fastest over the threads (see LMap).
+template <int N, int S, int NS, bool PR = false, bool LF = false>
 __device__ __forceinline__ float4 *tstages_ct(float4 *x, float4 *y, int nlines, int ls, const float4 *tw,
-                                              const TfConsts &k, int es, int lmax = -1)
+                                              const TfConsts &k, int es, int lmax = -1, LMap lm = LMap{})
 {
     constexpr RadPlan P = plan_of<N, PR>();
     if constexpr (S >= P.nst - (PR ? 1 : 0)) {
         return x;
     } else {
+        if constexpr (LF && S == 0) lm = lmap_lines_fastest(nlines);
         constexpr int R = P.r[S];
-        tstage_ct<N, R, NS, PR>(x, y, nlines, ls, tw, k, es, lmax);
+        tstage_ct<N, R, NS, PR, LF>(x, y, nlines, ls, tw, k, es, lmax, lm);
         __syncthreads();
-        return tstages_ct<N, S + 1, NS * R, PR>(y, x, nlines, ls, tw, k, es, lmax);
+        return tstages_ct<N, S + 1, NS * R, PR, LF>(y, x, nlines, ls, tw, k, es, lmax, lm);
     }
 }
 
 // Full two-float transform of nlines lines of length N (line stride ls, element stride es);
 // returns the result buffer.  lmax >= 0: lines beyond it are zero and skipped (see tstage_ct).
-template <int N>
+template <int N, bool LF = false>
 __device__ __forceinline__ float4 *tfft_lines_ct(float4 *a, float4 *b, int nlines, int ls, const float4 *tw,
                                                  const TfConsts &k, int es = 1, int lmax = -1)
 {
-    return tstages_ct<N, 0, 1>(a, b, nlines, ls, tw, k, es, lmax);
+    return tstages_ct<N, 0, 1, false, LF>(a, b, nlines, ls, tw, k, es, lmax);
 }
 
 // Warp-level stage over the calling warp's own lines (L lines of N points at x + l * N);

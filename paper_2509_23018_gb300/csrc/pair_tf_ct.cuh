@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         }
         __syncthreads(); // C complete
         // i1 on the K2 columns; A (and B after it) are free until the next slab
-        const float4 *y1 = tstages_ct<N, 0, 1, true>(C, A, K2, CS, tw, kc, 1);
+        const float4 *y1 = tstages_ct<N, 0, 1, true, true>(C, A, K2, CS, tw, kc, 1);
         float4 *Si = S + (size_t)i0 * K12;
         for (int d = threadIdx.x; d < K12; d += NT) {
             const int cl = cell[d];
@@ -223,12 +223,22 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
     double2 *out = M + row * pp.ng;
     for (int d0 = 0; d0 < K12; d0 += NB) {
         const int nbat = K12 - d0 < NB ? K12 - d0 : NB;
-        for (int i = threadIdx.x; i < nbat * N; i += NT) {
-            const int x = i / nbat, dl = i - x * nbat;
-            X[dl * CS + x] = S[(size_t)x * K12 + d0 + dl];
+        {
+            // element (x, dl) = i / nbat, i % nbat for i = threadIdx.x, threadIdx.x + NT, ...
+            int x = (int)threadIdx.x / nbat, dl = (int)threadIdx.x - x * nbat;
+            const int dx = NT / nbat, ddl = NT - dx * nbat;
+            while (x < N) {
+                X[dl * CS + x] = S[(size_t)x * K12 + d0 + dl];
+                dl += ddl;
+                x += dx;
+                if (dl >= nbat) {
+                    dl -= nbat;
+                    ++x;
+                }
+            }
         }
         __syncthreads();
-        const float4 *y0 = tstages_ct<N, 0, 1, true>(X, Y, nbat, CS, tw, kc, 1);
+        const float4 *y0 = tstages_ct<N, 0, 1, true, true>(X, Y, nbat, CS, tw, kc, 1);
         const int m1 = pp.cstart[d0 + nbat];
         for (int m = pp.cstart[d0] + threadIdx.x; m < m1; m += NT) {
             const int2 pt = pp.cpts[m]; // point index, k0 | cell << 8
@@ -339,14 +349,22 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
     }
     float4 *S = pp.scr + (size_t)slot * N * K12;
     const int64_t row = blockIdx.x;
-    const int nld = 2 * N * K2; // F entries of a slab pair
+    // F entries of a slab pair: line lx = sl N + i1 of the pair (slab i0 + sl), K2 contiguous
+    // entries per line; a thread's first (line, entry) and its step are computed once
+    const int fl0 = (int)threadIdx.x / K2, fq0 = (int)threadIdx.x - fl0 * K2;
+    const int fdl = NT / K2, fdq = NT - fdl * K2;
     auto fetch = [&](int i0, float4 *C) {
-        for (int e = threadIdx.x; e < nld; e += NT) {
-            const int sl = e / (N * K2), rem = e - sl * (N * K2);
-            const int i1 = rem / K2, q = rem - i1 * K2;
-            const int64_t fi = (((int64_t)(i0 + sl) * N + i1) * R + row) * K2 + q;
-            if (!GW_IN(fi, (int64_t)N * N * R * K2, pp.status)) continue;
-            cp_async16(C + (sl * K2 + q) * CS + i1, F + fi);
+        int lx = fl0, q = fq0;
+        while (lx < 2 * N) {
+            const int sl = lx >= N, i1 = lx - sl * N;
+            const int64_t fi = (((int64_t)i0 * N + lx) * R + row) * K2 + q;
+            if (GW_IN(fi, (int64_t)N * N * R * K2, pp.status)) cp_async16(C + (sl * K2 + q) * CS + i1, F + fi);
+            q += fdq;
+            lx += fdl;
+            if (q >= K2) {
+                q -= K2;
+                ++lx;
+            }
         }
         cp_async_commit();
     };
@@ -355,7 +373,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         float4 *X = Xb + b * ncols * CS, *Y = Xb + (b ^ 1) * ncols * CS;
         cp_async_wait_all();
         __syncthreads(); // X complete
-        const float4 *y1 = tstages_ct<N, 0, 1, true>(X, Y, ncols, CS, tw, kc, 1); // ends in X, then a barrier
+        const float4 *y1 = tstages_ct<N, 0, 1, true, true>(X, Y, ncols, CS, tw, kc, 1); // ends in X, then a barrier
         if (i0 + 2 < N) fetch(i0 + 2, Y);
         for (int d = threadIdx.x; d < 2 * K12; d += NT) {
             const int sl = d >= K12, dd = d - sl * K12;
@@ -372,12 +390,22 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
     double2 *out = M + row * pp.ng;
     for (int d0 = 0; d0 < K12; d0 += NB) {
         const int nbat = K12 - d0 < NB ? K12 - d0 : NB;
-        for (int i = threadIdx.x; i < nbat * N; i += NT) {
-            const int x = i / nbat, dl = i - x * nbat;
-            X[dl * CS + x] = S[(size_t)x * K12 + d0 + dl];
+        {
+            // element (x, dl) = i / nbat, i % nbat for i = threadIdx.x, threadIdx.x + NT, ...
+            int x = (int)threadIdx.x / nbat, dl = (int)threadIdx.x - x * nbat;
+            const int dx = NT / nbat, ddl = NT - dx * nbat;
+            while (x < N) {
+                X[dl * CS + x] = S[(size_t)x * K12 + d0 + dl];
+                dl += ddl;
+                x += dx;
+                if (dl >= nbat) {
+                    dl -= nbat;
+                    ++x;
+                }
+            }
         }
         __syncthreads();
-        const float4 *y0 = tstages_ct<N, 0, 1, true>(X, Y, nbat, CS, tw, kc, 1);
+        const float4 *y0 = tstages_ct<N, 0, 1, true, true>(X, Y, nbat, CS, tw, kc, 1);
         const int m1 = pp.cstart[d0 + nbat];
         for (int m = pp.cstart[d0] + threadIdx.x; m < m1; m += NT) {
             const int2 pt = pp.cpts[m];
@@ -462,7 +490,7 @@ __global__ void __launch_bounds__(256) band_slab_tf_ct(float4 *__restrict__ psi,
     __syncthreads();
     float4 *r = tfft_lines_ct<N>(a, b, N, N, tw, kc, 1, m1); // along i2, zero lines skipped
     float4 *o = (r == a) ? b : a;
-    r = tfft_lines_ct<N>(r, o, N, 1, tw, kc, N);              // along i1 (element stride N)
+    r = tfft_lines_ct<N, true>(r, o, N, 1, tw, kc, N);        // along i1 (element stride N)
     for (int i = threadIdx.x; i < ns; i += blockDim.x) g[i] = r[i];
 }
 
@@ -479,7 +507,7 @@ __global__ void __launch_bounds__(256) band_axis0_tf_ct(float4 *__restrict__ psi
         a[i] = g[(int64_t)i0 * N * N + i2];
     }
     __syncthreads();
-    float4 *r = tfft_lines_ct<N>(a, b, N, 1, tw, kc, N);      // lines along i0, element stride N
+    float4 *r = tfft_lines_ct<N, true>(a, b, N, 1, tw, kc, N); // lines along i0, element stride N
     for (int i = threadIdx.x; i < np; i += blockDim.x) {
         const int i0 = i / N, i2 = i - i0 * N;
         g[(int64_t)i0 * N * N + i2] = r[i];

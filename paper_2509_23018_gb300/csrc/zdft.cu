@@ -151,7 +151,12 @@ __host__ __device__ __forceinline__ int zd_conduction_per_tile_d(int K2)
 // one thread issues the tcgen05 products into four accumulators (two buffers of 4 x 64 TMEM
 // columns alternate between tiles), and the epilogue warps sum the accumulators into F.
 // (128-column tiles with one accumulator buffer, 16-entry column stages and a 32-byte swizzle
-// measured slower: 3.02 against 2.86 ms per 48^3 chunk, the epilogue no longer hidden.)
+// measured slower: 3.02 against 2.86 ms per 48^3 chunk, the epilogue no longer hidden; a third
+// column stage, room made by smaller ring slots and twiddles from the base table, gained nothing:
+// the producers keep up.)  A 128 x 64 x 16 product reads 4 KB of A and 2 KB of B from shared
+// memory, 48 clocks at 128 bytes per clock against 32 clocks of tensor work: at N = 64 the
+// operand reads bound the pipe (the probe's 128 x 64 rate is 2/3 of its 128 x 128 rate), and
+// four accumulator groups of 64 columns, double-buffered, fill the 512 TMEM columns.
 //  warp 0: TMA; warp 1: MMA (and TMEM); warps 2..5: epilogue (TMEM lane quadrant warp % 4);
 //  warps 6..11: producers.
 constexpr int kZdN = 64;                               // columns per tile
@@ -286,6 +291,8 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     } else if (warp == 1) {
         // ---- MMA issue
         if (lane == 0) {
+            // descriptor address fields count 16-byte units: offsets below 256 KB add in place
+            const uint64_t ad0 = sdesc_sw64(su32(sA)), bd0 = sdesc_sw64(su32(sB));
             uint32_t u = 0, it = 0, tile = 0;
             for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x, ++u) {
                 if (!bar_wait(aFull, u & 1)) { ok = false; break; }
@@ -293,24 +300,28 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                     const uint32_t buf = tile & 1;
                     if (!bar_wait(&tEmpty[buf], ((tile >> 1) & 1) ^ 1)) { ok = false; break; }
                     tc_fence_after();
-                    unsigned written = 0;
                     for (int kc = 0; kc < 3 && ok; ++kc, ++it) {
                         const uint32_t st = it & 1;
                         if (!bar_wait(&bFull[st], (it >> 1) & 1)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t a0 = su32(sA + kc * kZdAChunk), b0 = su32(sB + st * kZdBStage);
+                        // the 42 products of the K-chunk, unrolled: descriptors advance by constant
+                        // offsets, and a group's first product of the tile (K-chunk 0, i = 0,
+                        // j = group) starts its accumulator
+                        const uint64_t ad = ad0 + (uint64_t)((kc * kZdAChunk) >> 4);
+                        const uint64_t bd = bd0 + (uint64_t)((st * kZdBStage) >> 4);
+                        const uint32_t dbase = tbase + buf * 256, acc0 = kc > 0 ? 1u : 0u;
+#pragma unroll
                         for (int i = 0; i < kZdSlices; ++i)
-                            for (int j = 0; i + j < kZdSlices; ++j) {
-                                const int g = min(i + j, 3);
-                                const uint32_t d = tbase + buf * 256 + g * kZdN;
+#pragma unroll
+                            for (int j = 0; j < kZdSlices - i; ++j)
 #pragma unroll
                                 for (int s16 = 0; s16 < 2; ++s16) {
-                                    const uint32_t acc = (written >> g) & 1u;
-                                    umma_f16(d, sdesc_sw64(a0 + i * kZdASlice + s16 * 32),
-                                             sdesc_sw64(b0 + j * kZdBSlice + s16 * 32), kZdIdesc, acc);
-                                    written |= 1u << g;
+                                    const int g = i + j < 3 ? i + j : 3;
+                                    const bool first = i == 0 && j <= 3 && s16 == 0;
+                                    umma_f16(dbase + g * kZdN, ad + (uint64_t)((i * kZdASlice + s16 * 32) >> 4),
+                                             bd + (uint64_t)((j * kZdBSlice + s16 * 32) >> 4), kZdIdesc,
+                                             first ? acc0 : 1u);
                                 }
-                            }
                         umma_commit(&bEmpty[st]);
                     }
                     umma_commit(&tFull[buf]);
