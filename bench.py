@@ -282,9 +282,9 @@ TRAFFIC = {
                    "source": "ncu dram__bytes_read+write, pair_kernel_tf_ct<48>, p1_48cube_onechunk"},
     # the tensor-core route of the 48^3 workload: one 8192-pair chunk (128 valence x 64
     # conduction bands), the launch shape the bench's step repeats 16 times
-    "zdft": {"bytes_per_launch": 0.489212e9 + 4.488817e9,
+    "zdft": {"bytes_per_launch": 0.498707e9 + 4.493061e9,
              "source": "ncu dram__bytes_read+write, zd_gemm_kernel, p2_48cube_chunk"},
-    "pair_from_f": {"bytes_per_launch": 5.626491e9 + 1.483600e9,
+    "pair_from_f": {"bytes_per_launch": 5.738301e9 + 1.525466e9,
                     "source": "ncu dram__bytes_read+write, pair_kernel_tf_from_f<48>, p2_48cube_chunk"},
     # the single-stream launch (4-deep TMA ring) the tensor-core route runs
     "ozaki_gemm": {"bytes_per_launch": 7.620381e9 + 0.217023e9,
@@ -293,6 +293,21 @@ TRAFFIC = {
                                  "source": "ncu dram__bytes_read+write, oz_gemm_kernel<256,0,4> (s = 7), "
                                            "p2_48cube_chunk"},
 }
+
+
+# the launch shape of every capture above: 48^3 grid, N_G = 2000, 8192 pairs per launch
+TRAFFIC_SHAPE = ((48, 48, 48), 2000, 8192)
+
+
+def traffic_for(key, cfg):
+    """(DRAM bytes per launch, source) of a kernel, or (None, why) when the captures were taken
+    on another launch shape than cfg's."""
+    t = TRAFFIC.get(key) or {}
+    if t.get("bytes_per_launch") is None:
+        return None, None
+    if (tuple(cfg.grid), cfg.ng, min(cfg.pair_chunk, cfg.npairs)) != TRAFFIC_SHAPE:
+        return None, "no ncu capture of this launch shape (captures: 48^3, N_G = 2000, 8192 pairs per launch)"
+    return t["bytes_per_launch"], t["source"]
 
 
 # ---------------------------------------------------------------- pipe peaks
@@ -644,8 +659,8 @@ def roofline_zd(cfg, prob, res):
         peak, src = peak_for("ozaki")
         ach = flops / (kms / kn * 1e-3) * 1e-12
         out["zdft"] = {"bound": "tensor", "kernel": "zd_gemm_kernel", "achieved": ach, "peak": peak,
-                       "unit": "TFLOP/s", "frac": ach / peak, "traffic": TRAFFIC.get("zdft", {}).get("bytes_per_launch"),
-                       "traffic_source": TRAFFIC.get("zdft", {}).get("source"), "launches": kn,
+                       "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic_for("zdft", cfg)[0],
+                       "traffic_source": traffic_for("zdft", cfg)[1], "launches": kn,
                        "ms_per_launch": kms / kn, "flops_per_launch": flops, "useful_share": useful / flops,
                        "peak_source": src, "share_of_step": kms / res["total_ms"],
                        "unit_of_work": "BF16 flops of the 21 kept slice products (128 x 64 tiles, K = 2N)"}
@@ -656,8 +671,8 @@ def roofline_zd(cfg, prob, res):
         ach = per_launch / (kms2 / kn2 * 1e-3) * 1e-12
         out["pair_from_f"] = {"bound": "alu", "kernel": "pair_kernel_tf_from_f", "achieved": ach, "peak": peak,
                               "unit": "FP32 Tops/s", "frac": ach / peak,
-                              "traffic": TRAFFIC.get("pair_from_f", {}).get("bytes_per_launch"),
-                              "traffic_source": TRAFFIC.get("pair_from_f", {}).get("source"), "launches": kn2,
+                              "traffic": traffic_for("pair_from_f", cfg)[0],
+                              "traffic_source": traffic_for("pair_from_f", cfg)[1], "launches": kn2,
                               "ms_per_launch": kms2 / kn2, "ops_per_launch": per_launch, "ops_per_pair": ops_pair,
                               "peak_source": src, "share_of_step": kms2 / res["total_ms"],
                               "unit_of_work": "FP32 operations of the two-float i1 and i0 transforms as implemented"}
@@ -690,7 +705,7 @@ def roofline_pair(cfg, prob, res):
     hbm, hbm_src = _hbm_peak()
     dfma = LIVE_PEAKS.get("dfma")
     t_step = kms * 1e-3 * nchunk / kn if kn else None
-    traffic = TRAFFIC.get("pair_mtxel", {}).get("bytes_per_launch")
+    traffic = traffic_for("pair_mtxel", cfg)[0]
     method = {"bytes_per_step": mbytes, "flops_per_step": mflops,
               "hbm_frac": (mbytes / t_step * 1e-9 / hbm) if t_step else None, "hbm_peak_gbs": hbm,
               "hbm_peak_source": hbm_src,
@@ -708,7 +723,7 @@ def roofline_pair(cfg, prob, res):
             "ops_per_pair": per_pair, "peak_source": peak_src,
             "unit_of_work": "FP32 operations of the two-float transforms as implemented (issue efficiency)",
             "share_of_step": kms / res["total_ms"] if res["total_ms"] else None,
-            "traffic_source": TRAFFIC.get("pair_mtxel", {}).get("source"), "method": method,
+            "traffic_source": traffic_for("pair_mtxel", cfg)[1], "method": method,
             "method_bytes": mbytes, "method_flops": mflops, "hbm_frac": method["hbm_frac"]}
 
 
@@ -725,10 +740,10 @@ def roofline_for(cfg, prec, nslices, res, single_stream=False):
     achieved = per_launch_flops / (kms / kn * 1e-3) * 1e-12 if kn else None
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": TRAFFIC.get(tkey, {}).get("bytes_per_launch"), "kernel": kname,
+            "traffic": traffic_for(tkey, cfg)[0], "kernel": kname,
             "launches": kn, "ms_per_launch": kms / kn if kn else None, "flops_per_launch": per_launch_flops,
             "peak_source": peak_src, "share_of_step": kms / res["total_ms"] if res["total_ms"] else None,
-            "traffic_source": TRAFFIC.get(tkey, {}).get("source"),
+            "traffic_source": traffic_for(tkey, cfg)[1],
             "probe_peaks_tops": {k: v for k, v in LIVE_PEAKS.items() if not k.startswith("_")}}
 
 
@@ -854,7 +869,8 @@ def sweep(args):
                             "contract_tflops": rf["achieved"], "contract_ms": rf["ms_per_launch"],
                             "ms_per_q": r["ms_per_step"], "value": r["value"], "roofline": rf}
     if not args.no_cpu_baseline:
-        cpu = cpu_baseline(cfg, prob, args.cpu_sample_pairs)
+        # at N_G = 6000 the oracle takes about 47 ms a pair on 16 cores: 512 pairs stay near 25 s
+        cpu = cpu_baseline(cfg, prob, min(args.cpu_sample_pairs, 512))
         cpu.pop("seconds", None)
         out["cpu_baseline"] = cpu
     print(json.dumps(out), flush=True)

@@ -2,7 +2,8 @@
 two-float stage (a) on the 48^3 grid): pair elements of a conduction block against the oracle,
 element by element, and chi through that route, on shapes that exercise its tiles: a partial row
 tile (few valence bands), two row tiles, few kept z-frequencies (four conduction bands per tile),
-ragged conduction blocks, and the 2000-G sphere of the benchmark's workload."""
+ragged conduction blocks, and the 2000-G sphere of the benchmark's workload; and bands whose
+scales span many orders of magnitude on a sphere with G = 0, on both routes of stage (a)."""
 import numpy as np
 import pytest
 
@@ -73,3 +74,30 @@ def test_block_entry_rejects_other_routes(gw):
     assert e.value.status == _lib.GW_ERR_ARG
     h.pair_elements_block(0, 0, 6)       # still usable
     h.sync()
+
+
+@pytest.mark.parametrize("block", [True, False])
+def test_pair_elements_wide_dynamic_range(gw, block):
+    """Bands scaled over many orders of magnitude (valence 1e-3 .. 1e3, conduction 1e-6 .. 1e6,
+    so the rows of M span 1e-9 .. 1e9) on a sphere that includes G = 0, where M_vc(0) = <v|c>
+    vanishes for the orthonormal bands by cancellation over the grid: every row matches the
+    oracle to its own scale on the tensor-core route (block entry) and on the two-float FFT
+    route (general entry); M_vc(0) stays at rounding level relative to the row."""
+    import dataclasses
+    p = gwgen.make_problem((48, 48, 48), 6, 10, 900, 300, seed=47)
+    sv = 10.0 ** np.linspace(-3, 3, 6)
+    sc = 10.0 ** np.linspace(-6, 6, 10)
+    g = np.vstack([np.zeros((1, 3), np.int32), p.gchi]).astype(np.int32)
+    p = dataclasses.replace(p, cv=p.cv * sv[:, None], cc=p.cc * sc[:, None], gchi=g)
+    h = gw.from_problem(p, prec="ozaki", nslices=7, mtxel="twofloat")
+    Mo = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)              # rows v * nc + c
+    if block:
+        M = h.pair_elements_block(0, 0, 10).cpu().numpy()               # rows c * nv + v
+        M = M.reshape(10, 6, -1).transpose(1, 0, 2).reshape(60, -1)
+    else:
+        M = h.pair_elements(0, 0, 60).cpu().numpy()
+    h.sync()
+    scale = np.outer(sv, sc).reshape(-1)                                # |M_vc| ~ sv sc
+    rows = np.linalg.norm(M - Mo, axis=1) / np.linalg.norm(Mo, axis=1)
+    assert rows.max() < 1e-11, rows.max()
+    assert np.all(np.abs(M[:, 0]) < 1e-12 * scale)                      # <v|c> = 0 for v != c
