@@ -74,6 +74,51 @@ __global__ void oz_fill_kernel(int *E, int n, int v)
 }
 
 // ------------------------------------------------------------------ split, step 2: slices
+// A block forms the slices of a 64-pair x 32-column tile of M in shared memory, zs[i][j][p]
+// (j = 2 g + {Re, Im}, rows of 64 pairs padded to kOzLD), then writes them out as 128-byte row
+// pieces.  Thread roles: warp w takes tile rows 32 (w & 1) .. + 31 (lane = row: column g = row / 2,
+// component row & 1) and pairs 16 (w >> 1) .. + 15, so a warp reads 32 consecutive doubles of M
+// per pair, and writes each slice's 16 digits of a row as two 16-byte stores; consecutive rows
+// lie 144 bytes apart, so a quarter-warp's stores fall in 8 distinct bank groups.
+constexpr int kOzLD = 72;
+
+struct OzTileThread {
+    int row, gl, c, pl0;
+};
+__device__ __forceinline__ OzTileThread oz_tile_thread()
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    OzTileThread t;
+    t.row = 32 * (w & 1) + lane;
+    t.gl = t.row >> 1;
+    t.c = t.row & 1;
+    t.pl0 = 16 * (w >> 1);
+    return t;
+}
+
+// the s slices of the 16 biased integers nb[t] = N_t + bias (pairs pl0 + t of one row) into
+// zs + i plane + [0, 16)
+__device__ __forceinline__ void oz_store_row_digits(const long long nb[16], int s, uint16_t *row, int plane)
+{
+    for (int i = 0; i < s; ++i) {
+        uint32_t w[8];
+#pragma unroll
+        for (int t = 0; t < 16; t += 2) {
+            uint16_t d[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const long long v = nb[t + u];
+                d[u] = i == 0 ? oz_small_bf16((int)(v >> (kOzBeta * (s - 1))))
+                              : oz_small_bf16((int)((v >> (kOzBeta * (s - 1 - i))) & 63) - 32);
+            }
+            w[t >> 1] = (uint32_t)d[0] | ((uint32_t)d[1] << 16);
+        }
+        uint4 *o = (uint4 *)(row + (int64_t)i * plane);
+        o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
 // Z[i][j][p] (bf16, K-major rows of length kpad) for a 64-pair x 32-column block.
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double2 *__restrict__ M, int64_t P, int ng,
                                                        const double *__restrict__ spv, const int *__restrict__ E,
@@ -81,27 +126,24 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double2 *__restrict
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint16_t *zs = (uint16_t *)smem; // [s][64 rows j][64 + 8 pairs] (padded)
-    constexpr int LD = 72;
+    constexpr int LD = kOzLD;
     const int64_t p0 = (int64_t)blockIdx.y * 64;
     const int g0 = blockIdx.x * 32;
     const long long bias = oz_digit_bias(s);
-    for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
-        const int pl = e >> 5, gl = e & 31;
-        const int64_t p = p0 + pl;
-        const int g = g0 + gl;
-        double2 a = make_double2(0.0, 0.0);
-        int Eg = kOzNoColumn;
-        if (p < P && g < ng) {
-            const double sp = spv[p];
-            double2 m = M[p * ng + g];
-            a = make_double2(m.x * sp, m.y * sp);
-            Eg = E[g];
-        }
+    {
+        const OzTileThread tt = oz_tile_thread();
+        const int g = g0 + tt.gl;
         // N = round(a 2^(6 s - E)) and its balanced base-64 digits, in integer arithmetic
-        const int sh = kOzBeta * s - Eg;
+        const int sh = kOzBeta * s - (g < ng ? E[g] : kOzNoColumn);
+        const double *Md = (const double *)M;
+        long long nb[16];
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
-            oz_store_digits(oz_round_scaled(c ? a.y : a.x, sh), s, bias, zs + (2 * gl + c) * LD + pl, 64 * LD);
+        for (int t = 0; t < 16; ++t) {
+            const int64_t p = p0 + tt.pl0 + t;
+            const double a = (p < P && g < ng) ? Md[2 * (p * ng + g) + tt.c] * spv[p] : 0.0;
+            nb[t] = oz_round_scaled(a, sh) + bias;
+        }
+        oz_store_row_digits(nb, s, zs + tt.row * LD + tt.pl0, 64 * LD);
     }
     __syncthreads();
     // rows j = 2 g0 .. 2 g0 + 63 of each slice, 64 consecutive pairs = 128 bytes
@@ -165,37 +207,32 @@ __global__ void __launch_bounds__(256) oz_slice_multi_kernel(const double2 *__re
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint16_t *zs = (uint16_t *)smem; // [s][64 rows j][64 + 8 pairs] (padded)
-    constexpr int LD = 72;
+    constexpr int LD = kOzLD;
     const int64_t p0 = (int64_t)blockIdx.y * 64;
     const int g0 = blockIdx.x * 32;
     const int nrows = 2 * ng;
     const long long bias = oz_digit_bias(s);
-    // the block's 64 x 32 tile of M, read once for every frequency of the group
-    double2 m[8];
+    // the thread's part of the block's 64 x 32 tile of M, read once for every frequency
+    const OzTileThread tt = oz_tile_thread();
+    const int g = g0 + tt.gl;
+    const double *Md = (const double *)M;
+    double m[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int e = threadIdx.x + u * 256, pl = e >> 5, gl = e & 31;
-        const int64_t p = p0 + pl;
-        const int g = g0 + gl;
-        m[u] = (p < P && g < ng) ? M[p * ng + g] : make_double2(0.0, 0.0);
+    for (int t = 0; t < 16; ++t) {
+        const int64_t p = p0 + tt.pl0 + t;
+        m[t] = (p < P && g < ng) ? Md[2 * (p * ng + g) + tt.c] : 0.0;
     }
     for (int w = 0; w < nw; ++w) {
+        {
+            const int sh = kOzBeta * s - (g < ng ? E[(int64_t)w * ng + g] : kOzNoColumn);
+            long long nb[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = threadIdx.x + u * 256, pl = e >> 5, gl = e & 31;
-            const int64_t p = p0 + pl;
-            const int g = g0 + gl;
-            double2 a = make_double2(0.0, 0.0);
-            int Eg = kOzNoColumn;
-            if (p < P && g < ng) {
-                const double sp = spv[(int64_t)w * dstride + p];
-                a = make_double2(m[u].x * sp, m[u].y * sp);
-                Eg = E[(int64_t)w * ng + g];
+            for (int t = 0; t < 16; ++t) {
+                const int64_t p = p0 + tt.pl0 + t;
+                const double a = (p < P && g < ng) ? m[t] * spv[(int64_t)w * dstride + p] : 0.0;
+                nb[t] = oz_round_scaled(a, sh) + bias;
             }
-            const int sh = kOzBeta * s - Eg;
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-                oz_store_digits(oz_round_scaled(c ? a.y : a.x, sh), s, bias, zs + (2 * gl + c) * LD + pl, 64 * LD);
+            oz_store_row_digits(nb, s, zs + tt.row * LD + tt.pl0, 64 * LD);
         }
         __syncthreads();
         __nv_bfloat16 *Zw = Z + w * zstride;
@@ -737,7 +774,7 @@ cudaError_t launch_oz_split_multi(const double2 *M, int64_t P, int ng, const dou
         oz_colexp_multi_kernel<<<dim3((ng + 31) / 32, gy), 256, 0, st>>>(M, P, ng, sp, dstride, nw, E);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const size_t sm = (size_t)s * 64 * 72 * sizeof(uint16_t);
+    const size_t sm = (size_t)s * 64 * kOzLD * sizeof(uint16_t);
     e = cudaFuncSetAttribute(oz_slice_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     oz_slice_multi_kernel<<<dim3((ng + 31) / 32, (unsigned)(kpad / 64)), 256, sm, st>>>(
@@ -748,7 +785,7 @@ cudaError_t launch_oz_split_multi(const double2 *M, int64_t P, int ng, const dou
 cudaError_t launch_oz_slice(const double2 *M, int64_t P, int ng, const double *sp, const int *E, int s,
                             int64_t kpad, void *Z, cudaStream_t st)
 {
-    const size_t sm = (size_t)s * 64 * 72 * sizeof(uint16_t);
+    const size_t sm = (size_t)s * 64 * kOzLD * sizeof(uint16_t);
     cudaError_t e = cudaFuncSetAttribute(oz_slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     oz_slice_kernel<<<dim3((ng + 31) / 32, (unsigned)(kpad / 64)), 256, sm, st>>>(M, P, ng, sp, E, s, kpad,
