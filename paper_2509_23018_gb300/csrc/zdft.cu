@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     unsigned char *sB = sA + 3 * kZdAChunk;               // 2 stages x 24 KB
     float4 *ring = (float4 *)(sB + 2 * kZdBStage);        // [slots][4][N] conduction line tiles
     float4 *wt = ring + kZdPsiSlots * 4 * a.n;            // [K2][N] twiddles W^{kz[q] i2}
-    uint64_t *bar = (uint64_t *)(wt + a.K2 * a.n);
+    int2 *ctab = (int2 *)(wt + a.K2 * a.n);               // [32] column pair -> (band, F offset)
+    uint64_t *bar = (uint64_t *)(ctab + kZdN / 2);
     uint64_t *aFull = bar, *aEmpty = bar + 1, *bFull = bar + 2, *bEmpty = bar + 4, *tFull = bar + 6,
              *tEmpty = bar + 8, *fin = bar + 10, *pFull = bar + 11, *pEmpty = pFull + kZdPsiSlots;
     uint32_t *tslot = (uint32_t *)(pEmpty + kZdPsiSlots);
@@ -229,6 +230,12 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     for (int i = threadIdx.x; i < a.K2 * a.n; i += blockDim.x) {
         const int q = i / a.n, i2 = i - q * a.n;
         wt[i] = twf[(a.kz[q] * i2) % a.n];
+    }
+    // the epilogue's column pairs (Re, Im of kept frequency q of band cl of the tile): cl and the
+    // offset cl nv K2 + q of its F entry from the row's first (padding pairs: cl >= CT)
+    for (int pi = threadIdx.x; pi < kZdN / 2; pi += blockDim.x) {
+        const int cl = pi / a.K2, q = pi - cl * a.K2;
+        ctab[pi] = make_int2(cl, cl * a.nv * a.K2 + q);
     }
     {
         // the padding columns of both stages stay zero (their products never reach F)
@@ -340,6 +347,9 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
             const int l = unit / a.nmt, mt = unit - l * a.nmt;
             const int v = mt * 128 + r;
             for (int ct = 0; ct < nct; ++ct, ++tile) {
+                // F index of the row's first entry in this tile, and the bands the tile holds
+                const int64_t rowbase = ((int64_t)l * a.cb * a.nv + (int64_t)ct * a.CT * a.nv + v) * a.K2;
+                const int clmax = min(a.CT, a.cb - ct * a.CT);
                 const uint32_t buf = tile & 1;
                 const bool got = bar_wait(&tFull[buf], (tile >> 1) & 1);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
@@ -356,10 +366,8 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                     if (v < a.nv) {
 #pragma unroll
                         for (int cc = 0; cc < 32; cc += 2) {
-                            const int col = c0 + cc; // Re column; col + 1 is the Im column
-                            const int cl = col / ncol, q = (col - cl * ncol) >> 1;
-                            const int cbd = ct * a.CT + cl;
-                            if (cl < a.CT && cbd < a.cb) {
+                            const int2 cp = ctab[(c0 + cc) >> 1]; // Re column c0 + cc, Im column + 1
+                            if (cp.x < clmax) {
                                 float x[2], y[2];
 #pragma unroll
                                 for (int p = 0; p < 2; ++p) {
@@ -370,8 +378,7 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                                     x[p] = __fadd_rn(s2, t);
                                     y[p] = __fsub_rn(t, __fsub_rn(x[p], s2));
                                 }
-                                const int64_t row = (int64_t)cbd * a.nv + v;
-                                const int64_t fi = ((int64_t)l * ((int64_t)a.cb * a.nv) + row) * a.K2 + q;
+                                const int64_t fi = rowbase + cp.y;
                                 if (!GW_IN(fi, (int64_t)a.n * a.n * a.cb * a.nv * a.K2, a.status)) continue;
                                 a.F[fi] = make_float4(x[0], y[0], x[1], y[1]);
                             }
@@ -465,7 +472,8 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
 
 size_t zd_smem_bytes(int n, int K2)
 {
-    return 1024 + 3 * kZdAChunk + 2 * kZdBStage + 16 * (size_t)kZdPsiSlots * 4 * n + 16 * (size_t)K2 * n + 8 * 24 + 64;
+    return 1024 + 3 * kZdAChunk + 2 * kZdBStage + 16 * (size_t)kZdPsiSlots * 4 * n + 16 * (size_t)K2 * n +
+           8 * (kZdN / 2) + 8 * 24 + 64;
 }
 
 bool zd_supported(int n, int K2, int nv)
