@@ -136,7 +136,10 @@ GW_API gw_status gw_chi0_set_bands(gw_chi0 *h, int iq, int kind, int nb, int ngp
 GW_API gw_status gw_chi0_set_gsphere(gw_chi0 *h, int iq, int ng, const int32_t *gvec);
 
 /*
- * Forward chi0 for nq slots and nw imaginary frequencies (steps a1-a7 after setup).
+ * Forward chi0 for nq slots and nw imaginary frequencies (steps a1-a7 after setup).  With
+ * two-float stage (a) on the 48^3 grid the last axis of the pair transform runs on the BF16
+ * tensor cores (the route of gw_chi0_pair_elements_block); elsewhere stage (a) is the pruned
+ * FFT pair kernel.
  *   iq     host int [nq]      slots to compute.
  *   omega  host double [nw]   imaginary-axis frequencies w >= 0 (eV).
  *   chi    device complex128, packed by slot: for slot i, nw blocks of ng_i x ng_i

@@ -309,6 +309,43 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// L2 eviction-priority policies (per access, no device setting): the scratch cells are written
+// once and read back once by the same block, the pool (SMs x blocks x 148 KB on 48^3) fits in L2,
+// and the F stream passing through L2 beside it is read once
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void cp_async16_hint(void *dst, const void *src, uint64_t pol)
+{
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_hint(float4 *p, float4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float4 ld_hint(const float4 *p, uint64_t pol)
+{
+    float4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol)
+                 : "memory");
+    return v;
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int N>
@@ -351,6 +388,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
     const int64_t row = blockIdx.x;
     // F entries of a slab pair: line lx = sl N + i1 of the pair (slab i0 + sl), K2 contiguous
     // entries per line; a thread's first (line, entry) and its step are computed once
+    const uint64_t keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
     const int fl0 = (int)threadIdx.x / K2, fq0 = (int)threadIdx.x - fl0 * K2;
     const int fdl = NT / K2, fdq = NT - fdl * K2;
     auto fetch = [&](int i0, float4 *C) {
@@ -358,7 +396,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         while (lx < 2 * N) {
             const int sl = lx >= N, i1 = lx - sl * N;
             const int64_t fi = (((int64_t)i0 * N + lx) * R + row) * K2 + q;
-            if (GW_IN(fi, (int64_t)N * N * R * K2, pp.status)) cp_async16(C + (sl * K2 + q) * CS + i1, F + fi);
+            if (GW_IN(fi, (int64_t)N * N * R * K2, pp.status)) cp_async16_hint(C + (sl * K2 + q) * CS + i1, F + fi, stream);
             q += fdq;
             lx += fdl;
             if (q >= K2) {
@@ -379,7 +417,8 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
             const int sl = d >= K12, dd = d - sl * K12;
             const int cl = cell[dd];
             if (!GW_IN(cl >> 8, K2, pp.status)) continue;
-            tc_store(S + (size_t)(i0 + sl) * K12 + dd, tprune_ct<N>(y1 + (sl * K2 + (cl >> 8)) * CS, cl & 255, tw));
+            const tcx c = tprune_ct<N>(y1 + (sl * K2 + (cl >> 8)) * CS, cl & 255, tw);
+            st_hint(S + (size_t)(i0 + sl) * K12 + dd, make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo), keep);
         }
         __syncthreads(); // X read before the next step's first stage writes it
     }
@@ -395,7 +434,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
             int x = (int)threadIdx.x / nbat, dl = (int)threadIdx.x - x * nbat;
             const int dx = NT / nbat, ddl = NT - dx * nbat;
             while (x < N) {
-                X[dl * CS + x] = S[(size_t)x * K12 + d0 + dl];
+                X[dl * CS + x] = ld_hint(S + (size_t)x * K12 + d0 + dl, stream);
                 dl += ddl;
                 x += dx;
                 if (dl >= nbat) {

@@ -101,3 +101,29 @@ def test_pair_elements_wide_dynamic_range(gw, block):
     rows = np.linalg.norm(M - Mo, axis=1) / np.linalg.norm(Mo, axis=1)
     assert rows.max() < 1e-11, rows.max()
     assert np.all(np.abs(M[:, 0]) < 1e-12 * scale)                      # <v|c> = 0 for v != c
+
+
+@pytest.mark.parametrize("gzmax,route", [(15, True), (16, False)])
+def test_route_edge_kept_frequencies(gw, gzmax, route):
+    """The widest sphere the tensor-core route takes, K2 = 32 kept z-frequencies (one conduction
+    band per 64-column tile), and one more (K2 = 33), which must fall back to the FFT route:
+    chi against the oracle on both, and the route each took."""
+    import dataclasses
+    from paper_2509_23018_gb300 import _lib
+    p = gwgen.make_problem((48, 48, 48), 6, 10, 900, 200, seed=53)
+    g = np.array([(x, y, z) for z in range(-16, gzmax + 1) for y in (-1, 0, 1) for x in (-1, 0, 1)
+                  if (x, y, z) != (0, 0, 0)], np.int32)
+    p = dataclasses.replace(p, gchi=g)
+    h = gw.from_problem(p, prec="ozaki", nslices=7, mtxel="twofloat")
+    (chi,) = h.compute(0, [0.0])
+    h.sync()
+    M = oracle.m_conv(p.gpsi, p.cv, p.gpsi, p.cc, p.gchi)
+    assert rel(chi[0].cpu().numpy(), oracle.chi0(M, oracle.delta(p.ev, p.ec, 0.0))) < 1e-11
+    if route:
+        Mb = h.pair_elements_block(0, 0, 10).cpu().numpy().reshape(10, 6, -1).transpose(1, 0, 2).reshape(60, -1)
+        h.sync()
+        assert rel(Mb, M) < 1e-12
+    else:
+        with pytest.raises(gw.GwError) as e:
+            h.pair_elements_block(0, 0, 10)
+        assert e.value.status == _lib.GW_ERR_UNSUPPORTED
