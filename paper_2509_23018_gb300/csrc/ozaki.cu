@@ -74,14 +74,11 @@ __global__ void oz_fill_kernel(int *E, int n, int v)
 }
 
 // ------------------------------------------------------------------ split, step 2: slices
-// A block forms the slices of a 64-pair x 32-column tile of M in shared memory, zs[i][j][p]
-// (j = 2 g + {Re, Im}, rows of 64 pairs padded to kOzLD), then writes them out as 128-byte row
-// pieces.  Thread roles: warp w takes tile rows 32 (w & 1) .. + 31 (lane = row: column g = row / 2,
-// component row & 1) and pairs 16 (w >> 1) .. + 15, so a warp reads 32 consecutive doubles of M
-// per pair, and writes each slice's 16 digits of a row as two 16-byte stores; consecutive rows
-// lie 144 bytes apart, so a quarter-warp's stores fall in 8 distinct bank groups.
-constexpr int kOzLD = 72;
-
+// A block forms the slices of a 64-pair x 32-column tile of M and stores them straight into
+// Z[i][j][p] (j = 2 g + {Re, Im}, K-major rows of kpad pairs).  Thread roles: warp w takes tile
+// rows 32 (w & 1) .. + 31 (lane = row: column g = row / 2, component row & 1) and pairs
+// 16 (w >> 1) .. + 15, so a warp reads 32 consecutive doubles of M per pair, and each thread
+// writes each slice's 16 digits of its row as one aligned 32-byte segment (two 16-byte stores).
 struct OzTileThread {
     int row, gl, c, pl0;
 };
@@ -96,9 +93,9 @@ __device__ __forceinline__ OzTileThread oz_tile_thread()
     return t;
 }
 
-// the s slices of the 16 biased integers nb[t] = N_t + bias (pairs pl0 + t of one row) into
-// zs + i plane + [0, 16)
-__device__ __forceinline__ void oz_store_row_digits(const long long nb[16], int s, uint16_t *row, int plane)
+// the s slices of the 16 biased integers nb[t] = N_t + bias (consecutive pairs of one row) into
+// out + i plane + [0, 16)
+__device__ __forceinline__ void oz_store_row_digits(const long long nb[16], int s, __nv_bfloat16 *out, int64_t plane)
 {
     for (int i = 0; i < s; ++i) {
         uint32_t w[8];
@@ -113,7 +110,7 @@ __device__ __forceinline__ void oz_store_row_digits(const long long nb[16], int 
             }
             w[t >> 1] = (uint32_t)d[0] | ((uint32_t)d[1] << 16);
         }
-        uint4 *o = (uint4 *)(row + (int64_t)i * plane);
+        uint4 *o = (uint4 *)(out + i * plane);
         o[0] = make_uint4(w[0], w[1], w[2], w[3]);
         o[1] = make_uint4(w[4], w[5], w[6], w[7]);
     }
@@ -124,37 +121,23 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double2 *__restrict
                                                        const double *__restrict__ spv, const int *__restrict__ E,
                                                        int s, int64_t kpad, __nv_bfloat16 *__restrict__ Z)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint16_t *zs = (uint16_t *)smem; // [s][64 rows j][64 + 8 pairs] (padded)
-    constexpr int LD = kOzLD;
     const int64_t p0 = (int64_t)blockIdx.y * 64;
-    const int g0 = blockIdx.x * 32;
+    const OzTileThread tt = oz_tile_thread();
+    const int g = blockIdx.x * 32 + tt.gl;
+    if (g >= ng) return;
+    // N = round(a 2^(6 s - E)) and its balanced base-64 digits, in integer arithmetic
+    const int sh = kOzBeta * s - E[g];
+    const double *Md = (const double *)M;
     const long long bias = oz_digit_bias(s);
-    {
-        const OzTileThread tt = oz_tile_thread();
-        const int g = g0 + tt.gl;
-        // N = round(a 2^(6 s - E)) and its balanced base-64 digits, in integer arithmetic
-        const int sh = kOzBeta * s - (g < ng ? E[g] : kOzNoColumn);
-        const double *Md = (const double *)M;
-        long long nb[16];
+    long long nb[16];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            const int64_t p = p0 + tt.pl0 + t;
-            const double a = (p < P && g < ng) ? Md[2 * (p * ng + g) + tt.c] * spv[p] : 0.0;
-            nb[t] = oz_round_scaled(a, sh) + bias;
-        }
-        oz_store_row_digits(nb, s, zs + tt.row * LD + tt.pl0, 64 * LD);
+    for (int t = 0; t < 16; ++t) {
+        const int64_t p = p0 + tt.pl0 + t;
+        const double a = p < P ? Md[2 * (p * ng + g) + tt.c] * spv[p] : 0.0;
+        nb[t] = oz_round_scaled(a, sh) + bias;
     }
-    __syncthreads();
-    // rows j = 2 g0 .. 2 g0 + 63 of each slice, 64 consecutive pairs = 128 bytes
-    const int nrows = 2 * ng;
-    for (int e = threadIdx.x; e < s * 64 * 8; e += blockDim.x) {
-        const int i = e / (64 * 8), r = (e >> 3) & 63, v = e & 7;
-        const int j = 2 * g0 + r;
-        if (j >= nrows) continue;
-        const uint4 val = *(const uint4 *)(zs + (i * 64 + r) * LD + v * 8);
-        *(uint4 *)(Z + ((int64_t)i * nrows + j) * kpad + p0 + v * 8) = val;
-    }
+    const int64_t j = 2 * (int64_t)g + tt.c;
+    oz_store_row_digits(nb, s, Z + j * kpad + p0 + tt.pl0, 2 * (int64_t)ng * kpad);
 }
 
 // ------------------------------------------------------------------ split for several frequencies
@@ -205,45 +188,30 @@ __global__ void __launch_bounds__(256) oz_slice_multi_kernel(const double2 *__re
                                                              const int *__restrict__ E, int s, int64_t kpad,
                                                              int64_t zstride, __nv_bfloat16 *__restrict__ Z)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint16_t *zs = (uint16_t *)smem; // [s][64 rows j][64 + 8 pairs] (padded)
-    constexpr int LD = kOzLD;
     const int64_t p0 = (int64_t)blockIdx.y * 64;
-    const int g0 = blockIdx.x * 32;
-    const int nrows = 2 * ng;
-    const long long bias = oz_digit_bias(s);
-    // the thread's part of the block's 64 x 32 tile of M, read once for every frequency
     const OzTileThread tt = oz_tile_thread();
-    const int g = g0 + tt.gl;
+    const int g = blockIdx.x * 32 + tt.gl;
+    if (g >= ng) return;
+    const long long bias = oz_digit_bias(s);
+    // the thread's 16 entries of the block's tile of M, read once for every frequency
     const double *Md = (const double *)M;
     double m[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
         const int64_t p = p0 + tt.pl0 + t;
-        m[t] = (p < P && g < ng) ? Md[2 * (p * ng + g) + tt.c] : 0.0;
+        m[t] = p < P ? Md[2 * (p * ng + g) + tt.c] : 0.0;
     }
+    const int64_t j = 2 * (int64_t)g + tt.c;
     for (int w = 0; w < nw; ++w) {
-        {
-            const int sh = kOzBeta * s - (g < ng ? E[(int64_t)w * ng + g] : kOzNoColumn);
-            long long nb[16];
+        const int sh = kOzBeta * s - E[(int64_t)w * ng + g];
+        long long nb[16];
 #pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int64_t p = p0 + tt.pl0 + t;
-                const double a = (p < P && g < ng) ? m[t] * spv[(int64_t)w * dstride + p] : 0.0;
-                nb[t] = oz_round_scaled(a, sh) + bias;
-            }
-            oz_store_row_digits(nb, s, zs + tt.row * LD + tt.pl0, 64 * LD);
+        for (int t = 0; t < 16; ++t) {
+            const int64_t p = p0 + tt.pl0 + t;
+            const double a = p < P ? m[t] * spv[(int64_t)w * dstride + p] : 0.0;
+            nb[t] = oz_round_scaled(a, sh) + bias;
         }
-        __syncthreads();
-        __nv_bfloat16 *Zw = Z + w * zstride;
-        for (int e = threadIdx.x; e < s * 64 * 8; e += blockDim.x) {
-            const int i = e / (64 * 8), r = (e >> 3) & 63, v = e & 7;
-            const int j = 2 * g0 + r;
-            if (j >= nrows) continue;
-            const uint4 val = *(const uint4 *)(zs + (i * 64 + r) * LD + v * 8);
-            *(uint4 *)(Zw + ((int64_t)i * nrows + j) * kpad + p0 + v * 8) = val;
-        }
-        __syncthreads(); // before the next frequency rewrites zs
+        oz_store_row_digits(nb, s, Z + w * zstride + j * kpad + p0 + tt.pl0, 2 * (int64_t)ng * kpad);
     }
 }
 
@@ -774,10 +742,7 @@ cudaError_t launch_oz_split_multi(const double2 *M, int64_t P, int ng, const dou
         oz_colexp_multi_kernel<<<dim3((ng + 31) / 32, gy), 256, 0, st>>>(M, P, ng, sp, dstride, nw, E);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const size_t sm = (size_t)s * 64 * kOzLD * sizeof(uint16_t);
-    e = cudaFuncSetAttribute(oz_slice_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    oz_slice_multi_kernel<<<dim3((ng + 31) / 32, (unsigned)(kpad / 64)), 256, sm, st>>>(
+    oz_slice_multi_kernel<<<dim3((ng + 31) / 32, (unsigned)(kpad / 64)), 256, 0, st>>>(
         M, P, ng, sp, dstride, nw, E, s, kpad, zstride, (__nv_bfloat16 *)Z);
     return cudaGetLastError();
 }
@@ -785,10 +750,7 @@ cudaError_t launch_oz_split_multi(const double2 *M, int64_t P, int ng, const dou
 cudaError_t launch_oz_slice(const double2 *M, int64_t P, int ng, const double *sp, const int *E, int s,
                             int64_t kpad, void *Z, cudaStream_t st)
 {
-    const size_t sm = (size_t)s * 64 * kOzLD * sizeof(uint16_t);
-    cudaError_t e = cudaFuncSetAttribute(oz_slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    oz_slice_kernel<<<dim3((ng + 31) / 32, (unsigned)(kpad / 64)), 256, sm, st>>>(M, P, ng, sp, E, s, kpad,
+    oz_slice_kernel<<<dim3((ng + 31) / 32, (unsigned)(kpad / 64)), 256, 0, st>>>(M, P, ng, sp, E, s, kpad,
                                                                                   (__nv_bfloat16 *)Z);
     return cudaGetLastError();
 }

@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     unsigned char *sm = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = sm;                               // 3 K-chunks x 48 KB
     unsigned char *sB = sA + 3 * kZdAChunk;               // 2 stages x 24 KB
-    float4 *ring = (float4 *)(sB + 2 * kZdBStage);        // [slots][4][N] conduction line tiles
-    float4 *wt = ring + kZdPsiSlots * 4 * a.n;            // [K2][N] twiddles W^{kz[q] i2}
+    float4 *ring = (float4 *)(sB + 2 * kZdBStage);        // [slots][CT][N] conduction line tiles
+    float4 *wt = ring + kZdPsiSlots * a.CT * a.n;         // [K2][N] twiddles W^{kz[q] i2}
     int2 *ctab = (int2 *)(wt + a.K2 * a.n);               // [32] column pair -> (band, F offset)
     uint64_t *bar = (uint64_t *)(ctab + kZdN / 2);
     uint64_t *aFull = bar, *aEmpty = bar + 1, *bFull = bar + 2, *bEmpty = bar + 4, *tFull = bar + 6,
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                     const uint32_t ps = tile % kZdPsiSlots, pn = tile / kZdPsiSlots;
                     if (!bar_wait(&pEmpty[ps], (pn & 1) ^ 1)) { ok = false; break; }
                     bar_expect(&pFull[ps], pbytes);
-                    tma3(ring + ps * 4 * a.n, &a.tmC, &pFull[ps], 0, l, a.c0 + ct * a.CT);
+                    tma3(ring + ps * a.CT * a.n, &a.tmC, &pFull[ps], 0, l, a.c0 + ct * a.CT);
                 }
             }
             // every load has landed before the block may leave
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                 const uint32_t ps = tile % kZdPsiSlots, pn = tile / kZdPsiSlots;
                 const bool pgot = bar_wait(&pFull[ps], pn & 1);
                 if (!__all_sync(0xffffffffu, pgot)) { ok = false; break; }
-                const float4 *pl = ring + ps * 4 * a.n;
+                const float4 *pl = ring + ps * a.CT * a.n;
                 float4 x[2][3];
                 float sc[2], w[2][kZdSlices];
 #pragma unroll
@@ -472,13 +472,19 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
 
 size_t zd_smem_bytes(int n, int K2)
 {
-    return 1024 + 3 * kZdAChunk + 2 * kZdBStage + 16 * (size_t)kZdPsiSlots * 4 * n + 16 * (size_t)K2 * n +
+    return 1024 + 3 * kZdAChunk + 2 * kZdBStage + 16 * (size_t)kZdPsiSlots * zd_conduction_per_tile_d(K2) * n +
+           16 * (size_t)K2 * n +
            8 * (kZdN / 2) + 8 * 24 + 64;
 }
 
+// The route's shapes: 48-point lines (three K-chunks of 32 real entries), at most 32 kept
+// frequencies (2 K2 real columns of a band within a 64-column tile), and the block's shared
+// memory (valence slices, column stages, ring, twiddle table) within the 227 KB a block may
+// opt into.
 bool zd_supported(int n, int K2, int nv)
 {
-    return n == 48 && K2 >= 1 && 2 * K2 <= kZdN && nv >= 1 && 2 * n == 3 * kZdKC;
+    return n == 48 && K2 >= 1 && 2 * K2 <= kZdN && nv >= 1 && 2 * n == 3 * kZdKC &&
+           zd_smem_bytes(n, K2) <= (size_t)227 * 1024;
 }
 
 int zd_conduction_per_tile(int K2) { return zd_conduction_per_tile_d(K2); }
