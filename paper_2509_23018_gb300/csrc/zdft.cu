@@ -209,7 +209,26 @@ struct ZdArgs {
     float4 *F;              // [lines][R][K2] two-float, R = rows of the chunk = nv * cb, r = cl * nv + v
     int *status;
     int n, nv, c0, cb, K2, CT, nunits, nmt;
+    // work items: units (line, row tile) 0 .. nfull - 1 whole, then each remaining unit split
+    // into nsplit parts by conduction tiles (the last wave of the persistent blocks)
+    int nct, nfull, nsplit, nitems;
 };
+
+// work item -> line l, row tile mt and conduction tiles [ct0, ct1)
+__device__ __forceinline__ void zd_item(const ZdArgs &a, int item, int &l, int &mt, int &ct0, int &ct1)
+{
+    int unit = item, part = 0, np = 1;
+    if (item >= a.nfull) {
+        const int k = item - a.nfull;
+        unit = a.nfull + k / a.nsplit;
+        part = k - (k / a.nsplit) * a.nsplit;
+        np = a.nsplit;
+    }
+    l = unit / a.nmt;
+    mt = unit - l * a.nmt;
+    ct0 = part * a.nct / np;
+    ct1 = (part + 1) * a.nct / np;
+}
 
 __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_constant__ ZdArgs a,
                                                                 const float4 *__restrict__ twf)
@@ -268,7 +287,6 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    const int nct = (a.cb + a.CT - 1) / a.CT; // conduction tiles per unit
     const int ncol = 2 * a.K2;                // real columns per conduction band
     bool ok = true;
 
@@ -277,12 +295,13 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
         if (lane == 0) {
             uint32_t u = 0, tile = 0;
             const unsigned pbytes = (unsigned)a.CT * a.n * 16; // CT lines of N two-float points
-            for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x, ++u) {
-                const int l = unit / a.nmt, mt = unit - l * a.nmt;
+            for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x, ++u) {
+                int l, mt, ct0, ct1;
+                zd_item(a, item, l, mt, ct0, ct1);
                 if (!bar_wait(aEmpty, (u & 1) ^ 1)) { ok = false; break; }
                 bar_expect(aFull, 3 * kZdAChunk);
                 for (int kc = 0; kc < 3; ++kc) tma4(sA + kc * kZdAChunk, &a.tmA, aFull, kc * kZdKC, mt * 128, l, 0);
-                for (int ct = 0; ct < nct && ok; ++ct, ++tile) {
+                for (int ct = ct0; ct < ct1 && ok; ++ct, ++tile) {
                     const uint32_t ps = tile % kZdPsiSlots, pn = tile / kZdPsiSlots;
                     if (!bar_wait(&pEmpty[ps], (pn & 1) ^ 1)) { ok = false; break; }
                     bar_expect(&pFull[ps], pbytes);
@@ -301,9 +320,11 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
             // descriptor address fields count 16-byte units: offsets below 256 KB add in place
             const uint64_t ad0 = sdesc_sw64(su32(sA)), bd0 = sdesc_sw64(su32(sB));
             uint32_t u = 0, it = 0, tile = 0;
-            for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x, ++u) {
+            for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x, ++u) {
+                int l, mt, ct0, ct1;
+                zd_item(a, item, l, mt, ct0, ct1);
                 if (!bar_wait(aFull, u & 1)) { ok = false; break; }
-                for (int ct = 0; ct < nct && ok; ++ct, ++tile) {
+                for (int ct = ct0; ct < ct1 && ok; ++ct, ++tile) {
                     const uint32_t buf = tile & 1;
                     if (!bar_wait(&tEmpty[buf], ((tile >> 1) & 1) ^ 1)) { ok = false; break; }
                     tc_fence_after();
@@ -343,10 +364,11 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
         // ---- epilogue: one tile row (valence band) per thread
         const int q4 = warp & 3, r = q4 * 32 + lane;
         uint32_t tile = 0;
-        for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x) {
-            const int l = unit / a.nmt, mt = unit - l * a.nmt;
+        for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+            int l, mt, ct0, ct1;
+            zd_item(a, item, l, mt, ct0, ct1);
             const int v = mt * 128 + r;
-            for (int ct = 0; ct < nct; ++ct, ++tile) {
+            for (int ct = ct0; ct < ct1; ++ct, ++tile) {
                 // F index of the row's first entry in this tile, and the bands the tile holds
                 const int64_t rowbase = ((int64_t)l * a.cb * a.nv + (int64_t)ct * a.CT * a.nv + v) * a.K2;
                 const int clmax = min(a.CT, a.cb - ct * a.CT);
@@ -397,8 +419,10 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
         const int pw = warp - 6;
         const int ncomb = a.CT * 16; // (cl, k2) combinations, at most 64
         uint32_t it = 0, tile = 0;
-        for (int unit = blockIdx.x; unit < a.nunits && ok; unit += gridDim.x) {
-            for (int ct = 0; ct < nct && ok; ++ct, ++tile) {
+        for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+            int l, mt, ct0, ct1;
+            zd_item(a, item, l, mt, ct0, ct1);
+            for (int ct = ct0; ct < ct1 && ok; ++ct, ++tile) {
                 // the tile's conduction lines, staged by the TMA warp
                 const uint32_t ps = tile % kZdPsiSlots, pn = tile / kZdPsiSlots;
                 const bool pgot = bar_wait(&pFull[ps], pn & 1);
@@ -515,6 +539,13 @@ cudaError_t launch_zd_gemm(const CUtensorMap &tmA, const CUtensorMap &tmC, const
         (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
     const int grid = std::min(a.nunits, sms);
+    // the persistent blocks take items b, b + grid, ...: whole units while every block gets one,
+    // then the rem remaining units in parts, so that the last wave ends evenly
+    a.nct = (cb + a.CT - 1) / a.CT;
+    a.nfull = a.nunits / grid * grid;
+    const int rem = a.nunits - a.nfull;
+    a.nsplit = rem > 0 ? std::max(1, std::min(a.nct, grid / rem)) : 1;
+    a.nitems = a.nfull + rem * a.nsplit;
     zd_gemm_kernel<<<grid, kZdThreads, sm, st>>>(a, twf);
     return cudaGetLastError();
 }
