@@ -117,26 +117,4 @@ __host__ __device__ __forceinline__ void oz_store_digits(long long N, int s, lon
     out[0] = oz_small_bf16((int)(nb >> (6 * (s - 1))));
 }
 
-// val 2^max(-1022, ex) as an FP64 number: the term the split's epilogues add into FP64 results
-// (a slice group's FP32 sum, an exact integer, times the power of two of its scales).  FP64
-// conversions and multiplies run on this part's FP64 pipe, a small fraction of the integer rate,
-// so a normal result's bit pattern is formed with integer operations (exact: the significand of
-// |val| < 2^31 shifted into place, the exponent added); a result outside the normal range takes
-// the FP64 multiply.
-__host__ __device__ __forceinline__ double oz_scaled_int(int val, int ex)
-{
-    const int e = ex < -1022 ? -1022 : ex;
-    if (val == 0) return 0.0;
-    const unsigned n = val < 0 ? 0u - (unsigned)val : (unsigned)val;
-#ifdef __CUDA_ARCH__
-    const int msb = 31 - __clz((int)n);
-#else
-    const int msb = 31 - __builtin_clz(n);
-#endif
-    const int ef = 1023 + msb + e;
-    if (ef < 1 || ef > 2046) return (double)val * oz_bits_d((unsigned long long)(1023 + e) << 52);
-    const unsigned long long mant = ((unsigned long long)(n << (31 - msb)) << 21) & 0xFFFFFFFFFFFFFull;
-    return oz_bits_d(((unsigned long long)(val < 0) << 63) | ((unsigned long long)ef << 52) | mant);
-}
-
 } // namespace gw

@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                                 if (j < jb.rows_b && val != 0) {
                                     const int ex = Ea + __ldg(jb.E2 + (j >> 1)) - kOzBeta * t;
                                     // the tile belongs to this block alone: a plain add
-                                    orow[j] += oz_scaled_int(val, ex);
+                                    orow[j] += (double)val * __longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
                                 }
                             }
                         }
@@ -676,8 +676,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                             const int gp = J * C::BNC + (c0 >> 1) + cc;
                             if (g < ng && gp < ng && g <= gp && val != 0) {
                                 const int ex = Eg + __ldg(jb.E + gp) - kOzBeta * t;
+                                const double sc = -__longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
                                 // atomic: blocks of other pair segments may add into the same entry
-                                atomicAdd(crow + 2 * (int64_t)gp, oz_scaled_int(-val, ex));
+                                atomicAdd(crow + 2 * (int64_t)gp, (double)val * sc);
                             }
                         }
                     }
