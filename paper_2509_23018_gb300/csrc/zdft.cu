@@ -153,10 +153,10 @@ __host__ __device__ __forceinline__ int zd_conduction_per_tile_d(int K2)
 // (128-column tiles with one accumulator buffer, 16-entry column stages and a 32-byte swizzle
 // measured slower: 3.02 against 2.86 ms per 48^3 chunk, the epilogue no longer hidden; a third
 // column stage, room made by smaller ring slots and twiddles from the base table, gained nothing:
-// the producers keep up.)  A 128 x 64 x 16 product reads 4 KB of A and 2 KB of B from shared
-// memory, 48 clocks at 128 bytes per clock against 32 clocks of tensor work: at N = 64 the
-// operand reads bound the pipe (the probe's 128 x 64 rate is 2/3 of its 128 x 128 rate), and
-// four accumulator groups of 64 columns, double-buffered, fill the 512 TMEM columns.
+// the producers keep up.)  A 128 x N x 16 product costs about the same time at N = 64 as at
+// N = 128 (the probe's 128 x 64 rate is 2/3 of its 128 x 128 rate): feeding the 128 x 16 A operand
+// sets the pace, whether A is read from shared memory or from TMEM, and four accumulator groups of
+// 64 columns, double-buffered, fill the 512 TMEM columns.
 //  warp 0: TMA; warp 1: MMA (and TMEM); warps 2..5: epilogue (TMEM lane quadrant warp % 4);
 //  warps 6..11: producers.
 constexpr int kZdN = 64;                               // columns per tile
