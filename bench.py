@@ -297,8 +297,8 @@ TRAFFIC = {
                    "source": "ncu dram__bytes_read+write, pair_kernel_tf_ct<48>, p1_48cube_onechunk"},
     # the tensor-core route of the 48^3 workload: one 8192-pair chunk (128 valence x 64
     # conduction bands), the launch shape the bench's step repeats 16 times
-    "zdft": {"bytes_per_launch": 0.479873e9 + 4.483957e9,
-             "source": "ncu dram__bytes_read+write, zd_gemm_kernel, p2_48cube_chunk"},
+    "zdft": {"bytes_per_launch": 0.477185e9 + 4.482903e9,
+             "source": "ncu dram__bytes_read+write, zd_gemm_kernel (128-column tiles), p2_48cube_chunk"},
     "pair_from_f": {"bytes_per_launch": 5.357752e9 + 1.253676e9,
                     "source": "ncu dram__bytes_read+write, pair_kernel_tf_from_f<48>, p2_48cube_chunk"},
     # the single-stream launch (4-deep TMA ring) the tensor-core route runs

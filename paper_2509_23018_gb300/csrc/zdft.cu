@@ -139,7 +139,7 @@ cudaError_t launch_zd_aslices(const void *psiv, int nv, int n, uint16_t *A, cuda
 
 __host__ __device__ __forceinline__ int zd_conduction_per_tile_d(int K2)
 {
-    const int ct = 64 / (2 * K2);
+    const int ct = 128 / (2 * K2);
     return ct < 4 ? ct : 4;
 }
 
@@ -147,40 +147,49 @@ __host__ __device__ __forceinline__ int zd_conduction_per_tile_d(int K2)
 // One block per SM, persistent over units u = (line l, row tile mt); per unit the block keeps
 // the valence slices of its 128 rows resident (three K-chunks of 32 real entries, TMA) and
 // runs over the conduction tiles ct of the chunk (CT bands, 2 K2 real columns each, padded to
-// 64 columns): producer warps form the tile's column slices per K-chunk into a 2-deep ring,
-// one thread issues the tcgen05 products into four accumulators (two buffers of 4 x 64 TMEM
-// columns alternate between tiles), and the epilogue warps sum the accumulators into F.
-// (128-column tiles with one accumulator buffer, 16-entry column stages and a 32-byte swizzle
-// measured slower: 3.02 against 2.86 ms per 48^3 chunk, the epilogue no longer hidden; a third
-// column stage, room made by smaller ring slots and twiddles from the base table, gained nothing:
-// the producers keep up.)  A 128 x N x 16 product costs about the same time at N = 64 as at
-// N = 128 (the probe's 128 x 64 rate is 2/3 of its 128 x 128 rate): feeding the 128 x 16 A operand
-// sets the pace, whether A is read from shared memory or from TMEM, and four accumulator groups of
-// 64 columns, double-buffered, fill the 512 TMEM columns.
+// 128 columns): producer warps form the tile's column slices in stages of 16 real entries into a
+// 2-deep ring, one thread issues the tcgen05 products into four accumulators of 128 TMEM columns
+// each, and the epilogue warps sum the accumulators into F.  A 128 x N x 16 product costs about
+// the same time at N = 64 as at N = 128 (the probe's 128 x 64 rate is 2/3 of its 128 x 128 rate:
+// feeding the 128 x 16 A operand sets the pace, whether A is read from shared memory or from TMEM),
+// so the tile is 128 columns wide; its four accumulators then fill the 512 TMEM columns and are
+// not double-buffered.  The epilogue hands them back as soon as its last TMEM loads have landed,
+// before that chunk's arithmetic and stores.  (64-column tiles with two accumulator buffers took
+// 2.40 against 2.30 ms per 48^3 chunk; eight epilogue warps of 16-column chunks 2.36 ms; a Re/Im
+// column order without the producers' shared-memory store conflicts 2.34 ms.)
 //  warp 0: TMA; warp 1: MMA (and TMEM); warps 2..5: epilogue (TMEM lane quadrant warp % 4);
 //  warps 6..11: producers.
-constexpr int kZdN = 64;                               // columns per tile
-constexpr int kZdKC = 32;                              // real K entries per K-chunk
+constexpr int kZdN = 128;                              // columns per tile
+constexpr int kZdKC = 32;                              // real K entries per valence K-chunk
+constexpr int kZdKB = 16;                              // real K entries per column stage
+constexpr int kZdStages = 6;                           // column stages per tile (K = 96)
 constexpr int kZdThreads = 384;
 constexpr int kZdProducers = 6;                        // producer warps
 constexpr unsigned kZdASlice = 128 * kZdKC * 2;        // one slice of one K-chunk: 8 KB
 constexpr unsigned kZdAChunk = kZdSlices * kZdASlice;  // 48 KB
-constexpr unsigned kZdBSlice = kZdN * kZdKC * 2;       // 4 KB
+constexpr unsigned kZdBSlice = kZdN * kZdKB * 2;       // 4 KB
 constexpr unsigned kZdBStage = kZdSlices * kZdBSlice;  // 24 KB
-// idesc: D = F32, A = B = BF16, both K-major, N = 64, M = 128
+// idesc: D = F32, A = B = BF16, both K-major, N = 128, M = 128
 constexpr uint32_t kZdIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kZdN >> 3) << 17) |
                               ((uint32_t)(128 >> 4) << 24);
 
-// K-major operand tile with 64-byte swizzling: row r of 64 bytes (32 BF16), 8-row atoms of
-// 512 bytes, 16-byte chunk j of row r stored at chunk j ^ ((r % 8) >> 1).
+// K-major operand tiles.  Valence slices (written by TMA), 64-byte swizzling: row r of 64 bytes
+// (32 BF16), 8-row atoms of 512 bytes, 16-byte chunk j of row r stored at chunk j ^ ((r % 8) >> 1).
+// Column stages (written by the producers), 32-byte swizzling: row r of 32 bytes (16 BF16), 8-row
+// atoms of 256 bytes, chunk j of row r stored at chunk j ^ ((r % 8) >> 2).
 __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr)
 {
     return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
-__device__ __forceinline__ uint32_t sw64_off(int r, int k) // byte offset of element k of row r
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t addr)
 {
-    return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((k >> 3) ^ ((r & 7) >> 1)) & 3) << 4) + (k & 7) * 2);
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
+}
+__device__ __forceinline__ uint32_t sw32_off(int r, int k) // byte offset of element k (< 16) of row r
+{
+    return (uint32_t)((r >> 3) * 256 + (r & 7) * 32 + ((((k >> 3) ^ ((r & 7) >> 2)) & 1) << 4) + (k & 7) * 2);
 }
 
 __device__ __forceinline__ void tma4(void *dst, const CUtensorMap *m, uint64_t *b, int x, int y, int z, int w)
@@ -239,7 +248,7 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     unsigned char *sB = sA + 3 * kZdAChunk;               // 2 stages x 24 KB
     float4 *ring = (float4 *)(sB + 2 * kZdBStage);        // [slots][CT][N] conduction line tiles
     float4 *wt = ring + kZdPsiSlots * a.CT * a.n;         // [K2][N] twiddles W^{kz[q] i2}
-    int2 *ctab = (int2 *)(wt + a.K2 * a.n);               // [32] column pair -> (band, F offset)
+    int2 *ctab = (int2 *)(wt + a.K2 * a.n);               // [64] column pair -> (band, F offset)
     uint64_t *bar = (uint64_t *)(ctab + kZdN / 2);
     uint64_t *aFull = bar, *aEmpty = bar + 1, *bFull = bar + 2, *bEmpty = bar + 4, *tFull = bar + 6,
              *tEmpty = bar + 8, *fin = bar + 10, *pFull = bar + 11, *pEmpty = pFull + kZdPsiSlots;
@@ -259,11 +268,11 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
     {
         // the padding columns of both stages stay zero (their products never reach F)
         const int ncol = 2 * a.K2, npad = kZdN - zd_conduction_per_tile_d(a.K2) * ncol;
-        for (int e = threadIdx.x; e < 2 * kZdSlices * npad * (kZdKC / 2); e += blockDim.x) {
-            const int st = e / (kZdSlices * npad * (kZdKC / 2)), r1 = e % (kZdSlices * npad * (kZdKC / 2));
-            const int sl = r1 / (npad * (kZdKC / 2)), r2 = r1 % (npad * (kZdKC / 2));
-            const int col = kZdN - npad + r2 / (kZdKC / 2), k = 2 * (r2 % (kZdKC / 2));
-            *(uint32_t *)(sB + st * kZdBStage + sl * kZdBSlice + sw64_off(col, k)) = 0u;
+        for (int e = threadIdx.x; e < 2 * kZdSlices * npad * (kZdKB / 2); e += blockDim.x) {
+            const int st = e / (kZdSlices * npad * (kZdKB / 2)), r1 = e % (kZdSlices * npad * (kZdKB / 2));
+            const int sl = r1 / (npad * (kZdKB / 2)), r2 = r1 % (npad * (kZdKB / 2));
+            const int col = kZdN - npad + r2 / (kZdKB / 2), k = 2 * (r2 % (kZdKB / 2));
+            *(uint32_t *)(sB + st * kZdBStage + sl * kZdBSlice + sw32_off(col, k)) = 0u;
         }
     }
     if (threadIdx.x == 0) {
@@ -318,41 +327,38 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
         // ---- MMA issue
         if (lane == 0) {
             // descriptor address fields count 16-byte units: offsets below 256 KB add in place
-            const uint64_t ad0 = sdesc_sw64(su32(sA)), bd0 = sdesc_sw64(su32(sB));
+            const uint64_t ad0 = sdesc_sw64(su32(sA)), bd0 = sdesc_sw32(su32(sB));
             uint32_t u = 0, it = 0, tile = 0;
             for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x, ++u) {
                 int l, mt, ct0, ct1;
                 zd_item(a, item, l, mt, ct0, ct1);
                 if (!bar_wait(aFull, u & 1)) { ok = false; break; }
                 for (int ct = ct0; ct < ct1 && ok; ++ct, ++tile) {
-                    const uint32_t buf = tile & 1;
-                    if (!bar_wait(&tEmpty[buf], ((tile >> 1) & 1) ^ 1)) { ok = false; break; }
+                    if (!bar_wait(&tEmpty[0], (tile & 1) ^ 1)) { ok = false; break; }
                     tc_fence_after();
-                    for (int kc = 0; kc < 3 && ok; ++kc, ++it) {
+                    for (int ks = 0; ks < kZdStages && ok; ++ks, ++it) {
                         const uint32_t st = it & 1;
                         if (!bar_wait(&bFull[st], (it >> 1) & 1)) { ok = false; break; }
                         tc_fence_after();
-                        // the 42 products of the K-chunk, unrolled: descriptors advance by constant
-                        // offsets, and a group's first product of the tile (K-chunk 0, i = 0,
-                        // j = group) starts its accumulator
-                        const uint64_t ad = ad0 + (uint64_t)((kc * kZdAChunk) >> 4);
+                        // the 21 products of the stage, unrolled: A is K-chunk ks / 2 from its
+                        // 32-byte half ks % 2, descriptors advance by constant offsets, and a
+                        // group's first product of the tile (stage 0, i = 0, j = group) starts its
+                        // accumulator
+                        const uint64_t ad = ad0 + (uint64_t)(((ks >> 1) * kZdAChunk + (ks & 1) * 32) >> 4);
                         const uint64_t bd = bd0 + (uint64_t)((st * kZdBStage) >> 4);
-                        const uint32_t dbase = tbase + buf * 256, acc0 = kc > 0 ? 1u : 0u;
+                        const uint32_t acc0 = ks > 0 ? 1u : 0u;
 #pragma unroll
                         for (int i = 0; i < kZdSlices; ++i)
 #pragma unroll
-                            for (int j = 0; j < kZdSlices - i; ++j)
-#pragma unroll
-                                for (int s16 = 0; s16 < 2; ++s16) {
-                                    const int g = i + j < 3 ? i + j : 3;
-                                    const bool first = i == 0 && j <= 3 && s16 == 0;
-                                    umma_f16(dbase + g * kZdN, ad + (uint64_t)((i * kZdASlice + s16 * 32) >> 4),
-                                             bd + (uint64_t)((j * kZdBSlice + s16 * 32) >> 4), kZdIdesc,
-                                             first ? acc0 : 1u);
-                                }
+                            for (int j = 0; j < kZdSlices - i; ++j) {
+                                const int g = i + j < 3 ? i + j : 3;
+                                const bool first = i == 0 && j <= 3;
+                                umma_f16(tbase + g * kZdN, ad + (uint64_t)((i * kZdASlice) >> 4),
+                                         bd + (uint64_t)((j * kZdBSlice) >> 4), kZdIdesc, first ? acc0 : 1u);
+                            }
                         umma_commit(&bEmpty[st]);
                     }
-                    umma_commit(&tFull[buf]);
+                    umma_commit(&tFull[0]);
                 }
                 umma_commit(aEmpty);
             }
@@ -372,19 +378,24 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                 // F index of the row's first entry in this tile, and the bands the tile holds
                 const int64_t rowbase = ((int64_t)l * a.cb * a.nv + (int64_t)ct * a.CT * a.nv + v) * a.K2;
                 const int clmax = min(a.CT, a.cb - ct * a.CT);
-                const uint32_t buf = tile & 1;
-                const bool got = bar_wait(&tFull[buf], (tile >> 1) & 1);
+                const bool got = bar_wait(&tFull[0], tile & 1);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t ta = tbase + ((uint32_t)(q4 * 32) << 16) + buf * 256;
+                const uint32_t ta = tbase + ((uint32_t)(q4 * 32) << 16);
+                const int cend = a.CT * ncol; // columns holding bands
 #pragma unroll 1
-                for (int c0 = 0; c0 < kZdN; c0 += 32) {
+                for (int c0 = 0; c0 < cend; c0 += 32) {
                     uint32_t g0[32], g1[32], g2[32], g3[32];
                     GW_TMEM_LD32(ta + 0 * kZdN + c0, g0);
                     GW_TMEM_LD32(ta + 1 * kZdN + c0, g1);
                     GW_TMEM_LD32(ta + 2 * kZdN + c0, g2);
                     GW_TMEM_LD32(ta + 3 * kZdN + c0, g3);
                     tmem_wait_ld();
+                    if (c0 + 32 >= cend) {
+                        // the accumulators are in registers: the next tile's products may start
+                        tc_fence_before();
+                        bar_arrive(&tEmpty[0]);
+                    }
                     if (v < a.nv) {
 #pragma unroll
                         for (int cc = 0; cc < 32; cc += 2) {
@@ -407,17 +418,16 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                         }
                     }
                 }
-                tc_fence_before();
-                bar_arrive(&tEmpty[buf]);
             }
         }
         if (!ok && lane == 0) atomicOr(a.status, kStatusTimeout);
     } else {
-        // ---- producers: column slices of the conduction tile, K-chunk by K-chunk.  A lane owns
-        // the points (cl, i2 = 16 kc + k2) of one or two (cl, k2) combinations, loaded once per
-        // tile for the three K-chunks; producer warp pw forms the frequencies q = pw, pw + 6, ...
+        // ---- producers: column slices of the conduction tile, stage by stage.  Lane (cl, k2) =
+        // (lane / 8, lane % 8) owns the points i2 = 8 ks + k2 of band cl, loaded once per tile for
+        // the six stages; producer warp pw forms the frequencies q = pw, pw + 6, ...
         const int pw = warp - 6;
-        const int ncomb = a.CT * 16; // (cl, k2) combinations, at most 64
+        const int ncomb = a.CT * 8; // lanes holding a band (CT <= 4)
+        const int cl = lane >> 3, k2 = lane & 7;
         uint32_t it = 0, tile = 0;
         for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
             int l, mt, ct0, ct1;
@@ -428,50 +438,42 @@ __global__ void __launch_bounds__(kZdThreads, 1) zd_gemm_kernel(const __grid_con
                 const bool pgot = bar_wait(&pFull[ps], pn & 1);
                 if (!__all_sync(0xffffffffu, pgot)) { ok = false; break; }
                 const float4 *pl = ring + ps * a.CT * a.n;
-                float4 x[2][3];
-                float sc[2], w[2][kZdSlices];
+                const int c = ct * a.CT + cl;
+                float4 x[kZdStages];
+                float m = 0.0f;
 #pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const int comb = lane + 32 * h2;
-                    const int cl = comb >> 4, k2 = comb & 15, c = ct * a.CT + cl;
-                    float m = 0.0f;
-#pragma unroll
-                    for (int kc = 0; kc < 3; ++kc) {
-                        x[h2][kc] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (comb < ncomb && c < a.cb) x[h2][kc] = pl[cl * a.n + kc * 16 + k2];
-                        m = fmaxf(m, (fabsf(x[h2][kc].x) + fabsf(x[h2][kc].z)) * (1.0f + 0x1p-20f));
-                    }
-                    // the 16 lanes of one band hold its whole line: the band's maximum
-                    for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                    const int E = max(-70, zd_expo(m)); // keeps the scale and every weight normal
-                    sc[h2] = __int_as_float((127 + 47 - E) << 23);
-#pragma unroll
-                    for (int i = 0; i < kZdSlices; ++i) w[h2][i] = __int_as_float((127 + E - 7 - 8 * i) << 23);
+                for (int ks = 0; ks < kZdStages; ++ks) {
+                    x[ks] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (lane < ncomb && c < a.cb) x[ks] = pl[cl * a.n + ks * 8 + k2];
+                    m = fmaxf(m, (fabsf(x[ks].x) + fabsf(x[ks].z)) * (1.0f + 0x1p-20f));
                 }
+                // the 8 lanes of one band hold its whole line: the band's maximum
+                for (int o = 4; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                const int E = max(-70, zd_expo(m)); // keeps the scale and every weight normal
+                const float sc = __int_as_float((127 + 47 - E) << 23);
+                float w[kZdSlices];
+#pragma unroll
+                for (int i = 0; i < kZdSlices; ++i) w[i] = __int_as_float((127 + E - 7 - 8 * i) << 23);
                 __syncwarp();
                 if (lane == 0) bar_arrive(&pEmpty[ps]); // the slot's values are in registers
 #pragma unroll
-                for (int kc = 0; kc < 3; ++kc, ++it) {
+                for (int ks = 0; ks < kZdStages; ++ks, ++it) {
                     if (!ok) continue;
                     const uint32_t st = it & 1;
                     const bool got = bar_wait(&bEmpty[st], ((it >> 1) & 1) ^ 1);
                     if (!__all_sync(0xffffffffu, got)) { ok = false; continue; } // warp-uniform exit
                     unsigned char *B = sB + st * kZdBStage;
-#pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int comb = lane + 32 * h2;
-                        if (comb >= ncomb) continue;
-                        const int cl = comb >> 4, k2 = comb & 15;
-                        const tcx xv = {{x[h2][kc].x, x[h2][kc].y}, {x[h2][kc].z, x[h2][kc].w}};
-                        const float4 *wrow = wt + kc * 16 + k2;
+                    if (lane < ncomb) {
+                        const tcx xv = {{x[ks].x, x[ks].y}, {x[ks].z, x[ks].w}};
+                        const float4 *wrow = wt + ks * 8 + k2;
                         for (int q = pw; q < a.K2; q += kZdProducers) {
                             const tcx b = tc_mul(xv, tc_load(wrow + q * a.n));
                             uint16_t dr[kZdSlices], di[kZdSlices];
-                            zd_digits_w(b.re.hi, b.re.lo, sc[h2], w[h2], dr);
-                            zd_digits_w(b.im.hi, b.im.lo, sc[h2], w[h2], di);
+                            zd_digits_w(b.re.hi, b.re.lo, sc, w, dr);
+                            zd_digits_w(b.im.hi, b.im.lo, sc, w, di);
                             const int colr = cl * ncol + 2 * q;
                             if (!GW_IN(colr + 1, kZdN, a.status)) continue;
-                            unsigned char *pr = B + sw64_off(colr, 2 * k2), *pi = B + sw64_off(colr + 1, 2 * k2);
+                            unsigned char *pr = B + sw32_off(colr, 2 * k2), *pi = B + sw32_off(colr + 1, 2 * k2);
 #pragma unroll
                             for (int sl = 0; sl < kZdSlices; ++sl) {
                                 // Re column: (Re b, Im b); Im column: (Im b, -Re b)
@@ -501,13 +503,12 @@ size_t zd_smem_bytes(int n, int K2)
            8 * (kZdN / 2) + 8 * 24 + 64;
 }
 
-// The route's shapes: 48-point lines (three K-chunks of 32 real entries), at most 32 kept
-// frequencies (2 K2 real columns of a band within a 64-column tile), and the block's shared
-// memory (valence slices, column stages, ring, twiddle table) within the 227 KB a block may
-// opt into.
+// The route's shapes: 48-point lines (three valence K-chunks of 32 real entries, six column
+// stages of 16), at most 32 kept frequencies, and the block's shared memory (valence slices,
+// column stages, ring, twiddle table) within the 227 KB a block may opt into.
 bool zd_supported(int n, int K2, int nv)
 {
-    return n == 48 && K2 >= 1 && 2 * K2 <= kZdN && nv >= 1 && 2 * n == 3 * kZdKC &&
+    return n == 48 && K2 >= 1 && K2 <= 32 && nv >= 1 && 2 * n == 3 * kZdKC && 2 * n == kZdStages * kZdKB &&
            zd_smem_bytes(n, K2) <= (size_t)227 * 1024;
 }
 
