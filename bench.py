@@ -302,10 +302,10 @@ TRAFFIC = {
     "pair_from_f": {"bytes_per_launch": 5.357752e9 + 1.253676e9,
                     "source": "ncu dram__bytes_read+write, pair_kernel_tf_from_f<48>, p2_48cube_chunk"},
     # the single-stream launch (4-deep TMA ring) the tensor-core route runs
-    "ozaki_gemm": {"bytes_per_launch": 7.620381e9 + 0.217023e9,
-                   "source": "ncu dram__bytes_read+write, oz_gemm_kernel<256,0,4> (s = 7), p2_48cube_chunk"},
-    "ozaki_gemm_single_stream": {"bytes_per_launch": 7.620381e9 + 0.217023e9,
-                                 "source": "ncu dram__bytes_read+write, oz_gemm_kernel<256,0,4> (s = 7), "
+    "ozaki_gemm": {"bytes_per_launch": 5.176667e9 + 0.212558e9,
+                   "source": "ncu dram__bytes_read+write, oz_gemm_kernel<240,0,4> (s = 7), p2_48cube_chunk"},
+    "ozaki_gemm_single_stream": {"bytes_per_launch": 5.176667e9 + 0.212558e9,
+                                 "source": "ncu dram__bytes_read+write, oz_gemm_kernel<240,0,4> (s = 7), "
                                            "p2_48cube_chunk"},
 }
 

@@ -162,7 +162,7 @@ GW_API gw_status gw_chi0_compute(gw_chi0 *h, int nq, const int *iq, int nw, cons
  * block first.  The whole sequence is captured once per call signature (slots, sphere
  * sizes, frequencies, output pointers) into a CUDA graph and replayed on later calls.
  * On the first call of a problem shape an autotuner times the contraction's launch-shape
- * candidates (FP64 tile edge 32/64 and wave count; split-precision tile width 128/256
+ * candidates (FP64 tile edge 32/64 and wave count; split-precision tile width 128/240/256
  * columns) and keeps the fastest for the handle (see gw_chi0_tuning).  The first call
  * synchronises the stream; replays are asynchronous.  Slots must be distinct.
  * Errors: as gw_chi0_compute; GW_ERR_OOM when the resident buffers do not fit.
@@ -172,7 +172,9 @@ GW_API gw_status gw_chi0_compute_batch(gw_chi0 *h, int nq, const int *iq, int nw
 
 /*
  * Launch shapes in use (chosen by the autotuner of gw_chi0_compute_batch, or defaults):
- * FP64 tile edge (complex), FP64 waves, split-precision tile width (real columns).
+ * FP64 tile edge (complex), FP64 waves, split-precision tile width (real columns; 256 before
+ * tuning, when each contraction instead takes 240 or 256 columns by which fills the SMs' waves
+ * better).
  * Returns the number of problem shapes tuned so far.  Any pointer may be NULL.
  */
 GW_API int gw_chi0_tuning(const gw_chi0 *h, int *tile_f64, int *waves_f64, int *tile_split);

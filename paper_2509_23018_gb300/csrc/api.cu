@@ -256,6 +256,8 @@ gw_status make_tmap_z(gw_chi0 *h, CUtensorMap *map, void *Z, int64_t kpad, int n
     return GW_OK;
 }
 
+int contraction_bn(const gw_chi0 *h, int ng) { return h->bn_tuned ? h->tuned_bn : gw::oz_pick_bn(ng, num_sms()); }
+
 gw_status oz_job(gw_chi0 *h, gw::OzJob &j, void *Z, int64_t kpad, int ng, const int *E, double2 *chi, int bn)
 {
     std::memset(&j, 0, sizeof j);
@@ -317,7 +319,7 @@ gw_status contract_chunk_ozaki(gw_chi0 *h, const double2 *M, int64_t P, int ng, 
         Scope sc(h, "oz_split");
         CK(h, gw::launch_oz_sqrt(delta, (int64_t)nw * dstride, h->spbuf, h->st), "oz sqrt");
     }
-    const int bn = h->tuned_bn;
+    const int bn = contraction_bn(h, ng);
     for (int w0 = 0; w0 < nw; w0 += wg) {
         const int cnt = std::min(wg, nw - w0);
         const double *sp = h->spbuf + (int64_t)w0 * dstride;
@@ -608,7 +610,7 @@ bool overlap_enabled(gw_chi0 *h, const gw::PairPlan &pp)
         cudaGetLastError();
         return false;
     }
-    const size_t gs = gw::oz_smem_bytes(h->tuned_bn, 2);
+    const size_t gs = std::max(gw::oz_smem_bytes(256, 2), gw::oz_smem_bytes(h->tuned_bn, 2));
     return 2 * (ps + (size_t)resv) + gs + (size_t)resv <= (size_t)sm_bytes;
 }
 
@@ -649,7 +651,7 @@ gw_status compute_overlap(gw_chi0 *h, int iq, const gw::OmegaList &om, double2 *
             (st = grow(h, &h->ovJ[b], &h->ovJcap[b], sizeof(gw::OzJob) * 256, "job table")))
             return st;
     if ((st = ensure_overlap_stream(h))) return st;
-    const int bn = h->tuned_bn;
+    const int bn = contraction_bn(h, ng);
     gw::PairPlan pp = pair_plan(h, sp);
     bool used[2] = {false, false};
     int64_t j = 0;

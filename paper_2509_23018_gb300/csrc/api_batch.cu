@@ -156,6 +156,7 @@ gw_status batch_autotune(gw_chi0 *h, int nq, const int *iq, int nw, const gw::Om
         h->tuned_bt = it->second[0];
         h->tuned_waves = it->second[1];
         h->tuned_bn = it->second[2];
+        h->bn_tuned = h->d.prec != GW_PREC_FP64;
         return GW_OK;
     }
     gw_status s = batch_stage_a(h, nq, iq, om, L);
@@ -184,7 +185,7 @@ gw_status batch_autotune(gw_chi0 *h, int nq, const int *iq, int nw, const gw::Om
                 }
             }
     } else if (!(s = batch_oz_split(h, nq, 0, L))) {
-        for (int bn : {256, 128}) {
+        for (int bn : {256, 240, 128}) {
             std::vector<gw::OzJob> jobs;
             if ((s = batch_oz_jobs(h, nq, 0, L, chi, bn, jobs))) break;
             cudaEventRecord(e0, h->st);
@@ -207,6 +208,7 @@ gw_status batch_autotune(gw_chi0 *h, int nq, const int *iq, int nw, const gw::Om
     h->tuned_bt = pick[0];
     h->tuned_waves = pick[1];
     h->tuned_bn = pick[2];
+    h->bn_tuned = h->d.prec != GW_PREC_FP64;
     return GW_OK;
 }
 

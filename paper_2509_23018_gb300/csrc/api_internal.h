@@ -90,6 +90,7 @@ struct gw_chi0 {
     size_t jobcap = 0;
     // contraction launch shapes (set by the autotuner; these are the defaults)
     int tuned_bt = 64, tuned_waves = 4, tuned_bn = 256;
+    bool bn_tuned = false; // tuned_bn set by the autotuner (else the width follows the wave count)
     std::map<std::string, std::array<int, 3>> tune_cache; // signature -> (bt, waves, bn)
     // batched path: every slot's M resident, one graph per call signature
     double2 *Mall = nullptr;
@@ -217,6 +218,7 @@ void drain_timing(gw_chi0 *h);
 gw_status ensure_work(gw_chi0 *h, size_t m_elems, size_t d_elems);
 gw_status make_tmap(gw_chi0 *h, CUtensorMap *map, const void *M, int64_t P, int ng, int bt);
 int num_sms();
+int contraction_bn(const gw_chi0 *h, int ng); // split-precision tile width: tuned, else by the wave count
 void drop_graphs(gw_chi0 *h);
 gw_status grow(gw_chi0 *h, void **p, size_t *cap, size_t bytes, const char *what);
 gw_status upload_jobs(gw_chi0 *h, const void *src, size_t bytes, const void **dev);

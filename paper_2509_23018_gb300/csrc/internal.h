@@ -160,6 +160,7 @@ struct __align__(128) OzJob {
 cudaError_t launch_oz_gemm_jobs(int bn, const OzJob *jobs, int njobs, int nitems, int grid, int *status,
                                 cudaStream_t st, int stages = 4);
 int oz_tiles(int ng, int bn);
+int oz_pick_bn(int ng, int nsm); // tile width (240 or 256) by the wave count, without a tuned value
 // General split product: Y[rows][nout] (complex, row-major, overwritten) = A[rows][ka] B[ka][nout]
 // (complex, row-major), A split by rows and B by columns into s six-bit BF16 slices.
 // ZA: s * rows * kpad bf16, ZB: s * 2 nout * kpad bf16, EA: rows ints, EB: nout ints,

@@ -456,16 +456,18 @@ __global__ void __launch_bounds__(256, NE > 4 ? 3 : 4) gpp_prep_split_kernel(con
 // for one chi block, each with its own N_G, tensor maps and exponents) and the list of
 // their upper tiles; block b takes items b, b + gridDim.x, ... in the same order in every
 // role, so the TMA producer warp, the MMA warp and the epilogue warps need no exchange
-// beyond the mbarriers.  The tile width BN (128 or 256 real columns) is chosen by the
-// autotuner; two BN-column FP32 accumulators in TMEM alternate between slice groups so the
-// epilogue of group t overlaps the MMAs of group t+1.
+// beyond the mbarriers.  The tile width BN (128, 240 or 256 real columns) is chosen by the
+// autotuner or by the wave count (oz_pick_bn); two BN-column FP32 accumulators in TMEM alternate
+// between slice groups so the epilogue of group t overlaps the MMAs of group t+1.  At BN = 240 the
+// accumulators sit 256 columns apart and the epilogue's last 32-column chunk is cut at BN.
 template <int BN, int ST = kOzStages>
 struct OzCfg {
     static constexpr int Stages = ST;                        // TMA ring depth
     static constexpr int BM = kOzBM;
     static constexpr int BNC = BN / 2;                       // complex columns per tile
     static constexpr unsigned ABytes = kOzBM * kOzBK * 2, BBytes = BN * kOzBK * 2;
-    static constexpr uint32_t TmemCols = 2 * BN;             // 256 or 512
+    static constexpr uint32_t TmemBuf = BN > 128 ? 256 : 128; // TMEM columns per accumulator buffer
+    static constexpr uint32_t TmemCols = 2 * TmemBuf;        // 256 or 512 (a power of two)
     // idesc: D = F32, A = B = BF16, both K-major, N = BN, M = 128
     static constexpr uint32_t Idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(kOzBM >> 4) << 24);
@@ -580,7 +582,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                     const uint32_t b = grp & 1, u = grp >> 1;
                     if (!bar_wait(&tempty[b], (u & 1) ^ 1)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t d = tbase + b * BN;
+                    const uint32_t d = tbase + b * C::TmemBuf;
                     bool first = true;
                     for (int i = 1; i < t && ok; ++i)
                         for (int kb = k0; kb < min(jb.nk, k0 + kOzKSeg); ++kb, ++it) {
@@ -622,7 +624,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                     const bool got = bar_wait(&tfull[b], u & 1);
                     if (!__all_sync(0xffffffffu, got)) { ok = false; break; } // warp-uniform exit
                     tc_fence_after();
-                    const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * BN;
+                    const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * C::TmemBuf;
 #pragma unroll 1
                     for (int c0 = 0; c0 < BN; c0 += 32) {
                         uint32_t v[32];
@@ -633,7 +635,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                             for (int cc = 0; cc < 32; ++cc) {
                                 const int j = J * BN + c0 + cc; // output real column
                                 const int val = (int)__uint_as_float(v[cc]);
-                                if (j < jb.rows_b && val != 0) {
+                                if ((BN % 32 == 0 || c0 + cc < BN) && j < jb.rows_b && val != 0) {
                                     const int ex = Ea + __ldg(jb.E2 + (j >> 1)) - kOzBeta * t;
                                     // the tile belongs to this block alone: a plain add
                                     orow[j] += (double)val * __longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
@@ -661,7 +663,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                     const bool got = bar_wait(&tfull[b], u & 1);
                     if (!__all_sync(0xffffffffu, got)) { ok = false; break; } // warp-uniform exit
                     tc_fence_after();
-                    const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * BN;
+                    const uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + b * C::TmemBuf;
 #pragma unroll 1
                     for (int c0 = 0; c0 < BN; c0 += 32) {
                         uint32_t v[32];
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzJob *__r
                             const int rv = __shfl_xor_sync(0xffffffffu, od, 1);
                             const int val = odd ? (rv - ev) : (ev + rv);
                             const int gp = J * C::BNC + (c0 >> 1) + cc;
-                            if (g < ng && gp < ng && g <= gp && val != 0) {
+                            if ((BN % 32 == 0 || (c0 >> 1) + cc < C::BNC) && g < ng && gp < ng && g <= gp && val != 0) {
                                 const int ex = Eg + __ldg(jb.E + gp) - kOzBeta * t;
                                 const double sc = -__longlong_as_double((long long)(1023 + max(-1022, ex)) << 52);
                                 // atomic: blocks of other pair segments may add into the same entry
@@ -707,8 +709,26 @@ int oz_tiles(int ng, int bn)
 
 size_t oz_smem_bytes(int bn, int stages)
 {
-    if (stages == 2) return bn == 128 ? OzCfg<128, 2>::Smem : OzCfg<256, 2>::Smem;
-    return bn == 128 ? OzCfg<128>::Smem : OzCfg<256>::Smem;
+    if (stages == 2) return bn == 128 ? OzCfg<128, 2>::Smem : bn == 240 ? OzCfg<240, 2>::Smem : OzCfg<256, 2>::Smem;
+    return bn == 128 ? OzCfg<128>::Smem : bn == 240 ? OzCfg<240>::Smem : OzCfg<256>::Smem;
+}
+
+// Tile width of the Hermitian contraction without a tuned value: 240 or 256 real columns,
+// whichever leaves less work on the busiest SM (tiles per SM rounded up, times the width).  At
+// N_G = 2000 on 152 SMs, 294 tiles of 240 fill two waves to 97 % where 272 tiles of 256 fill them
+// to 89 %.
+int oz_pick_bn(int ng, int nsm)
+{
+    int best = 256;
+    long long bestw = 0;
+    for (int bn : {256, 240}) {
+        const long long w = (long long)((oz_tiles(ng, bn) + nsm - 1) / nsm) * bn;
+        if (bn == 256 || w < bestw) {
+            best = bn;
+            bestw = w;
+        }
+    }
+    return best;
 }
 
 cudaError_t launch_oz_sqrt(const double *delta, int64_t n, double *sp, cudaStream_t st)
@@ -770,21 +790,12 @@ cudaError_t launch_oz_gemm_jobs(int bn, const OzJob *jobs, int njobs, int nitems
 {
     if (nitems == 0) return cudaSuccess;
     if (stages == 2)
-        return bn == 128 ? launch_oz_chi<128, 2>(jobs, njobs, nitems, grid, status, st)
-                         : launch_oz_chi<256, 2>(jobs, njobs, nitems, grid, status, st);
-    cudaError_t e;
-    if (bn == 128) {
-        e = cudaFuncSetAttribute(oz_gemm_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)OzCfg<128>::Smem);
-        if (e != cudaSuccess) return e;
-        oz_gemm_kernel<128, false><<<grid, kOzThreads, OzCfg<128>::Smem, st>>>(jobs, njobs, nitems, status);
-    } else {
-        e = cudaFuncSetAttribute(oz_gemm_kernel<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)OzCfg<256>::Smem);
-        if (e != cudaSuccess) return e;
-        oz_gemm_kernel<256, false><<<grid, kOzThreads, OzCfg<256>::Smem, st>>>(jobs, njobs, nitems, status);
-    }
-    return cudaGetLastError();
+        return bn == 128   ? launch_oz_chi<128, 2>(jobs, njobs, nitems, grid, status, st)
+               : bn == 240 ? launch_oz_chi<240, 2>(jobs, njobs, nitems, grid, status, st)
+                           : launch_oz_chi<256, 2>(jobs, njobs, nitems, grid, status, st);
+    return bn == 128   ? launch_oz_chi<128, kOzStages>(jobs, njobs, nitems, grid, status, st)
+           : bn == 240 ? launch_oz_chi<240, kOzStages>(jobs, njobs, nitems, grid, status, st)
+                       : launch_oz_chi<256, kOzStages>(jobs, njobs, nitems, grid, status, st);
 }
 
 cudaError_t launch_oz_split_rows(const double2 *A, int64_t rows, int ka, int s, int64_t kpad, void *ZA, int *EA,
