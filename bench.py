@@ -642,12 +642,12 @@ def method_stage_a(cfg):
     return float(nbytes), float(flops)
 
 
-ZD_SLICES, ZD_TILE_N, ZD_TILE_M = 6, 64, 128
+ZD_SLICES, ZD_TILE_N, ZD_TILE_M = 6, 128, 128
 
 
 def zd_ops(cfg, prob):
     """Work of stage (a) on the tensor-core route per chunk: the low-precision flops the last-axis
-    split product executes (21 kept slice products of 128 x 64 x 2N tiles, padding included) and
+    split product executes (21 kept slice products of 128 x 128 x 2N tiles, padding included) and
     the useful share, and the FP32 operations of the middle/first-axis kernel per pair."""
     n0, n1, n2 = cfg.grid
     k2 = kept_columns(prob, n2)
@@ -678,7 +678,7 @@ def roofline_zd(cfg, prob, res):
                        "traffic_source": traffic_for("zdft", cfg)[1], "launches": kn,
                        "ms_per_launch": kms / kn, "flops_per_launch": flops, "useful_share": useful / flops,
                        "peak_source": src, "share_of_step": kms / res["total_ms"],
-                       "unit_of_work": "BF16 flops of the 21 kept slice products (128 x 64 tiles, K = 2N)"}
+                       "unit_of_work": "BF16 flops of the 21 kept slice products (128 x 128 tiles, K = 2N)"}
     kms2, kn2 = res["timing"].get("pair_from_f", (0.0, 0))
     if kn2:
         peak, src = fp32_lane_peak()
