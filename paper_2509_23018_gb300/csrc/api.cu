@@ -584,8 +584,20 @@ gw_status zd_stage_a(gw_chi0 *h, int iq, const CUtensorMap &tmA, const CUtensorM
                                  h->status, h->st),
            "last-axis transform");
     }
+    // F as [n^2 lines][R K2] two-float entries: the middle/first-axis kernel loads a slab pair's
+    // 2n lines of one row (K2 entries each) with one TMA box
+    const int64_t R = (int64_t)v.nb * cb;
+    CUtensorMap tmF;
+    cuuint64_t fd[2] = {(cuuint64_t)R * sp.K2 * 4, (cuuint64_t)n * n};
+    cuuint64_t fst[1] = {(cuuint64_t)R * sp.K2 * 16};
+    cuuint32_t fbox[2] = {(cuuint32_t)(sp.K2 * 4), (cuuint32_t)(2 * n)};
+    cuuint32_t fes[2] = {1, 1};
+    CUresult r = h->encode(&tmF, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->zdF, fd, fst, fbox, fes,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, GW_ERR_CUDA, "cuTensorMapEncodeTiled (last-axis output) failed (%d)", (int)r);
     Scope sc(h, "pair_from_f");
-    CK(h, gw::launch_pair_tf_from_f(h->zdF, (int64_t)v.nb * cb, pp, M, h->st), "pair elements from F");
+    CK(h, gw::launch_pair_tf_from_f(tmF, R, pp, M, h->st), "pair elements from F");
     return GW_OK;
 }
 

@@ -4,6 +4,7 @@
 #pragma once
 #include "internal.h"
 #include "fft_tf.cuh"
+#include "ptx.cuh"
 
 namespace gw {
 
@@ -301,8 +302,11 @@ inline bool pair_tf_ct_fits(const PairPlan &pp)
 // transforms the 2 K2 columns of slabs i0 and i0 + 1 (F[i0 N + i1][r][q], the kept last-axis
 // frequencies of every line) along i1 at once, two butterflies per thread per stage, and stores
 // the K12 cells of each slab in its scratch slot.  Two buffers alternate: the i1 stages run X -> Y
-// -> X, after which Y is free and receives the next pair of slabs (cp.async) while the pruned
-// stage reads X; the next step starts from Y.  Phase 2 is that of pair_kernel_tf_ct.
+// -> X, after which Y is free and receives the next pair of slabs while the pruned stage reads X;
+// the next step starts from Y.  A slab pair's F arrives by one TMA load (tensor map over F as
+// [lines][R K2] two-float entries, box of 2N lines x K2 entries) in line-major order, which the
+// first i1 stage reads directly (tstage0_rows); every later stage works on the column layout.
+// Phase 2 is that of pair_kernel_tf_ct.
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -347,26 +351,69 @@ __device__ __forceinline__ float4 ld_hint(const float4 *p, uint64_t pol)
     return v;
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void tma2_hint(void *dst, const CUtensorMap *m, uint64_t *b, int x, int y, uint64_t pol)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+                 "{%2, %3}], [%4], %5;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(m), "r"(x), "r"(y), "r"((uint32_t)__cvta_generic_to_shared(b)), "l"(pol)
+                 : "memory");
+}
+
+// First stage of the slab pair's i1 transform (lazy radix 4, no twiddles: make_prune_plan(N)'s
+// stage 0) from the line-major F rows, x[(sl N + i1) K2 + q], into the column layout y[l CS + k]
+// of column l = sl K2 + q; lines fastest over the threads (lm)
+template <int N>
+__device__ __forceinline__ void tstage0_rows(const float4 *__restrict__ x, float4 *__restrict__ y, int K2, int ncols,
+                                             int CS, LMap lm)
+{
+    constexpr int R = make_prune_plan(N).r[0], nb = N / R;
+    static_assert(R == 4, "the first stage is radix 4");
+    int l = lm.l0, j = lm.j0;
+    while (j < nb) {
+        const int sl = l >= K2 ? 1 : 0;
+        const float4 *xl = x + sl * N * K2 + (l - sl * K2);
+        tcx v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + (j + r * nb) * K2);
+        tdft4<false>(v);
+        float4 *yl = y + l * CS + j * R;
+#pragma unroll
+        for (int r = 0; r < R; ++r) tc_store(yl + r, v[r]);
+        l += lm.dl;
+        j += lm.dj;
+        if (l >= ncols) {
+            l -= ncols;
+            ++j;
+        }
+    }
+}
+
+// buffer of a slab pair's columns, in float4, rounded to 128 bytes (TMA destinations)
+__host__ __device__ constexpr int from_f_buf(int ncols, int cs) { return (ncols * cs + 7) / 8 * 8; }
 
 template <int N>
 __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
-    pair_kernel_tf_from_f(const float4 *__restrict__ F, int64_t R, PairPlan pp, TfConsts kc, tf inv_nr,
+    pair_kernel_tf_from_f(const __grid_constant__ CUtensorMap tmF, int64_t R, PairPlan pp, TfConsts kc, tf inv_nr,
                           double2 *__restrict__ M)
 {
     static_assert(N % 2 == 0, "slabs go in pairs");
     static_assert(make_prune_plan(N).nst == 3, "two full i1 stages: the result returns to the input buffer");
     constexpr int NT = pair_threads<N>();
     constexpr int CS = N + 1;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int slot_s;
+    __shared__ uint64_t fbar; // a slab pair's F has landed
     const int K2 = pp.K2, K12 = pp.K12;
     const int ncols = 2 * K2;                  // columns of a slab pair
-    float4 *Xb = (float4 *)smem;               // [2][ncols][CS]
-    float4 *tw = Xb + 2 * ncols * CS;
+    const int BUF = from_f_buf(ncols, CS);
+    float4 *Xb = (float4 *)(((uintptr_t)smraw + 127) & ~(uintptr_t)127); // [2][BUF]
+    float4 *tw = Xb + 2 * BUF;
     int *cell = (int *)(tw + N);
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = pp.ax[0].twf[i];
     for (int i = threadIdx.x; i < K12; i += NT) cell[i] = pp.cell[i];
     if (threadIdx.x == 0) {
+        bar_init(&fbar, 1);
+        bar_fence_init();
         int got = -1;
         int c = (int)((blockIdx.x * 2654435761u) % (unsigned)pp.nslots);
         for (int t = 0; t < pp.nslots; ++t) {
@@ -386,32 +433,31 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
     }
     float4 *S = pp.scr + (size_t)slot * N * K12;
     const int64_t row = blockIdx.x;
-    // F entries of a slab pair: line lx = sl N + i1 of the pair (slab i0 + sl), K2 contiguous
-    // entries per line; a thread's first (line, entry) and its step are computed once
+    // F of slabs i0, i0 + 1: lines i0 N .. i0 N + 2N - 1 of this row, K2 entries each (one TMA load;
+    // the buffer's earlier readers have passed a barrier)
     const uint64_t keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
-    const int fl0 = (int)threadIdx.x / K2, fq0 = (int)threadIdx.x - fl0 * K2;
-    const int fdl = NT / K2, fdq = NT - fdl * K2;
+    const unsigned fbytes = (unsigned)(2 * N * K2 * 16);
     auto fetch = [&](int i0, float4 *C) {
-        int lx = fl0, q = fq0;
-        while (lx < 2 * N) {
-            const int sl = lx >= N, i1 = lx - sl * N;
-            const int64_t fi = (((int64_t)i0 * N + lx) * R + row) * K2 + q;
-            if (GW_IN(fi, (int64_t)N * N * R * K2, pp.status)) cp_async16_hint(C + (sl * K2 + q) * CS + i1, F + fi, stream);
-            q += fdq;
-            lx += fdl;
-            if (q >= K2) {
-                q -= K2;
-                ++lx;
-            }
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bar_expect(&fbar, fbytes);
+            tma2_hint(C, &tmF, &fbar, (int)(row * K2 * 4), i0 * N, stream);
         }
-        cp_async_commit();
     };
+    const LMap lm = lmap_lines_fastest(ncols);
     fetch(0, Xb);
-    for (int i0 = 0, b = 0; i0 < N; i0 += 2, b ^= 1) {
-        float4 *X = Xb + b * ncols * CS, *Y = Xb + (b ^ 1) * ncols * CS;
-        cp_async_wait_all();
-        __syncthreads(); // X complete
-        const float4 *y1 = tstages_ct<N, 0, 1, true, true>(X, Y, ncols, CS, tw, kc, 1); // ends in X, then a barrier
+    uint32_t nf = 0;
+    for (int i0 = 0, b = 0; i0 < N; i0 += 2, b ^= 1, ++nf) {
+        float4 *X = Xb + b * BUF, *Y = Xb + (b ^ 1) * BUF;
+        const bool late = !bar_wait(&fbar, nf & 1);
+        if (__syncthreads_or(late)) { // X complete (or the wait ran out, for every thread alike)
+            if (threadIdx.x == 0) atomicOr(pp.status, kStatusTimeout);
+            return;
+        }
+        tstage0_rows<N>(X, Y, K2, ncols, CS, lm);
+        __syncthreads();
+        const float4 *y1 = tstages_ct<N, 1, make_prune_plan(N).r[0], true, true>(Y, X, ncols, CS, tw, kc, 1, -1, lm);
+        // y1 = X, after a barrier: Y is free
         if (i0 + 2 < N) fetch(i0 + 2, Y);
         for (int d = threadIdx.x; d < 2 * K12; d += NT) {
             const int sl = d >= K12, dd = d - sl * K12;
@@ -425,7 +471,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
 
     // Phase 2 (as in pair_kernel_tf_ct) in the two buffers
     const int NB = ncols;
-    float4 *X = Xb, *Y = Xb + NB * CS;
+    float4 *X = Xb, *Y = Xb + BUF;
     double2 *out = M + row * pp.ng;
     for (int d0 = 0; d0 < K12; d0 += NB) {
         const int nbat = K12 - d0 < NB ? K12 - d0 : NB;
@@ -463,12 +509,12 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
 template <int N>
 inline size_t pair_tf_from_f_smem(const PairPlan &pp)
 {
-    const size_t cs = N + 1, ncols = 2 * (size_t)pp.K2;
-    return sizeof(float4) * (2 * ncols * cs + N) + sizeof(int) * (size_t)pp.K12;
+    const int cs = N + 1, ncols = 2 * pp.K2;
+    return 128 + sizeof(float4) * (2 * (size_t)from_f_buf(ncols, cs) + N) + sizeof(int) * (size_t)pp.K12;
 }
 
 template <int N>
-inline cudaError_t launch_pair_tf_from_f_cube(const float4 *F, int64_t R, const PairPlan &pp, const TfConsts &kc,
+inline cudaError_t launch_pair_tf_from_f_cube(const CUtensorMap &tmF, int64_t R, const PairPlan &pp, const TfConsts &kc,
                                              tf inv_nr, double2 *M, cudaStream_t st)
 {
     const size_t sm = pair_tf_from_f_smem<N>(pp);
@@ -476,7 +522,7 @@ inline cudaError_t launch_pair_tf_from_f_cube(const float4 *F, int64_t R, const 
         cudaFuncSetAttribute(pair_kernel_tf_from_f<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(pp.slot_flags, 0, sizeof(int) * pp.nslots, st)) != cudaSuccess) return e;
-    pair_kernel_tf_from_f<N><<<(unsigned)R, pair_threads<N>(), sm, st>>>(F, R, pp, kc, inv_nr, M);
+    pair_kernel_tf_from_f<N><<<(unsigned)R, pair_threads<N>(), sm, st>>>(tmF, R, pp, kc, inv_nr, M);
     return cudaGetLastError();
 }
 
@@ -587,7 +633,7 @@ cudaError_t pair_tf_slots_g48(const PairPlan &, int *);
 cudaError_t launch_pair_tf_g72(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,
                                const TfConsts &, tf, double2 *, cudaStream_t);
 cudaError_t pair_tf_slots_g72(const PairPlan &, int *);
-cudaError_t launch_pair_tf_from_f_g48(const float4 *, int64_t, const PairPlan &, const TfConsts &, tf, double2 *,
+cudaError_t launch_pair_tf_from_f_g48(const CUtensorMap &, int64_t, const PairPlan &, const TfConsts &, tf, double2 *,
                                       cudaStream_t);
 
 } // namespace gw
