@@ -596,8 +596,17 @@ gw_status zd_stage_a(gw_chi0 *h, int iq, const CUtensorMap &tmA, const CUtensorM
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, GW_ERR_CUDA, "cuTensorMapEncodeTiled (last-axis output) failed (%d)", (int)r);
+    // the scratch slots as [nslots n rows][K12] entries: phase 2 loads batches of 2 K2 cells of
+    // all n rows of its slot with one TMA box
+    CUtensorMap tmS;
+    cuuint64_t sd[2] = {(cuuint64_t)pp.K12 * 4, (cuuint64_t)pp.nslots * n};
+    cuuint64_t sst[1] = {(cuuint64_t)pp.K12 * 16};
+    cuuint32_t sbox[2] = {(cuuint32_t)(8 * sp.K2), (cuuint32_t)n};
+    r = h->encode(&tmS, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pp.scr, sd, sst, sbox, fes, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, GW_ERR_CUDA, "cuTensorMapEncodeTiled (pair scratch) failed (%d)", (int)r);
     Scope sc(h, "pair_from_f");
-    CK(h, gw::launch_pair_tf_from_f(tmF, R, pp, M, h->st), "pair elements from F");
+    CK(h, gw::launch_pair_tf_from_f(tmF, tmS, R, pp, M, h->st), "pair elements from F");
     return GW_OK;
 }
 

@@ -71,8 +71,10 @@ cudaError_t launch_zd_gemm(const CUtensorMap &tmA, const CUtensorMap &tmC, const
                            const float4 *twf, int n, int nv, int c0, int cb, int K2, float4 *F, int *status,
                            cudaStream_t st);
 // M[r][g] of the chunk's R pairs from F (middle and first axis of the pair transform)
-// (tmF: F as [N^2 lines][R K2] two-float entries, FP32 elements, box {4 K2, 2 N}, no swizzle)
-cudaError_t launch_pair_tf_from_f(const CUtensorMap &tmF, int64_t R, const PairPlan &pp, double2 *M, cudaStream_t st);
+// (tmF: F as [N^2 lines][R K2] two-float entries, FP32 elements, box {4 K2, 2 N}; tmS: the plan's
+// scratch slots as [nslots N rows][K12] two-float entries, box {8 K2, N}; no swizzle)
+cudaError_t launch_pair_tf_from_f(const CUtensorMap &tmF, const CUtensorMap &tmS, int64_t R, const PairPlan &pp,
+                                  double2 *M, cudaStream_t st);
 // delta[w][cl nv + v] = 4x/(x^2 + w^2), x = ev[v] - ec[c0 + cl], the row order of the chunks above
 cudaError_t launch_delta_block(const double *ev, const double *ec, int nv, int c0, int cb, const OmegaList &om,
                                double *delta, cudaStream_t st);

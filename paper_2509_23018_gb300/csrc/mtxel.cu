@@ -392,7 +392,8 @@ size_t pair_tf_ct_smem_bytes(const PairPlan &pp)
     }
 }
 
-cudaError_t launch_pair_tf_from_f(const CUtensorMap &tmF, int64_t R, const PairPlan &pp, double2 *M, cudaStream_t st)
+cudaError_t launch_pair_tf_from_f(const CUtensorMap &tmF, const CUtensorMap &tmS, int64_t R, const PairPlan &pp,
+                                  double2 *M, cudaStream_t st)
 {
     if (R == 0) return cudaSuccess;
     if (pp.n[0] != 48 || pp.n[1] != 48 || pp.n[2] != 48 || !pp.scr || !pp.slot_flags || pp.nslots <= 0)
@@ -400,7 +401,7 @@ cudaError_t launch_pair_tf_from_f(const CUtensorMap &tmF, int64_t R, const PairP
     const double invd = 1.0 / ((double)pp.n[0] * pp.n[1] * pp.n[2]);
     const float invh = (float)invd;
     const tf inv{invh, (float)(invd - (double)invh)};
-    return launch_pair_tf_from_f_g48(tmF, R, pp, tf_consts(), inv, M, st);
+    return launch_pair_tf_from_f_g48(tmF, tmS, R, pp, tf_consts(), inv, M, st);
 }
 
 cudaError_t pair_tf_scratch(const PairPlan &pp, int *nslots, size_t *slot_elems)

@@ -359,30 +359,32 @@ __device__ __forceinline__ void tma2_hint(void *dst, const CUtensorMap *m, uint6
                  : "memory");
 }
 
-// First stage of the slab pair's i1 transform (lazy radix 4, no twiddles: make_prune_plan(N)'s
-// stage 0) from the line-major F rows, x[(sl N + i1) K2 + q], into the column layout y[l CS + k]
-// of column l = sl K2 + q; lines fastest over the threads (lm)
+// First stage (lazy radix 4, no twiddles: make_prune_plan(N)'s stage 0) of nlines lines stored
+// row-major as a TMA box leaves them: line l = sl half + q (sl = 0 or 1) has its point k at
+// x[(sl N + k) es + q].  The slab pair's F rows: half = K2, es = K2; a phase-2 batch of cells:
+// half = nlines, es = the box width.  Output in the column layout y[l CS + k]; lines fastest
+// over the threads (lm).
 template <int N>
-__device__ __forceinline__ void tstage0_rows(const float4 *__restrict__ x, float4 *__restrict__ y, int K2, int ncols,
-                                             int CS, LMap lm)
+__device__ __forceinline__ void tstage0_rows(const float4 *__restrict__ x, float4 *__restrict__ y, int half, int es,
+                                             int nlines, int CS, LMap lm)
 {
     constexpr int R = make_prune_plan(N).r[0], nb = N / R;
     static_assert(R == 4, "the first stage is radix 4");
     int l = lm.l0, j = lm.j0;
     while (j < nb) {
-        const int sl = l >= K2 ? 1 : 0;
-        const float4 *xl = x + sl * N * K2 + (l - sl * K2);
+        const int sl = l >= half ? 1 : 0;
+        const float4 *xl = x + sl * N * es + (l - sl * half);
         tcx v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + (j + r * nb) * K2);
+        for (int r = 0; r < R; ++r) v[r] = tc_load(xl + (j + r * nb) * es);
         tdft4<false>(v);
         float4 *yl = y + l * CS + j * R;
 #pragma unroll
         for (int r = 0; r < R; ++r) tc_store(yl + r, v[r]);
         l += lm.dl;
         j += lm.dj;
-        if (l >= ncols) {
-            l -= ncols;
+        if (l >= nlines) {
+            l -= nlines;
             ++j;
         }
     }
@@ -393,8 +395,8 @@ __host__ __device__ constexpr int from_f_buf(int ncols, int cs) { return (ncols 
 
 template <int N>
 __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
-    pair_kernel_tf_from_f(const __grid_constant__ CUtensorMap tmF, int64_t R, PairPlan pp, TfConsts kc, tf inv_nr,
-                          double2 *__restrict__ M)
+    pair_kernel_tf_from_f(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmS, int64_t R,
+                          PairPlan pp, TfConsts kc, tf inv_nr, double2 *__restrict__ M)
 {
     static_assert(N % 2 == 0, "slabs go in pairs");
     static_assert(make_prune_plan(N).nst == 3, "two full i1 stages: the result returns to the input buffer");
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
             if (threadIdx.x == 0) atomicOr(pp.status, kStatusTimeout);
             return;
         }
-        tstage0_rows<N>(X, Y, K2, ncols, CS, lm);
+        tstage0_rows<N>(X, Y, K2, K2, ncols, CS, lm);
         __syncthreads();
         const float4 *y1 = tstages_ct<N, 1, make_prune_plan(N).r[0], true, true>(Y, X, ncols, CS, tw, kc, 1, -1, lm);
         // y1 = X, after a barrier: Y is free
@@ -469,28 +471,38 @@ __global__ void __launch_bounds__(pair_threads<N>(), pair_min_blocks<N>())
         __syncthreads(); // X read before the next step's first stage writes it
     }
 
-    // Phase 2 (as in pair_kernel_tf_ct) in the two buffers
+    // Phase 2 (as in pair_kernel_tf_ct) in the two buffers: batches of NB cells of the slot, each one
+    // TMA box of the scratch (tensor map over the slots as [nslots N rows][K12] entries, box
+    // N x NB; cells past K12 read as zero), the next batch loaded while the current one is written
+    // out.  The scratch was written by this block's generic stores: each thread orders its own
+    // before the loads of the async proxy.
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
     const int NB = ncols;
-    float4 *X = Xb, *Y = Xb + BUF;
-    double2 *out = M + row * pp.ng;
-    for (int d0 = 0; d0 < K12; d0 += NB) {
-        const int nbat = K12 - d0 < NB ? K12 - d0 : NB;
-        {
-            // element (x, dl) = i / nbat, i % nbat for i = threadIdx.x, threadIdx.x + NT, ...
-            int x = (int)threadIdx.x / nbat, dl = (int)threadIdx.x - x * nbat;
-            const int dx = NT / nbat, ddl = NT - dx * nbat;
-            while (x < N) {
-                X[dl * CS + x] = ld_hint(S + (size_t)x * K12 + d0 + dl, stream);
-                dl += ddl;
-                x += dx;
-                if (dl >= nbat) {
-                    dl -= nbat;
-                    ++x;
-                }
-            }
+    const unsigned sbytes = (unsigned)(N * NB * 16);
+    auto fetch_cells = [&](int d0, float4 *C) {
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bar_expect(&fbar, sbytes);
+            tma2_hint(C, &tmS, &fbar, d0 * 4, slot * N, stream);
         }
+    };
+    double2 *out = M + row * pp.ng;
+    fetch_cells(0, Xb);
+    for (int d0 = 0, b = 0; d0 < K12; d0 += NB, b ^= 1, ++nf) {
+        float4 *X = Xb + b * BUF, *Y = Xb + (b ^ 1) * BUF;
+        const int nbat = K12 - d0 < NB ? K12 - d0 : NB;
+        const bool late = !bar_wait(&fbar, nf & 1);
+        if (__syncthreads_or(late)) {
+            if (threadIdx.x == 0) atomicOr(pp.status, kStatusTimeout);
+            return;
+        }
+        const LMap lm2 = lmap_lines_fastest(nbat);
+        tstage0_rows<N>(X, Y, nbat, NB, nbat, CS, lm2);
         __syncthreads();
-        const float4 *y0 = tstages_ct<N, 0, 1, true, true>(X, Y, nbat, CS, tw, kc, 1);
+        const float4 *y0 = tstages_ct<N, 1, make_prune_plan(N).r[0], true, true>(Y, X, nbat, CS, tw, kc, 1, -1, lm2);
+        // y0 = X, after a barrier: Y is free
+        if (d0 + NB < K12) fetch_cells(d0 + NB, Y);
         const int m1 = pp.cstart[d0 + nbat];
         for (int m = pp.cstart[d0] + threadIdx.x; m < m1; m += NT) {
             const int2 pt = pp.cpts[m];
@@ -514,15 +526,16 @@ inline size_t pair_tf_from_f_smem(const PairPlan &pp)
 }
 
 template <int N>
-inline cudaError_t launch_pair_tf_from_f_cube(const CUtensorMap &tmF, int64_t R, const PairPlan &pp, const TfConsts &kc,
-                                             tf inv_nr, double2 *M, cudaStream_t st)
+inline cudaError_t launch_pair_tf_from_f_cube(const CUtensorMap &tmF, const CUtensorMap &tmS, int64_t R,
+                                              const PairPlan &pp, const TfConsts &kc, tf inv_nr, double2 *M,
+                                              cudaStream_t st)
 {
     const size_t sm = pair_tf_from_f_smem<N>(pp);
     cudaError_t e =
         cudaFuncSetAttribute(pair_kernel_tf_from_f<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(pp.slot_flags, 0, sizeof(int) * pp.nslots, st)) != cudaSuccess) return e;
-    pair_kernel_tf_from_f<N><<<(unsigned)R, pair_threads<N>(), sm, st>>>(tmF, R, pp, kc, inv_nr, M);
+    pair_kernel_tf_from_f<N><<<(unsigned)R, pair_threads<N>(), sm, st>>>(tmF, tmS, R, pp, kc, inv_nr, M);
     return cudaGetLastError();
 }
 
@@ -633,7 +646,7 @@ cudaError_t pair_tf_slots_g48(const PairPlan &, int *);
 cudaError_t launch_pair_tf_g72(const float4 *, const float4 *, int, int64_t, int64_t, const PairPlan &,
                                const TfConsts &, tf, double2 *, cudaStream_t);
 cudaError_t pair_tf_slots_g72(const PairPlan &, int *);
-cudaError_t launch_pair_tf_from_f_g48(const CUtensorMap &, int64_t, const PairPlan &, const TfConsts &, tf, double2 *,
-                                      cudaStream_t);
+cudaError_t launch_pair_tf_from_f_g48(const CUtensorMap &, const CUtensorMap &, int64_t, const PairPlan &,
+                                      const TfConsts &, tf, double2 *, cudaStream_t);
 
 } // namespace gw
