@@ -299,8 +299,8 @@ TRAFFIC = {
     # conduction bands), the launch shape the bench's step repeats 16 times
     "zdft": {"bytes_per_launch": 0.477185e9 + 4.482903e9,
              "source": "ncu dram__bytes_read+write, zd_gemm_kernel (128-column tiles), p2_48cube_chunk"},
-    "pair_from_f": {"bytes_per_launch": 5.357752e9 + 1.253676e9,
-                    "source": "ncu dram__bytes_read+write, pair_kernel_tf_from_f<48>, p2_48cube_chunk"},
+    "pair_from_f": {"bytes_per_launch": 5.504037e9 + 1.240109e9,
+                    "source": "ncu dram__bytes_read+write, pair_kernel_tf_from_f<48> (TMA-fed), p2_48cube_chunk"},
     # the single-stream launch (4-deep TMA ring) the tensor-core route runs
     "ozaki_gemm": {"bytes_per_launch": 5.176667e9 + 0.212558e9,
                    "source": "ncu dram__bytes_read+write, oz_gemm_kernel<240,0,4> (s = 7), p2_48cube_chunk"},
