@@ -715,7 +715,7 @@ def roofline_pair(cfg, prob, res):
     ms_launch = kms / kn if kn else None
     achieved = per_launch / (ms_launch * 1e-3) * 1e-12 if kn else None
     peak, peak_src = fp32_lane_peak()
-    # the method-level bound of SURVEY-style stage (a): max(HBM bytes, FP64 ALU flops)
+    # the method-level bound of stage (a): max(HBM bytes, FP64 ALU flops)
     mbytes, mflops = method_stage_a(cfg)
     hbm, hbm_src = _hbm_peak()
     dfma = LIVE_PEAKS.get("dfma")
