@@ -174,7 +174,8 @@ GW_API gw_status gw_chi0_compute_batch(gw_chi0 *h, int nq, const int *iq, int nw
  * Launch shapes in use (chosen by the autotuner of gw_chi0_compute_batch, or defaults):
  * FP64 tile edge (complex), FP64 waves, split-precision tile width (real columns; 256 before
  * tuning, when each contraction instead takes 240 or 256 columns by which fills the SMs' waves
- * better).
+ * better).  The environment variable GW_CHI0_SPLIT_TILE=128, 240 or 256, read at every
+ * contraction, forces the split-precision tile width; the results do not depend on it.
  * Returns the number of problem shapes tuned so far.  Any pointer may be NULL.
  */
 GW_API int gw_chi0_tuning(const gw_chi0 *h, int *tile_f64, int *waves_f64, int *tile_split);

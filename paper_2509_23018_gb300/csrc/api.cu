@@ -256,7 +256,16 @@ gw_status make_tmap_z(gw_chi0 *h, CUtensorMap *map, void *Z, int64_t kpad, int n
     return GW_OK;
 }
 
-int contraction_bn(const gw_chi0 *h, int ng) { return h->bn_tuned ? h->tuned_bn : gw::oz_pick_bn(ng, num_sms()); }
+// GW_CHI0_SPLIT_TILE=128|240|256, read at every contraction, forces the width (the result does not
+// depend on it: every entry sums the same slice products in the same K order)
+int contraction_bn(const gw_chi0 *h, int ng)
+{
+    if (const char *e = getenv("GW_CHI0_SPLIT_TILE")) {
+        const int v = atoi(e);
+        if (v == 128 || v == 240 || v == 256) return v;
+    }
+    return h->bn_tuned ? h->tuned_bn : gw::oz_pick_bn(ng, num_sms());
+}
 
 gw_status oz_job(gw_chi0 *h, gw::OzJob &j, void *Z, int64_t kpad, int ng, const int *E, double2 *chi, int bn)
 {

@@ -94,6 +94,26 @@ def test_split_ragged(gw, ng):
     assert rel(chi, oracle.chi0(Mo, oracle.delta(p.ev, p.ec, 0.0))) <= TOL_SPLIT
 
 
+@pytest.mark.parametrize("ng", [65, 300, 2000])
+def test_split_tile_widths_agree(gw, ng, monkeypatch):
+    """The split contraction gives the same bits at tile widths 128, 240 and 256 real columns
+    (every entry sums the same slice products in the same K order), on spheres that leave ragged
+    row and column tiles at each width."""
+    rng = np.random.default_rng(1000 + ng)
+    nv, nc = 8, 40
+    M = rng.standard_normal((nv * nc, ng)) + 1j * rng.standard_normal((nv * nc, ng))
+    ev, ec = -1.0 - rng.random(nv), 1.0 + rng.random(nc)
+    outs = []
+    for width in (128, 240, 256):
+        monkeypatch.setenv("GW_CHI0_SPLIT_TILE", str(width))
+        h = gw.Chi0((8, 8, 8), prec="ozaki", nslices=7)
+        outs.append(h.contract(dev(ev), dev(ec), dev(M), [0.0, 1.5]).cpu().numpy())
+        h.sync()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+    assert np.array_equal(outs[0][0], outs[0][0].conj().T)
+
+
 def test_streams_query(gw):
     """The overlapped path is taken for a 24^3 slot in split precision and not in
     FP64 mode or with single_stream; an unset slot is an error."""
